@@ -1,0 +1,461 @@
+/*
+ * oracle.c -- plain CPU reference of the stereo hot path of arXiv 1709.06509.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.  See oracle.h for the
+ * definitions, layouts and the paper passages each function follows.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC oracle.c -lm
+ * (-ffp-contract=off keeps every FP64 multiply and add separately rounded; gcc would
+ * otherwise fuse them on aarch64.)
+ *
+ * The message passing runs in FP64 for both forms.  With integer costs, lambda and trunc
+ * every value stays an integer far below 2^53, so FP64 min/+/- are exact and the integer
+ * entry points return exactly the integer min-sum result.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { UP = 0, DOWN = 1, LEFT = 2, RIGHT = 3 };
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* ---------------------------------------------------------------- NCC (Correlation volume) */
+
+int oracle_ncc(const uint8_t *L, const uint8_t *R, int W, int H, int D, int window, double *ncc)
+{
+    if (!L || !R || !ncc || W < 1 || H < 1 || D < 1 || window < 1 || (window & 1) == 0)
+        return -1;
+    const int r = window / 2;
+    const int64_t N = (int64_t)window * window;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int d = 0; d < D; ++d) {
+                int64_t Sa = 0, Sb = 0, Saa = 0, Sbb = 0, Sab = 0;
+                for (int j = -r; j <= r; ++j)
+                    for (int i = -r; i <= r; ++i) {
+                        const int yy = clampi(y + j, 0, H - 1);
+                        const int64_t a = L[(int64_t)yy * W + clampi(x + i, 0, W - 1)];
+                        const int64_t b = R[(int64_t)yy * W + clampi(x - d + i, 0, W - 1)];
+                        Sa += a;
+                        Sb += b;
+                        Saa += a * a;
+                        Sbb += b * b;
+                        Sab += a * b;
+                    }
+                const int64_t num = N * Sab - Sa * Sb;
+                const int64_t va = N * Saa - Sa * Sa;
+                const int64_t vb = N * Sbb - Sb * Sb;
+                const double den = (double)va * (double)vb;
+                ncc[((int64_t)y * W + x) * D + d] = den == 0.0 ? 0.0 : (double)num / sqrt(den);
+            }
+    return 0;
+}
+
+int oracle_quantise(const double *ncc, int64_t n, int trunc_data, int32_t *cost)
+{
+    if (!ncc || !cost || n < 0 || trunc_data < 0)
+        return -1;
+    const double T = (double)trunc_data;
+    for (int64_t k = 0; k < n; ++k) {
+        const double t = 1.0 - ncc[k];
+        const double v = T * t;
+        const double w = v + 0.5;
+        const double f = floor(w);
+        int c = f < 0.0 ? 0 : (f > T ? trunc_data : (int)f);
+        cost[k] = c;
+    }
+    return 0;
+}
+
+int oracle_cost_float(const double *ncc, int64_t n, int trunc_data, double *cost)
+{
+    if (!ncc || !cost || n < 0 || trunc_data < 0)
+        return -1;
+    const double T = (double)trunc_data;
+    for (int64_t k = 0; k < n; ++k) {
+        const double v = T * (1.0 - ncc[k]);
+        cost[k] = v < 0.0 ? 0.0 : (v > T ? T : v);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- scales (GPU Implementation) */
+
+int oracle_level_dims(int W, int H, int levels, int *Ws, int *Hs)
+{
+    if (W < 1 || H < 1 || levels < 1 || !Ws || !Hs)
+        return -1;
+    Ws[0] = W;
+    Hs[0] = H;
+    for (int l = 1; l < levels; ++l) {
+        Ws[l] = (Ws[l - 1] + 1) / 2;
+        Hs[l] = (Hs[l - 1] + 1) / 2;
+    }
+    return levels;
+}
+
+int oracle_pyramid_f64(const double *cost0, int W, int H, int D, int levels, double *out)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !out || D < 1 || levels > 32 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    memcpy(out, cost0, sizeof(double) * (size_t)W * H * D);
+    double *fine = out;
+    for (int l = 1; l < levels; ++l) {
+        double *coarse = fine + (size_t)Ws[l - 1] * Hs[l - 1] * D;
+        for (int y = 0; y < Hs[l]; ++y)
+            for (int x = 0; x < Ws[l]; ++x)
+                for (int d = 0; d < D; ++d) {
+                    double s = 0.0;
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int fy = 2 * y + dy, fx = 2 * x + dx;
+                            if (fy < Hs[l - 1] && fx < Ws[l - 1])
+                                s += fine[((size_t)fy * Ws[l - 1] + fx) * D + d];
+                        }
+                    coarse[((size_t)y * Ws[l] + x) * D + d] = s;
+                }
+        fine = coarse;
+    }
+    return 0;
+}
+
+int oracle_pyramid_i32(const int32_t *cost0, int W, int H, int D, int levels, int32_t *out)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !out || D < 1 || levels > 32 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    size_t total = 0;
+    for (int l = 0; l < levels; ++l)
+        total += (size_t)Ws[l] * Hs[l] * D;
+    double *c = malloc(sizeof(double) * (size_t)W * H * D);
+    double *p = malloc(sizeof(double) * total);
+    if (!c || !p) {
+        free(c);
+        free(p);
+        return -1;
+    }
+    for (size_t k = 0; k < (size_t)W * H * D; ++k)
+        c[k] = cost0[k];
+    oracle_pyramid_f64(c, W, H, D, levels, p);
+    for (size_t k = 0; k < total; ++k)
+        out[k] = (int32_t)p[k];
+    free(c);
+    free(p);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- message update (Fast Converging BP) */
+
+void oracle_message_f64(const double *h, int D, double lambda, int trunc, double *m)
+{
+    double mn = INFINITY;
+    for (int d = 0; d < D; ++d) {
+        double best = INFINITY;
+        for (int e = 0; e < D; ++e) {
+            const int dist = abs(d - e);
+            const double v = h[e] + lambda * (double)(dist < trunc ? dist : trunc);
+            if (v < best)
+                best = v;
+        }
+        m[d] = best;
+        if (best < mn)
+            mn = best;
+    }
+    for (int d = 0; d < D; ++d)
+        m[d] -= mn;
+}
+
+void oracle_message_i32(const int32_t *h, int D, int lambda, int trunc, int32_t *m)
+{
+    if (D < 1)
+        return;
+    double *hd = malloc(sizeof(double) * 2 * (size_t)D);
+    if (!hd)
+        return;
+    for (int d = 0; d < D; ++d)
+        hd[d] = h[d];
+    oracle_message_f64(hd, D, (double)lambda, trunc, hd + D);
+    for (int d = 0; d < D; ++d)
+        m[d] = (int32_t)hd[D + d];
+    free(hd);
+}
+
+/* SplitMix64 step, used only to shuffle the update order inside a half-sweep. */
+static uint64_t sm64(uint64_t *s)
+{
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* One scale of red-black min-sum BP.  M: [4][H][W][D] incoming messages, updated in place. */
+static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int iters,
+                         double lambda, int trunc, int skip, uint64_t order_seed, int64_t *trace)
+{
+    const size_t plane = (size_t)H * W * D;
+    double *b = malloc(sizeof(double) * (size_t)D);
+    double *h = malloc(sizeof(double) * (size_t)D);
+    double *m = malloc(sizeof(double) * (size_t)D);
+    unsigned char *dirty = malloc((size_t)W * H);
+    int *order = malloc(sizeof(int) * ((size_t)W * H + 1));
+    memset(dirty, 1, (size_t)W * H);
+    uint64_t rng = order_seed;
+    for (int it = 0; it < iters; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            /* the pixels of this colour, in raster order or a seeded permutation */
+            int n = 0;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    if (((x + y) & 1) == colour)
+                        order[n++] = y * W + x;
+            if (order_seed)
+                for (int k = n - 1; k > 0; --k) {
+                    const int j = (int)(sm64(&rng) % (uint64_t)(k + 1));
+                    const int t = order[k];
+                    order[k] = order[j];
+                    order[j] = t;
+                }
+            int64_t updated = 0;
+            for (int k = 0; k < n; ++k) {
+                const int x = order[k] % W, y = order[k] / W;
+                const size_t p = (size_t)y * W + x;
+                if (skip && !dirty[p])
+                    continue;
+                ++updated;
+                const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
+                /* belief: data term plus every incoming message */
+                for (int d = 0; d < D; ++d) {
+                    double s = C[p * D + d];
+                    for (int q = 0; q < 4; ++q)
+                        if (has[q])
+                            s += M[q * plane + p * D + d];
+                    b[d] = s;
+                }
+                for (int q = 0; q < 4; ++q) {
+                    if (!has[q])
+                        continue;
+                    /* the message to neighbour q leaves out what q sent */
+                    for (int d = 0; d < D; ++d)
+                        h[d] = b[d] - M[q * plane + p * D + d];
+                    oracle_message_f64(h, D, lambda, trunc, m);
+                    int qx = x, qy = y, slot;
+                    switch (q) {
+                    case UP: qy = y - 1; slot = DOWN; break;   /* p is q's lower neighbour */
+                    case DOWN: qy = y + 1; slot = UP; break;
+                    case LEFT: qx = x - 1; slot = RIGHT; break;
+                    default: qx = x + 1; slot = LEFT; break;
+                    }
+                    double *dst = M + slot * plane + ((size_t)qy * W + qx) * D;
+                    int changed = 0;
+                    for (int d = 0; d < D; ++d) {
+                        if (dst[d] != m[d])
+                            changed = 1;
+                        dst[d] = m[d];
+                    }
+                    if (changed)
+                        dirty[(size_t)qy * W + qx] = 1;
+                }
+                dirty[p] = 0;
+            }
+            if (trace)
+                *trace++ = updated;
+        }
+    free(b);
+    free(h);
+    free(m);
+    free(dirty);
+    free(order);
+    return trace;
+}
+
+int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                  int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
+                  double *msg0_out, int64_t *trace)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !msg0_out || D < 1 || levels > 32 || iters < 0 || trunc < 0 ||
+        oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    size_t off[33];
+    off[0] = 0;
+    for (int l = 0; l < levels; ++l)
+        off[l + 1] = off[l] + (size_t)Ws[l] * Hs[l] * D;
+    double *pyr = malloc(sizeof(double) * off[levels]);
+    if (!pyr)
+        return -1;
+    oracle_pyramid_f64(cost0, W, H, D, levels, pyr);
+    double *parent = NULL;
+    int64_t *tr = trace;
+    for (int l = levels - 1; l >= 0; --l) {
+        const int w = Ws[l], h = Hs[l];
+        const size_t plane = (size_t)w * h * D;
+        double *M = calloc(4 * plane, sizeof(double));
+        if (!M) {
+            free(pyr);
+            free(parent);
+            return -1;
+        }
+        if (l == levels - 1) {
+            if (init_coarsest)
+                memcpy(M, init_coarsest, sizeof(double) * 4 * plane);
+        } else {
+            /* coarse-to-fine: each pixel starts from its parent's messages */
+            const int pw = Ws[l + 1], ph = Hs[l + 1];
+            const size_t pplane = (size_t)pw * ph * D;
+            for (int q = 0; q < 4; ++q)
+                for (int y = 0; y < h; ++y)
+                    for (int x = 0; x < w; ++x)
+                        memcpy(M + q * plane + ((size_t)y * w + x) * D,
+                               parent + q * pplane + ((size_t)(y / 2) * pw + x / 2) * D,
+                               sizeof(double) * D);
+        }
+        free(parent);
+        tr = bp_level(pyr + off[l], M, w, h, D, iters, lambda, trunc, skip, order_seed, tr);
+        parent = M;
+    }
+    memcpy(msg0_out, parent, sizeof(double) * 4 * (size_t)W * H * D);
+    free(parent);
+    free(pyr);
+    return 0;
+}
+
+int oracle_bp_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                  int trunc, int skip, const int32_t *init_coarsest, uint64_t order_seed,
+                  int32_t *msg0_out, int64_t *trace)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !msg0_out || D < 1 || levels > 32 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    const size_t n0 = (size_t)W * H * D;
+    const size_t nc = (size_t)Ws[levels - 1] * Hs[levels - 1] * D;
+    double *c = malloc(sizeof(double) * n0);
+    double *m = malloc(sizeof(double) * 4 * n0);
+    double *init = init_coarsest ? malloc(sizeof(double) * 4 * nc) : NULL;
+    if (!c || !m || (init_coarsest && !init)) {
+        free(c);
+        free(m);
+        free(init);
+        return -1;
+    }
+    for (size_t k = 0; k < n0; ++k)
+        c[k] = cost0[k];
+    if (init)
+        for (size_t k = 0; k < 4 * nc; ++k)
+            init[k] = init_coarsest[k];
+    const int rc = oracle_bp_f64(c, W, H, D, levels, iters, (double)lambda, trunc, skip, init,
+                                 order_seed, m, trace);
+    for (size_t k = 0; k < 4 * n0; ++k)
+        msg0_out[k] = (int32_t)m[k];
+    free(c);
+    free(m);
+    free(init);
+    return rc;
+}
+
+/* ---------------------------------------------------------------- read-out and energy */
+
+int oracle_wta_f64(const double *cost, const double *msg, int W, int H, int D, int32_t *disp)
+{
+    if (!cost || !msg || !disp || W < 1 || H < 1 || D < 1)
+        return -1;
+    const size_t plane = (size_t)W * H * D;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
+            double best = INFINITY;
+            int arg = 0;
+            for (int d = 0; d < D; ++d) {
+                double s = cost[p * D + d];
+                for (int q = 0; q < 4; ++q)
+                    if (has[q])
+                        s += msg[q * plane + p * D + d];
+                if (s < best) {
+                    best = s;
+                    arg = d;
+                }
+            }
+            disp[p] = arg;
+        }
+    return 0;
+}
+
+int oracle_wta_i32(const int32_t *cost, const int32_t *msg, int W, int H, int D, int32_t *disp)
+{
+    if (!cost || !msg || !disp || W < 1 || H < 1 || D < 1)
+        return -1;
+    const size_t plane = (size_t)W * H * D;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
+            int64_t best = INT64_MAX;
+            int arg = 0;
+            for (int d = 0; d < D; ++d) {
+                int64_t s = cost[p * D + d];
+                for (int q = 0; q < 4; ++q)
+                    if (has[q])
+                        s += msg[q * plane + p * D + d];
+                if (s < best) {
+                    best = s;
+                    arg = d;
+                }
+            }
+            disp[p] = arg;
+        }
+    return 0;
+}
+
+static int smooth_cost(int a, int b, int trunc)
+{
+    const int dist = abs(a - b);
+    return dist < trunc ? dist : trunc;
+}
+
+int64_t oracle_energy_i32(const int32_t *cost, const int32_t *disp, int W, int H, int D,
+                          int lambda, int trunc)
+{
+    if (!cost || !disp || W < 1 || H < 1 || D < 1)
+        return INT64_MIN;
+    int64_t e = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const int d = disp[p];
+            if (d < 0 || d >= D)
+                return INT64_MIN;
+            e += cost[p * D + d];
+            if (x + 1 < W)
+                e += (int64_t)lambda * smooth_cost(d, disp[p + 1], trunc);
+            if (y + 1 < H)
+                e += (int64_t)lambda * smooth_cost(d, disp[p + W], trunc);
+        }
+    return e;
+}
+
+double oracle_energy_f64(const double *cost, const int32_t *disp, int W, int H, int D,
+                         double lambda, int trunc)
+{
+    if (!cost || !disp || W < 1 || H < 1 || D < 1)
+        return NAN;
+    double e = 0.0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const int d = disp[p];
+            if (d < 0 || d >= D)
+                return NAN;
+            e += cost[p * D + d];
+            if (x + 1 < W)
+                e += lambda * smooth_cost(d, disp[p + 1], trunc);
+            if (y + 1 < H)
+                e += lambda * smooth_cost(d, disp[p + W], trunc);
+        }
+    return e;
+}

@@ -1,0 +1,90 @@
+/*
+ * oracle.h -- plain CPU reference of the stereo hot path of arXiv 1709.06509
+ * ("A LBP based correspondence identification scheme for multi-view sensing network").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load this library.  It shares no code with the CUDA path.
+ *
+ * Everything is a direct, unblocked transcription of the definitions:
+ *   - NCC matching cost (section "Correlation volume computation"), FP64 ratio of exact
+ *     integer window sums, replicate-clamped borders;
+ *   - quantised data cost c = clamp(floor(T_d (1 - ncc) + 1/2), 0, T_d);
+ *   - cost pyramid: a coarse pixel's cost is the sum of its existing 2x2 children
+ *     (section "GPU Implementation": four scales, same process at each scale);
+ *   - min-sum message update on the 4-connected grid from the data term, the messages of
+ *     the other three neighbours and the truncated-linear smoothness cost
+ *     V(d, d') = lambda * min(|d - d'|, T) (section "Fast Converging BP"), normalised so
+ *     that min_d m(d) = 0; O(D^2) minimisation exactly as the definition reads;
+ *   - red-black schedule: one iteration = all pixels with (x + y) even, then all odd;
+ *   - fast-converging BP: a pixel is recomputed only if one of its incoming messages
+ *     changed since it was last computed (exact: identical output to no skipping);
+ *   - coarse-to-fine: zero messages at the coarsest scale, each finer pixel starts from
+ *     its parent's messages;
+ *   - winner-take-all disparity (lowest d wins ties) and the energy
+ *     E(d) = E_D(d) + E_S(d) (section "Approach Description"), each grid edge once.
+ *
+ * Array layouts (all row-major, D innermost):
+ *   images        uint8  [H][W]
+ *   ncc / cost    [H][W][D]
+ *   messages      [4][H][W][D], direction index = neighbour the message comes FROM:
+ *                 0 = up (x, y-1), 1 = down (x, y+1), 2 = left (x-1, y), 3 = right (x+1, y).
+ *                 Slots of missing neighbours hold 0.
+ *   trace         one count per half-sweep, coarsest scale first: number of pixels
+ *                 recomputed in that half-sweep.
+ * Functions returning int return 0 on success and -1 on bad arguments or allocation failure.
+ */
+#ifndef BPS_ORACLE_H
+#define BPS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ncc[H][W][D] in FP64.  window odd >= 1. */
+int oracle_ncc(const uint8_t *L, const uint8_t *R, int W, int H, int D, int window, double *ncc);
+
+/* c = clamp(floor(trunc*(1 - ncc) + 0.5), 0, trunc), FP64 round-to-nearest, no contraction. */
+int oracle_quantise(const double *ncc, int64_t n, int trunc_data, int32_t *cost);
+
+/* float data cost for the FP64 / FP16 message forms: clamp(trunc*(1 - ncc), 0, trunc). */
+int oracle_cost_float(const double *ncc, int64_t n, int trunc_data, double *cost);
+
+/* Scale sizes: Ws[0] = W, Ws[l+1] = ceil(Ws[l] / 2) (same for H).  Returns levels. */
+int oracle_level_dims(int W, int H, int levels, int *Ws, int *Hs);
+
+/* Cost pyramid, all scales concatenated finest first, each [H_l][W_l][D]. */
+int oracle_pyramid_i32(const int32_t *cost0, int W, int H, int D, int levels, int32_t *out);
+int oracle_pyramid_f64(const double *cost0, int W, int H, int D, int levels, double *out);
+
+/* One message from the combined input h[D] (data term plus the three other incoming
+ * messages): m(d) = min_d' (h(d') + lambda*min(|d - d'|, trunc)) - min_d (same). */
+void oracle_message_i32(const int32_t *h, int D, int lambda, int trunc, int32_t *m);
+void oracle_message_f64(const double *h, int D, double lambda, int trunc, double *m);
+
+/* Hierarchical min-sum BP.  init_coarsest: nullable [4][H_c][W_c][D] start messages at the
+ * coarsest scale (zero when NULL).  order_seed: 0 = raster order inside a half-sweep,
+ * otherwise a seeded permutation (the result must not depend on it).  msg0_out receives
+ * the finest-scale messages [4][H][W][D].  trace: nullable, levels*iters*2 entries. */
+int oracle_bp_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                  int trunc, int skip, const int32_t *init_coarsest, uint64_t order_seed,
+                  int32_t *msg0_out, int64_t *trace);
+int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                  int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
+                  double *msg0_out, int64_t *trace);
+
+/* d*(p) = argmin_d [cost(p, d) + sum of incoming messages], lowest d on ties. */
+int oracle_wta_i32(const int32_t *cost, const int32_t *msg, int W, int H, int D, int32_t *disp);
+int oracle_wta_f64(const double *cost, const double *msg, int W, int H, int D, int32_t *disp);
+
+/* E = sum_p cost(p, d_p) + sum over right and down edges of lambda*min(|d_p - d_q|, trunc).
+ * Labels outside [0, D) make the call return INT64_MIN / NaN. */
+int64_t oracle_energy_i32(const int32_t *cost, const int32_t *disp, int W, int H, int D,
+                          int lambda, int trunc);
+double oracle_energy_f64(const double *cost, const int32_t *disp, int W, int H, int D,
+                         double lambda, int trunc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

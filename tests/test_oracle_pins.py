@@ -1,0 +1,450 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test checks one part of the method (NCC, quantiser, pyramid, message update,
+schedule, fast-converging skip, coarse-to-fine start, WTA, energy) against a hand-worked
+example, a closed form, an independent formulation (centred Pearson correlation, the
+two-pass distance transform, Viterbi dynamic programming, brute-force MAP) or an
+invariant of min-sum BP.  No GPU is needed.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_06509_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- independent helpers
+
+def ncc_centred(L, R, D, window):
+    """Pearson correlation of the clamped windows, computed from centred float64 values."""
+    H, W = L.shape
+    r = window // 2
+    Lp = np.pad(L.astype(np.float64), r, mode="edge")
+    out = np.zeros((H, W, D))
+    for d in range(D):
+        # R shifted right by d with the left border replicated, then padded like L
+        idx = np.clip(np.arange(-r, W + r) - d, 0, W - 1)
+        rows = np.clip(np.arange(-r, H + r), 0, H - 1)
+        Rs = R.astype(np.float64)[rows][:, idx]
+        for y in range(H):
+            for x in range(W):
+                a = Lp[y:y + window, x:x + window].ravel()
+                b = Rs[y:y + window, x:x + window].ravel()
+                a = a - a.mean()
+                b = b - b.mean()
+                den = np.sqrt((a * a).sum() * (b * b).sum())
+                out[y, x, d] = 0.0 if den == 0 else (a * b).sum() / den
+    return out
+
+
+def window_sums(L, R, x, y, d, window):
+    H, W = L.shape
+    r = window // 2
+    a = [int(L[min(max(y + j, 0), H - 1), min(max(x + i, 0), W - 1)])
+         for j in range(-r, r + 1) for i in range(-r, r + 1)]
+    b = [int(R[min(max(y + j, 0), H - 1), min(max(x - d + i, 0), W - 1)])
+         for j in range(-r, r + 1) for i in range(-r, r + 1)]
+    N = window * window
+    num = N * sum(p * q for p, q in zip(a, b)) - sum(a) * sum(b)
+    va = N * sum(p * p for p in a) - sum(a) ** 2
+    vb = N * sum(q * q for q in b) - sum(b) ** 2
+    return num, va, vb
+
+
+def exact_quantised(num, va, vb, T):
+    """floor(T (1 - num / sqrt(va vb)) + 1/2) clamped to [0, T], decided in exact integers.
+
+    c >= k  <=>  2 T num <= (2T - 2k + 1) sqrt(P),  P = va vb.  Returns (c, margin) where
+    margin is a lower bound-free proxy: the exact value's distance to the nearest boundary,
+    computed in float only to decide whether FP64 rounding could legitimately differ."""
+    P = va * vb
+    if P == 0:
+        c = T  # ncc = 0 for a flat window
+        return c, 0.5
+    A = 2 * T * num
+
+    def ge(k):
+        B = 2 * T - 2 * k + 1
+        if B >= 0:
+            return A <= 0 or A * A <= B * B * P
+        return A < 0 and A * A >= B * B * P
+
+    c = 0
+    for k in range(1, T + 1):
+        if ge(k):
+            c = k
+    v = T * (1 - num / np.sqrt(float(P))) + 0.5
+    margin = abs(v - round(v))
+    return c, margin
+
+
+def dt_message(h, lam, T):
+    """Felzenszwalb-Huttenlocher two-pass distance transform for the truncated-linear cost."""
+    f = list(h)
+    D = len(f)
+    for d in range(1, D):
+        f[d] = min(f[d], f[d - 1] + lam)
+    for d in range(D - 2, -1, -1):
+        f[d] = min(f[d], f[d + 1] + lam)
+    cap = min(h) + lam * T
+    f = [min(v, cap) for v in f]
+    mn = min(f)
+    return [v - mn for v in f]
+
+
+def V(a, b, lam, T):
+    return lam * np.minimum(np.abs(a - b), T)
+
+
+def energy_np(cost, disp, lam, T):
+    H, W, D = cost.shape
+    e = np.take_along_axis(cost, disp[..., None].astype(np.int64), axis=2).sum()
+    e += V(disp[:, 1:], disp[:, :-1], lam, T).sum() + V(disp[1:, :], disp[:-1, :], lam, T).sum()
+    return e
+
+
+def viterbi(cost, lam, T):
+    """MAP labelling of a chain and its per-node min-marginals (forward-backward min-sum)."""
+    n, D = cost.shape
+    lab = np.arange(D)
+    Vm = V(lab[:, None], lab[None, :], lam, T)
+    F = np.zeros((n, D), dtype=np.int64)
+    Bk = np.zeros((n, D), dtype=np.int64)
+    F[0] = cost[0]
+    for i in range(1, n):
+        F[i] = cost[i] + (F[i - 1][:, None] + Vm).min(axis=0)
+    for i in range(n - 2, -1, -1):
+        Bk[i] = ((cost[i + 1] + Bk[i + 1])[None, :] + Vm).min(axis=1)
+    marg = F + Bk
+    return marg, int(marg[0].min())
+
+
+def random_cost(rng, H, W, D, hi=20):
+    return rng.integers(0, hi + 1, size=(H, W, D)).astype(np.int32)
+
+
+# ---------------------------------------------------------------- NCC and quantiser
+
+def test_ncc_matches_centred_pearson():
+    rng = np.random.default_rng(7)
+    L = rng.integers(0, 256, (9, 11)).astype(np.uint8)
+    R = rng.integers(0, 256, (9, 11)).astype(np.uint8)
+    got = oracle.ncc(L, R, 5, 3)
+    want = ncc_centred(L, R, 5, 3)
+    assert np.abs(got - want).max() < 1e-12
+
+
+def test_ncc_border_reads_replicate():
+    # a disparity beyond the image width reads column 0 of R for every window tap
+    rng = np.random.default_rng(8)
+    L = rng.integers(0, 256, (5, 4)).astype(np.uint8)
+    R = rng.integers(0, 256, (5, 4)).astype(np.uint8)
+    got = oracle.ncc(L, R, 12, 3)
+    assert np.abs(got - ncc_centred(L, R, 12, 3)).max() < 1e-12
+    # at d >= W + r every tap of the right window is column 0, so the result stops changing
+    assert np.array_equal(got[:, :, 10], got[:, :, 11])
+
+
+def test_ncc_closed_forms():
+    tex = synth.texture(3, 1, 24, 16)
+    same = oracle.ncc(tex, tex, 1, 5)[:, :, 0]
+    assert np.abs(same - 1.0).max() < 1e-12  # identical windows correlate perfectly
+    neg = oracle.ncc(tex, (255 - tex).astype(np.uint8), 1, 5)[:, :, 0]
+    assert np.abs(neg + 1.0).max() < 1e-12  # negated contrast gives -1
+    flat = np.full((6, 7), 90, dtype=np.uint8)
+    assert np.all(oracle.ncc(flat, tex[:6, :7], 3, 3) == 0.0)  # flat window: defined as 0
+    # affine change of the right image (gain 2, offset 10, no clipping) leaves NCC unchanged
+    small = (tex // 3).astype(np.uint8)
+    aff = (2 * small.astype(np.int32) + 10).astype(np.uint8)
+    assert np.abs(oracle.ncc(small, aff, 4, 5) - oracle.ncc(small, small, 4, 5)).max() < 1e-12
+
+
+def test_ncc_bounded():
+    p = synth.make_pair(11, 40, 30, 8, 3, 2.0)
+    v = oracle.ncc(p.left, p.right, 8, 5)
+    assert np.all(np.abs(v) <= 1.0 + 1e-12)
+
+
+def test_quantiser_exact_decision():
+    rng = np.random.default_rng(12)
+    T = 20
+    checked = 0
+    for trial in range(6):
+        L = rng.integers(0, 256, (6, 7)).astype(np.uint8)
+        # right view = left plus small noise so correlations sweep (-1, 1]
+        R = np.clip(L.astype(int) + rng.integers(-40 * trial, 40 * trial + 1, L.shape), 0, 255).astype(np.uint8)
+        if trial % 2:
+            R = (255 - R).astype(np.uint8)
+        D, w = 3, 3
+        q = oracle.quantise(oracle.ncc(L, R, D, w), T)
+        for y in range(6):
+            for x in range(7):
+                for d in range(D):
+                    num, va, vb = window_sums(L, R, x, y, d, w)
+                    c, margin = exact_quantised(num, va, vb, T)
+                    if margin > 1e-9:
+                        assert q[y, x, d] == c, (y, x, d, num, va, vb)
+                        checked += 1
+    assert checked > 600
+
+
+def test_quantiser_boundaries():
+    # values straddling every rounding boundary of 20 * (1 - ncc) + 0.5
+    T = 20
+    eps = 1e-9
+    ks = np.arange(0, 2 * T + 1)
+    ncc_at = 1.0 - (ks - 0.5) / T  # exactly on the boundary k
+    lo = oracle.quantise(ncc_at + eps, T)  # slightly more correlated: rounds down
+    hi = oracle.quantise(ncc_at - eps, T)
+    assert np.array_equal(lo, np.clip(ks - 1, 0, T))
+    assert np.array_equal(hi, np.clip(ks, 0, T))
+    assert oracle.quantise(np.array([1.0 + 1e-15, -1.0, 0.0]), T).tolist() == [0, T, T]
+    assert oracle.quantise(np.array([0.3]), 0).tolist() == [0]
+
+
+def test_cost_float_closed_form():
+    v = np.array([1.0, 0.5, 0.0, -0.5, -1.0, 1.0 + 1e-16])
+    assert np.allclose(oracle.cost_float(v, 20), [0, 10, 20, 20, 20, 0])
+
+
+# ---------------------------------------------------------------- pyramid
+
+def test_level_dims_ceil():
+    assert oracle.level_dims(450, 375, 4) == [(450, 375), (225, 188), (113, 94), (57, 47)]
+    assert oracle.level_dims(96, 72, 4) == [(96, 72), (48, 36), (24, 18), (12, 9)]
+    assert oracle.level_dims(1, 1, 3) == [(1, 1), (1, 1), (1, 1)]
+
+
+def test_pyramid_matches_block_sums():
+    rng = np.random.default_rng(3)
+    c0 = random_cost(rng, 13, 9, 5)
+    pyr = oracle.pyramid(c0, 4)
+    cur = c0.astype(np.int64)
+    for l in range(1, 4):
+        H, W, D = cur.shape
+        pad = np.zeros((H + H % 2, W + W % 2, D), dtype=np.int64)
+        pad[:H, :W] = cur
+        want = pad.reshape((H + 1) // 2, 2, (W + 1) // 2, 2, D).sum(axis=(1, 3))
+        assert np.array_equal(pyr[l], want)
+        assert pyr[l].sum() == c0.astype(np.int64).sum()  # every fine pixel has one parent
+        cur = want
+    f = oracle.pyramid(c0.astype(np.float64), 4)
+    for a, b in zip(f, pyr):
+        assert np.array_equal(a, b.astype(np.float64))
+
+
+# ---------------------------------------------------------------- message update
+
+def read_golden_messages():
+    rows = []
+    with open(os.path.join(GOLDEN, "messages_hand.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            a, b, c = line.split("|")
+            lam, T = map(int, a.split())
+            rows.append((lam, T, [int(v) for v in b.split()], [int(v) for v in c.split()]))
+    return rows
+
+
+@pytest.mark.parametrize("lam,T,h,want", read_golden_messages())
+def test_message_hand_worked(lam, T, h, want):
+    assert oracle.message(np.array(h, dtype=np.int32), lam, T).tolist() == want
+    assert oracle.message(np.array(h, dtype=np.float64), lam, T).tolist() == want
+
+
+def test_message_equals_distance_transform_and_invariants():
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        D = int(rng.integers(1, 40))
+        lam = int(rng.integers(0, 30))
+        T = int(rng.integers(0, D + 2))
+        h = rng.integers(0, 400, D).astype(np.int32)
+        m = oracle.message(h, lam, T)
+        assert m.tolist() == dt_message(h.tolist(), lam, T)
+        assert m.min() == 0                      # normalised
+        assert m.max() <= lam * T                # bounded by the truncation
+        # adding a constant to h leaves the normalised message unchanged
+        assert np.array_equal(oracle.message(h + 17, lam, T), m)
+
+
+# ---------------------------------------------------------------- whole solver
+
+def read_chain_golden():
+    vals = {}
+    with open(os.path.join(GOLDEN, "chain_3x1_hand.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, *v = line.split()
+                vals[k] = [int(t) for t in v]
+    return vals
+
+
+def test_chain_hand_worked():
+    g = read_chain_golden()
+    cost = np.array(g["cost"], dtype=np.int32).reshape(1, 3, 2)
+    msg, trace = oracle.bp(cost, 1, 2, 1, 1, skip=True)
+    for q, k in enumerate(("msg_up", "msg_down", "msg_left", "msg_right")):
+        assert msg[q].ravel().tolist() == g[k]
+    assert trace.tolist() == g["trace"]
+    d = oracle.wta(cost, msg)
+    assert d.ravel().tolist() == g["disp"]
+    assert oracle.energy(cost, d, 1, 1) == g["energy"][0]
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+@pytest.mark.parametrize("vertical", [False, True])
+def test_chain_equals_viterbi(levels, vertical):
+    rng = np.random.default_rng(21 + levels + 10 * vertical)
+    done = 0
+    while done < 12:
+        n = int(rng.integers(2, 30))
+        D = int(rng.integers(2, 9))
+        lam = int(rng.integers(1, 8))
+        T = int(rng.integers(1, D + 1))
+        c = rng.integers(0, 25, (n, D)).astype(np.int64)
+        marg, emin = viterbi(c, lam, T)
+        srt = np.sort(marg, axis=1)
+        if np.any(srt[:, 0] == srt[:, 1]):
+            continue  # MAP not unique: skip the instance
+        cost = c.astype(np.int32).reshape((n, 1, D) if vertical else (1, n, D))
+        msg, _ = oracle.bp(cost, levels, n + 2, lam, T, skip=bool(done % 2))
+        d = oracle.wta(cost, msg)
+        assert np.array_equal(d.ravel(), marg.argmin(axis=1))
+        assert oracle.energy(cost, d, lam, T) == emin
+        # on a tree the converged beliefs are the min-marginals up to a constant
+        belief = cost.reshape(n, D).astype(np.int64) + msg.reshape(4, n, D).sum(axis=0)
+        assert np.array_equal(belief - belief.min(axis=1, keepdims=True),
+                              marg - marg.min(axis=1, keepdims=True))
+        done += 1
+
+
+def test_tiny_grids_against_brute_force():
+    rng = np.random.default_rng(9)
+    for H, W, D in [(2, 2, 3), (2, 3, 3), (3, 3, 3), (3, 3, 2), (1, 4, 4), (3, 2, 4)]:
+        lam, T = int(rng.integers(1, 6)), int(rng.integers(1, D + 1))
+        cost = random_cost(rng, H, W, D, 15)
+        labs = np.array(list(itertools.product(range(D), repeat=H * W))).reshape(-1, H, W)
+        E = np.array([energy_np(cost, l, lam, T) for l in labs])
+        # the oracle's energy agrees with the direct formula on every labelling
+        for k in rng.choice(len(labs), 20, replace=False):
+            assert oracle.energy(cost, labs[k], lam, T) == E[k]
+        msg, _ = oracle.bp(cost, 1, 20, lam, T)
+        d = oracle.wta(cost, msg)
+        assert oracle.energy(cost, d, lam, T) >= E.min()
+
+
+def test_skip_is_exact_and_order_free():
+    p = synth.make_pair(4, 40, 28, 12, 3, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 12, 5), 20)
+    m0, t0 = oracle.bp(cost, 3, 6, 10, 2, skip=False)
+    m1, t1 = oracle.bp(cost, 3, 6, 10, 2, skip=True)
+    m2, _ = oracle.bp(cost, 3, 6, 10, 2, skip=True, order_seed=99)
+    m3, _ = oracle.bp(cost, 3, 6, 10, 2, skip=False, order_seed=12345)
+    assert np.array_equal(m0, m1) and np.array_equal(m0, m2) and np.array_equal(m0, m3)
+    assert t1.sum() < t0.sum()  # the skip does remove work
+    # without skipping every half-sweep updates every pixel of its colour
+    dims = oracle.level_dims(40, 28, 3)[::-1]
+    want = []
+    for w, h in dims:
+        even = sum(1 for y in range(h) for x in range(w) if (x + y) % 2 == 0)
+        want += [even, w * h - even] * 6
+    assert t0.tolist() == want
+
+
+def test_message_range_and_shift_invariance():
+    rng = np.random.default_rng(2)
+    cost = random_cost(rng, 10, 12, 7)
+    msg, _ = oracle.bp(cost, 2, 5, 4, 3)
+    interior = msg[:, 1:-1, 1:-1]
+    assert interior.min() == 0 and msg.max() <= 4 * 3
+    assert np.all(msg.min(axis=3)[:, 1:-1, 1:-1] == 0)
+    shift = rng.integers(0, 50, (10, 12, 1)).astype(np.int32)
+    msg2, _ = oracle.bp(cost + shift, 2, 5, 4, 3)
+    assert np.array_equal(msg, msg2)
+    assert np.array_equal(oracle.wta(cost, msg), oracle.wta(cost + shift, msg2))
+
+
+@pytest.mark.parametrize("lam,T", [(0, 2), (5, 0)])
+def test_no_smoothness_gives_argmin(lam, T):
+    rng = np.random.default_rng(1)
+    cost = random_cost(rng, 7, 9, 6)
+    msg, _ = oracle.bp(cost, 3, 4, lam, T)
+    assert not msg.any()
+    assert np.array_equal(oracle.wta(cost, msg), cost.argmin(axis=2))
+
+
+def test_single_pixel_and_zero_iterations():
+    cost = np.array([[[5, 2, 2, 9]]], dtype=np.int32)
+    msg, trace = oracle.bp(cost, 4, 3, 10, 2)
+    assert not msg.any() and oracle.wta(cost, msg).tolist() == [[1]]
+    assert trace.tolist() == [1, 0, 0, 0, 0, 0] * 4
+    rng = np.random.default_rng(4)
+    c = random_cost(rng, 6, 5, 4)
+    msg, trace = oracle.bp(c, 2, 0, 10, 2)
+    assert not msg.any() and trace.size == 0
+
+
+def test_coarse_to_fine_copy():
+    # with zero iterations the finest messages are the coarsest start messages copied down
+    rng = np.random.default_rng(6)
+    H, W, D = 11, 7, 3
+    dims = oracle.level_dims(W, H, 3)
+    wc, hc = dims[-1]
+    init = rng.integers(0, 9, (4, hc, wc, D)).astype(np.int32)
+    cost = random_cost(rng, H, W, D)
+    msg, _ = oracle.bp(cost, 3, 0, 10, 2, init_coarsest=init)
+    want = init.repeat(4, axis=1).repeat(4, axis=2)[:, :H, :W]
+    assert np.array_equal(msg, want)
+
+
+def test_resume_from_messages():
+    # the BP state is the message set: k + m sweeps equal k sweeps, then m more from there
+    rng = np.random.default_rng(10)
+    cost = random_cost(rng, 9, 10, 5)
+    full, _ = oracle.bp(cost, 1, 7, 3, 2)
+    part, _ = oracle.bp(cost, 1, 3, 3, 2)
+    rest, _ = oracle.bp(cost, 1, 4, 3, 2, init_coarsest=part)
+    assert np.array_equal(full, rest)
+
+
+def test_wta_and_energy_direct():
+    rng = np.random.default_rng(13)
+    cost = random_cost(rng, 8, 9, 6)
+    msg, _ = oracle.bp(cost, 2, 3, 6, 2)
+    belief = cost.astype(np.int64) + msg.sum(axis=0)
+    d = oracle.wta(cost, msg)
+    assert np.array_equal(d, belief.argmin(axis=2))  # numpy argmin also keeps the lowest d
+    assert oracle.energy(cost, d, 6, 2) == energy_np(cost, d, 6, 2)
+    f = cost.astype(np.float64) + 0.25
+    assert oracle.energy(f, d, 6.0, 2) == pytest.approx(float(energy_np(f, d, 6, 2)), rel=1e-15)
+    with pytest.raises(ValueError):
+        oracle.energy(cost, np.full((8, 9), 6, dtype=np.int32), 6, 2)
+
+
+def test_fronto_parallel_recovery():
+    # a noise-free pair with one constant disparity is recovered away from the left border
+    W, H, D, d0, w = 64, 40, 10, 4, 5
+    L = synth.texture(17, 1, W, H)
+    R = np.empty_like(L)
+    R[:, : W - d0] = L[:, d0:]
+    R[:, W - d0:] = L[:, -1:]
+    res = oracle.stereo_int(L, R, D, w, 20, 3, 6, 10, 2)
+    inner = res["disp"][:, d0 + w:]
+    assert (inner == d0).mean() > 0.99
+
+
+def test_float_form_agrees_with_integer_form_on_integer_costs():
+    rng = np.random.default_rng(14)
+    cost = random_cost(rng, 9, 8, 6)
+    mi, ti = oracle.bp(cost, 3, 4, 10, 2)
+    mf, tf = oracle.bp(cost.astype(np.float64), 3, 4, 10.0, 2)
+    assert np.array_equal(mi, mf.astype(np.int32)) and np.array_equal(ti, tf)
