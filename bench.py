@@ -1,0 +1,328 @@
+"""Throughput of the stereo hot path (NCC cost volume + 4-scale min-sum BP with the
+fast-converging skip + WTA) in Mpix*disp/s, one JSON line on stdout.
+
+Workload (per GPU): the two single-pair configurations of the paper's test-set shapes,
+a 384x288 pair with D=16 and a 450x375 pair with D=64, 7x7 NCC window, data costs
+quantised with trunc 20, 4 scales, 10 iterations per scale, lambda=10, trunc=2, the
+fast-converging skip on, integer messages in uint8 storage (bit-exact with the int32
+method).  Seeded synthetic pairs stand in for the Middlebury images.  One step = both
+pairs through bps_stereo (a CUDA graph replay each).  The working set is smaller than
+L2, so a 256 MiB buffer is written between timed steps to flush it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica (different seeds, weak scaling); the
+per-rank device time is max-reduced and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix·disp/s (cost vol + BP) at equal energy; plain int32 vs FP16/learned/batched"
+UNIT = "Mpix·disp/s"
+WORKLOAD = ["tsukuba_384x288_d16", "teddy_450x375_d64"]
+TRUNC_DATA, LEVELS, ITERS, LAM, TRUNC = 20, 4, 10, 10, 2
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def work_units(pairs) -> int:
+    return sum(p.left.shape[0] * p.left.shape[1] * p.D for p, _ in pairs)
+
+
+def load_pairs(rank: int):
+    from paper_1709_06509_gb300 import shard, synth
+
+    return [synth.workload_pair(name, shard.seed_offset(rank)) for name in WORKLOAD]
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline)
+
+def oracle_pass(pairs) -> float:
+    import oracle
+
+    t0 = time.perf_counter()
+    for pair, window in pairs:
+        oracle.stereo_int(pair.left, pair.right, pair.D, window, TRUNC_DATA, LEVELS, ITERS, LAM, TRUNC, skip=True)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(pairs) -> dict:
+    oracle_pass(pairs[:1])  # load / build the library outside the timing
+    t = oracle_pass(pairs)
+    return {"value": work_units(pairs) / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one pass of both workload pairs (384x288 D16 + 450x375 D64) through the "
+                      f"single-threaded C oracle with the skip on, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1709_06509_gb300 import synth
+
+    pair = synth.workload_pair(WORKLOAD[0])
+    sample = [pair]
+    for _ in range(args.warmup):
+        oracle_pass(sample)
+    times = [oracle_pass(sample) for _ in range(args.steps)]
+    total = sum(times)
+    units = work_units(sample)
+    value = units * args.steps / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "tsukuba_384x288_d16 (one pair per step: the smaller pair of the "
+                               "384x288 D16 + 450x375 D64 workload)", "window": 7, "trunc_data": TRUNC_DATA,
+                   "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC, "fast_skip": True},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "the 384x288 D16 pair per step, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("bp.cu", "bps_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1709_06509_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(profile_name: str):
+    """DRAM bytes per sweep launch recorded by ncu for this kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    rank, world, local = dist_env()
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import _build
+
+    if not os.path.exists(bps.LIB_PATH) or _build.is_stale():
+        if rank == 0 or world == 1:
+            _build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        dist.barrier()
+        _build.build()  # no-op once rank 0 has built
+
+    pairs = load_pairs(rank)
+    ctxs, inputs, outs = [], [], []
+    for pair, window in pairs:
+        H, W = pair.left.shape
+        st = bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev)
+        ctxs.append((st, window))
+        inputs.append((torch.from_numpy(pair.left).to(dev), torch.from_numpy(pair.right).to(dev)))
+        outs.append(torch.empty((H, W), dtype=torch.int32, device=dev))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for (st, window), (L, R), out in zip(ctxs, inputs, outs):
+            st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    sampler = ClockSampler(("GPU-" + uuid if uuid and not uuid.startswith("GPU-") else uuid) or str(local))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # evict the previous step's working set from L2 (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = work_units(pairs) * world
+    value = units * args.steps / (total_ms / 1e3) / 1e6
+
+    # dominant kernel (the red-black sweep): per-launch CUDA events around every finest-scale
+    # sweep launch, on the launching stream, over a run of the same steps with the same flush
+    prof_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
+    for _ in range(max(3, min(args.steps, 20))):
+        for (st, window), (L, R), out in zip(ctxs, inputs, outs):
+            flush.fill_(1)
+            st.build_cost_volume(L, R, window, TRUNC_DATA)
+            st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
+            n, ms, px = st.read_profile()
+            Dp = (st.D + 15) // 16 * 16
+            Wh = (st.W + 1) // 2
+            # algorithmic bytes: per recomputed pixel, its int16 cost, 4 incoming and 4 old outgoing
+            # u8 messages read and 4 u8 messages written; plus the 1-byte skip flag of every slot
+            prof_bytes += px * Dp * (2 + 12 * 1) + n * st.H * Wh
+            prof_ms += ms
+            prof_launches += n
+    hbm, peak_kind = peaks()
+    achieved = prof_bytes / (prof_ms / 1e3) / 1e9
+    traffic = ncu_traffic("sweep_kernel_teddy_450x375_d64.txt")
+
+    # end to end through the public API with host buffers (pinned), H2D and D2H inside
+    host_in = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p, _ in pairs]
+    host_out = [torch.empty(p.left.shape, dtype=torch.int32).pin_memory() for p, _ in pairs]
+    for _ in range(3):
+        for (st, window), (hl, hr), hd in zip(ctxs, host_in, host_out):
+            st.stereo_host(hl, hr, window, TRUNC_DATA, ITERS, LAM, TRUNC, h_disp=hd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for (st, window), (hl, hr), hd in zip(ctxs, host_in, host_out):
+            st.stereo_host(hl, hr, window, TRUNC_DATA, ITERS, LAM, TRUNC, h_disp=hd)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(2 * p.left.size for p, _ in pairs)
+    d2h = sum(4 * p.left.size + 8 for p, _ in pairs)
+
+    launches_per_pair = 1 + (LEVELS - 1) + (LEVELS - 1) + LEVELS * ITERS * 2 + 1
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "384x288 D16 + 450x375 D64 pairs (one step = both)", "window": 7,
+                       "trunc_data": TRUNC_DATA, "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC,
+                       "fast_skip": True, "message_storage": "uint8 (exact: 0 <= m <= lambda*trunc)",
+                       "cost_storage": "int16", "cuda_graph": True, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_kernel<int16,uint8>",
+                         "peak_kind": peak_kind, "launches_timed": prof_launches},
+            "e2e": {"value": units * args.steps / e2e_s / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_pair * len(pairs) * args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(pairs)
+        print(json.dumps(line))
+    for st, _ in ctxs:
+        st.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * bpstereo.h -- C ABI of the GB300 (sm_103a) stereo hot path of arXiv 1709.06509:
+ * a dense NCC matching-cost volume, 4-scale coarse-to-fine min-sum loopy belief
+ * propagation with a truncated-linear smoothness term and the fast-converging skip of
+ * converged pixels, and a winner-take-all disparity read-out.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: BPS_OK (0) or a negative BPS_ERR_* code.
+ *     Nothing throws across this boundary.  Arguments are validated before anything is
+ *     launched; on a validation error nothing is enqueued and the context is unchanged.
+ *   - "d_" pointers are device pointers, "h_" pointers host pointers.  The caller owns
+ *     every buffer it passes in; the library never frees or keeps a caller buffer beyond
+ *     the call, except the workspace given to bps_create (see there).
+ *   - Work is enqueued on the CUDA stream given as `stream` (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) and is asynchronous unless stated.
+ *   - Images are uint8 grayscale, row-major, `pitch` bytes between rows (pitch >= W).
+ *     The left image is the reference: disparity d matches left pixel (x, y) with right
+ *     pixel (x - d, y).  Disparities are int32 [H][W], row-major, pitch W.
+ *   - A context is not thread-safe: calls on one context must be serialised by the caller.
+ *
+ * Numerical forms (msg_type)
+ *   BPS_MSG_INT32  quantised int32 data costs, int32 messages, int32 arithmetic: the plain
+ *                  integer min-sum method.  Bit-identical to the integer CPU oracle.
+ *   BPS_MSG_U8     the same integer method with narrow storage: int16 costs and uint8
+ *                  messages.  Exact (bit-identical to BPS_MSG_INT32) because a normalised
+ *                  message lies in [0, lambda*trunc]; requires lambda*trunc <= 255 and
+ *                  trunc_data * 4^(levels-1) <= 32767, otherwise BPS_ERR_UNSUPPORTED.
+ *   BPS_MSG_FP16   unquantised float data costs clamp(trunc_data*(1-ncc), 0, trunc_data)
+ *                  in fp32, fp16 messages, fp32 arithmetic, min-normalised per pixel.
+ *                  Approximate; compared with the FP64 oracle by energy gap.
+ */
+#ifndef BPSTEREO_H
+#define BPSTEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bps_ctx bps_ctx;
+
+/* status codes */
+#define BPS_OK 0
+#define BPS_ERR_ARG (-1)         /* invalid argument (size, pointer, parameter range) */
+#define BPS_ERR_UNSUPPORTED (-2) /* valid request outside what this build supports */
+#define BPS_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define BPS_ERR_WORKSPACE (-4)   /* workspace missing, too small or misaligned */
+#define BPS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define BPS_ERR_STATE (-6)       /* call order violated (e.g. bp_solve before a cost volume) */
+
+/* numerical forms */
+#define BPS_MSG_INT32 0
+#define BPS_MSG_U8 1
+#define BPS_MSG_FP16 2
+
+/* flags for bps_bp_solve / bps_stereo */
+#define BPS_FLAG_FAST_SKIP 1  /* fast-converging BP: skip pixels whose inputs did not change */
+#define BPS_FLAG_WARM_START 2 /* start the coarsest scale from d_init_msgs instead of zeros */
+#define BPS_FLAG_GRAPH 4      /* bps_stereo*: record the launch sequence once as a CUDA graph
+                                 and replay it while the arguments stay the same */
+#define BPS_FLAG_PROFILE 8    /* bps_bp_solve: time every finest-scale sweep launch with CUDA
+                                 events (read with bps_read_profile); not with BPS_FLAG_GRAPH */
+
+/* Limits of this build. */
+#define BPS_MAX_LEVELS 8
+#define BPS_MAX_D 512
+#define BPS_MAX_ITERS 1024
+#define BPS_MAX_WINDOW 31
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *bps_status_string(int status);
+
+/*
+ * Bytes of device workspace a context of this shape needs (cost pyramid, messages and
+ * skip flags of every scale, reduction scratch, staging buffers of bps_stereo_host).
+ * Returns 0 for invalid shapes (W, H >= 1; 1 <= D <= BPS_MAX_D; 1 <= levels <=
+ * BPS_MAX_LEVELS; msg_type one of BPS_MSG_*).
+ * Scale l has W_l = ceil(W_{l-1} / 2), H_l = ceil(H_{l-1} / 2) ("four scales", section
+ * "GPU Implementation"); every scale keeps all D labels.
+ */
+size_t bps_workspace_bytes(int W, int H, int D, int levels, int msg_type);
+
+/*
+ * Create a context for W x H images, D disparity labels and `levels` scales.
+ * d_workspace: device memory of at least bps_workspace_bytes(...) bytes, 256-byte aligned,
+ * owned by the caller and used exclusively by this context until bps_destroy; or NULL, in
+ * which case the context allocates (cudaMalloc) and frees it itself.
+ * On success *out receives the context.  Errors: BPS_ERR_ARG (shape, out == NULL),
+ * BPS_ERR_WORKSPACE (too small / misaligned), BPS_ERR_CUDA (allocation or stream creation).
+ */
+int bps_create(bps_ctx **out, int W, int H, int D, int levels, int msg_type, void *d_workspace,
+               size_t workspace_bytes);
+
+/* Destroy a context (synchronises its internal stream; frees what it allocated). NULL is a no-op. */
+int bps_destroy(bps_ctx *ctx);
+
+/*
+ * Matching-cost volume (section "Correlation volume computation": normalized cross
+ * correlation of the two views).  For every pixel p = (x, y) and label d < D:
+ *   ncc(p, d) = (N S_ab - S_a S_b) / sqrt((N S_aa - S_a^2)(N S_bb - S_b^2)),  N = window^2,
+ * over the window taps a = L(x+i, y+j), b = R(x-d+i, y+j), |i|, |j| <= window/2, with
+ * replicate-clamped coordinates; ncc = 0 where either window is flat.  The data cost is
+ *   integer forms:  c = clamp(floor(trunc_data * (1 - ncc) + 1/2), 0, trunc_data), decided
+ *                   exactly as FP64 round-to-nearest arithmetic decides it;
+ *   BPS_MSG_FP16:   c = clamp(trunc_data * (1 - ncc), 0, trunc_data) in fp32.
+ * The coarser scales' costs are then built as the sum of each coarse pixel's existing 2x2
+ * children.  d_ncc_out: nullable device float [H][W][D] receiving ncc (abs. error < 1e-5).
+ * Errors: BPS_ERR_ARG (NULL images, pitch < W, window even or > BPS_MAX_WINDOW,
+ * trunc_data < 0), BPS_ERR_UNSUPPORTED (BPS_MSG_U8 with trunc_data*4^(levels-1) > 32767).
+ */
+int bps_build_cost_volume(bps_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch,
+                          int window, int trunc_data, float *d_ncc_out, void *stream);
+
+/*
+ * Hierarchical min-sum loopy BP (sections "Fast Converging BP" and "GPU Implementation")
+ * on the cost volume of the last bps_build_cost_volume.  Runs `levels` (<= the context's)
+ * scales coarsest first; at each scale `iters` iterations of the red-black schedule (all
+ * pixels with x + y even, then all odd).  A pixel sends to each existing 4-neighbour q
+ *   m(d) = min_d' [h(d') + lambda * min(|d - d'|, trunc)] - min_d (same),
+ *   h = its data cost + the messages from its other existing neighbours,
+ * written in place into q's incoming slot.  The coarsest scale starts from zero messages
+ * (or d_init_msgs with BPS_FLAG_WARM_START: [4][H_c][W_c][D] int32 for the integer forms,
+ * float for BPS_MSG_FP16, direction = neighbour the message comes from: up, down, left,
+ * right); every finer pixel starts from its parent's messages.  With BPS_FLAG_FAST_SKIP a
+ * pixel is recomputed only if one of its incoming messages changed since its last update;
+ * the result is identical to running without the skip.
+ * Errors: BPS_ERR_STATE (no cost volume yet), BPS_ERR_ARG (levels, iters > BPS_MAX_ITERS,
+ * lambda < 0, trunc < 0, lambda*(D+trunc) >= 2^24, warm start without d_init_msgs),
+ * BPS_ERR_UNSUPPORTED (BPS_MSG_U8 with lambda*trunc > 255).
+ */
+int bps_bp_solve(bps_ctx *ctx, int levels, int iters, int lambda, int trunc, int flags,
+                 const void *d_init_msgs, void *stream);
+
+/*
+ * Winner-take-all read-out at the finest scale: d(p) = argmin_d [c(p, d) + sum of the
+ * messages into p], the lowest d on ties.  d_disp: device int32 [H][W].
+ * Errors: BPS_ERR_STATE (no cost volume), BPS_ERR_ARG (NULL).
+ */
+int bps_wta_disparity(bps_ctx *ctx, int32_t *d_disp, void *stream);
+
+/*
+ * Energy E(d) = E_D(d) + E_S(d) (section "Approach Description"): the finest-scale data
+ * cost of each pixel's label plus lambda * min(|d_p - d_q|, trunc) over every right and
+ * down grid edge.  Integer forms write an exact int64 to d_energy_i64; BPS_MSG_FP16 writes
+ * an FP64 sum (fixed reduction order, reproducible) to d_energy_f64.  Either output may be
+ * NULL; for the integer forms d_energy_f64 receives the same value as a double.
+ * Labels outside [0, D) are clamped to the nearest valid label.
+ * Errors: BPS_ERR_STATE (no cost volume), BPS_ERR_ARG (NULL d_disp, lambda or trunc < 0).
+ */
+int bps_energy(bps_ctx *ctx, const int32_t *d_disp, int lambda, int trunc, int64_t *d_energy_i64,
+               double *d_energy_f64, void *stream);
+
+/*
+ * The whole path in one call: bps_build_cost_volume, bps_bp_solve over all of the
+ * context's scales, bps_wta_disparity.  flags: BPS_FLAG_FAST_SKIP, BPS_FLAG_GRAPH.
+ * With BPS_FLAG_GRAPH the launch sequence is captured once into a CUDA graph kept by the
+ * context and replayed while every argument is unchanged (a change re-captures).
+ */
+int bps_stereo(bps_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch, int window,
+               int trunc_data, int iters, int lambda, int trunc, int flags, int32_t *d_disp,
+               void *stream);
+
+/*
+ * The whole path from host buffers: copies h_left/h_right (pitch bytes per row) to the
+ * context's staging buffers, runs bps_stereo, computes the energy and copies the
+ * disparities (int32 [H][W]) and the energy back.  h_energy_i64 / h_energy_f64 nullable.
+ * Synchronous: returns after the results are in host memory.  Pinned host memory makes
+ * the copies asynchronous with respect to other streams.
+ */
+int bps_stereo_host(bps_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right, int pitch,
+                    int window, int trunc_data, int iters, int lambda, int trunc, int flags,
+                    int32_t *h_disp, int64_t *h_energy_i64, double *h_energy_f64, void *stream);
+
+/*
+ * Per half-sweep count of recomputed pixels of the last bps_bp_solve (coarsest scale
+ * first, two entries per iteration): the fast-converging trace.  Synchronous.  Returns
+ * the number of entries written (<= cap) or a negative status.
+ */
+int bps_get_trace(bps_ctx *ctx, int64_t *h_counts, int cap);
+
+/*
+ * Copy scale `level`'s messages to d_out in the natural layout [4][H_l][W_l][D]
+ * (int32 for the integer forms, float for BPS_MSG_FP16; slots of missing neighbours are
+ * written as 0).  Used for parity checks, checkpoints and warm starts.
+ */
+int bps_export_messages(bps_ctx *ctx, int level, void *d_out, void *stream);
+
+/* Copy scale `level`'s data cost to d_out, natural layout [H_l][W_l][D] (int32 or float). */
+int bps_export_cost(bps_ctx *ctx, int level, void *d_out, void *stream);
+
+/*
+ * Read the launch timings recorded by the last bps_bp_solve run with BPS_FLAG_PROFILE:
+ * the number of finest-scale sweep launches, their summed duration in ms (CUDA events
+ * on the launching stream), and the number of pixels they recomputed.  Synchronous.
+ */
+int bps_read_profile(bps_ctx *ctx, int *h_launches, double *h_total_ms, int64_t *h_pixels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

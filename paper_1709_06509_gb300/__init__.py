@@ -1,0 +1,306 @@
+"""GB300-native stereo hot path of arXiv 1709.06509: NCC matching-cost volume, 4-scale
+coarse-to-fine min-sum loopy BP with a truncated-linear smoothness term and the
+fast-converging skip, winner-take-all disparity.
+
+This module is a thin ctypes binding of the C ABI declared in ``include/bpstereo.h``
+(library ``libbpstereo.so`` next to this file).  Every step of the path runs in the CUDA
+kernels behind that ABI; this file only marshals arguments.  PyTorch is used for device
+memory and streams.  If the library is missing, ``lib()`` raises: there is no CPU
+fallback.
+
+The ``bps_*`` functions mirror the C entry points one to one (same names, same argument
+order, tensors or raw device addresses for pointers, a CUDA stream or None for the
+current stream).  ``Stereo`` wraps one context and its workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+BPS_OK = 0
+BPS_ERR_ARG = -1
+BPS_ERR_UNSUPPORTED = -2
+BPS_ERR_CUDA = -3
+BPS_ERR_WORKSPACE = -4
+BPS_ERR_TIMEOUT = -5
+BPS_ERR_STATE = -6
+
+BPS_MSG_INT32 = 0
+BPS_MSG_U8 = 1
+BPS_MSG_FP16 = 2
+
+BPS_FLAG_FAST_SKIP = 1
+BPS_FLAG_WARM_START = 2
+BPS_FLAG_GRAPH = 4
+BPS_FLAG_PROFILE = 8
+
+BPS_MAX_LEVELS = 8
+BPS_MAX_D = 512
+BPS_MAX_ITERS = 1024
+BPS_MAX_WINDOW = 31
+
+
+class BPSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+_P, _I, _SZ, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int64
+_SIGS = {
+    "bps_status_string": (ctypes.c_char_p, [_I]),
+    "bps_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I]),
+    "bps_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _P, _SZ]),
+    "bps_destroy": (_I, [_P]),
+    "bps_build_cost_volume": (_I, [_P, _P, _P, _I, _I, _I, _P, _P]),
+    "bps_bp_solve": (_I, [_P, _I, _I, _I, _I, _I, _P, _P]),
+    "bps_wta_disparity": (_I, [_P, _P, _P]),
+    "bps_energy": (_I, [_P, _P, _I, _I, _P, _P, _P]),
+    "bps_stereo": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "bps_stereo_host": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "bps_get_trace": (_I, [_P, _P, _I]),
+    "bps_export_messages": (_I, [_P, _I, _P, _P]),
+    "bps_export_cost": (_I, [_P, _I, _P, _P]),
+    "bps_read_profile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbpstereo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1709_06509_gb300._build.build()")
+        _lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().bps_status_string(status).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise BPSError(rc, what)
+    return rc
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ one-to-one entry points
+
+def bps_workspace_bytes(W: int, H: int, D: int, levels: int, msg_type: int) -> int:
+    return lib().bps_workspace_bytes(W, H, D, levels, msg_type)
+
+
+def bps_create(W: int, H: int, D: int, levels: int, msg_type: int, workspace=None) -> int:
+    ctx = _P()
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().bps_create(ctypes.byref(ctx), W, H, D, levels, msg_type, _ptr(workspace), nbytes), "bps_create")
+    return ctx.value
+
+
+def bps_destroy(ctx: int) -> None:
+    _check(lib().bps_destroy(ctx), "bps_destroy")
+
+
+def bps_build_cost_volume(ctx, left, right, pitch, window, trunc_data, ncc_out=None, stream=None):
+    _check(lib().bps_build_cost_volume(ctx, _ptr(left), _ptr(right), pitch, window, trunc_data, _ptr(ncc_out),
+                                       _stream(stream)), "bps_build_cost_volume")
+
+
+def bps_bp_solve(ctx, levels, iters, lam, trunc, flags, init_msgs=None, stream=None):
+    _check(lib().bps_bp_solve(ctx, levels, iters, lam, trunc, flags, _ptr(init_msgs), _stream(stream)),
+           "bps_bp_solve")
+
+
+def bps_wta_disparity(ctx, disp, stream=None):
+    _check(lib().bps_wta_disparity(ctx, _ptr(disp), _stream(stream)), "bps_wta_disparity")
+
+
+def bps_energy(ctx, disp, lam, trunc, energy_i64=None, energy_f64=None, stream=None):
+    _check(lib().bps_energy(ctx, _ptr(disp), lam, trunc, _ptr(energy_i64), _ptr(energy_f64), _stream(stream)),
+           "bps_energy")
+
+
+def bps_stereo(ctx, left, right, pitch, window, trunc_data, iters, lam, trunc, flags, disp, stream=None):
+    _check(lib().bps_stereo(ctx, _ptr(left), _ptr(right), pitch, window, trunc_data, iters, lam, trunc, flags,
+                            _ptr(disp), _stream(stream)), "bps_stereo")
+
+
+def bps_stereo_host(ctx, h_left, h_right, pitch, window, trunc_data, iters, lam, trunc, flags, h_disp,
+                    h_energy_i64=None, h_energy_f64=None, stream=None):
+    _check(lib().bps_stereo_host(ctx, _ptr(h_left), _ptr(h_right), pitch, window, trunc_data, iters, lam, trunc,
+                                 flags, _ptr(h_disp), _ptr(h_energy_i64), _ptr(h_energy_f64), _stream(stream)),
+           "bps_stereo_host")
+
+
+def bps_get_trace(ctx, h_counts, cap: int) -> int:
+    return _check(lib().bps_get_trace(ctx, _ptr(h_counts), cap), "bps_get_trace")
+
+
+def bps_export_messages(ctx, level, out, stream=None):
+    _check(lib().bps_export_messages(ctx, level, _ptr(out), _stream(stream)), "bps_export_messages")
+
+
+def bps_export_cost(ctx, level, out, stream=None):
+    _check(lib().bps_export_cost(ctx, level, _ptr(out), _stream(stream)), "bps_export_cost")
+
+
+def bps_read_profile(ctx):
+    n, ms, px = _I(), ctypes.c_double(), _I64()
+    _check(lib().bps_read_profile(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(px)), "bps_read_profile")
+    return n.value, ms.value, px.value
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+def level_dims(W: int, H: int, levels: int) -> list[tuple[int, int]]:
+    dims = [(W, H)]
+    for _ in range(1, levels):
+        w, h = dims[-1]
+        dims.append(((w + 1) // 2, (h + 1) // 2))
+    return dims
+
+
+class Stereo:
+    """One context (W x H images, D labels, `levels` scales, numerical form `msg_type`) with
+    its workspace held in a torch uint8 tensor on `device`."""
+
+    def __init__(self, W: int, H: int, D: int, levels: int = 4, msg_type: int = BPS_MSG_U8, device="cuda"):
+        import torch
+
+        self.W, self.H, self.D, self.levels, self.msg_type = W, H, D, levels, msg_type
+        nbytes = bps_workspace_bytes(W, H, D, levels, msg_type)
+        if nbytes == 0:
+            raise BPSError(BPS_ERR_ARG, "bps_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.ctx = bps_create(W, H, D, levels, msg_type, self.workspace)
+        self.device = self.workspace.device
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            bps_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def msg_dtype(self):
+        import torch
+
+        return torch.float32 if self.msg_type == BPS_MSG_FP16 else torch.int32
+
+    def build_cost_volume(self, left, right, window: int, trunc_data: int, want_ncc: bool = False, stream=None):
+        import torch
+
+        ncc = torch.empty((self.H, self.W, self.D), dtype=torch.float32, device=self.device) if want_ncc else None
+        bps_build_cost_volume(self.ctx, left, right, left.stride(0), window, trunc_data, ncc, stream)
+        return ncc
+
+    def bp_solve(self, iters: int, lam: int, trunc: int, levels: int | None = None, skip: bool = True,
+                 init_msgs=None, profile: bool = False, stream=None):
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_WARM_START if init_msgs is not None else 0)
+        flags |= BPS_FLAG_PROFILE if profile else 0
+        bps_bp_solve(self.ctx, levels or self.levels, iters, lam, trunc, flags, init_msgs, stream)
+
+    def wta_disparity(self, out=None, stream=None):
+        import torch
+
+        out = out if out is not None else torch.empty((self.H, self.W), dtype=torch.int32, device=self.device)
+        bps_wta_disparity(self.ctx, out, stream)
+        return out
+
+    def energy(self, disp, lam: int, trunc: int, stream=None):
+        import torch
+
+        ei = torch.zeros(1, dtype=torch.int64, device=self.device)
+        ef = torch.zeros(1, dtype=torch.float64, device=self.device)
+        bps_energy(self.ctx, disp, lam, trunc, ei, ef, stream)
+        return ei, ef
+
+    def stereo(self, left, right, window, trunc_data, iters, lam, trunc, skip=True, graph=False, out=None,
+               stream=None):
+        import torch
+
+        out = out if out is not None else torch.empty((self.H, self.W), dtype=torch.int32, device=self.device)
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
+        bps_stereo(self.ctx, left, right, left.stride(0), window, trunc_data, iters, lam, trunc, flags, out, stream)
+        return out
+
+    def stereo_host(self, h_left, h_right, window, trunc_data, iters, lam, trunc, skip=True, graph=True,
+                    h_disp=None, stream=None):
+        """Host tensors in, host disparity and energy out (synchronous)."""
+        import torch
+
+        pin = h_left.is_pinned()
+        h_disp = h_disp if h_disp is not None else torch.empty((self.H, self.W), dtype=torch.int32).pin_memory() \
+            if pin else torch.empty((self.H, self.W), dtype=torch.int32)
+        ei = torch.zeros(1, dtype=torch.int64)
+        ef = torch.zeros(1, dtype=torch.float64)
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
+        bps_stereo_host(self.ctx, h_left, h_right, h_left.stride(0), window, trunc_data, iters, lam, trunc, flags,
+                        h_disp, ei if self.msg_type != BPS_MSG_FP16 else None, ef, stream)
+        return h_disp, (int(ei.item()) if self.msg_type != BPS_MSG_FP16 else float(ef.item()))
+
+    def get_trace(self):
+        import numpy as np
+
+        buf = np.zeros(self.levels * BPS_MAX_ITERS * 2, dtype=np.int64)
+        n = bps_get_trace(self.ctx, buf.ctypes.data, buf.size)
+        return buf[:n]
+
+    def export_messages(self, level: int = 0, stream=None):
+        import torch
+
+        w, h = level_dims(self.W, self.H, self.levels)[level]
+        out = torch.empty((4, h, w, self.D), dtype=self.msg_dtype, device=self.device)
+        bps_export_messages(self.ctx, level, out, stream)
+        return out
+
+    def export_cost(self, level: int = 0, stream=None):
+        import torch
+
+        w, h = level_dims(self.W, self.H, self.levels)[level]
+        out = torch.empty((h, w, self.D), dtype=self.msg_dtype, device=self.device)
+        bps_export_cost(self.ctx, level, out, stream)
+        return out
+
+    def read_profile(self):
+        return bps_read_profile(self.ctx)

@@ -1,0 +1,454 @@
+// api.cu -- the C ABI (include/bpstereo.h): context, workspace plan, argument checks and
+// the launch sequence of the hot path.  No exception crosses the boundary; every CUDA
+// error becomes BPS_ERR_CUDA.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bpstereo.h"
+#include "bps_launch.h"
+
+using namespace bps;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t up(size_t v, size_t a = ALIGN) { return (v + a - 1) / a * a; }
+
+struct Plan {
+    int levels = 0;
+    int Ws[BPS_MAX_LEVELS], Hs[BPS_MAX_LEVELS], Whs[BPS_MAX_LEVELS];
+    size_t cost[BPS_MAX_LEVELS][2], msg[BPS_MAX_LEVELS][2], dirty[BPS_MAX_LEVELS][2];
+    size_t trace, partials, img[2], disp, energy, total;
+};
+
+int cost_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? COST_I32 : msg_type == BPS_MSG_U8 ? COST_I16 : COST_F32; }
+int msg_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? MSG_I32 : msg_type == BPS_MSG_U8 ? MSG_U8 : MSG_F16; }
+size_t cost_size(int msg_type) { return msg_type == BPS_MSG_U8 ? 2 : 4; }
+size_t msg_size(int msg_type) { return msg_type == BPS_MSG_INT32 ? 4 : msg_type == BPS_MSG_U8 ? 1 : 2; }
+int pad_labels(int D) { return (D + VEC - 1) / VEC * VEC; }
+
+bool shape_ok(int W, int H, int D, int levels, int msg_type) {
+    return W >= 1 && H >= 1 && D >= 1 && D <= BPS_MAX_D && levels >= 1 && levels <= BPS_MAX_LEVELS &&
+           (msg_type == BPS_MSG_INT32 || msg_type == BPS_MSG_U8 || msg_type == BPS_MSG_FP16) &&
+           (int64_t)W * H <= (int64_t)1 << 31;
+}
+
+bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
+    if (!shape_ok(W, H, D, levels, msg_type)) return false;
+    const size_t Dp = (size_t)pad_labels(D);
+    size_t off = 0;
+    p.levels = levels;
+    for (int l = 0; l < levels; ++l) {
+        p.Ws[l] = l ? (p.Ws[l - 1] + 1) / 2 : W;
+        p.Hs[l] = l ? (p.Hs[l - 1] + 1) / 2 : H;
+        p.Whs[l] = (p.Ws[l] + 1) / 2;
+        const size_t nslot = (size_t)p.Hs[l] * p.Whs[l];
+        for (int c = 0; c < 2; ++c) {
+            p.cost[l][c] = off;
+            off += up(nslot * Dp * cost_size(msg_type));
+            p.msg[l][c] = off;
+            off += up(nslot * 4 * Dp * msg_size(msg_type));
+            p.dirty[l][c] = off;
+            off += up(nslot);
+        }
+    }
+    p.trace = off;
+    off += up((size_t)levels * BPS_MAX_ITERS * 2 * sizeof(unsigned long long));
+    p.partials = off;
+    off += up(1024 * 8);
+    p.img[0] = off;
+    off += up((size_t)W * H);
+    p.img[1] = off;
+    off += up((size_t)W * H);
+    p.disp = off;
+    off += up((size_t)W * H * 4);
+    p.energy = off;
+    off += up(16);
+    p.total = off;
+    return true;
+}
+
+struct GraphKey {
+    const void *L, *R;
+    int32_t *disp;
+    int pitch, window, trunc_data, iters, lambda, trunc, flags;
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+}  // namespace
+
+struct bps_ctx {
+    int W, H, D, Dp, Gp, levels, msg_type, cost_kind, msg_kind;
+    Plan plan;
+    LevelView lv[BPS_MAX_LEVELS];
+    char *ws = nullptr;
+    bool owns_ws = false;
+    unsigned long long *trace = nullptr;
+    void *partials = nullptr;
+    uint8_t *img[2] = {nullptr, nullptr};
+    int32_t *disp = nullptr;
+    int64_t *e_i64 = nullptr;
+    double *e_f64 = nullptr;
+    bool has_cost = false;
+    int last_levels = 0, last_iters = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    std::vector<cudaEvent_t> ev;
+    int prof_launches = 0;
+    int prof_first_trace = 0;
+};
+
+#define CK(x)                                     \
+    do {                                          \
+        if ((x) != cudaSuccess) return BPS_ERR_CUDA; \
+    } while (0)
+
+extern "C" const char *bps_status_string(int s) {
+    switch (s) {
+    case BPS_OK: return "ok";
+    case BPS_ERR_ARG: return "invalid argument";
+    case BPS_ERR_UNSUPPORTED: return "unsupported by this build";
+    case BPS_ERR_CUDA: return "CUDA error";
+    case BPS_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case BPS_ERR_TIMEOUT: return "bounded device wait gave up";
+    case BPS_ERR_STATE: return "call order violated";
+    default: return "unknown status";
+    }
+}
+
+extern "C" size_t bps_workspace_bytes(int W, int H, int D, int levels, int msg_type) {
+    Plan p;
+    return make_plan(W, H, D, levels, msg_type, p) ? p.total : 0;
+}
+
+extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int msg_type, void *d_workspace,
+                          size_t workspace_bytes) {
+    if (!out) return BPS_ERR_ARG;
+    *out = nullptr;
+    Plan p;
+    if (!make_plan(W, H, D, levels, msg_type, p)) return BPS_ERR_ARG;
+    if (d_workspace && (workspace_bytes < p.total || ((uintptr_t)d_workspace % ALIGN) != 0)) return BPS_ERR_WORKSPACE;
+    bps_ctx *c = new (std::nothrow) bps_ctx();
+    if (!c) return BPS_ERR_CUDA;
+    c->W = W;
+    c->H = H;
+    c->D = D;
+    c->Dp = pad_labels(D);
+    int G = c->Dp / VEC, Gp = 1;
+    while (Gp < G) Gp <<= 1;
+    c->Gp = Gp;
+    c->levels = levels;
+    c->msg_type = msg_type;
+    c->cost_kind = cost_kind_of(msg_type);
+    c->msg_kind = msg_kind_of(msg_type);
+    c->plan = p;
+    if (d_workspace) {
+        c->ws = static_cast<char *>(d_workspace);
+    } else {
+        if (cudaMalloc(&c->ws, p.total) != cudaSuccess) {
+            delete c;
+            return BPS_ERR_CUDA;
+        }
+        c->owns_ws = true;
+    }
+    for (int l = 0; l < levels; ++l) {
+        LevelView &v = c->lv[l];
+        v.W = p.Ws[l];
+        v.H = p.Hs[l];
+        v.Wh = p.Whs[l];
+        for (int k = 0; k < 2; ++k) {
+            v.cost[k] = c->ws + p.cost[l][k];
+            v.msg[k] = c->ws + p.msg[l][k];
+            v.dirty[k] = reinterpret_cast<uint8_t *>(c->ws + p.dirty[l][k]);
+        }
+    }
+    c->trace = reinterpret_cast<unsigned long long *>(c->ws + p.trace);
+    c->partials = c->ws + p.partials;
+    c->img[0] = reinterpret_cast<uint8_t *>(c->ws + p.img[0]);
+    c->img[1] = reinterpret_cast<uint8_t *>(c->ws + p.img[1]);
+    c->disp = reinterpret_cast<int32_t *>(c->ws + p.disp);
+    c->e_i64 = reinterpret_cast<int64_t *>(c->ws + p.energy);
+    c->e_f64 = reinterpret_cast<double *>(c->ws + p.energy + 8);
+    bool ok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    // the NCC kernel's shared memory depends on D and the window; allow the largest window now so
+    // that no attribute call happens while a launch sequence is being captured
+    ok = ok && ncc_prepare(c->cost_kind, D, BPS_MAX_WINDOW) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->ws, 0, p.total, c->cap) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(c->cap) == cudaSuccess;
+    if (!ok) {
+        bps_destroy(c);
+        return BPS_ERR_CUDA;
+    }
+    *out = c;
+    return BPS_OK;
+}
+
+extern "C" int bps_destroy(bps_ctx *c) {
+    if (!c) return BPS_OK;
+    int rc = BPS_OK;
+    if (c->cap && cudaStreamSynchronize(c->cap) != cudaSuccess) rc = BPS_ERR_CUDA;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->owns_ws && c->ws) {
+        cudaDeviceSynchronize();
+        if (cudaFree(c->ws) != cudaSuccess) rc = BPS_ERR_CUDA;
+    }
+    delete c;
+    return rc;
+}
+
+static int check_cost_args(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data) {
+    if (!c || !L || !R || pitch < c->W || window < 1 || (window & 1) == 0 || window > BPS_MAX_WINDOW ||
+        trunc_data < 0 || trunc_data > 65535)
+        return BPS_ERR_ARG;
+    if (c->msg_type == BPS_MSG_U8) {
+        int64_t top = trunc_data;
+        for (int l = 1; l < c->levels; ++l) top *= 4;
+        if (top > 32767) return BPS_ERR_UNSUPPORTED;
+    }
+    if (c->msg_type == BPS_MSG_INT32) {
+        int64_t top = trunc_data;
+        for (int l = 1; l < c->levels; ++l) top *= 4;
+        if (top >= (1 << 24)) return BPS_ERR_UNSUPPORTED;
+    }
+    return BPS_OK;
+}
+
+static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
+                        float *ncc_out, cudaStream_t st) {
+    const LevelView &v0 = c->lv[0];
+    CK(launch_ncc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0.Wh, v0.cost[0],
+                  v0.cost[1], ncc_out, st));
+    for (int l = 1; l < c->levels; ++l) CK(launch_pyramid(c->cost_kind, c->lv[l - 1], c->lv[l], c->Dp, st));
+    return BPS_OK;
+}
+
+extern "C" int bps_build_cost_volume(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window,
+                                     int trunc_data, float *ncc_out, void *stream) {
+    const int rc = check_cost_args(c, L, R, pitch, window, trunc_data);
+    if (rc != BPS_OK) return rc;
+    const int e = enqueue_cost(c, L, R, pitch, window, trunc_data, ncc_out, (cudaStream_t)stream);
+    if (e == BPS_OK) c->has_cost = true;
+    return e;
+}
+
+static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init) {
+    if (!c) return BPS_ERR_ARG;
+    if (!c->has_cost) return BPS_ERR_STATE;
+    if (levels < 1 || levels > c->levels || iters < 0 || iters > BPS_MAX_ITERS || lambda < 0 || trunc < 0 ||
+        (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_WARM_START | BPS_FLAG_GRAPH | BPS_FLAG_PROFILE)) ||
+        (int64_t)lambda * ((int64_t)c->Dp + trunc) >= ((int64_t)1 << 24) ||
+        ((flags & BPS_FLAG_WARM_START) && !init))
+        return BPS_ERR_ARG;
+    if (c->msg_type == BPS_MSG_U8 && (int64_t)lambda * trunc > 255) return BPS_ERR_UNSUPPORTED;
+    return BPS_OK;
+}
+
+static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
+                      cudaStream_t st) {
+    const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
+    const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
+    const int top = levels - 1;
+    const size_t mb = msg_size(c->msg_type);
+    const int ntrace = levels * iters * 2;
+    if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
+    if (prof) {
+        const size_t need = 2 * (size_t)iters * 2;
+        while (c->ev.size() < need) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev.push_back(e);
+        }
+        c->prof_launches = 0;
+        c->prof_first_trace = top * iters * 2;
+    }
+    {
+        const LevelView &v = c->lv[top];
+        if (flags & BPS_FLAG_WARM_START) {
+            CK(launch_import_msgs(c->msg_kind, v, c->D, c->Dp, init, st));
+        } else {
+            for (int k = 0; k < 2; ++k)
+                CK(cudaMemsetAsync(v.msg[k], 0, (size_t)v.H * v.Wh * 4 * c->Dp * mb, st));
+        }
+    }
+    int t = 0;
+    for (int l = top; l >= 0; --l) {
+        const LevelView &v = c->lv[l];
+        if (l < top) {
+            // only the even pixels' start messages are ever read: the first half-sweep overwrites
+            // every existing incoming slot of the odd pixels (unless there is no sweep at all)
+            CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, 0, c->Dp, st));
+            if (iters == 0) CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, 1, c->Dp, st));
+        }
+        if (skip)
+            for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(v.dirty[k], 1, (size_t)v.H * v.Wh, st));
+        for (int it = 0; it < iters; ++it)
+            for (int colour = 0; colour < 2; ++colour, ++t) {
+                const bool rec = prof && l == 0;
+                if (rec) CK(cudaEventRecord(c->ev[2 * c->prof_launches], st));
+                CK(launch_sweep(c->msg_kind, v, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st));
+                if (rec) {
+                    CK(cudaEventRecord(c->ev[2 * c->prof_launches + 1], st));
+                    ++c->prof_launches;
+                }
+            }
+    }
+    c->last_levels = levels;
+    c->last_iters = iters;
+    return BPS_OK;
+}
+
+extern "C" int bps_bp_solve(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
+                            void *stream) {
+    const int rc = check_bp_args(c, levels, iters, lambda, trunc, flags & ~BPS_FLAG_GRAPH, init);
+    if (rc != BPS_OK) return rc;
+    return enqueue_bp(c, levels, iters, lambda, trunc, flags & ~BPS_FLAG_GRAPH, init, (cudaStream_t)stream);
+}
+
+extern "C" int bps_wta_disparity(bps_ctx *c, int32_t *disp, void *stream) {
+    if (!c || !disp) return BPS_ERR_ARG;
+    if (!c->has_cost) return BPS_ERR_STATE;
+    CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, (cudaStream_t)stream));
+    return BPS_OK;
+}
+
+extern "C" int bps_energy(bps_ctx *c, const int32_t *disp, int lambda, int trunc, int64_t *e_i64, double *e_f64,
+                          void *stream) {
+    if (!c || !disp || lambda < 0 || trunc < 0) return BPS_ERR_ARG;
+    if (!c->has_cost) return BPS_ERR_STATE;
+    CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, disp, lambda, trunc, c->partials, e_i64, e_f64,
+                     (cudaStream_t)stream));
+    return BPS_OK;
+}
+
+static int enqueue_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
+                          int iters, int lambda, int trunc, int flags, int32_t *disp, cudaStream_t st) {
+    int rc = enqueue_cost(c, L, R, pitch, window, trunc_data, nullptr, st);
+    if (rc != BPS_OK) return rc;
+    rc = enqueue_bp(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr, st);
+    if (rc != BPS_OK) return rc;
+    CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+    return BPS_OK;
+}
+
+extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
+                          int iters, int lambda, int trunc, int flags, int32_t *disp, void *stream) {
+    int rc = check_cost_args(c, L, R, pitch, window, trunc_data);
+    if (rc != BPS_OK) return rc;
+    if (!disp || (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH))) return BPS_ERR_ARG;
+    const bool had_cost = c->has_cost;
+    c->has_cost = true;  // the sequence builds the cost volume first
+    rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
+    if (rc != BPS_OK) {
+        c->has_cost = had_cost;
+        return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(flags & BPS_FLAG_GRAPH)) return enqueue_stereo(c, L, R, pitch, window, trunc_data, iters, lambda, trunc, flags, disp, st);
+
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.L = L;
+    key.R = R;
+    key.disp = disp;
+    key.pitch = pitch;
+    key.window = window;
+    key.trunc_data = trunc_data;
+    key.iters = iters;
+    key.lambda = lambda;
+    key.trunc = trunc;
+    key.flags = flags;
+    if (!c->gexec || !(key == c->gkey)) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        CK(cudaStreamSynchronize(c->cap));
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_stereo(c, L, R, pitch, window, trunc_data, iters, lambda, trunc, flags, disp, c->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+        if (rc != BPS_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != BPS_OK ? rc : BPS_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return BPS_ERR_CUDA;
+        }
+        c->gkey = key;
+    }
+    CK(cudaGraphLaunch(c->gexec, st));
+    return BPS_OK;
+}
+
+extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR, int pitch, int window,
+                               int trunc_data, int iters, int lambda, int trunc, int flags, int32_t *h_disp,
+                               int64_t *h_e_i64, double *h_e_f64, void *stream) {
+    if (!c || !hL || !hR || !h_disp || pitch < c->W) return BPS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpy2DAsync(c->img[0], c->W, hL, pitch, c->W, c->H, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpy2DAsync(c->img[1], c->W, hR, pitch, c->W, c->H, cudaMemcpyHostToDevice, st));
+    int rc = bps_stereo(c, c->img[0], c->img[1], c->W, window, trunc_data, iters, lambda, trunc, flags, c->disp, stream);
+    if (rc != BPS_OK) return rc;
+    if (h_e_i64 || h_e_f64) {
+        CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, c->disp, lambda, trunc, c->partials,
+                         c->msg_type == BPS_MSG_FP16 ? nullptr : c->e_i64, c->e_f64, st));
+    }
+    CK(cudaMemcpyAsync(h_disp, c->disp, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, st));
+    if (h_e_i64 && c->msg_type != BPS_MSG_FP16) CK(cudaMemcpyAsync(h_e_i64, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
+    if (h_e_f64) CK(cudaMemcpyAsync(h_e_f64, c->e_f64, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return BPS_OK;
+}
+
+extern "C" int bps_get_trace(bps_ctx *c, int64_t *h_counts, int cap) {
+    if (!c || (!h_counts && cap > 0) || cap < 0) return BPS_ERR_ARG;
+    const int n = std::min(cap, c->last_levels * c->last_iters * 2);
+    if (n <= 0) return 0;
+    std::vector<unsigned long long> tmp(n);
+    CK(cudaMemcpy(tmp.data(), c->trace, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n; ++k) h_counts[k] = (int64_t)tmp[k];
+    return n;
+}
+
+extern "C" int bps_export_messages(bps_ctx *c, int level, void *d_out, void *stream) {
+    if (!c || !d_out || level < 0 || level >= c->levels) return BPS_ERR_ARG;
+    CK(launch_export_msgs(c->msg_kind, c->lv[level], c->D, c->Dp, d_out, (cudaStream_t)stream));
+    return BPS_OK;
+}
+
+extern "C" int bps_export_cost(bps_ctx *c, int level, void *d_out, void *stream) {
+    if (!c || !d_out || level < 0 || level >= c->levels) return BPS_ERR_ARG;
+    if (!c->has_cost) return BPS_ERR_STATE;
+    CK(launch_export_cost(c->cost_kind, c->lv[level], c->D, c->Dp, d_out, (cudaStream_t)stream));
+    return BPS_OK;
+}
+
+extern "C" int bps_read_profile(bps_ctx *c, int *h_launches, double *h_total_ms, int64_t *h_pixels) {
+    if (!c || !h_launches || !h_total_ms || !h_pixels) return BPS_ERR_ARG;
+    double total = 0.0;
+    for (int k = 0; k < c->prof_launches; ++k) {
+        CK(cudaEventSynchronize(c->ev[2 * k + 1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        total += ms;
+    }
+    int64_t px = 0;
+    if (c->prof_launches) {
+        std::vector<unsigned long long> tmp(c->prof_launches);
+        CK(cudaMemcpy(tmp.data(), c->trace + c->prof_first_trace, sizeof(unsigned long long) * c->prof_launches,
+                      cudaMemcpyDeviceToHost));
+        for (unsigned long long v : tmp) px += (int64_t)v;
+    }
+    *h_launches = c->prof_launches;
+    *h_total_ms = total;
+    *h_pixels = px;
+    return BPS_OK;
+}

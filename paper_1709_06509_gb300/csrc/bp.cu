@@ -1,0 +1,306 @@
+// bp.cu -- hierarchical min-sum loopy BP on the 4-connected grid (sections "Fast
+// Converging BP" and "GPU Implementation").
+//
+// sweep_kernel: one red-black half-sweep.  A group of Gp lanes owns one pixel of the
+// active colour (16 labels per lane).  It forms the belief b = cost + sum of the existing
+// incoming messages, and for each existing neighbour q the message
+//     m(d) = min(F(d), B(d), min h + lambda*trunc) - min h,   h = b - (message from q),
+// where F / B are the forward / backward passes of the distance transform for the linear
+// cost lambda*|d - d'| (F(d) = min(h(d), F(d-1) + lambda), B mirrored).  Within a lane the
+// passes run over its 16 labels; across the lanes of the group they are completed by a
+// Kogge-Stone scan of the segment ends (warp shuffles), and min h by a butterfly.  The
+// result is written straight into q's incoming slot (the other colour's arrays, so the
+// update is race-free in place).
+//
+// Fast-converging skip, exact form: dirty[c][s] = 1 while some incoming message of the
+// pixel changed since its last update.  A clean pixel would resend exactly what it sent
+// last time, so the group skips it; the warp exits early when all its pixels are clean.
+// With the skip on, a sender compares each new message with the stored one and writes
+// (and marks the receiver dirty) only on a change.
+#include <algorithm>
+#include <type_traits>
+
+#include "bps_internal.cuh"
+#include "bps_launch.h"
+
+namespace bps {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ inline unsigned group_bits(int Gp) { return Gp >= 32 ? FULL : ((1u << Gp) - 1u); }
+__device__ inline unsigned leader_bits(int Gp) {
+    unsigned m = 0;
+    for (int l = 0; l < 32; l += Gp) m |= 1u << l;
+    return m;
+}
+
+template <typename Acc>
+__device__ inline void min_convolve(const Acc (&h)[VEC], Acc lam, Acc lamT, int g, int Gp, Acc (&m)[VEC]) {
+    using A = Arith<Acc>;
+    Acc F[VEC], B[VEC];
+    F[0] = h[0];
+#pragma unroll
+    for (int k = 1; k < VEC; ++k) F[k] = A::mn(h[k], F[k - 1] + lam);
+    B[VEC - 1] = h[VEC - 1];
+#pragma unroll
+    for (int k = VEC - 2; k >= 0; --k) B[k] = A::mn(h[k], B[k + 1] + lam);
+    Acc hm = h[0];
+#pragma unroll
+    for (int k = 1; k < VEC; ++k) hm = A::mn(hm, h[k]);
+    if (Gp > 1) {
+        const Acc span = lam * (Acc)VEC;
+        Acc fe = F[VEC - 1], bs = B[0];
+        for (int o = 1; o < Gp; o <<= 1) {
+            const Acc tf = __shfl_up_sync(FULL, fe, o, Gp);
+            const Acc tb = __shfl_down_sync(FULL, bs, o, Gp);
+            const Acc th = __shfl_xor_sync(FULL, hm, o, Gp);
+            if (g >= o) fe = A::mn(fe, tf + span * (Acc)o);
+            if (g + o < Gp) bs = A::mn(bs, tb + span * (Acc)o);
+            hm = A::mn(hm, th);
+        }
+        Acc cf = __shfl_up_sync(FULL, fe, 1, Gp);
+        Acc cb = __shfl_down_sync(FULL, bs, 1, Gp);
+        if (g == 0) cf = A::big();
+        if (g == Gp - 1) cb = A::big();
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            F[k] = A::mn(F[k], cf + lam * (Acc)(k + 1));
+            B[k] = A::mn(B[k], cb + lam * (Acc)(VEC - k));
+        }
+    }
+    const Acc cap = hm + lamT;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) m[k] = A::mn(A::mn(F[k], B[k]), cap) - hm;
+}
+
+template <typename CostT, typename MsgT>
+__global__ void __launch_bounds__(256)
+sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<MsgT>::type lam,
+             typename AccOf<MsgT>::type lamT, int skip, unsigned long long *trace) {
+    using Acc = typename AccOf<MsgT>::type;
+    using A = Arith<Acc>;
+    const int lane = threadIdx.x & 31;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    int x = 0, y = 0;
+    bool valid = false;
+    if (s < nslot) {
+        y = (int)(s / lv.Wh);
+        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        valid = x < lv.W;
+    }
+    const bool active = valid && (!skip || lv.dirty[colour][s] != 0);
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) return;
+    if (trace && lane == 0) {
+        const int n = __popc(act & leader_bits(Gp));
+        if (n) atomicAdd(trace, (unsigned long long)n);
+    }
+    const int64_t sc = valid ? s : 0;
+    const int dbase = g * VEC;
+    const bool lane_data = dbase < Dp;
+    const bool has[4] = {valid && y > 0, valid && y < lv.H - 1, valid && x > 0, valid && x < lv.W - 1};
+
+    Acc b[VEC], in[4][VEC];
+    if (lane_data) {
+        load16(reinterpret_cast<const CostT *>(lv.cost[colour]) + sc * Dp + dbase, b);
+        const MsgT *mp = reinterpret_cast<const MsgT *>(lv.msg[colour]) + sc * 4 * Dp + dbase;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (has[q]) {
+                load16(mp + q * Dp, in[q]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) in[q][k] = Acc(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            b[k] = A::big();
+            in[0][k] = in[1][k] = in[2][k] = in[3][k] = Acc(0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) b[k] = b[k] + in[0][k] + in[1][k] + in[2][k] + in[3][k];
+
+    const int nbx[4] = {x, x, x - 1, x + 1};
+    const int nby[4] = {y - 1, y + 1, y, y};
+    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
+    MsgT *out = reinterpret_cast<MsgT *>(lv.msg[colour ^ 1]);
+    const int gshift = lane & ~(Gp - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        Acc h[VEC], m[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) h[k] = (dbase + k < D) ? b[k] - in[q][k] : A::big();
+        min_convolve(h, lam, lamT, g, Gp, m);
+        const bool send = active && has[q];
+        const int64_t qs = send ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+        MsgT *dst = out + (qs * 4 + opp[q]) * Dp + dbase;
+        if (skip) {
+            bool diff = false;
+            if (send && lane_data) {
+                Acc old[VEC];
+                load16_rw(dst, old);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) diff |= (old[k] != stored_value<MsgT>(m[k]));
+            }
+            const unsigned dm = __ballot_sync(FULL, diff);
+            const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
+            if (send && changed) {
+                if (lane_data) store16(dst, m);
+                if (g == 0) lv.dirty[colour ^ 1][qs] = 1;
+            }
+        } else if (send && lane_data) {
+            store16(dst, m);
+        }
+    }
+    if (skip && active && g == 0) lv.dirty[colour][s] = 0;
+}
+
+template <typename CostT, typename MsgT>
+static cudaError_t sweep_t(const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc, int skip,
+                           unsigned long long *trace, cudaStream_t st) {
+    using Acc = typename AccOf<MsgT>::type;
+    const int groups = 256 / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t blocks = (nslot + groups - 1) / groups;
+    if (blocks == 0) return cudaSuccess;
+    sweep_kernel<CostT, MsgT><<<(unsigned)blocks, 256, 0, st>>>(lv, colour, D, Dp, Gp, (Acc)lambda,
+                                                                (Acc)lambda * (Acc)trunc, skip, trace);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc,
+                         int skip, unsigned long long *trace, cudaStream_t st) {
+    switch (msg_kind) {
+    case MSG_I32: return sweep_t<int32_t, int32_t>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
+    case MSG_U8: return sweep_t<int16_t, uint8_t>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
+    default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
+    }
+}
+
+// ------------------------------------------------------------------ coarse-to-fine start
+// Fine pixel (x, y) of `colour` copies the whole message record of its parent
+// (x >> 1, y >> 1) in 16-byte chunks.
+__global__ void upsample_kernel(LevelView coarse, LevelView fine, int colour, int rec_chunks) {
+    const int64_t n = (int64_t)fine.H * fine.Wh * rec_chunks;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int chunk = (int)(k % rec_chunks);
+        const int64_t s = k / rec_chunks;
+        const int y = (int)(s / fine.Wh);
+        const int x = 2 * (int)(s - (int64_t)y * fine.Wh) + ((y + colour) & 1);
+        if (x >= fine.W) continue;
+        const int px = x >> 1, py = y >> 1;
+        const uint4 *src = reinterpret_cast<const uint4 *>(coarse.msg[colour_of(px, py)]) +
+                           slot_of(px, py, coarse.Wh) * rec_chunks + chunk;
+        uint4 *dst = reinterpret_cast<uint4 *>(fine.msg[colour]) + s * rec_chunks + chunk;
+        *dst = *src;
+    }
+}
+
+static int msg_bytes(int msg_kind) { return msg_kind == MSG_I32 ? 4 : (msg_kind == MSG_U8 ? 1 : 2); }
+
+static unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
+
+cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int colour, int Dp,
+                            cudaStream_t st) {
+    const int rec_chunks = 4 * Dp * msg_bytes(msg_kind) / 16;
+    const int64_t n = (int64_t)fine.H * fine.Wh * rec_chunks;
+    upsample_kernel<<<grid_for(n), 256, 0, st>>>(coarse, fine, colour, rec_chunks);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ natural-layout import / export
+template <typename MsgT> __device__ inline MsgT to_msg(int v);
+template <> __device__ inline int32_t to_msg<int32_t>(int v) { return v; }
+template <> __device__ inline uint8_t to_msg<uint8_t>(int v) { return (uint8_t)min(max(v, 0), 255); }
+template <typename MsgT> __device__ inline MsgT to_msg_f(float v);
+template <> __device__ inline __half to_msg_f<__half>(float v) { return __float2half_rn(v); }
+
+template <typename MsgT, typename SrcT>
+__global__ void import_kernel(LevelView lv, int D, int Dp, const SrcT *src) {
+    const int64_t n = 4LL * lv.H * lv.W * Dp;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(k % Dp);
+        int64_t r = k / Dp;
+        const int x = (int)(r % lv.W);
+        r /= lv.W;
+        const int y = (int)(r % lv.H);
+        const int q = (int)(r / lv.H);
+        const SrcT v = d < D ? src[(((int64_t)q * lv.H + y) * lv.W + x) * D + d] : SrcT(0);
+        MsgT *dst = reinterpret_cast<MsgT *>(lv.msg[colour_of(x, y)]) + (slot_of(x, y, lv.Wh) * 4 + q) * Dp + d;
+        if constexpr (sizeof(SrcT) == 4 && std::is_same<SrcT, float>::value)
+            *dst = to_msg_f<MsgT>(v);
+        else
+            *dst = to_msg<MsgT>(v);
+    }
+}
+
+template <typename MsgT, typename DstT>
+__global__ void export_msgs_kernel(LevelView lv, int D, int Dp, DstT *out) {
+    const int64_t n = 4LL * lv.H * lv.W * D;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(k % D);
+        int64_t r = k / D;
+        const int x = (int)(r % lv.W);
+        r /= lv.W;
+        const int y = (int)(r % lv.H);
+        const int q = (int)(r / lv.H);
+        const bool has = q == DIR_UP ? y > 0 : q == DIR_DOWN ? y < lv.H - 1 : q == DIR_LEFT ? x > 0 : x < lv.W - 1;
+        const MsgT *src = reinterpret_cast<const MsgT *>(lv.msg[colour_of(x, y)]) + (slot_of(x, y, lv.Wh) * 4 + q) * Dp + d;
+        DstT v = DstT(0);
+        if (has) {
+            if constexpr (std::is_same<MsgT, __half>::value)
+                v = (DstT)__half2float(*src);
+            else
+                v = (DstT)*src;
+        }
+        out[k] = v;
+    }
+}
+
+template <typename CostT, typename DstT>
+__global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
+    const int64_t n = (int64_t)lv.H * lv.W * D;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(k % D);
+        const int64_t p = k / D;
+        const int x = (int)(p % lv.W), y = (int)(p / lv.W);
+        out[k] = (DstT) reinterpret_cast<const CostT *>(lv.cost[colour_of(x, y)])[slot_of(x, y, lv.Wh) * Dp + d];
+    }
+}
+
+cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st) {
+    const unsigned g = grid_for(4LL * lv.H * lv.W * Dp);
+    switch (msg_kind) {
+    case MSG_I32: import_kernel<int32_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (const int32_t *)src); break;
+    case MSG_U8: import_kernel<uint8_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (const int32_t *)src); break;
+    default: import_kernel<__half, float><<<g, 256, 0, st>>>(lv, D, Dp, (const float *)src); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st) {
+    const unsigned g = grid_for(4LL * lv.H * lv.W * D);
+    switch (msg_kind) {
+    case MSG_I32: export_msgs_kernel<int32_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (int32_t *)dst); break;
+    case MSG_U8: export_msgs_kernel<uint8_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (int32_t *)dst); break;
+    default: export_msgs_kernel<__half, float><<<g, 256, 0, st>>>(lv, D, Dp, (float *)dst); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_cost(int cost_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st) {
+    const unsigned g = grid_for((int64_t)lv.H * lv.W * D);
+    switch (cost_kind) {
+    case COST_I32: export_cost_kernel<int32_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (int32_t *)dst); break;
+    case COST_I16: export_cost_kernel<int16_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (int32_t *)dst); break;
+    default: export_cost_kernel<float, float><<<g, 256, 0, st>>>(lv, D, Dp, (float *)dst); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bps

@@ -1,0 +1,181 @@
+// bps_internal.cuh -- device-side layout and helpers shared by the stereo kernels.
+//
+// Layout in HBM (per scale l, W_l x H_l pixels, Dp = D rounded up to 16 labels):
+//   Pixels are split by checkerboard colour c = (x + y) & 1 ("red-black").  Pixel (x, y)
+//   lives in the colour-c arrays at slot s = y * Wh + (x >> 1), Wh = ceil(W_l / 2).  A
+//   half-sweep of colour c then reads one dense block (the colour-c records) and writes
+//   one dense block (the other colour's message slots): no half-used 32-byte sectors.
+//   cost[c]   [H_l][Wh][Dp]      data cost            (int32 | int16 | float)
+//   msg[c]    [H_l][Wh][4][Dp]   incoming messages    (int32 | uint8 | half)
+//             direction = the neighbour the message comes from: 0 up, 1 down, 2 left, 3 right
+//   dirty[c]  [H_l][Wh]          1 = some incoming message changed since the last update
+//   Labels d >= D inside the Dp padding are never winners: the sweep treats their belief
+//   as +infinity.
+//
+// A pixel's Dp labels are handled by a group of Gp (a power of two <= 32) consecutive lanes,
+// VEC = 16 labels per lane, so one lane moves 16 labels with 16-byte vector accesses.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bps {
+
+constexpr int VEC = 16;              // labels per lane
+constexpr int DIR_UP = 0, DIR_DOWN = 1, DIR_LEFT = 2, DIR_RIGHT = 3;
+constexpr int BIG_I = 1 << 29;       // "+infinity" of the integer forms
+
+struct LevelView {
+    int W, H, Wh;
+    void *cost[2];
+    void *msg[2];
+    uint8_t *dirty[2];
+};
+
+__host__ __device__ inline int colour_of(int x, int y) { return (x + y) & 1; }
+__host__ __device__ inline int64_t slot_of(int x, int y, int Wh) { return (int64_t)y * Wh + (x >> 1); }
+
+// ------------------------------------------------------------------ arithmetic per form
+template <typename T> struct Arith;
+template <> struct Arith<int> {
+    __device__ static inline int big() { return BIG_I; }
+    __device__ static inline int mn(int a, int b) { return min(a, b); }
+};
+template <> struct Arith<float> {
+    __device__ static inline float big() { return __int_as_float(0x7f800000); }
+    __device__ static inline float mn(float a, float b) { return fminf(a, b); }
+};
+
+// ------------------------------------------------------------------ 16-label vector I/O
+// load16: read labels [0, 16) starting at p (16-byte aligned) into A registers.
+__device__ inline void load16(const uint8_t *p, int (&v)[VEC]) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = (w[k >> 2] >> (8 * (k & 3))) & 0xff;
+}
+__device__ inline void load16(const int16_t *p, int (&v)[VEC]) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint4 r = __ldg(q + h);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[8 * h + k] = (int)(int16_t)(w[k >> 1] >> (16 * (k & 1)));
+    }
+}
+__device__ inline void load16(const int32_t *p, int (&v)[VEC]) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int4 r = __ldg(q + h);
+        v[4 * h + 0] = r.x; v[4 * h + 1] = r.y; v[4 * h + 2] = r.z; v[4 * h + 3] = r.w;
+    }
+}
+__device__ inline void load16(const float *p, float (&v)[VEC]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float4 r = __ldg(q + h);
+        v[4 * h + 0] = r.x; v[4 * h + 1] = r.y; v[4 * h + 2] = r.z; v[4 * h + 3] = r.w;
+    }
+}
+__device__ inline void load16(const __half *p, float (&v)[VEC]) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint4 r = __ldg(q + h);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __half2 hv = *reinterpret_cast<const __half2 *>(&w[k]);
+            const float2 f = __half22float2(hv);
+            v[8 * h + 2 * k] = f.x;
+            v[8 * h + 2 * k + 1] = f.y;
+        }
+    }
+}
+
+// Plain (coherent) loads, for message slots the same kernel may also write.
+__device__ inline void load16_rw(const uint8_t *p, int (&v)[VEC]) {
+    const uint4 r = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = (w[k >> 2] >> (8 * (k & 3))) & 0xff;
+}
+__device__ inline void load16_rw(const int32_t *p, int (&v)[VEC]) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int4 r = q[h];
+        v[4 * h + 0] = r.x; v[4 * h + 1] = r.y; v[4 * h + 2] = r.z; v[4 * h + 3] = r.w;
+    }
+}
+__device__ inline void load16_rw(const __half *p, float (&v)[VEC]) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint4 r = q[h];
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+            v[8 * h + 2 * k] = f.x;
+            v[8 * h + 2 * k + 1] = f.y;
+        }
+    }
+}
+
+// The value a message takes once stored (fp16 rounds; the integer forms are exact).
+template <typename MsgT> __device__ inline int stored_value(int v) { return v; }
+template <typename MsgT> __device__ inline float stored_value(float v) { return __half2float(__float2half_rn(v)); }
+
+__device__ inline void store16(uint8_t *p, const int (&v)[VEC]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        w[j] = (uint32_t)(v[4 * j] & 0xff) | ((uint32_t)(v[4 * j + 1] & 0xff) << 8) |
+               ((uint32_t)(v[4 * j + 2] & 0xff) << 16) | ((uint32_t)(v[4 * j + 3] & 0xff) << 24);
+    *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ inline void store16(int16_t *p, const int (&v)[VEC]) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w[j] = (uint32_t)(uint16_t)v[8 * h + 2 * j] | ((uint32_t)(uint16_t)v[8 * h + 2 * j + 1] << 16);
+        q[h] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+__device__ inline void store16(int32_t *p, const int (&v)[VEC]) {
+    int4 *q = reinterpret_cast<int4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) q[h] = make_int4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+}
+__device__ inline void store16(float *p, const float (&v)[VEC]) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) q[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+}
+__device__ inline void store16(__half *p, const float (&v)[VEC]) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __half2 hv = __floats2half2_rn(v[8 * h + 2 * j], v[8 * h + 2 * j + 1]);
+            w[j] = *reinterpret_cast<const uint32_t *>(&hv);
+        }
+        q[h] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Accumulator type of each storage form.
+template <typename MsgT> struct AccOf { using type = int; };
+template <> struct AccOf<__half> { using type = float; };
+
+}  // namespace bps

@@ -1,0 +1,43 @@
+// bps_launch.h -- host-side launchers of the stereo kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "bps_internal.cuh"
+
+namespace bps {
+
+// storage kinds
+enum CostKind { COST_I32 = 0, COST_I16 = 1, COST_F32 = 2 };
+enum MsgKind { MSG_I32 = 0, MSG_U8 = 1, MSG_F16 = 2 };
+
+size_t ncc_smem_bytes(int D, int window);
+// Allow the NCC kernel the shared memory of the largest window (call outside stream capture).
+cudaError_t ncc_prepare(int cost_kind, int D, int max_window);
+cudaError_t launch_ncc(int cost_kind, const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int D, int Dp,
+                       int window, int T, int Wh, void *c0, void *c1, float *ncc_out, cudaStream_t st);
+cudaError_t launch_pyramid(int cost_kind, const LevelView &fine, const LevelView &coarse, int Dp, cudaStream_t st);
+
+// One red-black half-sweep of `colour` at one scale.  trace: nullable device counter of
+// recomputed pixels.
+cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
+                         int trunc, int skip, unsigned long long *trace, cudaStream_t st);
+// Coarse-to-fine start: copy parent messages into the fine pixels of `colour`.
+cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int colour, int Dp,
+                            cudaStream_t st);
+// Natural-layout [4][H][W][D] messages (int32 or float) into / out of colour-split storage.
+cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st);
+cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);
+cudaError_t launch_export_cost(int cost_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);
+
+// Winner-take-all disparity at the finest scale.
+cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);
+// Energy: per-block partial sums into `partials` (nblocks entries of 8 bytes), then one
+// block sums them in a fixed order.
+int energy_blocks(int W, int H);
+cudaError_t launch_energy(int cost_kind, const LevelView &lv, int D, int Dp, const int32_t *disp, int lambda,
+                          int trunc, void *partials, int64_t *out_i64, double *out_f64, cudaStream_t st);
+
+}  // namespace bps

@@ -1,0 +1,155 @@
+// readout.cu -- winner-take-all disparity and the energy E(d) = E_D(d) + E_S(d)
+// (section "Approach Description").
+//
+// wta_kernel: a group of Gp lanes per pixel (natural raster order) forms the belief
+// cost + sum of the existing incoming messages and takes the argmin, the lowest label on
+// ties (per-lane scan, then a butterfly that prefers the smaller label on equal values).
+//
+// energy: each thread walks pixels with a grid stride and adds the data cost of its label
+// and lambda * min(|d_p - d_q|, trunc) for the right and lower neighbours (each grid edge
+// once).  Integer forms sum in int64 (exact); the float form sums in FP64.  Per-block
+// partials go to scratch, then one block adds them in a fixed order, so the FP64 result
+// is reproducible run to run.
+#include <algorithm>
+#include <type_traits>
+
+#include "bps_internal.cuh"
+#include "bps_launch.h"
+
+namespace bps {
+
+constexpr unsigned FULLM = 0xffffffffu;
+
+template <typename CostT, typename MsgT>
+__global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, int Gp, int32_t *disp) {
+    using Acc = typename AccOf<MsgT>::type;
+    using A = Arith<Acc>;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t p = (int64_t)blockIdx.x * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const bool valid = p < (int64_t)lv.W * lv.H;
+    const int x = valid ? (int)(p % lv.W) : 0, y = valid ? (int)(p / lv.W) : 0;
+    const int c = colour_of(x, y);
+    const int64_t s = slot_of(x, y, lv.Wh);
+    const int dbase = g * VEC;
+    Acc best = A::big();
+    int arg = 0x7fffffff;
+    if (valid && dbase < Dp) {
+        Acc b[VEC], t[VEC];
+        load16(reinterpret_cast<const CostT *>(lv.cost[c]) + s * Dp + dbase, b);
+        const MsgT *mp = reinterpret_cast<const MsgT *>(lv.msg[c]) + s * 4 * Dp + dbase;
+        const bool has[4] = {y > 0, y < lv.H - 1, x > 0, x < lv.W - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!has[q]) continue;
+            load16(mp + q * Dp, t);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) b[k] += t[k];
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if (dbase + k < D && b[k] < best) {
+                best = b[k];
+                arg = dbase + k;
+            }
+    }
+    for (int o = Gp >> 1; o > 0; o >>= 1) {
+        const Acc ob = __shfl_xor_sync(FULLM, best, o, Gp);
+        const int oa = __shfl_xor_sync(FULLM, arg, o, Gp);
+        if (ob < best || (ob == best && oa < arg)) {
+            best = ob;
+            arg = oa;
+        }
+    }
+    if (valid && g == 0) disp[p] = arg;
+}
+
+cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st) {
+    const int groups = 256 / Gp;
+    const int64_t blocks = ((int64_t)lv.W * lv.H + groups - 1) / groups;
+    switch (msg_kind) {
+    case MSG_I32: wta_kernel<int32_t, int32_t><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
+    case MSG_U8: wta_kernel<int16_t, uint8_t><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
+    default: wta_kernel<float, __half><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ energy
+constexpr int E_THREADS = 256, E_MAX_BLOCKS = 1024;
+
+int energy_blocks(int W, int H) {
+    const int64_t n = (int64_t)W * H;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + E_THREADS - 1) / E_THREADS, E_MAX_BLOCKS));
+}
+
+template <typename Sum>
+__device__ inline Sum block_sum(Sum v, Sum *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    Sum t = Sum(0);
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : Sum(0);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULLM, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+template <typename CostT>
+__global__ void __launch_bounds__(E_THREADS)
+energy_partial_kernel(LevelView lv, int D, int Dp, const int32_t *disp, int lambda, int trunc, void *partials) {
+    using Sum = typename std::conditional<std::is_same<CostT, float>::value, double, long long>::type;
+    __shared__ Sum sh[E_THREADS / 32];
+    Sum acc = Sum(0);
+    const int64_t n = (int64_t)lv.W * lv.H;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(p % lv.W), y = (int)(p / lv.W);
+        const int d = min(max(disp[p], 0), D - 1);
+        acc += (Sum) reinterpret_cast<const CostT *>(lv.cost[colour_of(x, y)])[slot_of(x, y, lv.Wh) * Dp + d];
+        if (x + 1 < lv.W) {
+            const int e = min(max(disp[p + 1], 0), D - 1);
+            acc += (Sum)((long long)lambda * min(abs(d - e), trunc));
+        }
+        if (y + 1 < lv.H) {
+            const int e = min(max(disp[p + lv.W], 0), D - 1);
+            acc += (Sum)((long long)lambda * min(abs(d - e), trunc));
+        }
+    }
+    const Sum t = block_sum(acc, sh);
+    if (threadIdx.x == 0) reinterpret_cast<Sum *>(partials)[blockIdx.x] = t;
+}
+
+template <typename Sum>
+__global__ void __launch_bounds__(E_THREADS)
+energy_final_kernel(const void *partials, int nblocks, int64_t *out_i64, double *out_f64) {
+    __shared__ Sum sh[E_THREADS / 32];
+    Sum acc = Sum(0);
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) acc += reinterpret_cast<const Sum *>(partials)[k];
+    const Sum t = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        if (out_i64) *out_i64 = (int64_t)t;
+        if (out_f64) *out_f64 = (double)t;
+    }
+}
+
+cudaError_t launch_energy(int cost_kind, const LevelView &lv, int D, int Dp, const int32_t *disp, int lambda,
+                          int trunc, void *partials, int64_t *out_i64, double *out_f64, cudaStream_t st) {
+    const int nb = energy_blocks(lv.W, lv.H);
+    switch (cost_kind) {
+    case COST_I32:
+        energy_partial_kernel<int32_t><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
+        energy_final_kernel<long long><<<1, E_THREADS, 0, st>>>(partials, nb, out_i64, out_f64);
+        break;
+    case COST_I16:
+        energy_partial_kernel<int16_t><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
+        energy_final_kernel<long long><<<1, E_THREADS, 0, st>>>(partials, nb, out_i64, out_f64);
+        break;
+    default:
+        energy_partial_kernel<float><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
+        energy_final_kernel<double><<<1, E_THREADS, 0, st>>>(partials, nb, nullptr, out_f64);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bps

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer forms (BPS_MSG_INT32 and the narrow-storage BPS_MSG_U8) must match the oracle
+bit for bit: data costs at every scale, finest messages, disparities, energy and the
+fast-converging trace.  The NCC volume must agree with the FP64 oracle to 1e-5.  The fp16
+form is judged against the FP64 oracle by its energy gap.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1709_06509_gb300 as bps
+from paper_1709_06509_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+INT_FORMS = [bps.BPS_MSG_INT32, bps.BPS_MSG_U8]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run_gpu(L, R, D, window, trunc_data, levels, iters, lam, trunc, msg_type, skip=True, init=None):
+    H, W = L.shape
+    with bps.Stereo(W, H, D, levels, msg_type, device=DEV) as st:
+        ncc = st.build_cost_volume(to_dev(L), to_dev(R), window, trunc_data, want_ncc=True)
+        costs = [st.export_cost(l).cpu().numpy() for l in range(levels)]
+        st.bp_solve(iters, lam, trunc, skip=skip, init_msgs=None if init is None else to_dev(init))
+        disp = st.wta_disparity()
+        ei, ef = st.energy(disp, lam, trunc)
+        msg = st.export_messages(0)
+        torch.cuda.synchronize()
+        return {"ncc": ncc.cpu().numpy(), "cost": costs, "msg": msg.cpu().numpy(), "disp": disp.cpu().numpy(),
+                "energy_i": int(ei.item()), "energy_f": float(ef.item()), "trace": st.get_trace()}
+
+
+def assert_int_parity(g, L, R, D, window, trunc_data, levels, iters, lam, trunc, skip=True, init=None):
+    ncc = oracle.ncc(L, R, D, window)
+    assert np.abs(g["ncc"] - ncc).max() < 1e-5
+    c0 = oracle.quantise(ncc, trunc_data)
+    for lvl, want in enumerate(oracle.pyramid(c0, levels)):
+        assert np.array_equal(g["cost"][lvl], want), f"cost level {lvl}"
+    msg, trace = oracle.bp(c0, levels, iters, lam, trunc, skip=skip, init_coarsest=init)
+    assert np.array_equal(g["msg"], msg), "finest messages"
+    disp = oracle.wta(c0, msg)
+    assert np.array_equal(g["disp"], disp), "disparity"
+    e = oracle.energy(c0, disp, lam, trunc)
+    assert g["energy_i"] == e and g["energy_f"] == float(e)
+    if skip:
+        assert np.array_equal(g["trace"], trace), "fast-converging trace"
+    else:
+        assert np.array_equal(g["trace"], trace)
+
+
+# (W, H, D, window, levels, iters, lambda, trunc): tile-spanning, ragged, degenerate shapes
+CASES = [
+    (96, 72, 16, 5, 4, 10, 10, 2),    # the small published-shape workload
+    (45, 19, 33, 7, 3, 4, 7, 3),      # D=33: three lanes of labels, one padded lane
+    (130, 9, 64, 9, 4, 3, 10, 2),     # several NCC tiles wide, ragged tail
+    (1, 7, 3, 3, 2, 3, 5, 1),         # W = 1
+    (7, 1, 5, 1, 3, 4, 4, 5),         # H = 1, 1x1 window, trunc > D
+    (1, 1, 4, 3, 4, 2, 10, 2),        # a single pixel
+    (33, 13, 17, 31, 2, 2, 3, 4),     # the largest window
+    (20, 15, 1, 3, 3, 3, 10, 2),      # one label
+    (24, 16, 2, 5, 1, 5, 10, 2),      # two labels, flat BP
+    (40, 30, 12, 5, 3, 0, 10, 2),     # zero iterations
+    (40, 30, 12, 5, 3, 3, 0, 2),      # lambda = 0
+    (40, 30, 12, 5, 3, 3, 10, 0),     # trunc = 0
+    (24, 6, 256, 3, 2, 2, 10, 2),     # D = 256: 16 lanes per pixel
+    (12, 5, 512, 3, 1, 1, 3, 7),      # D = 512: a full warp per pixel
+]
+
+
+@pytest.mark.parametrize("msg_type", INT_FORMS)
+@pytest.mark.parametrize("skip", [True, False])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
+def test_int_parity(case, skip, msg_type):
+    W, H, D, window, levels, iters, lam, trunc = case
+    if msg_type == bps.BPS_MSG_U8 and lam * trunc > 255:
+        pytest.skip("outside the u8 range")
+    pair = synth.make_pair(100 + W + H + D, W, H, D, 3, 2.0)
+    g = run_gpu(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, msg_type, skip)
+    assert_int_parity(g, pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, skip)
+
+
+def test_pitched_images_and_random_texture():
+    rng = np.random.default_rng(3)
+    H, W, D = 23, 37, 9
+    big_l = rng.integers(0, 256, (H, W + 11)).astype(np.uint8)
+    big_r = rng.integers(0, 256, (H, W + 11)).astype(np.uint8)
+    L, R = big_l[:, :W], big_r[:, :W]
+    with bps.Stereo(W, H, D, 2, bps.BPS_MSG_U8, device=DEV) as st:
+        tl, tr = to_dev(big_l), to_dev(big_r)
+        bps.bps_build_cost_volume(st.ctx, tl, tr, W + 11, 5, 20)
+        got = st.export_cost(0).cpu().numpy()
+    assert np.array_equal(got, oracle.quantise(oracle.ncc(L, R, D, 5), 20))
+
+
+def test_quantiser_rounding_boundaries():
+    # windows whose NCC sits on a rounding boundary of the quantiser exercise the FP64 fallback
+    H, W, D = 16, 40, 8
+    base = synth.texture(21, 1, W, H)
+    L = base
+    R = np.clip(base.astype(int) * 3 // 4 + (np.arange(W) % 3)[None, :] * 9, 0, 255).astype(np.uint8)
+    for T in (1, 7, 20, 64, 255):
+        with bps.Stereo(W, H, D, 1, bps.BPS_MSG_INT32, device=DEV) as st:
+            st.build_cost_volume(to_dev(L), to_dev(R), 3, T)
+            got = st.export_cost(0).cpu().numpy()
+        assert np.array_equal(got, oracle.quantise(oracle.ncc(L, R, D, 3), T)), T
+
+
+def test_u8_form_equals_int32_form():
+    pair = synth.make_pair(7, 70, 50, 24, 4, 3.0)
+    a = run_gpu(pair.left, pair.right, 24, 7, 20, 4, 6, 10, 2, bps.BPS_MSG_INT32)
+    b = run_gpu(pair.left, pair.right, 24, 7, 20, 4, 6, 10, 2, bps.BPS_MSG_U8)
+    for k in ("msg", "disp", "energy_i", "trace"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("msg_type", INT_FORMS)
+def test_warm_start_matches_oracle(msg_type):
+    pair = synth.make_pair(9, 50, 40, 10, 3, 2.0)
+    dims = oracle.level_dims(50, 40, 3)
+    wc, hc = dims[-1]
+    init = np.random.default_rng(1).integers(0, 21, (4, hc, wc, 10)).astype(np.int32)
+    g = run_gpu(pair.left, pair.right, 10, 5, 20, 3, 4, 10, 2, msg_type, True, init)
+    assert_int_parity(g, pair.left, pair.right, 10, 5, 20, 3, 4, 10, 2, True, init)
+
+
+def test_fewer_levels_than_the_context():
+    pair = synth.make_pair(12, 60, 44, 16, 3, 2.0)
+    with bps.Stereo(60, 44, 16, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 5, 20)
+        st.bp_solve(5, 10, 2, levels=2)
+        msg = st.export_messages(0).cpu().numpy()
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, 16, 5), 20)
+    assert np.array_equal(msg, oracle.bp(c0, 2, 5, 10, 2)[0])
+
+
+def test_graph_replay_and_host_entry():
+    pair = synth.make_pair(5, 96, 72, 16, 3, 2.0)
+    L, R = to_dev(pair.left), to_dev(pair.right)
+    with bps.Stereo(96, 72, 16, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        plain = st.stereo(L, R, 5, 20, 10, 10, 2, graph=False).clone()
+        g1 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()
+        g2 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()   # replay
+        g3 = st.stereo(L, R, 5, 20, 6, 10, 2, graph=True).clone()    # new arguments: re-capture
+        torch.cuda.synchronize()
+        hl = torch.from_numpy(pair.left).pin_memory()
+        hr = torch.from_numpy(pair.right).pin_memory()
+        hd, he = st.stereo_host(hl, hr, 5, 20, 10, 10, 2)
+    ref = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 4, 10, 10, 2)
+    assert np.array_equal(plain.cpu().numpy(), ref["disp"])
+    assert np.array_equal(g1.cpu().numpy(), ref["disp"]) and np.array_equal(g2.cpu().numpy(), ref["disp"])
+    ref6 = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 4, 6, 10, 2)
+    assert np.array_equal(g3.cpu().numpy(), ref6["disp"])
+    assert np.array_equal(hd.numpy(), ref["disp"]) and he == ref["energy"]
+
+
+def test_argument_errors_on_a_live_context():
+    with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_U8, device=DEV) as st:
+        with pytest.raises(bps.BPSError) as e:
+            st.bp_solve(3, 10, 2)  # no cost volume yet
+        assert e.value.status == bps.BPS_ERR_STATE
+        L = torch.zeros((8, 16), dtype=torch.uint8, device=DEV)
+        with pytest.raises(bps.BPSError) as e:
+            st.build_cost_volume(L, L, 4, 20)  # even window
+        assert e.value.status == bps.BPS_ERR_ARG
+        with pytest.raises(bps.BPSError) as e:
+            st.build_cost_volume(L, L, 3, 20000)  # coarse costs overflow int16 storage
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+        st.build_cost_volume(L, L, 3, 20)
+        with pytest.raises(bps.BPSError) as e:
+            st.bp_solve(3, 100, 3)  # lambda * trunc > 255 in the u8 form
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+        with pytest.raises(bps.BPSError) as e:
+            st.bp_solve(3, 10, 2, levels=3)
+        assert e.value.status == bps.BPS_ERR_ARG
+        with pytest.raises(bps.BPSError) as e:
+            st.bp_solve(bps.BPS_MAX_ITERS + 1, 10, 2)
+        assert e.value.status == bps.BPS_ERR_ARG
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+@pytest.fixture(scope="module")
+def teddy():
+    pair, window = synth.workload_pair("teddy_450x375_d64")
+    return pair, window
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["tsukuba_384x288_d16", "teddy_450x375_d64"])
+def test_full_size_bit_exact(name):
+    """The benchmark's workloads, in the benchmark's launch configuration (u8 form, skip on,
+    CUDA graph through bps_stereo), bit-exact against the oracle."""
+    pair, window = synth.workload_pair(name)
+    H, W = pair.left.shape
+    D = pair.D
+    ref = oracle.stereo_int(pair.left, pair.right, D, window, 20, 4, 10, 10, 2)
+    with bps.Stereo(W, H, D, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        L, R = to_dev(pair.left), to_dev(pair.right)
+        disp = st.stereo(L, R, window, 20, 10, 10, 2, graph=True)
+        disp = st.stereo(L, R, window, 20, 10, 10, 2, graph=True)  # a replay
+        ei, _ = st.energy(disp, 10, 2)
+        msg = st.export_messages(0)
+        torch.cuda.synchronize()
+        assert np.array_equal(msg.cpu().numpy(), ref["msg"])
+        assert np.array_equal(disp.cpu().numpy(), ref["disp"])
+        assert int(ei.item()) == ref["energy"]
+        assert np.array_equal(st.get_trace(), ref["trace"])
+
+
+@pytest.mark.slow
+def test_hd_256_properties():
+    """1920x1080, D=256, 9x9 window: too large for the oracle, so sampled NCC entries are
+    checked one by one and the BP result through properties that hold at any size."""
+    pair, window = synth.workload_pair("hd_1920x1080_d256")
+    H, W = pair.left.shape
+    D, r, lam, T = 256, window // 2, 10, 2
+    with bps.Stereo(W, H, D, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        L, R = to_dev(pair.left), to_dev(pair.right)
+        st.build_cost_volume(L, R, window, 20)
+        cost = st.export_cost(0)
+        rng = np.random.default_rng(0)
+        ys = rng.integers(r, H - r, 40)
+        xs = rng.integers(D - 1 + r, W - r, 40)
+        for y, x in zip(ys, xs):
+            # a crop with no clamped taps gives the same window sums as the full image
+            cl = pair.left[y - r: y + r + 1, x - D + 1 - r: x + r + 1]
+            cr = pair.right[y - r: y + r + 1, x - D + 1 - r: x + r + 1]
+            want = oracle.quantise(oracle.ncc(cl, cr, D, window), 20)[r, D - 1 + r]
+            assert np.array_equal(cost[y, x].cpu().numpy(), want)
+        st.bp_solve(10, lam, T, skip=True)
+        d_skip = st.wta_disparity().clone()
+        msg_skip = st.export_messages(0)
+        trace = st.get_trace()
+        st.bp_solve(10, lam, T, skip=False)
+        d_full = st.wta_disparity()
+        msg_full = st.export_messages(0)
+        assert torch.equal(msg_skip, msg_full) and torch.equal(d_skip, d_full)  # the skip is exact
+        interior = msg_full[:, 1:-1, 1:-1]
+        assert int(interior.min()) == 0 and int(msg_full.max()) <= lam * T
+        assert int(interior.amin(dim=3).max()) == 0  # every message is min-normalised
+        ei, _ = st.energy(d_full, lam, T)
+        c = cost.to(torch.int64)
+        d = d_full.to(torch.int64)
+        e = c.gather(2, d[..., None]).sum()
+        e += lam * ((d[:, 1:] - d[:, :-1]).abs().clamp(max=T).sum() + (d[1:] - d[:-1]).abs().clamp(max=T).sum())
+        assert int(ei.item()) == int(e.item())
+        n0 = W * H
+        assert trace[-20:].sum() < 10 * n0  # the skip removes work at the finest scale
+        bad = ((d_full.cpu().numpy() - pair.disparity).__abs__() > 1) & ~pair.occluded
+        assert bad.mean() < 0.1
+
+
+# ------------------------------------------------------------------ fp16 messages vs the FP64 oracle
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["tsukuba_384x288_d16", "teddy_450x375_d64"])
+def test_fp16_energy_gap(name):
+    pair, window = synth.workload_pair(name)
+    H, W = pair.left.shape
+    D = pair.D
+    ref = oracle.stereo_f64(pair.left, pair.right, D, window, 20, 4, 10, 10.0, 2)
+    with bps.Stereo(W, H, D, 4, bps.BPS_MSG_FP16, device=DEV) as st:
+        ncc = st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20, want_ncc=True)
+        st.bp_solve(10, 10, 2, skip=True)
+        disp = st.wta_disparity()
+        _, ef = st.energy(disp, 10, 2)
+        d = disp.cpu().numpy()
+        cf = st.export_cost(0).cpu().numpy()
+    assert np.abs(cf - ref["cost"]).max() < 1e-4
+    e_gpu = oracle.energy(ref["cost"], d, 10.0, 2)  # the GPU labels, scored by the FP64 oracle
+    gap = (e_gpu - ref["energy"]) / ref["energy"]
+    assert gap <= 0.005, gap
+    assert abs(float(ef.item()) - e_gpu) / e_gpu < 1e-5  # the GPU's own FP64 energy reduction
+    assert (d != ref["disp"]).mean() < 0.02
