@@ -136,6 +136,9 @@ sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<Msg
 #pragma unroll
         for (int k = 0; k < VEC; ++k) h[k] = (dbase + k < D) ? b[k] - in[q][k] : A::big();
         min_convolve(h, lam, lamT, g, Gp, m);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if (dbase + k >= D) m[k] = Acc(0);  // the label padding always holds 0
         const bool send = active && has[q];
         const int64_t qs = send ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
         MsgT *dst = out + (qs * 4 + opp[q]) * Dp + dbase;

@@ -133,6 +133,9 @@ def test_warm_start_matches_oracle(msg_type):
     dims = oracle.level_dims(50, 40, 3)
     wc, hc = dims[-1]
     init = np.random.default_rng(1).integers(0, 21, (4, hc, wc, 10)).astype(np.int32)
+    # slots of neighbours outside the image hold 0 (the layout both sides document)
+    init[0, 0] = init[1, -1] = 0
+    init[2, :, 0] = init[3, :, -1] = 0
     g = run_gpu(pair.left, pair.right, 10, 5, 20, 3, 4, 10, 2, msg_type, True, init)
     assert_int_parity(g, pair.left, pair.right, 10, 5, 20, 3, 4, 10, 2, True, init)
 
