@@ -24,7 +24,7 @@
  *   BPS_MSG_U8     the same integer method with narrow storage: int16 costs and uint8
  *                  messages.  Exact (bit-identical to BPS_MSG_INT32) because a normalised
  *                  message lies in [0, lambda*trunc]; requires lambda*trunc <= 255 and
- *                  trunc_data * 4^(levels-1) <= 32767, otherwise BPS_ERR_UNSUPPORTED.
+ *                  trunc_data * 4^(levels-1) <= 27000, otherwise BPS_ERR_UNSUPPORTED.
  *   BPS_MSG_FP16   unquantised float data costs clamp(trunc_data*(1-ncc), 0, trunc_data)
  *                  in fp32, fp16 messages, fp32 arithmetic, min-normalised per pixel.
  *                  Approximate; compared with the FP64 oracle by energy gap.
@@ -108,7 +108,7 @@ int bps_destroy(bps_ctx *ctx);
  * The coarser scales' costs are then built as the sum of each coarse pixel's existing 2x2
  * children.  d_ncc_out: nullable device float [H][W][D] receiving ncc (abs. error < 1e-5).
  * Errors: BPS_ERR_ARG (NULL images, pitch < W, window even or > BPS_MAX_WINDOW,
- * trunc_data < 0), BPS_ERR_UNSUPPORTED (BPS_MSG_U8 with trunc_data*4^(levels-1) > 32767).
+ * trunc_data < 0), BPS_ERR_UNSUPPORTED (BPS_MSG_U8 with trunc_data*4^(levels-1) > 27000).
  */
 int bps_build_cost_volume(bps_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch,
                           int window, int trunc_data, float *d_ncc_out, void *stream);

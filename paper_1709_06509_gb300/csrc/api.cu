@@ -208,7 +208,7 @@ static int check_cost_args(bps_ctx *c, const uint8_t *L, const uint8_t *R, int p
     if (c->msg_type == BPS_MSG_U8) {
         int64_t top = trunc_data;
         for (int l = 1; l < c->levels; ++l) top *= 4;
-        if (top > 32767) return BPS_ERR_UNSUPPORTED;
+        if (top > 27000) return BPS_ERR_UNSUPPORTED;  // keeps every belief below 2^15 (packed 16-bit sweep)
     }
     if (c->msg_type == BPS_MSG_INT32) {
         int64_t top = trunc_data;

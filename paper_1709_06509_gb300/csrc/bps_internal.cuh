@@ -174,6 +174,23 @@ __device__ inline void store16(__half *p, const float (&v)[VEC]) {
     }
 }
 
+// Storage order of labels.  The u8 form (int16 costs, uint8 messages) interleaves each
+// aligned group of 16 labels: position 2k holds label k and position 2k+1 holds label k+8
+// (k < 8), so one 32-bit word of int16 costs, or one byte pair of messages, carries labels
+// (k, k+8).  The other forms keep the natural order.
+template <typename T> __host__ __device__ inline int label_pos(int d) { return d; }
+template <> __host__ __device__ inline int label_pos<int16_t>(int d) {
+    const int k = d & 15;
+    return (d & ~15) | (k < 8 ? 2 * k : 2 * (k - 8) + 1);
+}
+template <> __host__ __device__ inline int label_pos<uint8_t>(int d) { return label_pos<int16_t>(d); }
+template <typename T> __host__ __device__ inline int pos_label(int p) { return p; }
+template <> __host__ __device__ inline int pos_label<int16_t>(int p) {
+    const int k = p & 15;
+    return (p & ~15) | ((k & 1) ? 8 + (k >> 1) : (k >> 1));
+}
+template <> __host__ __device__ inline int pos_label<uint8_t>(int p) { return pos_label<int16_t>(p); }
+
 // Accumulator type of each storage form.
 template <typename MsgT> struct AccOf { using type = int; };
 template <> struct AccOf<__half> { using type = float; };

@@ -132,7 +132,7 @@ ncc_cost_kernel(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R, in
             const int x = x0 + tx, y = y0 + ty, d = d0 + dd;
             if (x >= W || y >= H) continue;
             const int c = colour_of(x, y);
-            CostT *dst = (c ? cost1 : cost0) + slot_of(x, y, Wh) * Dp + d;
+            CostT *dst = (c ? cost1 : cost0) + slot_of(x, y, Wh) * Dp + label_pos<CostT>(d);
             if (d >= D) {
                 *dst = CostT(0);
                 continue;

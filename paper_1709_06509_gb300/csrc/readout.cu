@@ -46,11 +46,13 @@ __global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, i
             for (int k = 0; k < VEC; ++k) b[k] += t[k];
         }
 #pragma unroll
-        for (int k = 0; k < VEC; ++k)
-            if (dbase + k < D && b[k] < best) {
+        for (int k = 0; k < VEC; ++k) {
+            const int lab = dbase + pos_label<MsgT>(k);
+            if (lab < D && (b[k] < best || (b[k] == best && lab < arg))) {
                 best = b[k];
-                arg = dbase + k;
+                arg = lab;
             }
+        }
     }
     for (int o = Gp >> 1; o > 0; o >>= 1) {
         const Acc ob = __shfl_xor_sync(FULLM, best, o, Gp);
@@ -105,7 +107,8 @@ energy_partial_kernel(LevelView lv, int D, int Dp, const int32_t *disp, int lamb
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(p % lv.W), y = (int)(p / lv.W);
         const int d = min(max(disp[p], 0), D - 1);
-        acc += (Sum) reinterpret_cast<const CostT *>(lv.cost[colour_of(x, y)])[slot_of(x, y, lv.Wh) * Dp + d];
+        acc += (Sum) reinterpret_cast<const CostT *>(lv.cost[colour_of(x, y)])[slot_of(x, y, lv.Wh) * Dp +
+                                                                               label_pos<CostT>(d)];
         if (x + 1 < lv.W) {
             const int e = min(max(disp[p + 1], 0), D - 1);
             acc += (Sum)((long long)lambda * min(abs(d - e), trunc));
