@@ -159,7 +159,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("bp.cu", "bps_internal.cuh"):
+    for f in ("persist.cu", "sweep_body.cuh", "bps_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1709_06509_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -181,6 +181,30 @@ def ncu_traffic(profile_name: str):
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def persistent_bytes(st, trace) -> float:
+    """Algorithmic DRAM bytes of one persistent BP launch of the u8 form.
+
+    Per recomputed pixel of a half-sweep: its int16 cost and 4 incoming uint8 messages read,
+    4 old outgoing messages read (change test of the skip) and 4 messages written, Dp labels
+    each; plus the 1-byte skip flag of every slot read per half-sweep; per scale below the
+    coarsest the copy of the even pixels' parent records (read + write); the skip flags set
+    per scale; and the read-out (cost + 4 messages read, one int32 written per pixel)."""
+    from paper_1709_06509_gb300 import level_dims
+
+    Dp = (st.D + 15) // 16 * 16
+    dims = level_dims(st.W, st.H, st.levels)[::-1]  # coarsest first, like the trace
+    per = ITERS * 2
+    total = 0.0
+    for k, (w, h) in enumerate(dims):
+        slots = h * ((w + 1) // 2)
+        total += float(trace[k * per:(k + 1) * per].sum()) * Dp * (2 + 12 * 1)
+        total += per * slots + 2 * slots
+        if k > 0:
+            total += 2 * slots * 4 * Dp
+    total += st.W * st.H * (Dp * (2 + 4) + 4)
+    return total
 
 
 def peaks():
@@ -264,25 +288,21 @@ def main():
     units = work_units(pairs) * world
     value = units * args.steps / (total_ms / 1e3) / 1e6
 
-    # dominant kernel (the red-black sweep): per-launch CUDA events around every finest-scale
-    # sweep launch, on the launching stream, over a run of the same steps with the same flush
+    # dominant kernel: the persistent BP kernel (every scale, iteration and colour, then the
+    # read-out), timed with CUDA events around its launch on the launching stream
     prof_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
     for _ in range(max(3, min(args.steps, 20))):
         for (st, window), (L, R), out in zip(ctxs, inputs, outs):
             flush.fill_(1)
             st.build_cost_volume(L, R, window, TRUNC_DATA)
             st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
-            n, ms, px = st.read_profile()
-            Dp = (st.D + 15) // 16 * 16
-            Wh = (st.W + 1) // 2
-            # algorithmic bytes: per recomputed pixel, its int16 cost, 4 incoming and 4 old outgoing
-            # u8 messages read and 4 u8 messages written; plus the 1-byte skip flag of every slot
-            prof_bytes += px * Dp * (2 + 12 * 1) + n * st.H * Wh
+            n, ms, _px = st.read_profile()
+            prof_bytes += persistent_bytes(st, st.get_trace())
             prof_ms += ms
             prof_launches += n
     hbm, peak_kind = peaks()
     achieved = prof_bytes / (prof_ms / 1e3) / 1e9
-    traffic = ncu_traffic("sweep_kernel_teddy_450x375_d64.txt")
+    traffic = ncu_traffic("bp_persistent_u8_teddy_450x375_d64.txt")
 
     # end to end through the public API with host buffers (pinned), H2D and D2H inside
     host_in = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p, _ in pairs]
@@ -303,7 +323,9 @@ def main():
     h2d = sum(2 * p.left.size for p, _ in pairs)
     d2h = sum(4 * p.left.size + 8 for p, _ in pairs)
 
-    launches_per_pair = 1 + (LEVELS - 1) + (LEVELS - 1) + LEVELS * ITERS * 2 + 1
+    # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the persistent
+    # BP kernel (all scales, iterations and the read-out)
+    launches_per_pair = 1 + max(0, LEVELS - 2) + 1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -315,7 +337,7 @@ def main():
                        "cost_storage": "int16", "cuda_graph": True, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_kernel<int16,uint8>",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "bp_persistent_kernel<u8>",
                          "peak_kind": peak_kind, "launches_timed": prof_launches},
             "e2e": {"value": units * args.steps / e2e_s / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

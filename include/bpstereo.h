@@ -60,8 +60,13 @@ typedef struct bps_ctx bps_ctx;
 #define BPS_FLAG_WARM_START 2 /* start the coarsest scale from d_init_msgs instead of zeros */
 #define BPS_FLAG_GRAPH 4      /* bps_stereo*: record the launch sequence once as a CUDA graph
                                  and replay it while the arguments stay the same */
-#define BPS_FLAG_PROFILE 8    /* bps_bp_solve: time every finest-scale sweep launch with CUDA
-                                 events (read with bps_read_profile); not with BPS_FLAG_GRAPH */
+#define BPS_FLAG_PROFILE 8    /* bps_bp_solve: time the BP launches with CUDA events (read with
+                                 bps_read_profile / bps_read_launch_times); not with BPS_FLAG_GRAPH */
+#define BPS_FLAG_PER_SWEEP 16 /* one kernel launch per red-black half-sweep instead of the single
+                                 persistent launch (same results; used for per-sweep tracing) */
+#define BPS_FLAG_TEST_TIMEOUT 32 /* test hook: the persistent kernel's grid barrier waits for one
+                                    block more than it has, gives up after 2 ms and the solve
+                                    reports BPS_ERR_TIMEOUT through bps_get_error */
 
 /* Limits of this build. */
 #define BPS_MAX_LEVELS 8
@@ -174,6 +179,13 @@ int bps_stereo_host(bps_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                     int32_t *h_disp, int64_t *h_energy_i64, double *h_energy_f64, void *stream);
 
 /*
+ * Status of the last persistent solve on this context: BPS_OK, or BPS_ERR_TIMEOUT when a
+ * grid barrier of the persistent kernel gave up waiting (its results are then incomplete).
+ * Synchronous (reads one device word).
+ */
+int bps_get_error(bps_ctx *ctx);
+
+/*
  * Per half-sweep count of recomputed pixels of the last bps_bp_solve (coarsest scale
  * first, two entries per iteration): the fast-converging trace.  Synchronous.  Returns
  * the number of entries written (<= cap) or a negative status.
@@ -196,6 +208,13 @@ int bps_export_cost(bps_ctx *ctx, int level, void *d_out, void *stream);
  * on the launching stream), and the number of pixels they recomputed.  Synchronous.
  */
 int bps_read_profile(bps_ctx *ctx, int *h_launches, double *h_total_ms, int64_t *h_pixels);
+
+/*
+ * Per-launch durations (ms, CUDA events on the launching stream) of every sweep launch of
+ * the last bps_bp_solve run with BPS_FLAG_PROFILE, in launch order (coarsest scale first,
+ * two per iteration).  Synchronous.  Returns the number written (<= cap) or a status.
+ */
+int bps_read_launch_times(bps_ctx *ctx, double *h_ms, int cap);
 
 #ifdef __cplusplus
 }

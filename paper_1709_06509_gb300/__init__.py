@@ -37,6 +37,8 @@ BPS_FLAG_FAST_SKIP = 1
 BPS_FLAG_WARM_START = 2
 BPS_FLAG_GRAPH = 4
 BPS_FLAG_PROFILE = 8
+BPS_FLAG_PER_SWEEP = 16
+BPS_FLAG_TEST_TIMEOUT = 32
 
 BPS_MAX_LEVELS = 8
 BPS_MAX_D = 512
@@ -68,6 +70,8 @@ _SIGS = {
     "bps_export_messages": (_I, [_P, _I, _P, _P]),
     "bps_export_cost": (_I, [_P, _I, _P, _P]),
     "bps_read_profile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "bps_read_launch_times": (_I, [_P, _P, _I]),
+    "bps_get_error": (_I, [_P]),
 }
 
 
@@ -179,6 +183,18 @@ def bps_read_profile(ctx):
     return n.value, ms.value, px.value
 
 
+def bps_get_error(ctx) -> int:
+    """BPS_OK or BPS_ERR_TIMEOUT for the last persistent solve (returned, not raised)."""
+    rc = lib().bps_get_error(ctx)
+    if rc not in (BPS_OK, BPS_ERR_TIMEOUT):
+        raise BPSError(rc, "bps_get_error")
+    return rc
+
+
+def bps_read_launch_times(ctx, h_ms, cap: int) -> int:
+    return _check(lib().bps_read_launch_times(ctx, _ptr(h_ms), cap), "bps_read_launch_times")
+
+
 # ------------------------------------------------------------------ convenience wrapper
 
 def level_dims(W: int, H: int, levels: int) -> list[tuple[int, int]]:
@@ -235,9 +251,11 @@ class Stereo:
         return ncc
 
     def bp_solve(self, iters: int, lam: int, trunc: int, levels: int | None = None, skip: bool = True,
-                 init_msgs=None, profile: bool = False, stream=None):
+                 init_msgs=None, profile: bool = False, per_sweep: bool = False, test_timeout: bool = False,
+                 stream=None):
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_WARM_START if init_msgs is not None else 0)
-        flags |= BPS_FLAG_PROFILE if profile else 0
+        flags |= (BPS_FLAG_PROFILE if profile else 0) | (BPS_FLAG_PER_SWEEP if per_sweep else 0)
+        flags |= BPS_FLAG_TEST_TIMEOUT if test_timeout else 0
         bps_bp_solve(self.ctx, levels or self.levels, iters, lam, trunc, flags, init_msgs, stream)
 
     def wta_disparity(self, out=None, stream=None):
@@ -256,11 +274,12 @@ class Stereo:
         return ei, ef
 
     def stereo(self, left, right, window, trunc_data, iters, lam, trunc, skip=True, graph=False, out=None,
-               stream=None):
+               per_sweep=False, stream=None):
         import torch
 
         out = out if out is not None else torch.empty((self.H, self.W), dtype=torch.int32, device=self.device)
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
+        flags |= BPS_FLAG_PER_SWEEP if per_sweep else 0
         bps_stereo(self.ctx, left, right, left.stride(0), window, trunc_data, iters, lam, trunc, flags, out, stream)
         return out
 
@@ -304,3 +323,13 @@ class Stereo:
 
     def read_profile(self):
         return bps_read_profile(self.ctx)
+
+    def get_error(self) -> int:
+        return bps_get_error(self.ctx)
+
+    def read_launch_times(self):
+        import numpy as np
+
+        buf = np.zeros(self.levels * BPS_MAX_ITERS * 2, dtype=np.float64)
+        n = bps_read_launch_times(self.ctx, buf.ctypes.data, buf.size)
+        return buf[:n]

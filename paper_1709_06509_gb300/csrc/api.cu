@@ -20,7 +20,7 @@ struct Plan {
     int levels = 0;
     int Ws[BPS_MAX_LEVELS], Hs[BPS_MAX_LEVELS], Whs[BPS_MAX_LEVELS];
     size_t cost[BPS_MAX_LEVELS][2], msg[BPS_MAX_LEVELS][2], dirty[BPS_MAX_LEVELS][2];
-    size_t trace, partials, img[2], disp, energy, total;
+    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, total;
 };
 
 int cost_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? COST_I32 : msg_type == BPS_MSG_U8 ? COST_I16 : COST_F32; }
@@ -66,6 +66,12 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
     off += up((size_t)W * H * 4);
     p.energy = off;
     off += up(16);
+    p.desc = off;
+    off += up(sizeof(PairDesc));
+    p.prefix = off;
+    off += up(sizeof(int) * 2 * (levels + 1));
+    p.barrier = off;
+    off += up(16);
     p.total = off;
     return true;
 }
@@ -97,9 +103,44 @@ struct bps_ctx {
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
     std::vector<cudaEvent_t> ev;
-    int prof_launches = 0;
+    PairDesc *d_desc = nullptr;      // this context as a batch of one (device)
+    int *d_prefix = nullptr;         // [levels][2] sweep block prefix, then [2] read-out prefix
+    unsigned *d_barrier = nullptr;   // {arrival count, error word} of the persistent kernel
+    int grid = 0;                    // co-resident CTAs of the persistent kernel
+    int prof_launches = 0;  // finest-scale sweep launches of the last profiled solve
+    int prof_all = 0;       // all sweep launches of the last profiled solve
     int prof_first_trace = 0;
+    int prof_trace_n = 0;   // trace entries covered by the profiled launches
 };
+
+namespace {
+
+int sweep_blocks(const bps_ctx *c, int l) {
+    const int groups = 256 / c->Gp;
+    return (int)(((int64_t)c->plan.Hs[l] * c->plan.Whs[l] + groups - 1) / groups);
+}
+
+int wta_blocks(const bps_ctx *c) {
+    const int groups = 256 / c->Gp;
+    return (int)(((int64_t)c->W * c->H + groups - 1) / groups);
+}
+
+PairDesc make_desc(const bps_ctx *c) {
+    PairDesc d;
+    std::memset(&d, 0, sizeof(d));
+    for (int l = 0; l < c->levels; ++l) d.lv[l] = c->lv[l];
+    d.D = c->D;
+    d.Dp = c->Dp;
+    d.Gp = c->Gp;
+    d.trace = c->trace;
+    d.disp = nullptr;
+    return d;
+}
+
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 4000000000ull;  // 4 s: far above any phase
+constexpr unsigned long long TEST_TIMEOUT_NS = 2000000ull;        // 2 ms, for BPS_FLAG_TEST_TIMEOUT
+
+}  // namespace
 
 #define CK(x)                                     \
     do {                                          \
@@ -172,11 +213,27 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->disp = reinterpret_cast<int32_t *>(c->ws + p.disp);
     c->e_i64 = reinterpret_cast<int64_t *>(c->ws + p.energy);
     c->e_f64 = reinterpret_cast<double *>(c->ws + p.energy + 8);
+    c->d_desc = reinterpret_cast<PairDesc *>(c->ws + p.desc);
+    c->d_prefix = reinterpret_cast<int *>(c->ws + p.prefix);
+    c->d_barrier = reinterpret_cast<unsigned *>(c->ws + p.barrier);
+    PairDesc hd = make_desc(c);
+    std::vector<int> prefix(2 * (levels + 1));
+    for (int l = 0; l < levels; ++l) {
+        prefix[2 * l] = 0;
+        prefix[2 * l + 1] = sweep_blocks(c, l);
+    }
+    prefix[2 * levels] = 0;
+    prefix[2 * levels + 1] = wta_blocks(c);
     bool ok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && persistent_grid(c->msg_kind, &c->grid) == cudaSuccess;
     // the NCC kernel's shared memory depends on D and the window; allow the largest window now so
     // that no attribute call happens while a launch sequence is being captured
     ok = ok && ncc_prepare(c->cost_kind, D, BPS_MAX_WINDOW) == cudaSuccess;
+    ok = ok && ncc_rows_prepare(c->cost_kind, D, c->Dp) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->ws, 0, p.total, c->cap) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->d_desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->cap) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->d_prefix, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice,
+                               c->cap) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(c->cap) == cudaSuccess;
     if (!ok) {
         bps_destroy(c);
@@ -221,9 +278,18 @@ static int check_cost_args(bps_ctx *c, const uint8_t *L, const uint8_t *R, int p
 static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
                         float *ncc_out, cudaStream_t st) {
     const LevelView &v0 = c->lv[0];
-    CK(launch_ncc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0.Wh, v0.cost[0],
-                  v0.cost[1], ncc_out, st));
-    for (int l = 1; l < c->levels; ++l) CK(launch_pyramid(c->cost_kind, c->lv[l - 1], c->lv[l], c->Dp, st));
+    int first_pyramid = 1;
+    if (window <= NCC_ROWS_MAX_WINDOW) {
+        // the row-streaming kernel also writes scale 1 in the integer forms
+        const bool fuse = c->levels > 1 && c->cost_kind != COST_F32;
+        CK(launch_ncc_rows(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0,
+                           fuse ? &c->lv[1] : nullptr, ncc_out, st));
+        if (fuse) first_pyramid = 2;
+    } else {
+        CK(launch_ncc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0.Wh, v0.cost[0],
+                      v0.cost[1], ncc_out, st));
+    }
+    for (int l = first_pyramid; l < c->levels; ++l) CK(launch_pyramid(c->cost_kind, c->lv[l - 1], c->lv[l], c->Dp, st));
     return BPS_OK;
 }
 
@@ -240,7 +306,8 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
     if (!c) return BPS_ERR_ARG;
     if (!c->has_cost) return BPS_ERR_STATE;
     if (levels < 1 || levels > c->levels || iters < 0 || iters > BPS_MAX_ITERS || lambda < 0 || trunc < 0 ||
-        (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_WARM_START | BPS_FLAG_GRAPH | BPS_FLAG_PROFILE)) ||
+        (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_WARM_START | BPS_FLAG_GRAPH | BPS_FLAG_PROFILE |
+                   BPS_FLAG_PER_SWEEP | BPS_FLAG_TEST_TIMEOUT)) ||
         (int64_t)lambda * ((int64_t)c->Dp + trunc) >= ((int64_t)1 << 24) ||
         ((flags & BPS_FLAG_WARM_START) && !init))
         return BPS_ERR_ARG;
@@ -248,32 +315,104 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
     return BPS_OK;
 }
 
+static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
+                             cudaStream_t st);
+
+// The start messages of the coarsest scale: zero, or imported from the caller.
+static int enqueue_start(bps_ctx *c, int top, int flags, const void *init, cudaStream_t st) {
+    const LevelView &v = c->lv[top];
+    if (flags & BPS_FLAG_WARM_START) {
+        CK(launch_import_msgs(c->msg_kind, v, c->D, c->Dp, init, st));
+    } else {
+        for (int k = 0; k < 2; ++k)
+            CK(cudaMemsetAsync(v.msg[k], 0, (size_t)v.H * v.Wh * 4 * c->Dp * msg_size(c->msg_type), st));
+    }
+    return BPS_OK;
+}
+
+static PersistParams persist_params(int npairs, const PairDesc *pairs, const int *sweep_prefix, const int *wta_prefix,
+                                    unsigned *barrier, int levels, int iters, int lambda, int trunc, int flags) {
+    PersistParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.pairs = pairs;
+    P.sweep_prefix = sweep_prefix;
+    P.wta_prefix = wta_prefix;
+    P.npairs = npairs;
+    P.levels = levels;
+    P.iters = iters;
+    P.lam = lambda;
+    P.lam_u8 = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
+    P.trunc = trunc;
+    P.skip = (flags & BPS_FLAG_FAST_SKIP) ? 1 : 0;
+    P.barrier = barrier;
+    P.extra_arrivals = (flags & BPS_FLAG_TEST_TIMEOUT) ? 1u : 0u;
+    P.timeout_ns = (flags & BPS_FLAG_TEST_TIMEOUT) ? TEST_TIMEOUT_NS : BARRIER_TIMEOUT_NS;
+    return P;
+}
+
+// The whole solve (and the read-out into disp when it is not NULL) as one persistent launch.
 static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
-                      cudaStream_t st) {
+                      cudaStream_t st, int32_t *disp = nullptr) {
+    if (flags & BPS_FLAG_PER_SWEEP) {
+        const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st);
+        if (rc == BPS_OK && disp) CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+        return rc;
+    }
+    const int top = levels - 1;
+    const int ntrace = levels * iters * 2;
+    if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
+    const int rc = enqueue_start(c, top, flags, init, st);
+    if (rc != BPS_OK) return rc;
+    CK(cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), st));
+    // a batch of one: the read-out target is patched into a private descriptor copy only when it
+    // changes, so a captured graph keeps pointing at valid data
+    PersistParams P = persist_params(1, c->d_desc, c->d_prefix, c->d_prefix + 2 * c->levels, c->d_barrier, levels,
+                                     iters, lambda, trunc, flags);
+    P.disp_override = disp;
+    const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
+    if (prof) {
+        while (c->ev.size() < 2) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev.push_back(e);
+        }
+        CK(cudaEventRecord(c->ev[0], st));
+    }
+    CK(launch_persistent(c->msg_kind, P, c->grid, st));
+    if (prof) {
+        CK(cudaEventRecord(c->ev[1], st));
+        c->prof_all = 1;
+        c->prof_launches = 1;
+        c->prof_first_trace = 0;
+        c->prof_trace_n = ntrace;
+    }
+    c->last_levels = levels;
+    c->last_iters = iters;
+    return BPS_OK;
+}
+
+static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
+                             cudaStream_t st) {
     const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
     const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
     const int top = levels - 1;
-    const size_t mb = msg_size(c->msg_type);
     const int ntrace = levels * iters * 2;
     if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
     if (prof) {
-        const size_t need = 2 * (size_t)iters * 2;
+        const size_t need = 2 * (size_t)levels * iters * 2;
         while (c->ev.size() < need) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
             c->ev.push_back(e);
         }
         c->prof_launches = 0;
+        c->prof_all = 0;
         c->prof_first_trace = top * iters * 2;
+        c->prof_trace_n = iters * 2;
     }
     {
-        const LevelView &v = c->lv[top];
-        if (flags & BPS_FLAG_WARM_START) {
-            CK(launch_import_msgs(c->msg_kind, v, c->D, c->Dp, init, st));
-        } else {
-            for (int k = 0; k < 2; ++k)
-                CK(cudaMemsetAsync(v.msg[k], 0, (size_t)v.H * v.Wh * 4 * c->Dp * mb, st));
-        }
+        const int rc = enqueue_start(c, top, flags, init, st);
+        if (rc != BPS_OK) return rc;
     }
     int t = 0;
     for (int l = top; l >= 0; --l) {
@@ -288,12 +427,12 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
             for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(v.dirty[k], 1, (size_t)v.H * v.Wh, st));
         for (int it = 0; it < iters; ++it)
             for (int colour = 0; colour < 2; ++colour, ++t) {
-                const bool rec = prof && l == 0;
-                if (rec) CK(cudaEventRecord(c->ev[2 * c->prof_launches], st));
+                if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
                 CK(launch_sweep(c->msg_kind, v, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st));
-                if (rec) {
-                    CK(cudaEventRecord(c->ev[2 * c->prof_launches + 1], st));
-                    ++c->prof_launches;
+                if (prof) {
+                    CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
+                    ++c->prof_all;
+                    if (l == 0) ++c->prof_launches;
                 }
             }
     }
@@ -329,17 +468,15 @@ static int enqueue_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
                           int iters, int lambda, int trunc, int flags, int32_t *disp, cudaStream_t st) {
     int rc = enqueue_cost(c, L, R, pitch, window, trunc_data, nullptr, st);
     if (rc != BPS_OK) return rc;
-    rc = enqueue_bp(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr, st);
-    if (rc != BPS_OK) return rc;
-    CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
-    return BPS_OK;
+    return enqueue_bp(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PER_SWEEP), nullptr,
+                      st, disp);
 }
 
 extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
                           int iters, int lambda, int trunc, int flags, int32_t *disp, void *stream) {
     int rc = check_cost_args(c, L, R, pitch, window, trunc_data);
     if (rc != BPS_OK) return rc;
-    if (!disp || (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH))) return BPS_ERR_ARG;
+    if (!disp || (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PER_SWEEP))) return BPS_ERR_ARG;
     const bool had_cost = c->has_cost;
     c->has_cost = true;  // the sequence builds the cost volume first
     rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
@@ -405,7 +542,14 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
     if (h_e_i64 && c->msg_type != BPS_MSG_FP16) CK(cudaMemcpyAsync(h_e_i64, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
     if (h_e_f64) CK(cudaMemcpyAsync(h_e_f64, c->e_f64, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return BPS_OK;
+    return bps_get_error(c);
+}
+
+extern "C" int bps_get_error(bps_ctx *c) {
+    if (!c) return BPS_ERR_ARG;
+    unsigned w[2] = {0u, 0u};
+    CK(cudaMemcpy(w, c->d_barrier, sizeof(w), cudaMemcpyDeviceToHost));
+    return w[1] ? BPS_ERR_TIMEOUT : BPS_OK;
 }
 
 extern "C" int bps_get_trace(bps_ctx *c, int64_t *h_counts, int cap) {
@@ -434,16 +578,16 @@ extern "C" int bps_export_cost(bps_ctx *c, int level, void *d_out, void *stream)
 extern "C" int bps_read_profile(bps_ctx *c, int *h_launches, double *h_total_ms, int64_t *h_pixels) {
     if (!c || !h_launches || !h_total_ms || !h_pixels) return BPS_ERR_ARG;
     double total = 0.0;
-    for (int k = 0; k < c->prof_launches; ++k) {
+    for (int k = c->prof_all - c->prof_launches; k < c->prof_all; ++k) {
         CK(cudaEventSynchronize(c->ev[2 * k + 1]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
         total += ms;
     }
     int64_t px = 0;
-    if (c->prof_launches) {
-        std::vector<unsigned long long> tmp(c->prof_launches);
-        CK(cudaMemcpy(tmp.data(), c->trace + c->prof_first_trace, sizeof(unsigned long long) * c->prof_launches,
+    if (c->prof_launches && c->prof_trace_n) {
+        std::vector<unsigned long long> tmp(c->prof_trace_n);
+        CK(cudaMemcpy(tmp.data(), c->trace + c->prof_first_trace, sizeof(unsigned long long) * c->prof_trace_n,
                       cudaMemcpyDeviceToHost));
         for (unsigned long long v : tmp) px += (int64_t)v;
     }
@@ -451,4 +595,16 @@ extern "C" int bps_read_profile(bps_ctx *c, int *h_launches, double *h_total_ms,
     *h_total_ms = total;
     *h_pixels = px;
     return BPS_OK;
+}
+
+extern "C" int bps_read_launch_times(bps_ctx *c, double *h_ms, int cap) {
+    if (!c || cap < 0 || (!h_ms && cap > 0)) return BPS_ERR_ARG;
+    const int n = std::min(cap, c->prof_all);
+    for (int k = 0; k < n; ++k) {
+        CK(cudaEventSynchronize(c->ev[2 * k + 1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        h_ms[k] = ms;
+    }
+    return n;
 }

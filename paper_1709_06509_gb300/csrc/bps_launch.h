@@ -20,6 +20,14 @@ cudaError_t launch_ncc(int cost_kind, const uint8_t *L, const uint8_t *R, int pi
                        int window, int T, int Wh, void *c0, void *c1, float *ncc_out, cudaStream_t st);
 cudaError_t launch_pyramid(int cost_kind, const LevelView &fine, const LevelView &coarse, int Dp, cudaStream_t st);
 
+// Row-streaming NCC for windows up to NCC_ROWS_MAX_WINDOW; with l1 != NULL (integer forms)
+// it also writes scale 1 of the pyramid.
+constexpr int NCC_ROWS_MAX_WINDOW = 15;
+cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int D, int Dp,
+                            int window, int T, const LevelView &l0, const LevelView *l1, float *ncc_out,
+                            cudaStream_t st);
+cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
+
 // One red-black half-sweep of `colour` at one scale.  trace: nullable device counter of
 // recomputed pixels.
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
@@ -31,6 +39,27 @@ cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelVi
 cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st);
 cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);
 cudaError_t launch_export_cost(int cost_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);
+
+// ------------------------------------------------------------------ persistent batched solve
+// One pair of a batch as the persistent kernel sees it (device memory).
+struct PairDesc {
+    LevelView lv[8];
+    int D, Dp, Gp;
+    unsigned long long *trace;  // per half-sweep counters of this pair (nullable)
+    int32_t *disp;              // winner-take-all output (nullable: no read-out)
+};
+struct PersistParams {
+    const PairDesc *pairs;        // [npairs]
+    const int *sweep_prefix;      // [levels][npairs + 1]: first work block of each pair in a half-sweep
+    const int *wta_prefix;        // [npairs + 1]: first work block of each pair in the read-out
+    int npairs, levels, iters, lam, lam_u8, trunc, skip;
+    unsigned *barrier;            // {arrival count, error word}, zeroed before the launch
+    unsigned extra_arrivals;      // test hook: > 0 makes every barrier wait for blocks that never come
+    unsigned long long timeout_ns;
+    int32_t *disp_override;       // single-pair launches: read-out target of pair 0 (nullable)
+};
+cudaError_t persistent_grid(int form, int *grid);
+cudaError_t launch_persistent(int form, const PersistParams &P, int grid, cudaStream_t st);
 
 // Winner-take-all disparity at the finest scale.
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);

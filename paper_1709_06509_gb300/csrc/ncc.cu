@@ -161,6 +161,264 @@ ncc_cost_kernel(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R, in
     }
 }
 
+// ------------------------------------------------------------------ row-streaming NCC (windows up to 15)
+// ncc_rows_kernel: a CTA owns a strip of rows [y0, y0 + TYS) and XS * 16 columns; thread
+// (label d, column group xs) owns 16 consecutive columns at one label.  Walking down the
+// rows, each thread keeps the vertical window sums V of L(x') * R(x' - d) for its 16 + 2R
+// columns in registers (one row enters, one leaves: O(1) per row), and slides a horizontal
+// window over V for its 16 outputs.  Per row the CTA stages the entering row of L and R in
+// a shared ring of 2R + 2 rows, updates column sums of L, L^2, R, R^2 and forms, once per
+// pixel and once per right position, the window sums S, the variance term N S_xx - S_x^2
+// and its reciprocal square root (correctly rounded).  The data cost of each (pixel,
+// label) then needs one multiply-add for the numerator and two multiplies for the
+// correlation.  The 2x2 sum of the next scale is accumulated over row pairs in registers
+// and written directly (scale 1 of the pyramid).
+//
+// Quantiser: the fp32 correlation num * rsqrt(va) * rsqrt(vb) has a relative error below
+// 6 * 2^-24 (six correctly rounded steps), so v = T (1 - ncc) + 1/2 is within (T + 1) * 2^-20
+// of its exact value; the FP64 sequence decides only where v lies within (T + 1) * 2^-17 of
+// an integer.
+constexpr int NR_TX = 16;
+
+template <int R> struct NccInt { using type = int; };
+template <> struct NccInt<7> { using type = long long; };  // 15x15: N S_ab - S_a S_b needs 33 bits
+
+template <typename CostT, int R>
+__global__ void __launch_bounds__(512)
+ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Rimg, int pitch, int W, int H, int D,
+                int Dp, int T, int TYS, LevelView l0, LevelView l1, int write_l1, float *ncc_out) {
+    using Num = typename NccInt<R>::type;
+    constexpr int WIN = 2 * R + 1, RING = 2 * R + 2, VN = NR_TX + 2 * R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int XS = blockDim.x / Dp;
+    const int CW = XS * NR_TX;
+    const int LW = CW + 2 * R, RW = CW + 2 * R + D - 1, UW = CW + D - 1;
+    const int dl = threadIdx.x % Dp, xs = threadIdx.x / Dp;
+    const int d = min(dl, D - 1);
+    const int x0 = blockIdx.x * CW, y0 = blockIdx.y * TYS, y1 = min(H, y0 + TYS);
+    const int N = WIN * WIN;
+
+    int *colA = reinterpret_cast<int *>(smem);   // [LW]  column sums of L over the window rows
+    int *colAA = colA + LW;                      // [LW]
+    int *colB = colAA + LW;                      // [RW]
+    int *colBB = colB + RW;                      // [RW]
+    int *sA = colBB + RW;                        // [CW]  window sum of L at pixel x0 + i
+    unsigned *vA = reinterpret_cast<unsigned *>(sA + CW);  // [CW]  N S_aa - S_a^2
+    float *iA = reinterpret_cast<float *>(vA + CW);        // [CW]  its reciprocal square root
+    int *sB = reinterpret_cast<int *>(iA + CW);            // [UW]  window sum of R at u = x0 - (D-1) + i
+    unsigned *vB = reinterpret_cast<unsigned *>(sB + UW);  // [UW]
+    float *iB = reinterpret_cast<float *>(vB + UW);        // [UW]
+    uint8_t *Lr = reinterpret_cast<uint8_t *>(iB + UW);    // [RING][LW]
+    uint8_t *Rr = Lr + RING * LW;                          // [RING][RW]
+
+    for (int i = threadIdx.x; i < LW; i += blockDim.x) colA[i] = colAA[i] = 0;
+    for (int i = threadIdx.x; i < RW; i += blockDim.x) colB[i] = colBB[i] = 0;
+    int V[VN];
+#pragma unroll
+    for (int i = 0; i < VN; ++i) V[i] = 0;
+    int acc[NR_TX / 2];
+#pragma unroll
+    for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
+
+    const int lbase = xs * NR_TX;               // this thread's first staged left column
+    const int rbase = xs * NR_TX + D - 1 - d;   // ... and the right column matching it at label d
+    // rows y0-1-R .. y1-1+R enter in turn; a row leaves 2R+1 rows after it entered
+    for (int e = y0 - 1 - R; e < y1 + R; ++e) {
+        const int slot_e = (e - (y0 - 1 - R)) % RING;
+        const int lv = e - WIN;                 // the row leaving the window
+        const bool leave = lv >= y0 - 1 - R;
+        const int slot_l = leave ? (lv - (y0 - 1 - R)) % RING : 0;
+        __syncthreads();  // the ring slot about to be refilled is no longer read
+        {
+            const size_t row = (size_t)clampi(e, 0, H - 1) * pitch;
+            for (int i = threadIdx.x; i < LW; i += blockDim.x)
+                Lr[slot_e * LW + i] = __ldg(Limg + row + clampi(x0 - R + i, 0, W - 1));
+            for (int i = threadIdx.x; i < RW; i += blockDim.x)
+                Rr[slot_e * RW + i] = __ldg(Rimg + row + clampi(x0 - R - (D - 1) + i, 0, W - 1));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < LW; i += blockDim.x) {
+            const int a = Lr[slot_e * LW + i], o = leave ? Lr[slot_l * LW + i] : 0;
+            colA[i] += a - o;
+            colAA[i] += a * a - o * o;
+        }
+        for (int i = threadIdx.x; i < RW; i += blockDim.x) {
+            const int b = Rr[slot_e * RW + i], o = leave ? Rr[slot_l * RW + i] : 0;
+            colB[i] += b - o;
+            colBB[i] += b * b - o * o;
+        }
+#pragma unroll
+        for (int i = 0; i < VN; ++i) {
+            const int enter = (int)Lr[slot_e * LW + lbase + i] * (int)Rr[slot_e * RW + rbase + i];
+            const int out = leave ? (int)Lr[slot_l * LW + lbase + i] * (int)Rr[slot_l * RW + rbase + i] : 0;
+            V[i] += enter - out;
+        }
+        const int y = e - R;  // the row whose window is now complete
+        if (y < y0) continue;
+        __syncthreads();
+        for (int i = threadIdx.x; i < CW; i += blockDim.x) {
+            int s = 0, ss = 0;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                s += colA[i + k];
+                ss += colAA[i + k];
+            }
+            const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
+            sA[i] = s;
+            vA[i] = v;
+            iA[i] = v ? __frsqrt_rn((float)v) : 0.f;
+        }
+        for (int i = threadIdx.x; i < UW; i += blockDim.x) {
+            int s = 0, ss = 0;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) {
+                s += colB[i + k];
+                ss += colBB[i + k];
+            }
+            const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
+            sB[i] = s;
+            vB[i] = v;
+            iB[i] = v ? __frsqrt_rn((float)v) : 0.f;
+        }
+        __syncthreads();
+        int S = 0;
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) S += V[i];
+        const int cy = y >> 1;
+        const bool row_done = (y & 1) || y == H - 1;  // the coarse pixel of this row pair is complete
+#pragma unroll
+        for (int j = 0; j < NR_TX; ++j) {
+            if (j) S += V[j + 2 * R] - V[j - 1];
+            const int x = x0 + lbase + j;
+            const int pi = lbase + j, ui = lbase + j + D - 1 - d;
+            const unsigned va = vA[pi], vb = vB[ui];
+            const Num num = (Num)N * (Num)S - (Num)sA[pi] * (Num)sB[ui];
+            int c;
+            float nccf;
+            if constexpr (CostOut<CostT>::is_float) {
+                nccf = (va == 0u || vb == 0u) ? 0.f : __fmul_rn(__fmul_rn((float)num, iA[pi]), iB[ui]);
+                c = 0;
+            } else {
+                if (va == 0u || vb == 0u) {
+                    nccf = 0.f;
+                    c = T;
+                } else {
+                    nccf = __fmul_rn(__fmul_rn((float)num, iA[pi]), iB[ui]);
+                    const float v = __fadd_rn(__fmul_rn((float)T, __fsub_rn(1.f, nccf)), 0.5f);
+                    const float fl = floorf(v);
+                    if (fminf(v - fl, fl + 1.f - v) > (float)(T + 1) * (1.f / 131072.f)) {
+                        c = (int)fl;
+                    } else {
+                        const double den = __dmul_rn((double)va, (double)vb);
+                        const double n64 = __ddiv_rn((double)num, __dsqrt_rn(den));
+                        c = (int)floor(__dadd_rn(__dmul_rn((double)T, __dadd_rn(1.0, -n64)), 0.5));
+                    }
+                    c = c < 0 ? 0 : (c > T ? T : c);
+                }
+            }
+            if (x < W) {
+                const int colour = colour_of(x, y);
+                CostT *dst = reinterpret_cast<CostT *>(colour ? l0.cost[1] : l0.cost[0]) + slot_of(x, y, l0.Wh) * Dp +
+                             label_pos<CostT>(dl);
+                if constexpr (CostOut<CostT>::is_float) {
+                    const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
+                    *dst = dl < D ? cf : 0.f;
+                } else {
+                    *dst = dl < D ? (CostT)c : (CostT)0;
+                }
+                if (ncc_out && dl < D) ncc_out[((size_t)y * W + x) * D + dl] = nccf;
+            }
+            if constexpr (!CostOut<CostT>::is_float) {
+                if (write_l1) {
+                    if ((y & 1) == 0 && (j & 1) == 0) acc[j >> 1] = 0;
+                    if (x < W && dl < D) acc[j >> 1] += c;
+                }
+            }
+        }
+        if constexpr (!CostOut<CostT>::is_float) {
+            if (write_l1 && row_done) {
+#pragma unroll
+                for (int jj = 0; jj < NR_TX / 2; ++jj) {
+                    const int cx = (x0 + lbase) / 2 + jj;
+                    if (cx < l1.W) {
+                        CostT *dst = reinterpret_cast<CostT *>(colour_of(cx, cy) ? l1.cost[1] : l1.cost[0]) +
+                                     slot_of(cx, cy, l1.Wh) * Dp + label_pos<CostT>(dl);
+                        *dst = (CostT)acc[jj];
+                    }
+                }
+            }
+        }
+    }
+}
+
+size_t ncc_rows_smem_bytes(int D, int Dp, int window) {
+    const int R = window / 2;
+    const int XS = Dp >= 256 ? 1 : 256 / Dp;
+    const int CW = XS * NR_TX, LW = CW + 2 * R, RW = CW + 2 * R + D - 1, UW = CW + D - 1;
+    return (size_t)4 * (2 * LW + 2 * RW + 3 * CW + 3 * UW) + (size_t)(2 * R + 2) * (LW + RW);
+}
+
+template <typename CostT, int R>
+static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp, int T,
+                                 const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st, bool prep) {
+    const size_t smem = ncc_rows_smem_bytes(D, Dp, 2 * R + 1);
+    if (prep)
+        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int XS = Dp >= 256 ? 1 : 256 / Dp;
+    const int threads = XS * Dp;
+    const int CW = XS * NR_TX;
+    const int nx = (W + CW - 1) / CW;
+    // short strips when the image is small, so that every SM gets work; even for the 2x2 sums
+    int tys = (int)(((int64_t)H * nx + 151) / 152);
+    tys = std::max(8, std::min(64, (tys + 1) & ~1));
+    const int ny = (H + tys - 1) / tys;
+    LevelView none = l0;
+    ncc_rows_kernel<CostT, R><<<dim3(nx, ny), threads, smem, st>>>(L, Rim, pitch, W, H, D, Dp, T, tys, l0,
+                                                                   l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
+    return cudaGetLastError();
+}
+
+template <typename CostT>
+static cudaError_t launch_rows(int R, const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp,
+                               int T, const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st,
+                               bool prep) {
+    switch (R) {
+    case 0: return launch_rows_t<CostT, 0>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 1: return launch_rows_t<CostT, 1>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 2: return launch_rows_t<CostT, 2>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 3: return launch_rows_t<CostT, 3>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 4: return launch_rows_t<CostT, 4>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 5: return launch_rows_t<CostT, 5>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 6: return launch_rows_t<CostT, 6>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    default: return launch_rows_t<CostT, 7>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    }
+}
+
+cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp,
+                            int window, int T, const LevelView &l0, const LevelView *l1, float *ncc_out,
+                            cudaStream_t st) {
+    const int R = window / 2;
+    switch (cost_kind) {
+    case COST_I32: return launch_rows<int32_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false);
+    case COST_I16: return launch_rows<int16_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false);
+    default: return launch_rows<float>(R, L, Rim, pitch, W, H, D, Dp, T, l0, nullptr, ncc_out, st, false);
+    }
+}
+
+cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp) {
+    for (int R = 0; R <= NCC_ROWS_MAX_WINDOW / 2; ++R) {
+        const LevelView none{};
+        cudaError_t e;
+        switch (cost_kind) {
+        case COST_I32: e = launch_rows<int32_t>(R, nullptr, nullptr, 0, 1, 1, D, Dp, 0, none, nullptr, nullptr, 0, true); break;
+        case COST_I16: e = launch_rows<int16_t>(R, nullptr, nullptr, 0, 1, 1, D, Dp, 0, none, nullptr, nullptr, 0, true); break;
+        default: e = launch_rows<float>(R, nullptr, nullptr, 0, 1, 1, D, Dp, 0, none, nullptr, nullptr, 0, true); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 size_t ncc_smem_bytes(int D, int window) {
     const int r = window / 2;
     const int TW = NCC_TX + 2 * r, RW = TW + D - 1, SH = NCC_TY + 2 * r, UW = NCC_TX + D - 1;

@@ -13,56 +13,14 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "bps_internal.cuh"
 #include "bps_launch.h"
+#include "sweep_body.cuh"
 
 namespace bps {
 
-constexpr unsigned FULLM = 0xffffffffu;
-
 template <typename CostT, typename MsgT>
 __global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, int Gp, int32_t *disp) {
-    using Acc = typename AccOf<MsgT>::type;
-    using A = Arith<Acc>;
-    const int g = threadIdx.x & (Gp - 1);
-    const int64_t p = (int64_t)blockIdx.x * (blockDim.x / Gp) + threadIdx.x / Gp;
-    const bool valid = p < (int64_t)lv.W * lv.H;
-    const int x = valid ? (int)(p % lv.W) : 0, y = valid ? (int)(p / lv.W) : 0;
-    const int c = colour_of(x, y);
-    const int64_t s = slot_of(x, y, lv.Wh);
-    const int dbase = g * VEC;
-    Acc best = A::big();
-    int arg = 0x7fffffff;
-    if (valid && dbase < Dp) {
-        Acc b[VEC], t[VEC];
-        load16(reinterpret_cast<const CostT *>(lv.cost[c]) + s * Dp + dbase, b);
-        const MsgT *mp = reinterpret_cast<const MsgT *>(lv.msg[c]) + s * 4 * Dp + dbase;
-        const bool has[4] = {y > 0, y < lv.H - 1, x > 0, x < lv.W - 1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!has[q]) continue;
-            load16(mp + q * Dp, t);
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) b[k] += t[k];
-        }
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-            const int lab = dbase + pos_label<MsgT>(k);
-            if (lab < D && (b[k] < best || (b[k] == best && lab < arg))) {
-                best = b[k];
-                arg = lab;
-            }
-        }
-    }
-    for (int o = Gp >> 1; o > 0; o >>= 1) {
-        const Acc ob = __shfl_xor_sync(FULLM, best, o, Gp);
-        const int oa = __shfl_xor_sync(FULLM, arg, o, Gp);
-        if (ob < best || (ob == best && oa < arg)) {
-            best = ob;
-            arg = oa;
-        }
-    }
-    if (valid && g == 0) disp[p] = arg;
+    wta_group<CostT, MsgT>(lv, D, Dp, Gp, disp, blockIdx.x);
 }
 
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st) {
@@ -86,13 +44,13 @@ int energy_blocks(int W, int H) {
 
 template <typename Sum>
 __device__ inline Sum block_sum(Sum v, Sum *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
     Sum t = Sum(0);
     if (threadIdx.x < 32) {
         t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : Sum(0);
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULLM, t, o);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     }
     return t;  // valid in thread 0
 }

@@ -1,0 +1,401 @@
+// sweep_body.cuh -- the per-pixel work of the BP kernels, shared by the one-launch-per-
+// half-sweep kernels (bp.cu) and the persistent batched kernel (persist.cu).
+//
+// sweep_group / sweep_group_u8: one red-black half-sweep for the pixels of block `block`
+// of the active colour (256 / Gp pixels, Gp lanes each, 16 labels per lane).  A group
+// forms the belief b = cost + sum of the existing incoming messages, and for each existing
+// neighbour q the message
+//     m(d) = min(F(d), B(d), min h + lambda*trunc) - min h,   h = b - (message from q),
+// where F / B are the forward / backward passes of the distance transform for the linear
+// cost lambda*|d - d'| (F(d) = min(h(d), F(d-1) + lambda), B mirrored).  Within a lane the
+// passes run over its 16 labels; across the lanes of the group they are completed by a
+// Kogge-Stone scan of the segment ends (warp shuffles), and min h by a butterfly.  The
+// result is written straight into q's incoming slot (the other colour's arrays, so the
+// update is race-free in place).
+//
+// Fast-converging skip, exact form: dirty[c][s] = 1 while some incoming message of the
+// pixel changed since its last update.  A clean pixel would resend exactly what it sent
+// last time, so the group skips it; a warp whose pixels are all clean returns at once.
+// With the skip on, a sender compares each new message with the stored one and writes
+// (and marks the receiver dirty) only on a change.
+#pragma once
+
+#include "bps_internal.cuh"
+
+namespace bps {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ inline unsigned group_bits(int Gp) { return Gp >= 32 ? FULL : ((1u << Gp) - 1u); }
+__device__ inline unsigned leader_bits(int Gp) {
+    unsigned m = 0;
+    for (int l = 0; l < 32; l += Gp) m |= 1u << l;
+    return m;
+}
+
+template <typename Acc>
+__device__ inline void min_convolve(const Acc (&h)[VEC], Acc lam, Acc lamT, int g, int Gp, Acc (&m)[VEC]) {
+    using A = Arith<Acc>;
+    Acc F[VEC], B[VEC];
+    F[0] = h[0];
+#pragma unroll
+    for (int k = 1; k < VEC; ++k) F[k] = A::mn(h[k], F[k - 1] + lam);
+    B[VEC - 1] = h[VEC - 1];
+#pragma unroll
+    for (int k = VEC - 2; k >= 0; --k) B[k] = A::mn(h[k], B[k + 1] + lam);
+    Acc hm = h[0];
+#pragma unroll
+    for (int k = 1; k < VEC; ++k) hm = A::mn(hm, h[k]);
+    if (Gp > 1) {
+        const Acc span = lam * (Acc)VEC;
+        Acc fe = F[VEC - 1], bs = B[0];
+        for (int o = 1; o < Gp; o <<= 1) {
+            const Acc tf = __shfl_up_sync(FULL, fe, o, Gp);
+            const Acc tb = __shfl_down_sync(FULL, bs, o, Gp);
+            const Acc th = __shfl_xor_sync(FULL, hm, o, Gp);
+            if (g >= o) fe = A::mn(fe, tf + span * (Acc)o);
+            if (g + o < Gp) bs = A::mn(bs, tb + span * (Acc)o);
+            hm = A::mn(hm, th);
+        }
+        Acc cf = __shfl_up_sync(FULL, fe, 1, Gp);
+        Acc cb = __shfl_down_sync(FULL, bs, 1, Gp);
+        if (g == 0) cf = A::big();
+        if (g == Gp - 1) cb = A::big();
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            F[k] = A::mn(F[k], cf + lam * (Acc)(k + 1));
+            B[k] = A::mn(B[k], cb + lam * (Acc)(VEC - k));
+        }
+    }
+    const Acc cap = hm + lamT;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) m[k] = A::mn(A::mn(F[k], B[k]), cap) - hm;
+}
+
+template <typename CostT, typename MsgT>
+__device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int D, int Dp, int Gp,
+                                            typename AccOf<MsgT>::type lam, typename AccOf<MsgT>::type lamT,
+                                            int skip, unsigned long long *trace, int64_t block) {
+    using Acc = typename AccOf<MsgT>::type;
+    using A = Arith<Acc>;
+    const int lane = threadIdx.x & 31;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    int x = 0, y = 0;
+    bool valid = false;
+    if (s < nslot) {
+        y = (int)(s / lv.Wh);
+        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        valid = x < lv.W;
+    }
+    const bool active = valid && (!skip || (colour ? lv.dirty[1] : lv.dirty[0])[s] != 0);
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) return;
+    if (trace && lane == 0) {
+        const int n = __popc(act & leader_bits(Gp));
+        if (n) atomicAdd(trace, (unsigned long long)n);
+    }
+    const int64_t sc = valid ? s : 0;
+    const int dbase = g * VEC;
+    const bool lane_data = dbase < Dp;
+    const bool has[4] = {valid && y > 0, valid && y < lv.H - 1, valid && x > 0, valid && x < lv.W - 1};
+
+    Acc b[VEC], in[4][VEC];
+    if (lane_data) {
+        load16(reinterpret_cast<const CostT *>(colour ? lv.cost[1] : lv.cost[0]) + sc * Dp + dbase, b);
+        const MsgT *mp = reinterpret_cast<const MsgT *>(colour ? lv.msg[1] : lv.msg[0]) + sc * 4 * Dp + dbase;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (has[q]) {
+                load16(mp + q * Dp, in[q]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) in[q][k] = Acc(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            b[k] = A::big();
+            in[0][k] = in[1][k] = in[2][k] = in[3][k] = Acc(0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) b[k] = b[k] + in[0][k] + in[1][k] + in[2][k] + in[3][k];
+
+    const int nbx[4] = {x, x, x - 1, x + 1};
+    const int nby[4] = {y - 1, y + 1, y, y};
+    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
+    MsgT *out = reinterpret_cast<MsgT *>(colour ? lv.msg[0] : lv.msg[1]);
+    const int gshift = lane & ~(Gp - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        Acc h[VEC], m[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) h[k] = (dbase + k < D) ? b[k] - in[q][k] : A::big();
+        min_convolve(h, lam, lamT, g, Gp, m);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if (dbase + k >= D) m[k] = Acc(0);  // the label padding always holds 0
+        const bool send = active && has[q];
+        const int64_t qs = send ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+        MsgT *dst = out + (qs * 4 + opp[q]) * Dp + dbase;
+        if (skip) {
+            bool diff = false;
+            if (send && lane_data) {
+                Acc old[VEC];
+                load16_rw(dst, old);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) diff |= (old[k] != stored_value<MsgT>(m[k]));
+            }
+            const unsigned dm = __ballot_sync(FULL, diff);
+            const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
+            if (send && changed) {
+                if (lane_data) store16(dst, m);
+                if (g == 0) (colour ? lv.dirty[0] : lv.dirty[1])[qs] = 1;
+            }
+        } else if (send && lane_data) {
+            store16(dst, m);
+        }
+    }
+    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0;
+}
+
+// ------------------------------------------------------------------ u8 form, packed 16-bit arithmetic
+// int16 costs and uint8 messages in the interleaved label order (see label_pos): register j
+// of a lane holds labels (j, j + 8) of its 16 as two unsigned 16-bit halves.  Every value
+// the update forms is a non-negative integer below 2^15 (beliefs <= 27000 + 4*255 by the
+// host checks, padding labels are BIG16), so 32-bit adds and subtracts never carry between
+// halves and the fused add-min / 3-way min on u16x2 are exact.  The two halves run the
+// distance-transform chains of labels 0..7 and 8..15 side by side; a fix-up then carries
+// the low chain's end into the high chain (forward) and back (backward), together with
+// the carries from the neighbouring lanes.
+constexpr uint32_t BIG16 = 0x7000u;
+
+__device__ inline uint32_t pk(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+
+__device__ inline void unpack_msg(const uint4 r, uint32_t (&v)[8]) {
+    v[0] = __byte_perm(r.x, 0u, 0x4140); v[1] = __byte_perm(r.x, 0u, 0x4342);
+    v[2] = __byte_perm(r.y, 0u, 0x4140); v[3] = __byte_perm(r.y, 0u, 0x4342);
+    v[4] = __byte_perm(r.z, 0u, 0x4140); v[5] = __byte_perm(r.z, 0u, 0x4342);
+    v[6] = __byte_perm(r.w, 0u, 0x4140); v[7] = __byte_perm(r.w, 0u, 0x4342);
+}
+
+__device__ inline uint4 pack_msg(const uint32_t (&v)[8]) {
+    return make_uint4(__byte_perm(v[0], v[1], 0x6420), __byte_perm(v[2], v[3], 0x6420),
+                      __byte_perm(v[4], v[5], 0x6420), __byte_perm(v[6], v[7], 0x6420));
+}
+
+__device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
+                                               int lamT, int skip, unsigned long long *trace, int64_t block) {
+    const int lane = threadIdx.x & 31;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    int x = 0, y = 0;
+    bool valid = false;
+    if (s < nslot) {
+        y = (int)(s / lv.Wh);
+        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        valid = x < lv.W;
+    }
+    const uint8_t *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
+    const bool active = valid && (!skip || dirty_in[s] != 0);
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) return;
+    if (trace && lane == 0) {
+        const int n = __popc(act & leader_bits(Gp));
+        if (n) atomicAdd(trace, (unsigned long long)n);
+    }
+    const int64_t sc = valid ? s : 0;
+    const int dbase = g * VEC;
+    const bool lane_data = dbase < Dp;
+    const bool has[4] = {valid && y > 0, valid && y < lv.H - 1, valid && x > 0, valid && x < lv.W - 1};
+    const int16_t *cost = reinterpret_cast<const int16_t *>(colour ? lv.cost[1] : lv.cost[0]);
+    const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
+    uint8_t *msg_out = reinterpret_cast<uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
+    uint8_t *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
+
+    uint32_t b[8], padv[8], keep[8];
+    uint4 in[4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool plo = dbase + j >= D, phi = dbase + 8 + j >= D;
+        padv[j] = pk(plo ? BIG16 : 0u, phi ? BIG16 : 0u);
+        keep[j] = (plo ? 0u : 0xffffu) | (phi ? 0u : 0xffff0000u);
+    }
+    if (lane_data) {
+        const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
+        const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
+        b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
+        b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+        const uint8_t *mp = msg_in + sc * 4 * Dp + dbase;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            in[q] = has[q] ? __ldg(reinterpret_cast<const uint4 *>(mp + q * Dp)) : make_uint4(0u, 0u, 0u, 0u);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) in[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t t[8];
+        unpack_msg(in[q], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] += t[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = __vimax3_u16x2(b[j], padv[j], 0u);
+
+    const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
+    const int nbx[4] = {x, x, x - 1, x + 1};
+    const int nby[4] = {y - 1, y + 1, y, y};
+    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
+    const int gshift = lane & ~(Gp - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t t[8], h[8], F[8], B[8];
+        unpack_msg(in[q], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = b[j] - t[j];
+        uint32_t mm = __vimin3_u16x2(h[0], h[1], h[2]);
+        mm = __vimin3_u16x2(mm, h[3], h[4]);
+        mm = __vimin3_u16x2(mm, h[5], h[6]);
+        mm = __vimin3_u16x2(mm, h[7], h[7]);
+        int hm = (int)min(mm & 0xffffu, mm >> 16);
+        F[0] = h[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) F[j] = __viaddmin_u16x2(F[j - 1], LAM2, h[j]);
+        B[7] = h[7];
+#pragma unroll
+        for (int j = 6; j >= 0; --j) B[j] = __viaddmin_u16x2(B[j + 1], LAM2, h[j]);
+        const int fl = (int)(F[7] & 0xffffu), fh = (int)(F[7] >> 16);  // local forward at labels 7, 15
+        const int bl = (int)(B[0] & 0xffffu), bh = (int)(B[0] >> 16);  // local backward at labels 0, 8
+        int cf = (int)BIG16, cb = (int)BIG16;
+        if (Gp > 1) {
+            int fe = min(fh, fl + 8 * lam);  // forward value at this lane's last label
+            int bs = min(bl, bh + 8 * lam);  // backward value at this lane's first label
+            for (int o = 1; o < Gp; o <<= 1) {
+                const int tf = __shfl_up_sync(FULL, fe, o, Gp);
+                const int tb = __shfl_down_sync(FULL, bs, o, Gp);
+                const int th = __shfl_xor_sync(FULL, hm, o, Gp);
+                if (g >= o) fe = min(fe, tf + 16 * lam * o);
+                if (g + o < Gp) bs = min(bs, tb + 16 * lam * o);
+                hm = min(hm, th);
+            }
+            cf = __shfl_up_sync(FULL, fe, 1, Gp);
+            cb = __shfl_down_sync(FULL, bs, 1, Gp);
+            if (g == 0) cf = (int)BIG16;
+            if (g == Gp - 1) cb = (int)BIG16;
+            cf = min(cf, (int)BIG16);
+            cb = min(cb, (int)BIG16);
+        }
+        // forward: label j gets cf + lam*(j+1); label 8+j gets F(7) + lam*(j+1)
+        const int f7 = min(min(fl, cf + 8 * lam), (int)BIG16);
+        const uint32_t xF = pk((uint32_t)cf, (uint32_t)f7);
+        // backward: label 8+j gets cb + lam*(8-j); label j gets B(8) + lam*(8-j)
+        const int b8 = min(min(bh, cb + 8 * lam), (int)BIG16);
+        const uint32_t xB = pk((uint32_t)b8, (uint32_t)cb);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            F[j] = __viaddmin_u16x2(xF, (uint32_t)(lam * (j + 1)) * 0x10001u, F[j]);
+            B[j] = __viaddmin_u16x2(xB, (uint32_t)(lam * (8 - j)) * 0x10001u, B[j]);
+        }
+        const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
+        const uint32_t HM2 = (uint32_t)hm * 0x10001u;
+        uint32_t m[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m[j] = (__vimin3_u16x2(F[j], B[j], CAP2) - HM2) & keep[j];
+        const uint4 out = pack_msg(m);
+
+        const bool send = active && has[q];
+        const int64_t qs = send ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+        uint4 *dst = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
+        if (skip) {
+            bool diff = false;
+            if (send && lane_data) {
+                const uint4 old = *dst;
+                diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
+            }
+            const unsigned dm = __ballot_sync(FULL, diff);
+            const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
+            if (send && changed) {
+                if (lane_data) *dst = out;
+                if (g == 0) dirty_out[qs] = 1;
+            }
+        } else if (send && lane_data) {
+            *dst = out;
+        }
+    }
+    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0;
+}
+
+
+// ------------------------------------------------------------------ coarse-to-fine start
+// Element k of the copy of parent records into the fine pixels of `colour` (16-byte chunks).
+__device__ __forceinline__ void upsample_chunk(const LevelView &coarse, const LevelView &fine, int colour,
+                                               int rec_chunks, int64_t k) {
+    const int chunk = (int)(k % rec_chunks);
+    const int64_t s = k / rec_chunks;
+    const int y = (int)(s / fine.Wh);
+    const int x = 2 * (int)(s - (int64_t)y * fine.Wh) + ((y + colour) & 1);
+    if (x >= fine.W) return;
+    const int px = x >> 1, py = y >> 1;
+    const uint4 *src = reinterpret_cast<const uint4 *>(colour_of(px, py) ? coarse.msg[1] : coarse.msg[0]) +
+                       slot_of(px, py, coarse.Wh) * rec_chunks + chunk;
+    uint4 *dst = reinterpret_cast<uint4 *>(colour ? fine.msg[1] : fine.msg[0]) + s * rec_chunks + chunk;
+    *dst = *src;
+}
+
+// ------------------------------------------------------------------ winner-take-all
+// Pixels of block `block` in raster order, Gp lanes each: argmin of the belief, the lowest
+// label on ties (labels are compared through the storage order of the form).
+template <typename CostT, typename MsgT>
+__device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, int64_t block) {
+    using Acc = typename AccOf<MsgT>::type;
+    using A = Arith<Acc>;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t p = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const bool valid = p < (int64_t)lv.W * lv.H;
+    const int x = valid ? (int)(p % lv.W) : 0, y = valid ? (int)(p / lv.W) : 0;
+    const int c = colour_of(x, y);
+    const int64_t s = slot_of(x, y, lv.Wh);
+    const int dbase = g * VEC;
+    Acc best = A::big();
+    int arg = 0x7fffffff;
+    if (valid && dbase < Dp) {
+        Acc b[VEC], t[VEC];
+        load16(reinterpret_cast<const CostT *>(c ? lv.cost[1] : lv.cost[0]) + s * Dp + dbase, b);
+        const MsgT *mp = reinterpret_cast<const MsgT *>(c ? lv.msg[1] : lv.msg[0]) + s * 4 * Dp + dbase;
+        const bool has[4] = {y > 0, y < lv.H - 1, x > 0, x < lv.W - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!has[q]) continue;
+            load16(mp + q * Dp, t);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) b[k] += t[k];
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const int lab = dbase + pos_label<MsgT>(k);
+            if (lab < D && (b[k] < best || (b[k] == best && lab < arg))) {
+                best = b[k];
+                arg = lab;
+            }
+        }
+    }
+    for (int o = Gp >> 1; o > 0; o >>= 1) {
+        const Acc ob = __shfl_xor_sync(FULL, best, o, Gp);
+        const int oa = __shfl_xor_sync(FULL, arg, o, Gp);
+        if (ob < best || (ob == best && oa < arg)) {
+            best = ob;
+            arg = oa;
+        }
+    }
+    if (valid && g == 0) disp[p] = arg;
+}
+
+}  // namespace bps

@@ -30,12 +30,15 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def run_gpu(L, R, D, window, trunc_data, levels, iters, lam, trunc, msg_type, skip=True, init=None):
+def run_gpu(L, R, D, window, trunc_data, levels, iters, lam, trunc, msg_type, skip=True, init=None,
+            per_sweep=False):
     H, W = L.shape
     with bps.Stereo(W, H, D, levels, msg_type, device=DEV) as st:
         ncc = st.build_cost_volume(to_dev(L), to_dev(R), window, trunc_data, want_ncc=True)
         costs = [st.export_cost(l).cpu().numpy() for l in range(levels)]
-        st.bp_solve(iters, lam, trunc, skip=skip, init_msgs=None if init is None else to_dev(init))
+        st.bp_solve(iters, lam, trunc, skip=skip, init_msgs=None if init is None else to_dev(init),
+                    per_sweep=per_sweep)
+        assert st.get_error() == bps.BPS_OK
         disp = st.wta_disparity()
         ei, ef = st.energy(disp, lam, trunc)
         msg = st.export_messages(0)
@@ -81,16 +84,34 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("per_sweep", [False, True], ids=["persistent", "per_sweep"])
 @pytest.mark.parametrize("msg_type", INT_FORMS)
 @pytest.mark.parametrize("skip", [True, False])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
-def test_int_parity(case, skip, msg_type):
+def test_int_parity(case, skip, msg_type, per_sweep):
     W, H, D, window, levels, iters, lam, trunc = case
     if msg_type == bps.BPS_MSG_U8 and lam * trunc > 255:
         pytest.skip("outside the u8 range")
     pair = synth.make_pair(100 + W + H + D, W, H, D, 3, 2.0)
-    g = run_gpu(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, msg_type, skip)
+    g = run_gpu(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, msg_type, skip, per_sweep=per_sweep)
     assert_int_parity(g, pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, skip)
+
+
+def test_barrier_timeout_is_reported_and_the_context_survives():
+    # the test hook makes every grid barrier wait for one block more than the grid has: the
+    # bounded wait gives up after 2 ms, the kernel returns, and the host reads the status
+    pair = synth.make_pair(31, 64, 48, 16, 3, 2.0)
+    with bps.Stereo(64, 48, 16, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 5, 20)
+        st.bp_solve(4, 10, 2, test_timeout=True)
+        torch.cuda.synchronize()
+        assert st.get_error() == bps.BPS_ERR_TIMEOUT
+        st.bp_solve(4, 10, 2)
+        disp = st.wta_disparity()
+        torch.cuda.synchronize()
+        assert st.get_error() == bps.BPS_OK
+        ref = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 3, 4, 10, 2)
+        assert np.array_equal(disp.cpu().numpy(), ref["disp"])
 
 
 def test_pitched_images_and_random_texture():
@@ -155,6 +176,7 @@ def test_graph_replay_and_host_entry():
     L, R = to_dev(pair.left), to_dev(pair.right)
     with bps.Stereo(96, 72, 16, 4, bps.BPS_MSG_U8, device=DEV) as st:
         plain = st.stereo(L, R, 5, 20, 10, 10, 2, graph=False).clone()
+        sweeps = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True, per_sweep=True).clone()
         g1 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()
         g2 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()   # replay
         g3 = st.stereo(L, R, 5, 20, 6, 10, 2, graph=True).clone()    # new arguments: re-capture
@@ -164,6 +186,7 @@ def test_graph_replay_and_host_entry():
         hd, he = st.stereo_host(hl, hr, 5, 20, 10, 10, 2)
     ref = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 4, 10, 10, 2)
     assert np.array_equal(plain.cpu().numpy(), ref["disp"])
+    assert np.array_equal(sweeps.cpu().numpy(), ref["disp"])
     assert np.array_equal(g1.cpu().numpy(), ref["disp"]) and np.array_equal(g2.cpu().numpy(), ref["disp"])
     ref6 = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 4, 6, 10, 2)
     assert np.array_equal(g3.cpu().numpy(), ref6["disp"])
