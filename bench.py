@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
+    ap.add_argument("--workload", default=None,
+                    help="with --ncu-case: one named pair of paper_1709_06509_gb300.synth.WORKLOADS instead of the default two")
     return ap.parse_args()
 
 
@@ -159,7 +161,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("persist.cu", "sweep_body.cuh", "bps_internal.cuh"):
+    for f in ("bp.cu", "sweep_body.cuh", "bps_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1709_06509_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -183,28 +185,14 @@ def ncu_traffic(profile_name: str):
         return None
 
 
-def persistent_bytes(st, trace) -> float:
-    """Algorithmic DRAM bytes of one persistent BP launch of the u8 form.
-
-    Per recomputed pixel of a half-sweep: its int16 cost and 4 incoming uint8 messages read,
-    4 old outgoing messages read (change test of the skip) and 4 messages written, Dp labels
-    each; plus the 1-byte skip flag of every slot read per half-sweep; per scale below the
-    coarsest the copy of the even pixels' parent records (read + write); the skip flags set
-    per scale; and the read-out (cost + 4 messages read, one int32 written per pixel)."""
-    from paper_1709_06509_gb300 import level_dims
-
+def sweep_bytes(st, recomputed: int, launches: int) -> float:
+    """Algorithmic bytes of `launches` finest-scale half-sweeps of the u8 form that recomputed
+    `recomputed` pixels in total: per recomputed pixel its int16 cost, 4 incoming and 4 old
+    outgoing uint8 messages read (the old ones for the skip's change test) and 4 uint8
+    messages written, Dp labels each; plus the 1-byte skip flag of every slot per launch."""
     Dp = (st.D + 15) // 16 * 16
-    dims = level_dims(st.W, st.H, st.levels)[::-1]  # coarsest first, like the trace
-    per = ITERS * 2
-    total = 0.0
-    for k, (w, h) in enumerate(dims):
-        slots = h * ((w + 1) // 2)
-        total += float(trace[k * per:(k + 1) * per].sum()) * Dp * (2 + 12 * 1)
-        total += per * slots + 2 * slots
-        if k > 0:
-            total += 2 * slots * 4 * Dp
-    total += st.W * st.H * (Dp * (2 + 4) + 4)
-    return total
+    slots = st.H * ((st.W + 1) // 2)
+    return float(recomputed) * Dp * (2 + 12 * 1) + launches * slots
 
 
 def peaks():
@@ -240,6 +228,10 @@ def main():
         _build.build()  # no-op once rank 0 has built
 
     pairs = load_pairs(rank)
+    if args.ncu_case and args.workload:
+        from paper_1709_06509_gb300 import synth
+
+        pairs = [synth.workload_pair(args.workload)]
     ctxs, inputs, outs = [], [], []
     for pair, window in pairs:
         H, W = pair.left.shape
@@ -288,21 +280,21 @@ def main():
     units = work_units(pairs) * world
     value = units * args.steps / (total_ms / 1e3) / 1e6
 
-    # dominant kernel: the persistent BP kernel (every scale, iteration and colour, then the
-    # read-out), timed with CUDA events around its launch on the launching stream
+    # dominant kernel: the red-black sweep at the finest scale.  CUDA events around each of its
+    # launches, on the launching stream, over the same steps (with the same L2 flush)
     prof_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
     for _ in range(max(3, min(args.steps, 20))):
         for (st, window), (L, R), out in zip(ctxs, inputs, outs):
             flush.fill_(1)
             st.build_cost_volume(L, R, window, TRUNC_DATA)
             st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
-            n, ms, _px = st.read_profile()
-            prof_bytes += persistent_bytes(st, st.get_trace())
+            n, ms, px = st.read_profile()
+            prof_bytes += sweep_bytes(st, px, n)
             prof_ms += ms
             prof_launches += n
     hbm, peak_kind = peaks()
     achieved = prof_bytes / (prof_ms / 1e3) / 1e9
-    traffic = ncu_traffic("bp_persistent_u8_teddy_450x375_d64.txt")
+    traffic = ncu_traffic("sweep_u8_teddy_450x375_d64.txt")
 
     # end to end through the public API with host buffers (pinned), H2D and D2H inside
     host_in = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p, _ in pairs]
@@ -323,9 +315,9 @@ def main():
     h2d = sum(2 * p.left.size for p, _ in pairs)
     d2h = sum(4 * p.left.size + 8 for p, _ in pairs)
 
-    # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the persistent
-    # BP kernel (all scales, iterations and the read-out)
-    launches_per_pair = 1 + max(0, LEVELS - 2) + 1
+    # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the solve-start
+    # kernel, one upsample kernel per scale below the coarsest, 2 * ITERS sweeps per scale, WTA
+    launches_per_pair = 1 + max(0, LEVELS - 2) + 1 + (LEVELS - 1) + LEVELS * ITERS * 2 + 1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -337,7 +329,7 @@ def main():
                        "cost_storage": "int16", "cuda_graph": True, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "kernel": "bp_persistent_kernel<u8>",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_u8_kernel (finest scale)",
                          "peak_kind": peak_kind, "launches_timed": prof_launches},
             "e2e": {"value": units * args.steps / e2e_s / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -62,9 +62,10 @@ typedef struct bps_ctx bps_ctx;
                                  and replay it while the arguments stay the same */
 #define BPS_FLAG_PROFILE 8    /* bps_bp_solve: time the BP launches with CUDA events (read with
                                  bps_read_profile / bps_read_launch_times); not with BPS_FLAG_GRAPH */
-#define BPS_FLAG_PER_SWEEP 16 /* one kernel launch per red-black half-sweep instead of the single
-                                 persistent launch (same results; used for per-sweep tracing) */
-#define BPS_FLAG_TEST_TIMEOUT 32 /* test hook: the persistent kernel's grid barrier waits for one
+#define BPS_FLAG_PERSISTENT 16 /* run the whole solve as one persistent cooperative launch instead
+                                  of one programmatically chained launch per half-sweep (same
+                                  results) */
+#define BPS_FLAG_TEST_TIMEOUT 32 /* test hook (with BPS_FLAG_PERSISTENT): the grid barrier waits for one
                                     block more than it has, gives up after 2 ms and the solve
                                     reports BPS_ERR_TIMEOUT through bps_get_error */
 
@@ -76,6 +77,11 @@ typedef struct bps_ctx bps_ctx;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *bps_status_string(int status);
+
+/* The cudaError_t behind the calling thread's last BPS_ERR_CUDA (0 if none yet), and its
+ * name as the CUDA runtime reports it (static string). */
+int bps_last_cuda_error(void);
+const char *bps_cuda_error_string(int code);
 
 /*
  * Bytes of device workspace a context of this shape needs (cost pyramid, messages and

@@ -37,7 +37,7 @@ BPS_FLAG_FAST_SKIP = 1
 BPS_FLAG_WARM_START = 2
 BPS_FLAG_GRAPH = 4
 BPS_FLAG_PROFILE = 8
-BPS_FLAG_PER_SWEEP = 16
+BPS_FLAG_PERSISTENT = 16
 BPS_FLAG_TEST_TIMEOUT = 32
 
 BPS_MAX_LEVELS = 8
@@ -49,7 +49,11 @@ BPS_MAX_WINDOW = 31
 class BPSError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        msg = f"{what}: {status_string(status)} ({status})"
+        if status == BPS_ERR_CUDA:
+            code = lib().bps_last_cuda_error()
+            msg += f": {lib().bps_cuda_error_string(code).decode()} ({code})"
+        super().__init__(msg)
 
 
 _lib = None
@@ -72,6 +76,8 @@ _SIGS = {
     "bps_read_profile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "bps_read_launch_times": (_I, [_P, _P, _I]),
     "bps_get_error": (_I, [_P]),
+    "bps_last_cuda_error": (_I, []),
+    "bps_cuda_error_string": (ctypes.c_char_p, [_I]),
 }
 
 
@@ -183,6 +189,14 @@ def bps_read_profile(ctx):
     return n.value, ms.value, px.value
 
 
+def bps_last_cuda_error() -> int:
+    return lib().bps_last_cuda_error()
+
+
+def bps_cuda_error_string(code: int) -> str:
+    return lib().bps_cuda_error_string(code).decode()
+
+
 def bps_get_error(ctx) -> int:
     """BPS_OK or BPS_ERR_TIMEOUT for the last persistent solve (returned, not raised)."""
     rc = lib().bps_get_error(ctx)
@@ -251,10 +265,10 @@ class Stereo:
         return ncc
 
     def bp_solve(self, iters: int, lam: int, trunc: int, levels: int | None = None, skip: bool = True,
-                 init_msgs=None, profile: bool = False, per_sweep: bool = False, test_timeout: bool = False,
+                 init_msgs=None, profile: bool = False, persistent: bool = False, test_timeout: bool = False,
                  stream=None):
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_WARM_START if init_msgs is not None else 0)
-        flags |= (BPS_FLAG_PROFILE if profile else 0) | (BPS_FLAG_PER_SWEEP if per_sweep else 0)
+        flags |= (BPS_FLAG_PROFILE if profile else 0) | (BPS_FLAG_PERSISTENT if persistent else 0)
         flags |= BPS_FLAG_TEST_TIMEOUT if test_timeout else 0
         bps_bp_solve(self.ctx, levels or self.levels, iters, lam, trunc, flags, init_msgs, stream)
 
@@ -274,12 +288,12 @@ class Stereo:
         return ei, ef
 
     def stereo(self, left, right, window, trunc_data, iters, lam, trunc, skip=True, graph=False, out=None,
-               per_sweep=False, stream=None):
+               persistent=False, stream=None):
         import torch
 
         out = out if out is not None else torch.empty((self.H, self.W), dtype=torch.int32, device=self.device)
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
-        flags |= BPS_FLAG_PER_SWEEP if per_sweep else 0
+        flags |= BPS_FLAG_PERSISTENT if persistent else 0
         bps_stereo(self.ctx, left, right, left.stride(0), window, trunc_data, iters, lam, trunc, flags, out, stream)
         return out
 

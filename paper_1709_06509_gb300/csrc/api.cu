@@ -142,10 +142,24 @@ constexpr unsigned long long TEST_TIMEOUT_NS = 2000000ull;        // 2 ms, for B
 
 }  // namespace
 
-#define CK(x)                                     \
-    do {                                          \
-        if ((x) != cudaSuccess) return BPS_ERR_CUDA; \
+// The CUDA error behind the last BPS_ERR_CUDA of this thread (see bps_last_cuda_error).
+static thread_local int g_last_cuda_error = 0;
+
+static int cuda_failed(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    cudaGetLastError();  // clear a sticky launch error so the context stays usable
+    return BPS_ERR_CUDA;
+}
+
+#define CK(x)                                          \
+    do {                                               \
+        const cudaError_t ck_e_ = (x);                 \
+        if (ck_e_ != cudaSuccess) return cuda_failed(ck_e_); \
     } while (0)
+
+extern "C" int bps_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" const char *bps_cuda_error_string(int code) { return cudaGetErrorString((cudaError_t)code); }
 
 extern "C" const char *bps_status_string(int s) {
     switch (s) {
@@ -230,6 +244,9 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     // that no attribute call happens while a launch sequence is being captured
     ok = ok && ncc_prepare(c->cost_kind, D, BPS_MAX_WINDOW) == cudaSuccess;
     ok = ok && ncc_rows_prepare(c->cost_kind, D, c->Dp) == cudaSuccess;
+    ok = ok && preload_cost_kernels(c->cost_kind) == cudaSuccess;
+    ok = ok && preload_bp_kernels(c->msg_kind) == cudaSuccess;
+    ok = ok && preload_readout_kernels(c->msg_kind) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->ws, 0, p.total, c->cap) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->d_desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->cap) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->d_prefix, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice,
@@ -307,7 +324,7 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
     if (!c->has_cost) return BPS_ERR_STATE;
     if (levels < 1 || levels > c->levels || iters < 0 || iters > BPS_MAX_ITERS || lambda < 0 || trunc < 0 ||
         (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_WARM_START | BPS_FLAG_GRAPH | BPS_FLAG_PROFILE |
-                   BPS_FLAG_PER_SWEEP | BPS_FLAG_TEST_TIMEOUT)) ||
+                   BPS_FLAG_PERSISTENT | BPS_FLAG_TEST_TIMEOUT)) ||
         (int64_t)lambda * ((int64_t)c->Dp + trunc) >= ((int64_t)1 << 24) ||
         ((flags & BPS_FLAG_WARM_START) && !init))
         return BPS_ERR_ARG;
@@ -353,7 +370,7 @@ static PersistParams persist_params(int npairs, const PairDesc *pairs, const int
 // The whole solve (and the read-out into disp when it is not NULL) as one persistent launch.
 static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
                       cudaStream_t st, int32_t *disp = nullptr) {
-    if (flags & BPS_FLAG_PER_SWEEP) {
+    if (!(flags & BPS_FLAG_PERSISTENT)) {
         const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st);
         if (rc == BPS_OK && disp) CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
         return rc;
@@ -397,7 +414,6 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
     const int top = levels - 1;
     const int ntrace = levels * iters * 2;
-    if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
     if (prof) {
         const size_t need = 2 * (size_t)levels * iters * 2;
         while (c->ev.size() < need) {
@@ -410,21 +426,16 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         c->prof_first_trace = top * iters * 2;
         c->prof_trace_n = iters * 2;
     }
-    {
-        const int rc = enqueue_start(c, top, flags, init, st);
-        if (rc != BPS_OK) return rc;
-    }
+    // a chain of kernels only (no memset nodes), so that every launch overlaps its predecessor
+    const bool warm = (flags & BPS_FLAG_WARM_START) != 0;
+    if (warm) CK(launch_import_msgs(c->msg_kind, c->lv[top], c->D, c->Dp, init, st));
+    CK(launch_solve_start(c->msg_kind, c->lv[top], c->Dp, warm ? 0 : 1, skip ? 1 : 0, c->trace, ntrace, st));
     int t = 0;
     for (int l = top; l >= 0; --l) {
         const LevelView &v = c->lv[l];
-        if (l < top) {
-            // only the even pixels' start messages are ever read: the first half-sweep overwrites
-            // every existing incoming slot of the odd pixels (unless there is no sweep at all)
-            CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, 0, c->Dp, st));
-            if (iters == 0) CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, 1, c->Dp, st));
-        }
-        if (skip)
-            for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(v.dirty[k], 1, (size_t)v.H * v.Wh, st));
+        // only the even pixels' start messages are ever read: the first half-sweep overwrites every
+        // existing incoming slot of the odd pixels (unless there is no sweep at all)
+        if (l < top) CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, iters == 0 ? 1 : 0, c->Dp, skip ? 1 : 0, st));
         for (int it = 0; it < iters; ++it)
             for (int colour = 0; colour < 2; ++colour, ++t) {
                 if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
@@ -468,7 +479,7 @@ static int enqueue_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
                           int iters, int lambda, int trunc, int flags, int32_t *disp, cudaStream_t st) {
     int rc = enqueue_cost(c, L, R, pitch, window, trunc_data, nullptr, st);
     if (rc != BPS_OK) return rc;
-    return enqueue_bp(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PER_SWEEP), nullptr,
+    return enqueue_bp(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PERSISTENT), nullptr,
                       st, disp);
 }
 
@@ -476,7 +487,7 @@ extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
                           int iters, int lambda, int trunc, int flags, int32_t *disp, void *stream) {
     int rc = check_cost_args(c, L, R, pitch, window, trunc_data);
     if (rc != BPS_OK) return rc;
-    if (!disp || (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PER_SWEEP))) return BPS_ERR_ARG;
+    if (!disp || (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT))) return BPS_ERR_ARG;
     const bool had_cost = c->has_cost;
     c->has_cost = true;  // the sequence builds the cost volume first
     rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);

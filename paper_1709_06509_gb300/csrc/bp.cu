@@ -14,12 +14,14 @@ template <typename CostT, typename MsgT>
 __global__ void __launch_bounds__(256)
 sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<MsgT>::type lam,
              typename AccOf<MsgT>::type lamT, int skip, unsigned long long *trace) {
+    pdl_enter();
     sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256, 3)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                 unsigned long long *trace) {
+    pdl_enter();
     sweep_group_u8(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
 }
 
@@ -31,9 +33,8 @@ static cudaError_t sweep_t(const LevelView &lv, int colour, int D, int Dp, int G
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     const int64_t blocks = (nslot + groups - 1) / groups;
     if (blocks == 0) return cudaSuccess;
-    sweep_kernel<CostT, MsgT><<<(unsigned)blocks, 256, 0, st>>>(lv, colour, D, Dp, Gp, (Acc)lambda,
-                                                                (Acc)lambda * (Acc)trunc, skip, trace);
-    return cudaGetLastError();
+    return launch_k(sweep_kernel<CostT, MsgT>, dim3((unsigned)blocks), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                    (Acc)lambda, (Acc)lambda * (Acc)trunc, skip, trace);
 }
 
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc,
@@ -45,8 +46,8 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
         if (blocks == 0) return cudaSuccess;
         const int lam = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
-        sweep_u8_kernel<<<(unsigned)blocks, 256, 0, st>>>(lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace);
-        return cudaGetLastError();
+        return launch_k(sweep_u8_kernel, dim3((unsigned)blocks), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                        lam * trunc, skip, trace);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -55,22 +56,56 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
 // ------------------------------------------------------------------ coarse-to-fine start
 // Fine pixel (x, y) of `colour` copies the whole message record of its parent
 // (x >> 1, y >> 1) in 16-byte chunks.
-__global__ void upsample_kernel(LevelView coarse, LevelView fine, int colour, int rec_chunks) {
+__global__ void upsample_kernel(LevelView coarse, LevelView fine, int both_colours, int rec_chunks, int set_dirty) {
+    pdl_enter();
     const int64_t n = (int64_t)fine.H * fine.Wh * rec_chunks;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-        upsample_chunk(coarse, fine, colour, rec_chunks, k);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int colour = 0; colour <= both_colours; ++colour)
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride)
+            upsample_chunk(coarse, fine, colour, rec_chunks, k);
+    if (set_dirty) {
+        const int64_t m = (int64_t)fine.H * fine.Wh;
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += stride)
+            fine.dirty[0][k] = fine.dirty[1][k] = 1;
+    }
+}
+
+__global__ void solve_start_kernel(LevelView top, int rec_words, int zero_msgs, int set_dirty,
+                                   unsigned long long *trace, int ntrace) {
+    pdl_enter();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t slots = (int64_t)top.H * top.Wh;
+    if (zero_msgs) {
+        const int64_t n = slots * rec_words;  // 16-byte words of one colour's message array
+        for (int64_t k = t0; k < n; k += stride) {
+            reinterpret_cast<uint4 *>(top.msg[0])[k] = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<uint4 *>(top.msg[1])[k] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    if (set_dirty)
+        for (int64_t k = t0; k < slots; k += stride) top.dirty[0][k] = top.dirty[1][k] = 1;
+    for (int64_t k = t0; k < ntrace; k += stride) trace[k] = 0ull;
 }
 
 static int msg_bytes(int msg_kind) { return msg_kind == MSG_I32 ? 4 : (msg_kind == MSG_U8 ? 1 : 2); }
 
 static unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
 
-cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int colour, int Dp,
-                            cudaStream_t st) {
+cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int both_colours, int Dp,
+                            int set_dirty, cudaStream_t st) {
     const int rec_chunks = 4 * Dp * msg_bytes(msg_kind) / 16;
     const int64_t n = (int64_t)fine.H * fine.Wh * rec_chunks;
-    upsample_kernel<<<grid_for(n), 256, 0, st>>>(coarse, fine, colour, rec_chunks);
-    return cudaGetLastError();
+    return launch_k(upsample_kernel, dim3(grid_for(n)), dim3(256), 0, st, coarse, fine, both_colours, rec_chunks,
+                    set_dirty);
+}
+
+cudaError_t launch_solve_start(int msg_kind, const LevelView &top, int Dp, int zero_msgs, int set_dirty,
+                               unsigned long long *trace, int ntrace, cudaStream_t st) {
+    const int rec_words = 4 * Dp * msg_bytes(msg_kind) / 16;
+    const int64_t n = std::max<int64_t>((int64_t)top.H * top.Wh * (zero_msgs ? rec_words : 1), ntrace);
+    return launch_k(solve_start_kernel, dim3(grid_for(n)), dim3(256), 0, st, top, rec_words, zero_msgs, set_dirty,
+                    trace, ntrace);
 }
 
 // ------------------------------------------------------------------ natural-layout import / export
@@ -82,6 +117,7 @@ template <> __device__ inline __half to_msg_f<__half>(float v) { return __float2
 
 template <typename MsgT, typename SrcT>
 __global__ void import_kernel(LevelView lv, int D, int Dp, const SrcT *src) {
+    pdl_enter();
     const int64_t n = 4LL * lv.H * lv.W * Dp;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(k % Dp);
@@ -102,6 +138,7 @@ __global__ void import_kernel(LevelView lv, int D, int Dp, const SrcT *src) {
 
 template <typename MsgT, typename DstT>
 __global__ void export_msgs_kernel(LevelView lv, int D, int Dp, DstT *out) {
+    pdl_enter();
     const int64_t n = 4LL * lv.H * lv.W * D;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(k % D);
@@ -126,6 +163,7 @@ __global__ void export_msgs_kernel(LevelView lv, int D, int Dp, DstT *out) {
 
 template <typename CostT, typename DstT>
 __global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
+    pdl_enter();
     const int64_t n = (int64_t)lv.H * lv.W * D;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(k % D);
@@ -136,14 +174,35 @@ __global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
     }
 }
 
+cudaError_t preload_bp_kernels(int msg_kind) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, upsample_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, solve_start_kernel);
+    if (e != cudaSuccess) return e;
+    switch (msg_kind) {
+    case MSG_I32:
+        e = cudaFuncGetAttributes(&a, sweep_kernel<int32_t, int32_t>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<int32_t, int32_t>);
+        break;
+    case MSG_U8:
+        e = cudaFuncGetAttributes(&a, sweep_u8_kernel);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<uint8_t, int32_t>);
+        break;
+    default:
+        e = cudaFuncGetAttributes(&a, sweep_kernel<float, __half>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<__half, float>);
+        break;
+    }
+    return e;
+}
+
 cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st) {
     const unsigned g = grid_for(4LL * lv.H * lv.W * Dp);
     switch (msg_kind) {
-    case MSG_I32: import_kernel<int32_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (const int32_t *)src); break;
-    case MSG_U8: import_kernel<uint8_t, int32_t><<<g, 256, 0, st>>>(lv, D, Dp, (const int32_t *)src); break;
-    default: import_kernel<__half, float><<<g, 256, 0, st>>>(lv, D, Dp, (const float *)src); break;
+    case MSG_I32: return launch_k(import_kernel<int32_t, int32_t>, dim3(g), dim3(256), 0, st, lv, D, Dp, (const int32_t *)src);
+    case MSG_U8: return launch_k(import_kernel<uint8_t, int32_t>, dim3(g), dim3(256), 0, st, lv, D, Dp, (const int32_t *)src);
+    default: return launch_k(import_kernel<__half, float>, dim3(g), dim3(256), 0, st, lv, D, Dp, (const float *)src);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st) {

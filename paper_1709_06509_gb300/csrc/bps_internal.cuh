@@ -33,6 +33,15 @@ struct LevelView {
     uint8_t *dirty[2];
 };
 
+// Programmatic dependent launch: every kernel of the stereo chain is launched so that it may
+// start while its predecessor is still running; it waits here until the predecessor's grid
+// has completed and its writes are visible, then lets its own successor start launching.
+// Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __host__ __device__ inline int colour_of(int x, int y) { return (x + y) & 1; }
 __host__ __device__ inline int64_t slot_of(int x, int y, int Wh) { return (int64_t)y * Wh + (x >> 1); }
 

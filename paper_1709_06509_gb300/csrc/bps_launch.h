@@ -9,6 +9,25 @@
 
 namespace bps {
 
+// Launch `kernel` so that it may begin while the previous kernel on the stream finishes
+// (programmatic stream serialisation; the kernel itself waits in pdl_enter()).  Also valid
+// under stream capture, where it becomes a programmatic graph edge.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // storage kinds
 enum CostKind { COST_I32 = 0, COST_I16 = 1, COST_F32 = 2 };
 enum MsgKind { MSG_I32 = 0, MSG_U8 = 1, MSG_F16 = 2 };
@@ -32,9 +51,15 @@ cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
 // recomputed pixels.
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
                          int trunc, int skip, unsigned long long *trace, cudaStream_t st);
-// Coarse-to-fine start: copy parent messages into the fine pixels of `colour`.
-cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int colour, int Dp,
-                            cudaStream_t st);
+// Coarse-to-fine start: copy parent messages into the fine pixels of `colour` (and of the
+// other colour too when both_colours), and mark every pixel of the fine scale dirty when
+// set_dirty (fast-converging skip).
+cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelView &fine, int both_colours, int Dp,
+                            int set_dirty, cudaStream_t st);
+// Start of a solve at scale `top`: zero its messages (zero_msgs), mark its pixels dirty
+// (set_dirty) and zero ntrace trace counters, in one kernel.
+cudaError_t launch_solve_start(int msg_kind, const LevelView &top, int Dp, int zero_msgs, int set_dirty,
+                               unsigned long long *trace, int ntrace, cudaStream_t st);
 // Natural-layout [4][H][W][D] messages (int32 or float) into / out of colour-split storage.
 cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st);
 cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);
@@ -60,6 +85,12 @@ struct PersistParams {
 };
 cudaError_t persistent_grid(int form, int *grid);
 cudaError_t launch_persistent(int form, const PersistParams &P, int grid, cudaStream_t st);
+
+// Load every kernel a launch sequence may use (CUDA loads modules lazily on first use,
+// which must not happen inside a stream capture).
+cudaError_t preload_cost_kernels(int cost_kind);
+cudaError_t preload_bp_kernels(int msg_kind);
+cudaError_t preload_readout_kernels(int msg_kind);
 
 // Winner-take-all disparity at the finest scale.
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);

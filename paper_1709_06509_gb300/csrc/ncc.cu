@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(NCC_THREADS)
 ncc_cost_kernel(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R, int pitch, int W, int H,
                 int D, int Dp, int window, int T, int Wh, CostT *cost0, CostT *cost1, float *ncc_out) {
     extern __shared__ __align__(16) unsigned char smem[];
+    pdl_enter();
     const int r = window / 2;
     const int TW = NCC_TX + 2 * r;          // staged left columns
     const int RW = TW + D - 1;              // staged right columns
@@ -161,6 +162,15 @@ ncc_cost_kernel(const uint8_t *__restrict__ L, const uint8_t *__restrict__ R, in
     }
 }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared by every
+// context in the process, so it is raised once to the device's opt-in maximum; each launch
+// still requests only what its shape needs.
+static int smem_optin() {
+    int dev = 0, v = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
 // ------------------------------------------------------------------ row-streaming NCC (windows up to 15)
 // ncc_rows_kernel: a CTA owns a strip of rows [y0, y0 + TYS) and XS * 16 columns; thread
 // (label d, column group xs) owns 16 consecutive columns at one label.  Walking down the
@@ -188,6 +198,7 @@ __global__ void __launch_bounds__(512)
 ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Rimg, int pitch, int W, int H, int D,
                 int Dp, int T, int TYS, LevelView l0, LevelView l1, int write_l1, float *ncc_out) {
     using Num = typename NccInt<R>::type;
+    pdl_enter();
     constexpr int WIN = 2 * R + 1, RING = 2 * R + 2, VN = NR_TX + 2 * R;
     extern __shared__ __align__(16) unsigned char smem[];
     const int XS = blockDim.x / Dp;
@@ -362,8 +373,11 @@ template <typename CostT, int R>
 static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp, int T,
                                  const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st, bool prep) {
     const size_t smem = ncc_rows_smem_bytes(D, Dp, 2 * R + 1);
-    if (prep)
-        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (prep) {
+        if ((int)smem > smem_optin()) return cudaErrorInvalidValue;
+        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_optin());
+    }
     const int XS = Dp >= 256 ? 1 : 256 / Dp;
     const int threads = XS * Dp;
     const int CW = XS * NR_TX;
@@ -373,9 +387,8 @@ static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch
     tys = std::max(8, std::min(64, (tys + 1) & ~1));
     const int ny = (H + tys - 1) / tys;
     LevelView none = l0;
-    ncc_rows_kernel<CostT, R><<<dim3(nx, ny), threads, smem, st>>>(L, Rim, pitch, W, H, D, Dp, T, tys, l0,
-                                                                   l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
-    return cudaGetLastError();
+    return launch_k(ncc_rows_kernel<CostT, R>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp, T,
+                    tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
 }
 
 template <typename CostT>
@@ -432,13 +445,13 @@ static cudaError_t launch_ncc_t(const uint8_t *L, const uint8_t *R, int pitch, i
                                 int window, int T, int Wh, void *c0, void *c1, float *ncc_out, cudaStream_t st) {
     const size_t smem = ncc_smem_bytes(D, window);
     dim3 grid((W + NCC_TX - 1) / NCC_TX, (H + NCC_TY - 1) / NCC_TY);
-    ncc_cost_kernel<CostT><<<grid, NCC_THREADS, smem, st>>>(L, R, pitch, W, H, D, Dp, window, T, Wh,
-                                                            (CostT *)c0, (CostT *)c1, ncc_out);
-    return cudaGetLastError();
+    return launch_k(ncc_cost_kernel<CostT>, grid, dim3(NCC_THREADS), smem, st, L, R, pitch, W, H, D, Dp, window, T,
+                    Wh, (CostT *)c0, (CostT *)c1, ncc_out);
 }
 
 cudaError_t ncc_prepare(int cost_kind, int D, int max_window) {
-    const int smem = (int)ncc_smem_bytes(D, max_window);
+    if ((int)ncc_smem_bytes(D, max_window) > smem_optin()) return cudaErrorInvalidValue;
+    const int smem = smem_optin();
     switch (cost_kind) {
     case COST_I32: return cudaFuncSetAttribute(ncc_cost_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     case COST_I16: return cudaFuncSetAttribute(ncc_cost_kernel<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -461,6 +474,7 @@ cudaError_t launch_ncc(int cost_kind, const uint8_t *L, const uint8_t *R, int pi
 // 2y + b) sits at fine slot (2y + b) * Wh_f + x.
 template <typename CostT>
 __global__ void pyramid_kernel(LevelView fine, LevelView coarse, int Dp) {
+    pdl_enter();
     using Acc = typename std::conditional<CostOut<CostT>::is_float, float, int>::type;
     const int64_t n = (int64_t)coarse.H * coarse.W * Dp;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -481,15 +495,23 @@ __global__ void pyramid_kernel(LevelView fine, LevelView coarse, int Dp) {
     }
 }
 
+cudaError_t preload_cost_kernels(int cost_kind) {
+    cudaFuncAttributes a;
+    switch (cost_kind) {
+    case COST_I32: return cudaFuncGetAttributes(&a, pyramid_kernel<int32_t>);
+    case COST_I16: return cudaFuncGetAttributes(&a, pyramid_kernel<int16_t>);
+    default: return cudaFuncGetAttributes(&a, pyramid_kernel<float>);
+    }
+}
+
 cudaError_t launch_pyramid(int cost_kind, const LevelView &fine, const LevelView &coarse, int Dp, cudaStream_t st) {
     const int64_t n = (int64_t)coarse.H * coarse.W * Dp;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     switch (cost_kind) {
-    case COST_I32: pyramid_kernel<int32_t><<<blocks, 256, 0, st>>>(fine, coarse, Dp); break;
-    case COST_I16: pyramid_kernel<int16_t><<<blocks, 256, 0, st>>>(fine, coarse, Dp); break;
-    default: pyramid_kernel<float><<<blocks, 256, 0, st>>>(fine, coarse, Dp); break;
+    case COST_I32: return launch_k(pyramid_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, fine, coarse, Dp);
+    case COST_I16: return launch_k(pyramid_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, fine, coarse, Dp);
+    default: return launch_k(pyramid_kernel<float>, dim3(blocks), dim3(256), 0, st, fine, coarse, Dp);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace bps

@@ -20,18 +20,27 @@ namespace bps {
 
 template <typename CostT, typename MsgT>
 __global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, int Gp, int32_t *disp) {
+    pdl_enter();
     wta_group<CostT, MsgT>(lv, D, Dp, Gp, disp, blockIdx.x);
+}
+
+cudaError_t preload_readout_kernels(int msg_kind) {
+    cudaFuncAttributes a;
+    switch (msg_kind) {
+    case MSG_I32: return cudaFuncGetAttributes(&a, wta_kernel<int32_t, int32_t>);
+    case MSG_U8: return cudaFuncGetAttributes(&a, wta_kernel<int16_t, uint8_t>);
+    default: return cudaFuncGetAttributes(&a, wta_kernel<float, __half>);
+    }
 }
 
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st) {
     const int groups = 256 / Gp;
     const int64_t blocks = ((int64_t)lv.W * lv.H + groups - 1) / groups;
     switch (msg_kind) {
-    case MSG_I32: wta_kernel<int32_t, int32_t><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
-    case MSG_U8: wta_kernel<int16_t, uint8_t><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
-    default: wta_kernel<float, __half><<<(unsigned)blocks, 256, 0, st>>>(lv, D, Dp, Gp, disp); break;
+    case MSG_I32: return launch_k(wta_kernel<int32_t, int32_t>, dim3((unsigned)blocks), dim3(256), 0, st, lv, D, Dp, Gp, disp);
+    case MSG_U8: return launch_k(wta_kernel<int16_t, uint8_t>, dim3((unsigned)blocks), dim3(256), 0, st, lv, D, Dp, Gp, disp);
+    default: return launch_k(wta_kernel<float, __half>, dim3((unsigned)blocks), dim3(256), 0, st, lv, D, Dp, Gp, disp);
     }
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ energy
@@ -58,6 +67,7 @@ __device__ inline Sum block_sum(Sum v, Sum *sh) {
 template <typename CostT>
 __global__ void __launch_bounds__(E_THREADS)
 energy_partial_kernel(LevelView lv, int D, int Dp, const int32_t *disp, int lambda, int trunc, void *partials) {
+    pdl_enter();
     using Sum = typename std::conditional<std::is_same<CostT, float>::value, double, long long>::type;
     __shared__ Sum sh[E_THREADS / 32];
     Sum acc = Sum(0);
@@ -83,6 +93,7 @@ energy_partial_kernel(LevelView lv, int D, int Dp, const int32_t *disp, int lamb
 template <typename Sum>
 __global__ void __launch_bounds__(E_THREADS)
 energy_final_kernel(const void *partials, int nblocks, int64_t *out_i64, double *out_f64) {
+    pdl_enter();
     __shared__ Sum sh[E_THREADS / 32];
     Sum acc = Sum(0);
     for (int k = threadIdx.x; k < nblocks; k += blockDim.x) acc += reinterpret_cast<const Sum *>(partials)[k];
@@ -96,21 +107,31 @@ energy_final_kernel(const void *partials, int nblocks, int64_t *out_i64, double 
 cudaError_t launch_energy(int cost_kind, const LevelView &lv, int D, int Dp, const int32_t *disp, int lambda,
                           int trunc, void *partials, int64_t *out_i64, double *out_f64, cudaStream_t st) {
     const int nb = energy_blocks(lv.W, lv.H);
+    cudaError_t e = cudaSuccess;
     switch (cost_kind) {
     case COST_I32:
-        energy_partial_kernel<int32_t><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
-        energy_final_kernel<long long><<<1, E_THREADS, 0, st>>>(partials, nb, out_i64, out_f64);
+        e = launch_k(energy_partial_kernel<int32_t>, dim3(nb), dim3(E_THREADS), 0, st, lv, D, Dp, disp, lambda, trunc,
+                     partials);
+        if (e == cudaSuccess)
+            e = launch_k(energy_final_kernel<long long>, dim3(1), dim3(E_THREADS), 0, st, (const void *)partials, nb,
+                         out_i64, out_f64);
         break;
     case COST_I16:
-        energy_partial_kernel<int16_t><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
-        energy_final_kernel<long long><<<1, E_THREADS, 0, st>>>(partials, nb, out_i64, out_f64);
+        e = launch_k(energy_partial_kernel<int16_t>, dim3(nb), dim3(E_THREADS), 0, st, lv, D, Dp, disp, lambda, trunc,
+                     partials);
+        if (e == cudaSuccess)
+            e = launch_k(energy_final_kernel<long long>, dim3(1), dim3(E_THREADS), 0, st, (const void *)partials, nb,
+                         out_i64, out_f64);
         break;
     default:
-        energy_partial_kernel<float><<<nb, E_THREADS, 0, st>>>(lv, D, Dp, disp, lambda, trunc, partials);
-        energy_final_kernel<double><<<1, E_THREADS, 0, st>>>(partials, nb, nullptr, out_f64);
+        e = launch_k(energy_partial_kernel<float>, dim3(nb), dim3(E_THREADS), 0, st, lv, D, Dp, disp, lambda, trunc,
+                     partials);
+        if (e == cudaSuccess)
+            e = launch_k(energy_final_kernel<double>, dim3(1), dim3(E_THREADS), 0, st, (const void *)partials, nb,
+                         (int64_t *)nullptr, out_f64);
         break;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace bps

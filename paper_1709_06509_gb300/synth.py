@@ -158,6 +158,7 @@ WORKLOADS = {
     "tsukuba_384x288_d16": (384, 288, 16, 7, 8, 3.0, 2),
     "teddy_450x375_d64": (450, 375, 64, 7, 8, 3.0, 3),
     "hd_1920x1080_d256": (1920, 1080, 256, 9, 8, 3.0, 5),
+    "qhd_960x540_d256": (960, 540, 256, 9, 8, 3.0, 6),  # a quarter of the HD pair, for profiling
 }
 
 

@@ -31,13 +31,13 @@ def to_dev(a):
 
 
 def run_gpu(L, R, D, window, trunc_data, levels, iters, lam, trunc, msg_type, skip=True, init=None,
-            per_sweep=False):
+            persistent=False):
     H, W = L.shape
     with bps.Stereo(W, H, D, levels, msg_type, device=DEV) as st:
         ncc = st.build_cost_volume(to_dev(L), to_dev(R), window, trunc_data, want_ncc=True)
         costs = [st.export_cost(l).cpu().numpy() for l in range(levels)]
         st.bp_solve(iters, lam, trunc, skip=skip, init_msgs=None if init is None else to_dev(init),
-                    per_sweep=per_sweep)
+                    persistent=persistent)
         assert st.get_error() == bps.BPS_OK
         disp = st.wta_disparity()
         ei, ef = st.energy(disp, lam, trunc)
@@ -84,16 +84,16 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("per_sweep", [False, True], ids=["persistent", "per_sweep"])
+@pytest.mark.parametrize("persistent", [False, True], ids=["chained", "persistent"])
 @pytest.mark.parametrize("msg_type", INT_FORMS)
 @pytest.mark.parametrize("skip", [True, False])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
-def test_int_parity(case, skip, msg_type, per_sweep):
+def test_int_parity(case, skip, msg_type, persistent):
     W, H, D, window, levels, iters, lam, trunc = case
     if msg_type == bps.BPS_MSG_U8 and lam * trunc > 255:
         pytest.skip("outside the u8 range")
     pair = synth.make_pair(100 + W + H + D, W, H, D, 3, 2.0)
-    g = run_gpu(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, msg_type, skip, per_sweep=per_sweep)
+    g = run_gpu(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, msg_type, skip, persistent=persistent)
     assert_int_parity(g, pair.left, pair.right, D, window, 20, levels, iters, lam, trunc, skip)
 
 
@@ -103,10 +103,10 @@ def test_barrier_timeout_is_reported_and_the_context_survives():
     pair = synth.make_pair(31, 64, 48, 16, 3, 2.0)
     with bps.Stereo(64, 48, 16, 3, bps.BPS_MSG_U8, device=DEV) as st:
         st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 5, 20)
-        st.bp_solve(4, 10, 2, test_timeout=True)
+        st.bp_solve(4, 10, 2, persistent=True, test_timeout=True)
         torch.cuda.synchronize()
         assert st.get_error() == bps.BPS_ERR_TIMEOUT
-        st.bp_solve(4, 10, 2)
+        st.bp_solve(4, 10, 2, persistent=True)
         disp = st.wta_disparity()
         torch.cuda.synchronize()
         assert st.get_error() == bps.BPS_OK
@@ -176,7 +176,7 @@ def test_graph_replay_and_host_entry():
     L, R = to_dev(pair.left), to_dev(pair.right)
     with bps.Stereo(96, 72, 16, 4, bps.BPS_MSG_U8, device=DEV) as st:
         plain = st.stereo(L, R, 5, 20, 10, 10, 2, graph=False).clone()
-        sweeps = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True, per_sweep=True).clone()
+        sweeps = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True, persistent=True).clone()
         g1 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()
         g2 = st.stereo(L, R, 5, 20, 10, 10, 2, graph=True).clone()   # replay
         g3 = st.stereo(L, R, 5, 20, 6, 10, 2, graph=True).clone()    # new arguments: re-capture
@@ -191,6 +191,21 @@ def test_graph_replay_and_host_entry():
     ref6 = oracle.stereo_int(pair.left, pair.right, 16, 5, 20, 4, 6, 10, 2)
     assert np.array_equal(g3.cpu().numpy(), ref6["disp"])
     assert np.array_equal(hd.numpy(), ref["disp"]) and he == ref["energy"]
+
+
+def test_contexts_of_different_shapes_coexist():
+    # kernel attributes are process-wide: creating a second context must not break the first
+    pairs = [synth.make_pair(40 + k, W, H, D, 3, 2.0) for k, (W, H, D) in enumerate([(80, 40, 16), (60, 30, 64)])]
+    ctxs = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 3, bps.BPS_MSG_U8, device=DEV) for p in pairs]
+    try:
+        for rep in range(2):
+            for p, st in zip(pairs, ctxs):
+                d = st.stereo(to_dev(p.left), to_dev(p.right), 5, 20, 4, 10, 2, graph=bool(rep))
+                ref = oracle.stereo_int(p.left, p.right, p.D, 5, 20, 3, 4, 10, 2)
+                assert np.array_equal(d.cpu().numpy(), ref["disp"])
+    finally:
+        for st in ctxs:
+            st.close()
 
 
 def test_argument_errors_on_a_live_context():
