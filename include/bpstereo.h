@@ -222,6 +222,34 @@ int bps_read_profile(bps_ctx *ctx, int *h_launches, double *h_total_ms, int64_t 
  */
 int bps_read_launch_times(bps_ctx *ctx, double *h_ms, int cap);
 
+/*
+ * Energy of a labelling without allocating any memory.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory when they need the
+ * energy -- code running while a CUDA graph is being captured, real-time loops that may not
+ * wait on an allocator, programs whose allocator this library cannot reach.
+ *
+ * Computes E(d) = sum_p cost(p, d_p) + sum over right and down grid edges of
+ * lambda * min(|d_p - d_q|, trunc), exactly, in int64, from
+ *   d_cost   device int32 [H][W][D], natural layout (e.g. what bps_export_cost writes),
+ *   d_disp   device int32 [H][W] labels (values outside [0, D) are clamped),
+ * into d_energy (device int64).  Asynchronous on `stream`.  Caller owns all three buffers.
+ *
+ * Scratch: one partial sum per 1024 pixels in a fixed array compiled into the library
+ * (BPS_NOALLOC_MAX_BLOCKS entries, 128 KiB of device memory on every GPU that loads the
+ * library, held until the process exits); nothing is allocated, no cudaMalloc or cudaFree is
+ * called.  Images with more than BPS_NOALLOC_MAX_PIXELS pixels are rejected with
+ * BPS_ERR_UNSUPPORTED before anything is launched.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race on it; calls in order on one stream are
+ * safe.  Errors: BPS_ERR_ARG (NULL pointer, sizes < 1, lambda or trunc < 0),
+ * BPS_ERR_UNSUPPORTED (too many pixels), BPS_ERR_CUDA.
+ */
+#define BPS_NOALLOC_MAX_BLOCKS 16384
+#define BPS_NOALLOC_MAX_PIXELS (BPS_NOALLOC_MAX_BLOCKS * 1024)
+int bps_energy_noalloc(const int32_t *d_cost, const int32_t *d_disp, int W, int H, int D, int lambda, int trunc,
+                       int64_t *d_energy, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,8 @@ BPS_MAX_LEVELS = 8
 BPS_MAX_D = 512
 BPS_MAX_ITERS = 1024
 BPS_MAX_WINDOW = 31
+BPS_NOALLOC_MAX_BLOCKS = 16384
+BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
 
 class BPSError(RuntimeError):
@@ -78,6 +80,7 @@ _SIGS = {
     "bps_get_error": (_I, [_P]),
     "bps_last_cuda_error": (_I, []),
     "bps_cuda_error_string": (ctypes.c_char_p, [_I]),
+    "bps_energy_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
 }
 
 
@@ -187,6 +190,13 @@ def bps_read_profile(ctx):
     n, ms, px = _I(), ctypes.c_double(), _I64()
     _check(lib().bps_read_profile(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(px)), "bps_read_profile")
     return n.value, ms.value, px.value
+
+
+def bps_energy_noalloc(cost, disp, W, H, D, lam, trunc, energy, stream=None):
+    """Energy of `disp` over the natural-layout int32 cost volume `cost`, into the int64
+    device tensor `energy`, with no memory allocated (scratch is a fixed device array)."""
+    _check(lib().bps_energy_noalloc(_ptr(cost), _ptr(disp), W, H, D, lam, trunc, _ptr(energy), _stream(stream)),
+           "bps_energy_noalloc")
 
 
 def bps_last_cuda_error() -> int:
