@@ -6,7 +6,8 @@ a 384x288 pair with D=16 and a 450x375 pair with D=64, 7x7 NCC window, data cost
 quantised with trunc 20, 4 scales, 10 iterations per scale, lambda=10, trunc=2, the
 fast-converging skip on, integer messages in uint8 storage (bit-exact with the int32
 method).  Seeded synthetic pairs stand in for the Middlebury images.  One step = both
-pairs through bps_stereo (a CUDA graph replay each).  The working set is smaller than
+pairs as one bps_batch_stereo call (one CUDA graph replay whose branches are the pairs'
+launch chains, running concurrently).  The working set is smaller than
 L2, so a 256 MiB buffer is written between timed steps to flush it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -42,6 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the HBM-sized roofline_large measurement")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
     ap.add_argument("--workload", default=None,
@@ -201,6 +203,44 @@ def sweep_bytes(st, trace) -> float:
     return total
 
 
+def large_roofline(dev, flush) -> dict:
+    """The same sweep kernel on an HBM-sized working set: the 960x540 pair with D=256 (9x9
+    window; 1.1 GB of state, far above L2).  Per-launch CUDA events over every finest-scale
+    half-sweep of three solves; algorithmic bytes from the live trace as in sweep_bytes()."""
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import level_dims, synth
+
+    pair, window = synth.workload_pair("qhd_960x540_d256")
+    H, W = pair.left.shape
+    st = bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev)
+    L = torch_from(pair.left, dev)
+    R = torch_from(pair.right, dev)
+    Dp = (st.D + 15) // 16 * 16
+    w0, h0 = level_dims(W, H, LEVELS)[0]
+    slots = h0 * ((w0 + 1) // 2)
+    ms, nbytes = 0.0, 0.0
+    for _ in range(3):
+        flush.fill_(2)
+        st.build_cost_volume(L, R, window, TRUNC_DATA)
+        st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
+        t = st.read_launch_times()[-2 * ITERS:]
+        tr = st.get_trace()[-2 * ITERS:]
+        ms += float(t.sum())
+        nbytes += float(tr.sum()) * Dp * (2 + 12) + len(t) * slots
+    st.close()
+    hbm, kind = peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"workload": "960x540 D256 pair, 9x9 window, finest-scale half-sweeps", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "sweep_u8_kernel", "peak_kind": kind}
+
+
+def torch_from(a, dev):
+    import torch
+
+    return torch.from_numpy(a).to(dev)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -248,9 +288,14 @@ def main():
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # one step = every pair of the workload as one batch: one CUDA graph whose branches are the
+    # pairs' launch chains, so the pairs run concurrently
+    batch = bps.Batch([st for st, _ in ctxs])
+    windows = [w for _, w in ctxs]
+    Ls, Rs = [L for L, _ in inputs], [R for _, R in inputs]
+
     def step():
-        for (st, window), (L, R), out in zip(ctxs, inputs, outs):
-            st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, out=out)
+        batch.stereo(Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, outs=outs)
 
     for _ in range(args.warmup):
         step()
@@ -302,17 +347,17 @@ def main():
     achieved = prof_bytes / (prof_ms / 1e3) / 1e9
     traffic = ncu_traffic("sweep_u8_tsukuba_teddy_pairs.txt")
 
-    # end to end through the public API with host buffers (pinned), H2D and D2H inside
-    host_in = [(torch.from_numpy(p.left).pin_memory(), torch.from_numpy(p.right).pin_memory()) for p, _ in pairs]
+    # end to end through the public API with host buffers (pinned): bps_batch_stereo_host copies
+    # both pairs' images in, runs the batch, and copies disparities and energies out, every step
+    host_in_l = [torch.from_numpy(p.left).pin_memory() for p, _ in pairs]
+    host_in_r = [torch.from_numpy(p.right).pin_memory() for p, _ in pairs]
     host_out = [torch.empty(p.left.shape, dtype=torch.int32).pin_memory() for p, _ in pairs]
     for _ in range(3):
-        for (st, window), (hl, hr), hd in zip(ctxs, host_in, host_out):
-            st.stereo_host(hl, hr, window, TRUNC_DATA, ITERS, LAM, TRUNC, h_disp=hd)
+        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for (st, window), (hl, hr), hd in zip(ctxs, host_in, host_out):
-            st.stereo_host(hl, hr, window, TRUNC_DATA, ITERS, LAM, TRUNC, h_disp=hd)
+        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
     e2e_s = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
@@ -324,6 +369,7 @@ def main():
     # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the solve-start
     # kernel, one upsample kernel per scale below the coarsest, 2 * ITERS sweeps per scale, WTA
     launches_per_pair = 1 + max(0, LEVELS - 2) + 1 + (LEVELS - 1) + LEVELS * ITERS * 2 + 1
+    large = large_roofline(dev, flush) if rank == 0 and not args.no_large else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -332,7 +378,7 @@ def main():
             "config": {"workload": "384x288 D16 + 450x375 D64 pairs (one step = both)", "window": 7,
                        "trunc_data": TRUNC_DATA, "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC,
                        "fast_skip": True, "message_storage": "uint8 (exact: 0 <= m <= lambda*trunc)",
-                       "cost_storage": "int16", "cuda_graph": True, "l2": "flushed between timed steps (256 MiB write)",
+                       "cost_storage": "int16", "cuda_graph": True, "batch": "both pairs, concurrent graph branches", "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_u8_kernel (all scales, both pairs)",
@@ -342,9 +388,12 @@ def main():
             "gpu_launches": launches_per_pair * len(pairs) * args.steps,
             "clocks": clocks,
         }
+        if large:
+            line["roofline_large"] = large
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pairs)
         print(json.dumps(line))
+    batch.close()
     for st, _ in ctxs:
         st.close()
     if world > 1:

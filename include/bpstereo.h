@@ -223,6 +223,40 @@ int bps_read_profile(bps_ctx *ctx, int *h_launches, double *h_total_ms, int64_t 
 int bps_read_launch_times(bps_ctx *ctx, double *h_ms, int cap);
 
 /*
+ * Batches: several contexts (pairs of possibly different sizes and label counts, all with
+ * the same number of scales and the same numerical form) processed together.
+ * bps_batch_stereo runs, for every pair i, the whole path of bps_stereo on
+ * (d_lefts[i], d_rights[i], pitches[i], windows[i]) into d_disps[i]:
+ *   - by default each pair's launch chain runs on its own branch stream, forked from and
+ *     joined back into `stream`, so the pairs' chains run concurrently;
+ *   - with BPS_FLAG_PERSISTENT the cost volumes run on the branches, then ONE persistent
+ *     cooperative launch solves every pair in lockstep and writes every read-out;
+ *   - with BPS_FLAG_GRAPH the whole batch is recorded once as one CUDA graph and replayed
+ *     while every argument is unchanged.
+ * The host arrays (d_lefts ... d_disps) hold n entries each and are read during the call
+ * only.  A batch keeps pointers to its contexts: destroy the batch before them.
+ * bps_batch_get_error reports BPS_ERR_TIMEOUT when the last persistent launch gave up.
+ */
+typedef struct bps_batch bps_batch;
+#define BPS_MAX_BATCH 256
+int bps_batch_create(bps_batch **out, bps_ctx *const *ctxs, int n);
+int bps_batch_destroy(bps_batch *batch);
+int bps_batch_stereo(bps_batch *batch, const uint8_t *const *d_lefts, const uint8_t *const *d_rights,
+                     const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
+                     int flags, int32_t *const *d_disps, void *stream);
+int bps_batch_get_error(bps_batch *batch);
+
+/*
+ * bps_batch_stereo from host buffers: copies every pair's images (pitches[i] bytes per row)
+ * to its context's staging buffers, runs the batch, computes every pair's energy into
+ * h_energies[i] (int64, integer forms; nullable) and copies every disparity map (int32
+ * [H_i][W_i]) to h_disps[i].  Synchronous.  Pinned host memory makes the copies asynchronous.
+ */
+int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const uint8_t *const *h_rights,
+                          const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
+                          int flags, int32_t *const *h_disps, int64_t *h_energies, void *stream);
+
+/*
  * Energy of a labelling without allocating any memory.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory when they need the
  * energy -- code running while a CUDA graph is being captured, real-time loops that may not

@@ -44,6 +44,7 @@ BPS_MAX_LEVELS = 8
 BPS_MAX_D = 512
 BPS_MAX_ITERS = 1024
 BPS_MAX_WINDOW = 31
+BPS_MAX_BATCH = 256
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
@@ -81,6 +82,11 @@ _SIGS = {
     "bps_last_cuda_error": (_I, []),
     "bps_cuda_error_string": (ctypes.c_char_p, [_I]),
     "bps_energy_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "bps_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),
+    "bps_batch_destroy": (_I, [_P]),
+    "bps_batch_stereo": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "bps_batch_get_error": (_I, [_P]),
+    "bps_batch_stereo_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
 }
 
 
@@ -197,6 +203,48 @@ def bps_energy_noalloc(cost, disp, W, H, D, lam, trunc, energy, stream=None):
     device tensor `energy`, with no memory allocated (scratch is a fixed device array)."""
     _check(lib().bps_energy_noalloc(_ptr(cost), _ptr(disp), W, H, D, lam, trunc, _ptr(energy), _stream(stream)),
            "bps_energy_noalloc")
+
+
+def bps_batch_create(ctxs) -> int:
+    arr = (_P * len(ctxs))(*ctxs)
+    out = _P()
+    _check(lib().bps_batch_create(ctypes.byref(out), arr, len(ctxs)), "bps_batch_create")
+    return out.value
+
+
+def bps_batch_destroy(batch: int) -> None:
+    _check(lib().bps_batch_destroy(batch), "bps_batch_destroy")
+
+
+def bps_batch_stereo(batch, lefts, rights, pitches, windows, trunc_data, iters, lam, trunc, flags, disps,
+                     stream=None):
+    n = len(lefts)
+    P = (_P * n)(*[_ptr(t) for t in lefts])
+    Q = (_P * n)(*[_ptr(t) for t in rights])
+    pi = (_I * n)(*pitches)
+    wi = (_I * n)(*windows)
+    D = (_P * n)(*[_ptr(t) for t in disps])
+    _check(lib().bps_batch_stereo(batch, P, Q, pi, wi, trunc_data, iters, lam, trunc, flags, D, _stream(stream)),
+           "bps_batch_stereo")
+
+
+def bps_batch_stereo_host(batch, h_lefts, h_rights, pitches, windows, trunc_data, iters, lam, trunc, flags, h_disps,
+                          h_energies=None, stream=None):
+    n = len(h_lefts)
+    P = (_P * n)(*[_ptr(t) for t in h_lefts])
+    Q = (_P * n)(*[_ptr(t) for t in h_rights])
+    pi = (_I * n)(*pitches)
+    wi = (_I * n)(*windows)
+    D = (_P * n)(*[_ptr(t) for t in h_disps])
+    _check(lib().bps_batch_stereo_host(batch, P, Q, pi, wi, trunc_data, iters, lam, trunc, flags, D, _ptr(h_energies),
+                                       _stream(stream)), "bps_batch_stereo_host")
+
+
+def bps_batch_get_error(batch) -> int:
+    rc = lib().bps_batch_get_error(batch)
+    if rc not in (BPS_OK, BPS_ERR_TIMEOUT):
+        raise BPSError(rc, "bps_batch_get_error")
+    return rc
 
 
 def bps_last_cuda_error() -> int:
@@ -357,3 +405,57 @@ class Stereo:
         buf = np.zeros(self.levels * BPS_MAX_ITERS * 2, dtype=np.float64)
         n = bps_read_launch_times(self.ctx, buf.ctypes.data, buf.size)
         return buf[:n]
+
+
+class Batch:
+    """Several Stereo contexts solved together (concurrent chains, or one persistent launch)."""
+
+    def __init__(self, stereos):
+        self.stereos = list(stereos)
+        self.handle = bps_batch_create([st.ctx for st in self.stereos])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bps_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stereo(self, lefts, rights, windows, trunc_data, iters, lam, trunc, skip=True, graph=True,
+               persistent=False, outs=None, stream=None):
+        import torch
+
+        if outs is None:
+            outs = [torch.empty((st.H, st.W), dtype=torch.int32, device=st.device) for st in self.stereos]
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
+        flags |= BPS_FLAG_PERSISTENT if persistent else 0
+        bps_batch_stereo(self.handle, lefts, rights, [t.stride(0) for t in lefts], windows, trunc_data, iters, lam,
+                         trunc, flags, outs, stream)
+        return outs
+
+    def get_error(self) -> int:
+        return bps_batch_get_error(self.handle)
+
+    def stereo_host(self, h_lefts, h_rights, windows, trunc_data, iters, lam, trunc, skip=True, graph=True,
+                    persistent=False, h_disps=None, stream=None):
+        """Host tensors in; host disparities and int64 energies out (synchronous)."""
+        import torch
+
+        if h_disps is None:
+            h_disps = [torch.empty((st.H, st.W), dtype=torch.int32).pin_memory() for st in self.stereos]
+        energies = torch.zeros(len(self.stereos), dtype=torch.int64)
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
+        flags |= BPS_FLAG_PERSISTENT if persistent else 0
+        bps_batch_stereo_host(self.handle, h_lefts, h_rights, [t.stride(0) for t in h_lefts], windows, trunc_data,
+                              iters, lam, trunc, flags, h_disps, energies, stream)
+        return h_disps, energies

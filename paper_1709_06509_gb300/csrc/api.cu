@@ -619,3 +619,252 @@ extern "C" int bps_read_launch_times(bps_ctx *c, double *h_ms, int cap) {
     }
     return n;
 }
+
+// ------------------------------------------------------------------ batches of pairs
+
+struct bps_batch {
+    std::vector<bps_ctx *> ctxs;
+    int levels = 0, msg_type = 0, msg_kind = 0;
+    std::vector<cudaStream_t> streams;  // one branch stream per pair
+    std::vector<cudaEvent_t> events;    // fork event, then one join event per pair
+    cudaStream_t cap = nullptr;
+    // lockstep persistent launch over all pairs
+    PairDesc *d_desc = nullptr;
+    int *d_prefix = nullptr;  // [levels][n + 1] sweep prefixes, then [n + 1] read-out prefix
+    unsigned *d_barrier = nullptr;
+    std::vector<PairDesc> h_desc;
+    int grid = 0;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<intptr_t> gkey;
+};
+
+namespace {
+
+std::vector<intptr_t> batch_key(const bps_batch *b, const uint8_t *const *L, const uint8_t *const *R,
+                                const int *pitches, const int *windows, int trunc_data, int iters, int lambda,
+                                int trunc, int flags, int32_t *const *disps) {
+    std::vector<intptr_t> k = {trunc_data, iters, lambda, trunc, flags};
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        k.push_back((intptr_t)L[i]);
+        k.push_back((intptr_t)R[i]);
+        k.push_back(pitches[i]);
+        k.push_back(windows[i]);
+        k.push_back((intptr_t)disps[i]);
+    }
+    return k;
+}
+
+void batch_free(bps_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_barrier) cudaFree(b->d_barrier);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" int bps_batch_create(bps_batch **out, bps_ctx *const *ctxs, int n) {
+    if (!out || !ctxs || n < 1 || n > BPS_MAX_BATCH) return BPS_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || ctxs[i]->levels != ctxs[0]->levels || ctxs[i]->msg_type != ctxs[0]->msg_type)
+            return BPS_ERR_ARG;
+    bps_batch *b = new (std::nothrow) bps_batch();
+    if (!b) return BPS_ERR_CUDA;
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->levels = ctxs[0]->levels;
+    b->msg_type = ctxs[0]->msg_type;
+    b->msg_kind = ctxs[0]->msg_kind;
+    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i) {
+        cudaStream_t s;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) b->streams.push_back(s);
+    }
+    for (int i = 0; ok && i <= n; ++i) {
+        cudaEvent_t e;
+        ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) b->events.push_back(e);
+    }
+    // descriptors of the lockstep persistent launch
+    const int L = b->levels;
+    std::vector<int> prefix((size_t)(L + 1) * (n + 1), 0);
+    for (int l = 0; l < L; ++l)
+        for (int i = 0; i < n; ++i) prefix[(size_t)l * (n + 1) + i + 1] = prefix[(size_t)l * (n + 1) + i] + sweep_blocks(ctxs[i], l);
+    for (int i = 0; i < n; ++i) prefix[(size_t)L * (n + 1) + i + 1] = prefix[(size_t)L * (n + 1) + i] + wta_blocks(ctxs[i]);
+    for (int i = 0; i < n; ++i) b->h_desc.push_back(make_desc(ctxs[i]));
+    ok = ok && cudaMalloc(&b->d_desc, sizeof(PairDesc) * n) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_prefix, sizeof(int) * prefix.size()) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_barrier, 2 * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && persistent_grid(b->msg_kind, &b->grid) == cudaSuccess;
+    if (!ok) {
+        batch_free(b);
+        return BPS_ERR_CUDA;
+    }
+    *out = b;
+    return BPS_OK;
+}
+
+extern "C" int bps_batch_destroy(bps_batch *b) {
+    if (!b) return BPS_OK;
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    batch_free(b);
+    return BPS_OK;
+}
+
+// Every pair's chain on its own branch stream, forked from and joined back into `st`.
+static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *const *R, const int *pitches,
+                         const int *windows, int trunc_data, int iters, int lambda, int trunc, int flags,
+                         int32_t *const *disps, cudaStream_t st) {
+    const int n = (int)b->ctxs.size();
+    if (flags & BPS_FLAG_PERSISTENT) {
+        // costs of every pair on the branches, then one lockstep launch for all pairs
+        CK(cudaEventRecord(b->events[0], st));
+        for (int i = 0; i < n; ++i) {
+            bps_ctx *c = b->ctxs[i];
+            CK(cudaStreamWaitEvent(b->streams[i], b->events[0], 0));
+            int rc = enqueue_cost(c, L[i], R[i], pitches[i], windows[i], trunc_data, nullptr, b->streams[i]);
+            if (rc == BPS_OK) rc = enqueue_start(c, b->levels - 1, 0, nullptr, b->streams[i]);
+            if (rc != BPS_OK) return rc;
+            if (iters) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * b->levels * iters * 2, b->streams[i]));
+            CK(cudaEventRecord(b->events[i + 1], b->streams[i]));
+            CK(cudaStreamWaitEvent(st, b->events[i + 1], 0));
+        }
+        CK(cudaMemsetAsync(b->d_barrier, 0, 2 * sizeof(unsigned), st));
+        PersistParams P = persist_params(n, b->d_desc, b->d_prefix, b->d_prefix + (size_t)b->levels * (n + 1),
+                                         b->d_barrier, b->levels, iters, lambda, trunc, flags);
+        CK(launch_persistent(b->msg_kind, P, b->grid, st));
+        for (bps_ctx *c : b->ctxs) {
+            c->last_levels = b->levels;
+            c->last_iters = iters;
+        }
+        return BPS_OK;
+    }
+    CK(cudaEventRecord(b->events[0], st));
+    for (int i = 0; i < n; ++i) {
+        CK(cudaStreamWaitEvent(b->streams[i], b->events[0], 0));
+        const int rc = enqueue_stereo(b->ctxs[i], L[i], R[i], pitches[i], windows[i], trunc_data, iters, lambda, trunc,
+                                      flags & BPS_FLAG_FAST_SKIP, disps[i], b->streams[i]);
+        if (rc != BPS_OK) return rc;
+        CK(cudaEventRecord(b->events[i + 1], b->streams[i]));
+        CK(cudaStreamWaitEvent(st, b->events[i + 1], 0));
+    }
+    return BPS_OK;
+}
+
+extern "C" int bps_batch_stereo(bps_batch *b, const uint8_t *const *d_lefts, const uint8_t *const *d_rights,
+                                const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
+                                int flags, int32_t *const *d_disps, void *stream) {
+    if (!b || !d_lefts || !d_rights || !pitches || !windows || !d_disps ||
+        (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT)))
+        return BPS_ERR_ARG;
+    const int n = (int)b->ctxs.size();
+    for (int i = 0; i < n; ++i) {
+        bps_ctx *c = b->ctxs[i];
+        int rc = check_cost_args(c, d_lefts[i], d_rights[i], pitches[i], windows[i], trunc_data);
+        if (rc != BPS_OK) return rc;
+        if (!d_disps[i]) return BPS_ERR_ARG;
+        const bool had = c->has_cost;
+        c->has_cost = true;
+        rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
+        if (rc != BPS_OK) {
+            c->has_cost = had;
+            return rc;
+        }
+    }
+    if (flags & BPS_FLAG_PERSISTENT) {
+        // the read-out targets live in the device descriptors: refresh them when they change
+        bool changed = false;
+        for (int i = 0; i < n; ++i)
+            if (b->h_desc[i].disp != d_disps[i]) {
+                b->h_desc[i].disp = d_disps[i];
+                changed = true;
+            }
+        if (changed) {
+            for (cudaStream_t s : b->streams) CK(cudaStreamSynchronize(s));
+            CK(cudaStreamSynchronize((cudaStream_t)stream));
+            CK(cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice));
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(flags & BPS_FLAG_GRAPH))
+        return enqueue_batch(b, d_lefts, d_rights, pitches, windows, trunc_data, iters, lambda, trunc, flags, d_disps, st);
+    std::vector<intptr_t> key = batch_key(b, d_lefts, d_rights, pitches, windows, trunc_data, iters, lambda, trunc,
+                                          flags, d_disps);
+    if (!b->gexec || key != b->gkey) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        CK(cudaStreamSynchronize(b->cap));
+        CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_batch(b, d_lefts, d_rights, pitches, windows, trunc_data, iters, lambda, trunc, flags,
+                                     d_disps, b->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != BPS_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != BPS_OK ? rc : cuda_failed(ec);
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            b->gexec = nullptr;
+            return cuda_failed(ei);
+        }
+        b->gkey = key;
+    }
+    CK(cudaGraphLaunch(b->gexec, st));
+    return BPS_OK;
+}
+
+extern "C" int bps_batch_get_error(bps_batch *b) {
+    if (!b) return BPS_ERR_ARG;
+    unsigned w[2] = {0u, 0u};
+    CK(cudaMemcpy(w, b->d_barrier, sizeof(w), cudaMemcpyDeviceToHost));
+    return w[1] ? BPS_ERR_TIMEOUT : BPS_OK;
+}
+
+extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts, const uint8_t *const *h_rights,
+                                     const int *pitches, const int *windows, int trunc_data, int iters, int lambda,
+                                     int trunc, int flags, int32_t *const *h_disps, int64_t *h_energies,
+                                     void *stream) {
+    if (!b || !h_lefts || !h_rights || !pitches || !windows || !h_disps) return BPS_ERR_ARG;
+    const int n = (int)b->ctxs.size();
+    std::vector<const uint8_t *> L(n), R(n);
+    std::vector<int> pitch(n);
+    std::vector<int32_t *> disp(n);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        bps_ctx *c = b->ctxs[i];
+        if (!h_lefts[i] || !h_rights[i] || !h_disps[i] || pitches[i] < c->W) return BPS_ERR_ARG;
+        CK(cudaMemcpy2DAsync(c->img[0], c->W, h_lefts[i], pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpy2DAsync(c->img[1], c->W, h_rights[i], pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
+        L[i] = c->img[0];
+        R[i] = c->img[1];
+        pitch[i] = c->W;
+        disp[i] = c->disp;
+    }
+    int rc = bps_batch_stereo(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda, trunc, flags,
+                              disp.data(), stream);
+    if (rc != BPS_OK) return rc;
+    for (int i = 0; i < n; ++i) {
+        bps_ctx *c = b->ctxs[i];
+        if (h_energies) {
+            CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, c->disp, lambda, trunc, c->partials,
+                             c->msg_type == BPS_MSG_FP16 ? nullptr : c->e_i64, c->e_f64, st));
+            CK(cudaMemcpyAsync(h_energies + i, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaMemcpyAsync(h_disps[i], c->disp, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return (flags & BPS_FLAG_PERSISTENT) ? bps_batch_get_error(b) : BPS_OK;
+}

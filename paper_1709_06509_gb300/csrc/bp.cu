@@ -18,11 +18,19 @@ sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<Msg
     sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256, 3)
+// Grid-stride over the colour's pixel blocks: the grid is capped at what is resident at
+// once, so a launch pays for block scheduling once, not once per wave.
+#ifndef BPS_SWEEP_MIN_BLOCKS
+#define BPS_SWEEP_MIN_BLOCKS 3  // resident CTAs per SM the u8 sweep is compiled for
+#endif
+
+template <bool PADDED>
+__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
-                unsigned long long *trace) {
+                unsigned long long *trace, int nblocks) {
     pdl_enter();
-    sweep_group_u8(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
+        sweep_group_u8<PADDED>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
 }
 
 template <typename CostT, typename MsgT>
@@ -37,6 +45,19 @@ static cudaError_t sweep_t(const LevelView &lv, int colour, int D, int Dp, int G
                     (Acc)lambda, (Acc)lambda * (Acc)trunc, skip, trace);
 }
 
+// CTAs of the u8 sweep that fit on the GPU at once (looked up once per process).
+static int resident_blocks(int msg_kind) {
+    static int cached[3] = {0, 0, 0};
+    if (!cached[msg_kind]) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false>, 256, 0);
+        cached[msg_kind] = std::max(1, sms * std::max(1, per_sm));
+    }
+    return cached[msg_kind];
+}
+
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc,
                          int skip, unsigned long long *trace, cudaStream_t st) {
     switch (msg_kind) {
@@ -46,8 +67,12 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
         if (blocks == 0) return cudaSuccess;
         const int lam = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
-        return launch_k(sweep_u8_kernel, dim3((unsigned)blocks), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
-                        lam * trunc, skip, trace);
+        const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_blocks(MSG_U8));
+        if (D & 15)
+            return launch_k(sweep_u8_kernel<true>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                            lam * trunc, skip, trace, (int)blocks);
+        return launch_k(sweep_u8_kernel<false>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam, lam * trunc,
+                        skip, trace, (int)blocks);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -185,7 +210,9 @@ cudaError_t preload_bp_kernels(int msg_kind) {
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<int32_t, int32_t>);
         break;
     case MSG_U8:
-        e = cudaFuncGetAttributes(&a, sweep_u8_kernel);
+        e = cudaFuncGetAttributes(&a, sweep_u8_kernel<false>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<true>);
+        if (e == cudaSuccess) resident_blocks(MSG_U8);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<uint8_t, int32_t>);
         break;
     default:

@@ -110,7 +110,12 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
                     const int64_t b = vb - prefix[p];
                     unsigned long long *trace = pd.trace ? pd.trace + t : nullptr;
                     if constexpr (FORM == MSG_U8) {
-                        sweep_group_u8(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc, P.skip, trace, b);
+                        if (pd.D & 15)
+                            sweep_group_u8<true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
+                                                 P.skip, trace, b);
+                        else
+                            sweep_group_u8<false>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
+                                                  P.skip, trace, b);
                     } else if constexpr (FORM == MSG_I32) {
                         sweep_group<int32_t, int32_t>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam, P.lam * P.trunc,
                                                       P.skip, trace, b);

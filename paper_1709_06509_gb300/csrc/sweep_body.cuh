@@ -187,6 +187,9 @@ __device__ inline uint4 pack_msg(const uint32_t (&v)[8]) {
                       __byte_perm(v[4], v[5], 0x6420), __byte_perm(v[6], v[7], 0x6420));
 }
 
+// PADDED: D is not a multiple of 16, so the last lane holds labels >= D that must stay out
+// of every minimum and be stored as 0.
+template <bool PADDED>
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
                                                int lamT, int skip, unsigned long long *trace, int64_t block) {
     const int lane = threadIdx.x & 31;
@@ -217,14 +220,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     uint8_t *msg_out = reinterpret_cast<uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
     uint8_t *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
 
-    uint32_t b[8], padv[8], keep[8];
+    uint32_t b[8];
     uint4 in[4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const bool plo = dbase + j >= D, phi = dbase + 8 + j >= D;
-        padv[j] = pk(plo ? BIG16 : 0u, phi ? BIG16 : 0u);
-        keep[j] = (plo ? 0u : 0xffffu) | (phi ? 0u : 0xffff0000u);
-    }
     if (lane_data) {
         const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
         const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
@@ -247,14 +244,29 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) b[j] += t[j];
     }
+    if constexpr (PADDED) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) b[j] = __vimax3_u16x2(b[j], padv[j], 0u);
+        for (int j = 0; j < 8; ++j) {
+            const bool plo = dbase + j >= D, phi = dbase + 8 + j >= D;
+            b[j] = __vimax3_u16x2(b[j], pk(plo ? BIG16 : 0u, phi ? BIG16 : 0u), 0u);
+        }
+    }
 
     const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
     const int nbx[4] = {x, x, x - 1, x + 1};
     const int nby[4] = {y - 1, y + 1, y, y};
     const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
     const int gshift = lane & ~(Gp - 1);
+    // the old outgoing messages (the skip's change test) are loaded together with the inputs,
+    // so a recomputed pixel waits for one round trip to memory, not two
+    uint4 *dst[4];
+    uint4 old[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t qs = (active && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+        dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
+        old[q] = (skip && active && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t t[8], h[8], F[8], B[8];
@@ -308,26 +320,26 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         const uint32_t HM2 = (uint32_t)hm * 0x10001u;
         uint32_t m[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) m[j] = (__vimin3_u16x2(F[j], B[j], CAP2) - HM2) & keep[j];
+        for (int j = 0; j < 8; ++j) {
+            m[j] = __vimin3_u16x2(F[j], B[j], CAP2) - HM2;
+            if constexpr (PADDED)
+                m[j] &= (dbase + j < D ? 0xffffu : 0u) | (dbase + 8 + j < D ? 0xffff0000u : 0u);
+        }
         const uint4 out = pack_msg(m);
 
         const bool send = active && has[q];
-        const int64_t qs = send ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
-        uint4 *dst = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
         if (skip) {
             bool diff = false;
-            if (send && lane_data) {
-                const uint4 old = *dst;
-                diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
-            }
+            if (send && lane_data)
+                diff = (old[q].x != out.x) | (old[q].y != out.y) | (old[q].z != out.z) | (old[q].w != out.w);
             const unsigned dm = __ballot_sync(FULL, diff);
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             if (send && changed) {
-                if (lane_data) *dst = out;
-                if (g == 0) dirty_out[qs] = 1;
+                if (lane_data) *dst[q] = out;
+                if (g == 0) dirty_out[slot_of(nbx[q], nby[q], lv.Wh)] = 1;
             }
         } else if (send && lane_data) {
-            *dst = out;
+            *dst[q] = out;
         }
     }
     if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0;

@@ -208,6 +208,36 @@ def test_contexts_of_different_shapes_coexist():
             st.close()
 
 
+@pytest.mark.parametrize("persistent", [False, True], ids=["chains", "persistent"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_of_mixed_pairs(persistent, graph):
+    shapes = [(70, 40, 16, 5), (45, 33, 64, 7), (96, 20, 33, 3)]
+    pairs = [synth.make_pair(60 + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+    windows = [w for *_, w in shapes]
+    refs = [oracle.stereo_int(p.left, p.right, p.D, w, 20, 3, 5, 10, 2) for p, w in zip(pairs, windows)]
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 3, bps.BPS_MSG_U8, device=DEV) for p in pairs]
+    try:
+        with bps.Batch(sts) as batch:
+            Ls = [to_dev(p.left) for p in pairs]
+            Rs = [to_dev(p.right) for p in pairs]
+            for rep in range(3):  # the graph is recorded once, then replayed
+                outs = batch.stereo(Ls, Rs, windows, 20, 5, 10, 2, graph=graph, persistent=persistent)
+                torch.cuda.synchronize()
+                if persistent:
+                    assert batch.get_error() == bps.BPS_OK
+                for out, ref, st in zip(outs, refs, sts):
+                    assert np.array_equal(out.cpu().numpy(), ref["disp"])
+                    assert np.array_equal(st.get_trace(), ref["trace"])
+            hl = [torch.from_numpy(p.left).pin_memory() for p in pairs]
+            hr = [torch.from_numpy(p.right).pin_memory() for p in pairs]
+            hd, he = batch.stereo_host(hl, hr, windows, 20, 5, 10, 2, graph=graph, persistent=persistent)
+            for d, e, ref in zip(hd, he.tolist(), refs):
+                assert np.array_equal(d.numpy(), ref["disp"]) and e == ref["energy"]
+    finally:
+        for st in sts:
+            st.close()
+
+
 def test_argument_errors_on_a_live_context():
     with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_U8, device=DEV) as st:
         with pytest.raises(bps.BPSError) as e:
