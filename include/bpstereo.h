@@ -257,6 +257,22 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
                           int flags, int32_t *const *h_disps, int64_t *h_energies, void *stream);
 
 /*
+ * Kernel variant of the half-sweeps at one scale (integer u8 form; results are identical
+ * for every variant, only the speed differs):
+ *   BPS_VARIANT_GENERAL_DT  minimise with the forward/backward distance transform even
+ *                           when trunc <= 2 allows the shorter stencil forms;
+ *   BPS_VARIANT_LISTS       with the fast-converging skip, process only the listed dirty
+ *                           pixels after the scale's first iteration.
+ * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
+ * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
+ * The autotuner (paper_1709_06509_gb300/autotune.py) picks them by measurement.
+ */
+#define BPS_VARIANT_GENERAL_DT 1
+#define BPS_VARIANT_LISTS 2
+int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
+int bps_get_sweep_variant(bps_ctx *ctx, int level);
+
+/*
  * Energy of a labelling without allocating any memory.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory when they need the
  * energy -- code running while a CUDA graph is being captured, real-time loops that may not

@@ -45,6 +45,8 @@ BPS_MAX_D = 512
 BPS_MAX_ITERS = 1024
 BPS_MAX_WINDOW = 31
 BPS_MAX_BATCH = 256
+BPS_VARIANT_GENERAL_DT = 1
+BPS_VARIANT_LISTS = 2
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
@@ -87,6 +89,8 @@ _SIGS = {
     "bps_batch_stereo": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "bps_batch_get_error": (_I, [_P]),
     "bps_batch_stereo_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "bps_set_sweep_variant": (_I, [_P, _I, _I]),
+    "bps_get_sweep_variant": (_I, [_P, _I]),
 }
 
 
@@ -247,6 +251,14 @@ def bps_batch_get_error(batch) -> int:
     return rc
 
 
+def bps_set_sweep_variant(ctx, level: int, variant: int) -> None:
+    _check(lib().bps_set_sweep_variant(ctx, level, variant), "bps_set_sweep_variant")
+
+
+def bps_get_sweep_variant(ctx, level: int) -> int:
+    return _check(lib().bps_get_sweep_variant(ctx, level), "bps_get_sweep_variant")
+
+
 def bps_last_cuda_error() -> int:
     return lib().bps_last_cuda_error()
 
@@ -398,6 +410,12 @@ class Stereo:
 
     def get_error(self) -> int:
         return bps_get_error(self.ctx)
+
+    def set_variant(self, level: int, variant: int) -> None:
+        bps_set_sweep_variant(self.ctx, level, variant)
+
+    def variants(self) -> list[int]:
+        return [bps_get_sweep_variant(self.ctx, l) for l in range(self.levels)]
 
     def read_launch_times(self):
         import numpy as np

@@ -20,7 +20,7 @@ struct Plan {
     int levels = 0;
     int Ws[BPS_MAX_LEVELS], Hs[BPS_MAX_LEVELS], Whs[BPS_MAX_LEVELS];
     size_t cost[BPS_MAX_LEVELS][2], msg[BPS_MAX_LEVELS][2], dirty[BPS_MAX_LEVELS][2];
-    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, total;
+    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, lists[2], list_counts, total;
 };
 
 int cost_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? COST_I32 : msg_type == BPS_MSG_U8 ? COST_I16 : COST_F32; }
@@ -51,7 +51,7 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
             p.msg[l][c] = off;
             off += up(nslot * 4 * Dp * msg_size(msg_type));
             p.dirty[l][c] = off;
-            off += up(nslot);
+            off += up(nslot * sizeof(unsigned));
         }
     }
     p.trace = off;
@@ -72,6 +72,14 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
     off += up(sizeof(int) * 2 * (levels + 1));
     p.barrier = off;
     off += up(16);
+    // active lists of the two colours (sized for the finest scale, reused at every scale) and
+    // one entry count per half-sweep
+    for (int c = 0; c < 2; ++c) {
+        p.lists[c] = off;
+        off += up((size_t)p.Hs[0] * p.Whs[0] * sizeof(unsigned));
+    }
+    p.list_counts = off;
+    off += up((size_t)levels * BPS_MAX_ITERS * 2 * sizeof(unsigned));
     p.total = off;
     return true;
 }
@@ -107,6 +115,9 @@ struct bps_ctx {
     int *d_prefix = nullptr;         // [levels][2] sweep block prefix, then [2] read-out prefix
     unsigned *d_barrier = nullptr;   // {arrival count, error word} of the persistent kernel
     int grid = 0;                    // co-resident CTAs of the persistent kernel
+    unsigned *lists[2] = {nullptr, nullptr};  // active lists of the even / odd pixels
+    unsigned *list_counts = nullptr;          // entries appended during each half-sweep
+    int variant[BPS_MAX_LEVELS] = {};         // u8 sweep kernel variant per scale
     int prof_launches = 0;  // finest-scale sweep launches of the last profiled solve
     int prof_all = 0;       // all sweep launches of the last profiled solve
     int prof_first_trace = 0;
@@ -135,6 +146,16 @@ PairDesc make_desc(const bps_ctx *c) {
     d.trace = c->trace;
     d.disp = nullptr;
     return d;
+}
+
+// Defaults of the per-scale sweep variant, from measurements on GB300 (the autotuner may
+// replace them): the stencil forms win below about half a million pixels of a colour, the
+// distance transform above; active lists pay off from about 128 K pixels of a colour.
+int default_variant(int64_t slots) {
+    int v = 0;
+    if (slots >= 512 * 1024) v |= VARIANT_GENERAL_DT;
+    if (slots >= 128 * 1024) v |= VARIANT_LISTS;
+    return v;
 }
 
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 4000000000ull;  // 4 s: far above any phase
@@ -217,7 +238,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         for (int k = 0; k < 2; ++k) {
             v.cost[k] = c->ws + p.cost[l][k];
             v.msg[k] = c->ws + p.msg[l][k];
-            v.dirty[k] = reinterpret_cast<uint8_t *>(c->ws + p.dirty[l][k]);
+            v.dirty[k] = reinterpret_cast<unsigned *>(c->ws + p.dirty[l][k]);
         }
     }
     c->trace = reinterpret_cast<unsigned long long *>(c->ws + p.trace);
@@ -230,6 +251,10 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->d_desc = reinterpret_cast<PairDesc *>(c->ws + p.desc);
     c->d_prefix = reinterpret_cast<int *>(c->ws + p.prefix);
     c->d_barrier = reinterpret_cast<unsigned *>(c->ws + p.barrier);
+    c->lists[0] = reinterpret_cast<unsigned *>(c->ws + p.lists[0]);
+    c->lists[1] = reinterpret_cast<unsigned *>(c->ws + p.lists[1]);
+    c->list_counts = reinterpret_cast<unsigned *>(c->ws + p.list_counts);
+    for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l]);
     PairDesc hd = make_desc(c);
     std::vector<int> prefix(2 * (levels + 1));
     for (int l = 0; l < levels; ++l) {
@@ -429,7 +454,12 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     // a chain of kernels only (no memset nodes), so that every launch overlaps its predecessor
     const bool warm = (flags & BPS_FLAG_WARM_START) != 0;
     if (warm) CK(launch_import_msgs(c->msg_kind, c->lv[top], c->D, c->Dp, init, st));
-    CK(launch_solve_start(c->msg_kind, c->lv[top], c->Dp, warm ? 0 : 1, skip ? 1 : 0, c->trace, ntrace, st));
+    CK(launch_solve_start(c->msg_kind, c->lv[top], c->Dp, warm ? 0 : 1, skip ? 1 : 0, c->trace, c->list_counts, ntrace,
+                          st));
+    // u8 form with the skip, on scales whose variant asks for it (large, bandwidth-bound ones by
+    // default): after a scale's first iteration each half-sweep runs over the active list its
+    // predecessor built (entry count list_counts[t - 1]).  Small scales are latency-bound and
+    // keep the dense launch, whose clean warps exit after one flag load.
     int t = 0;
     for (int l = top; l >= 0; --l) {
         const LevelView &v = c->lv[l];
@@ -439,7 +469,19 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         for (int it = 0; it < iters; ++it)
             for (int colour = 0; colour < 2; ++colour, ++t) {
                 if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
-                CK(launch_sweep(c->msg_kind, v, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st));
+                SweepLists sl{nullptr, nullptr, nullptr, nullptr};
+                const bool lists = skip && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_LISTS);
+                // the scale's first half-sweep cannot grow a list: every flag is still set
+                if (lists && (it > 0 || colour == 1)) {
+                    sl.out = c->lists[colour ^ 1];
+                    sl.n_out = c->list_counts + t;
+                }
+                if (lists && it > 0) {
+                    sl.in = c->lists[colour];
+                    sl.n_in = c->list_counts + t - 1;
+                }
+                CK(launch_sweep(c->msg_kind, v, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st, sl,
+                                c->variant[l]));
                 if (prof) {
                     CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
                     ++c->prof_all;
@@ -867,4 +909,20 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
     }
     CK(cudaStreamSynchronize(st));
     return (flags & BPS_FLAG_PERSISTENT) ? bps_batch_get_error(b) : BPS_OK;
+}
+
+extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
+    if (!c || level < 0 || level >= c->levels || variant < -1 || variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS))
+        return BPS_ERR_ARG;
+    c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level]) : variant;
+    if (c->gexec) {  // a recorded graph holds the old kernels
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BPS_OK;
+}
+
+extern "C" int bps_get_sweep_variant(bps_ctx *c, int level) {
+    if (!c || level < 0 || level >= c->levels) return BPS_ERR_ARG;
+    return c->variant[level];
 }

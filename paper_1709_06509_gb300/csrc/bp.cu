@@ -24,13 +24,54 @@ sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<Msg
 #define BPS_SWEEP_MIN_BLOCKS 3  // resident CTAs per SM the u8 sweep is compiled for
 #endif
 
-template <bool PADDED>
+template <bool PADDED, bool APPEND, int TS>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
-                unsigned long long *trace, int nblocks) {
+                unsigned long long *trace, int nblocks, ActiveList al) {
     pdl_enter();
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group_u8<PADDED>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+        sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+}
+
+// The same half-sweep over the pixels of an active list; its length is read on the device
+// (a recorded graph keeps the launch shape, the list decides the work).
+template <bool PADDED, int TS>
+__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
+                     unsigned long long *trace, ActiveList al) {
+    pdl_enter();
+    const int64_t n = *al.n_in;
+    const int groups = blockDim.x / Gp;
+    const int64_t nblocks = (n + groups - 1) / groups;
+    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x)
+        sweep_group_u8<PADDED, true, TS>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n);
+}
+
+// Kernel of one u8 half-sweep: padding variant x list / append mode x minimisation form.
+template <bool PADDED, int TS>
+static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                                unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
+                                cudaStream_t st) {
+    if (skip && al.in)
+        return launch_k(sweep_u8_list_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                        lamT, trace, al);
+    const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
+    if (al.out)
+        return launch_k(sweep_u8_kernel<PADDED, true, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                        lamT, skip, trace, (int)blocks, dense);
+    return launch_k(sweep_u8_kernel<PADDED, false, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam, lamT,
+                    skip, trace, (int)blocks, dense);
+}
+
+template <bool PADDED>
+static cudaError_t launch_u8(int ts, const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                             unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
+                             cudaStream_t st) {
+    switch (ts) {
+    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
+    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
+    default: return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
+    }
 }
 
 template <typename CostT, typename MsgT>
@@ -52,14 +93,14 @@ static int resident_blocks(int msg_kind) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 0>, 256, 0);
         cached[msg_kind] = std::max(1, sms * std::max(1, per_sm));
     }
     return cached[msg_kind];
 }
 
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc,
-                         int skip, unsigned long long *trace, cudaStream_t st) {
+                         int skip, unsigned long long *trace, cudaStream_t st, const SweepLists &lists, int variant) {
     switch (msg_kind) {
     case MSG_I32: return sweep_t<int32_t, int32_t>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     case MSG_U8: {
@@ -68,11 +109,10 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         if (blocks == 0) return cudaSuccess;
         const int lam = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
         const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_blocks(MSG_U8));
-        if (D & 15)
-            return launch_k(sweep_u8_kernel<true>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
-                            lam * trunc, skip, trace, (int)blocks);
-        return launch_k(sweep_u8_kernel<false>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam, lam * trunc,
-                        skip, trace, (int)blocks);
+        const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
+        const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
+        if (D & 15) return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, st);
+        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, st);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -96,7 +136,7 @@ __global__ void upsample_kernel(LevelView coarse, LevelView fine, int both_colou
 }
 
 __global__ void solve_start_kernel(LevelView top, int rec_words, int zero_msgs, int set_dirty,
-                                   unsigned long long *trace, int ntrace) {
+                                   unsigned long long *trace, unsigned *list_counts, int ntrace) {
     pdl_enter();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -110,7 +150,10 @@ __global__ void solve_start_kernel(LevelView top, int rec_words, int zero_msgs, 
     }
     if (set_dirty)
         for (int64_t k = t0; k < slots; k += stride) top.dirty[0][k] = top.dirty[1][k] = 1;
-    for (int64_t k = t0; k < ntrace; k += stride) trace[k] = 0ull;
+    for (int64_t k = t0; k < ntrace; k += stride) {
+        trace[k] = 0ull;
+        if (list_counts) list_counts[k] = 0u;
+    }
 }
 
 static int msg_bytes(int msg_kind) { return msg_kind == MSG_I32 ? 4 : (msg_kind == MSG_U8 ? 1 : 2); }
@@ -126,11 +169,11 @@ cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelVi
 }
 
 cudaError_t launch_solve_start(int msg_kind, const LevelView &top, int Dp, int zero_msgs, int set_dirty,
-                               unsigned long long *trace, int ntrace, cudaStream_t st) {
+                               unsigned long long *trace, unsigned *list_counts, int ntrace, cudaStream_t st) {
     const int rec_words = 4 * Dp * msg_bytes(msg_kind) / 16;
     const int64_t n = std::max<int64_t>((int64_t)top.H * top.Wh * (zero_msgs ? rec_words : 1), ntrace);
     return launch_k(solve_start_kernel, dim3(grid_for(n)), dim3(256), 0, st, top, rec_words, zero_msgs, set_dirty,
-                    trace, ntrace);
+                    trace, list_counts, ntrace);
 }
 
 // ------------------------------------------------------------------ natural-layout import / export
@@ -199,6 +242,14 @@ __global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
     }
 }
 
+template <bool PADDED, int TS> static cudaError_t preload_u8() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, false, TS>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, true, TS>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_list_kernel<PADDED, TS>);
+    return e;
+}
+
 cudaError_t preload_bp_kernels(int msg_kind) {
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncGetAttributes(&a, upsample_kernel);
@@ -210,8 +261,12 @@ cudaError_t preload_bp_kernels(int msg_kind) {
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<int32_t, int32_t>);
         break;
     case MSG_U8:
-        e = cudaFuncGetAttributes(&a, sweep_u8_kernel<false>);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<true>);
+        e = preload_u8<false, 0>();
+        if (e == cudaSuccess) e = preload_u8<false, 1>();
+        if (e == cudaSuccess) e = preload_u8<false, 2>();
+        if (e == cudaSuccess) e = preload_u8<true, 0>();
+        if (e == cudaSuccess) e = preload_u8<true, 1>();
+        if (e == cudaSuccess) e = preload_u8<true, 2>();
         if (e == cudaSuccess) resident_blocks(MSG_U8);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<uint8_t, int32_t>);
         break;

@@ -8,7 +8,7 @@
 //   cost[c]   [H_l][Wh][Dp]      data cost            (int32 | int16 | float)
 //   msg[c]    [H_l][Wh][4][Dp]   incoming messages    (int32 | uint8 | half)
 //             direction = the neighbour the message comes from: 0 up, 1 down, 2 left, 3 right
-//   dirty[c]  [H_l][Wh]          1 = some incoming message changed since the last update
+//   dirty[c]  [H_l][Wh] uint32   1 = some incoming message changed since the last update
 //   Labels d >= D inside the Dp padding are never winners: the sweep treats their belief
 //   as +infinity.
 //
@@ -30,7 +30,7 @@ struct LevelView {
     int W, H, Wh;
     void *cost[2];
     void *msg[2];
-    uint8_t *dirty[2];
+    unsigned *dirty[2];  // 32-bit words so a sender can flip them atomically
 };
 
 // Programmatic dependent launch: every kernel of the stereo chain is launched so that it may

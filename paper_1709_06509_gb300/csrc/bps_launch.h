@@ -47,10 +47,23 @@ cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *R, i
                             cudaStream_t st);
 cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
 
+// Kernel variant of the u8 half-sweep at one scale (bit set; see bps_set_sweep_variant).
+constexpr int VARIANT_GENERAL_DT = 1;  // the distance transform even where a stencil form exists
+constexpr int VARIANT_LISTS = 2;       // active lists after the scale's first iteration (skip on)
+
+// Active lists of a half-sweep (u8 form with the skip on; all members nullable).
+struct SweepLists {
+    const unsigned *in;    // pixels to process (NULL: every pixel of the colour)
+    const unsigned *n_in;  // device count of `in`
+    unsigned *out;         // list of the other colour's newly dirty pixels
+    unsigned *n_out;       // its device count (zeroed before the half-sweep)
+};
+
 // One red-black half-sweep of `colour` at one scale.  trace: nullable device counter of
 // recomputed pixels.
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
-                         int trunc, int skip, unsigned long long *trace, cudaStream_t st);
+                         int trunc, int skip, unsigned long long *trace, cudaStream_t st,
+                         const SweepLists &lists = SweepLists{nullptr, nullptr, nullptr, nullptr}, int variant = 0);
 // Coarse-to-fine start: copy parent messages into the fine pixels of `colour` (and of the
 // other colour too when both_colours), and mark every pixel of the fine scale dirty when
 // set_dirty (fast-converging skip).
@@ -59,7 +72,7 @@ cudaError_t launch_upsample(int msg_kind, const LevelView &coarse, const LevelVi
 // Start of a solve at scale `top`: zero its messages (zero_msgs), mark its pixels dirty
 // (set_dirty) and zero ntrace trace counters, in one kernel.
 cudaError_t launch_solve_start(int msg_kind, const LevelView &top, int Dp, int zero_msgs, int set_dirty,
-                               unsigned long long *trace, int ntrace, cudaStream_t st);
+                               unsigned long long *trace, unsigned *list_counts, int ntrace, cudaStream_t st);
 // Natural-layout [4][H][W][D] messages (int32 or float) into / out of colour-split storage.
 cudaError_t launch_import_msgs(int msg_kind, const LevelView &lv, int D, int Dp, const void *src, cudaStream_t st);
 cudaError_t launch_export_msgs(int msg_kind, const LevelView &lv, int D, int Dp, void *dst, cudaStream_t st);

@@ -89,7 +89,7 @@ __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int
         x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
-    const bool active = valid && (!skip || (colour ? lv.dirty[1] : lv.dirty[0])[s] != 0);
+    const bool active = valid && (!skip || (colour ? lv.dirty[1] : lv.dirty[0])[s] != 0u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -153,13 +153,13 @@ __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             if (send && changed) {
                 if (lane_data) store16(dst, m);
-                if (g == 0) (colour ? lv.dirty[0] : lv.dirty[1])[qs] = 1;
+                if (g == 0) (colour ? lv.dirty[0] : lv.dirty[1])[qs] = 1u;
             }
         } else if (send && lane_data) {
             store16(dst, m);
         }
     }
-    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0;
+    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
 }
 
 // ------------------------------------------------------------------ u8 form, packed 16-bit arithmetic
@@ -187,15 +187,37 @@ __device__ inline uint4 pack_msg(const uint32_t (&v)[8]) {
                       __byte_perm(v[4], v[5], 0x6420), __byte_perm(v[6], v[7], 0x6420));
 }
 
+// Active lists (fast-converging skip).  After the first two half-sweeps of a scale, a
+// half-sweep processes only the pixels listed for it, packed densely: a sender that flips a
+// neighbour's skip flag from 0 to 1 appends the neighbour to the other colour's list (one
+// atomic per warp and direction).  A pixel enters a list only on that 0 -> 1 flip and leaves
+// the flag at 0 when it is processed, so no list holds a pixel twice.
+struct ActiveList {
+    const unsigned *in;   // slots to process (nullable: every slot of the colour)
+    const unsigned *n_in; // number of entries of `in`
+    unsigned *out;        // where newly dirty pixels of the other colour go (nullable: no list)
+    unsigned *n_out;
+};
+
 // PADDED: D is not a multiple of 16, so the last lane holds labels >= D that must stay out
 // of every minimum and be stored as 0.
-template <bool PADDED>
+// APPEND: newly dirty neighbours are appended to the other colour's active list.
+// TS: how the truncated-linear minimisation is formed.
+//   TS = 0, any trunc: the forward/backward distance transform described above.
+//   TS = 1, trunc <= 1: m(d) = min(h(d), min h + lambda*trunc) - min h.
+//   TS = 2, trunc == 2: m(d) = min(h(d), h(d-1) + lambda, h(d+1) + lambda, min h + 2 lambda) - min h,
+//           the same function (a label two or more away costs the cap at least), needing only
+//           each label's immediate neighbours: no chains, no scan across the lanes.
+template <bool PADDED, bool APPEND = false, int TS = 0>
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
-                                               int lamT, int skip, unsigned long long *trace, int64_t block) {
+                                               int lamT, int skip, unsigned long long *trace, int64_t block,
+                                               const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
+                                               int64_t n_in = 0) {
     const int lane = threadIdx.x & 31;
     const int g = threadIdx.x & (Gp - 1);
-    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    if (al.in) s = s < n_in ? (int64_t)al.in[s] : nslot;
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
@@ -203,8 +225,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
-    const uint8_t *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
-    const bool active = valid && (!skip || dirty_in[s] != 0);
+    const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
+    const bool active = valid && (!skip || dirty_in[s] != 0u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -218,7 +240,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     const int16_t *cost = reinterpret_cast<const int16_t *>(colour ? lv.cost[1] : lv.cost[0]);
     const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
     uint8_t *msg_out = reinterpret_cast<uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
-    uint8_t *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
+    unsigned *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
 
     uint32_t b[8];
     uint4 in[4];
@@ -269,7 +291,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint32_t t[8], h[8], F[8], B[8];
+        uint32_t t[8], h[8], m[8];
         unpack_msg(in[q], t);
 #pragma unroll
         for (int j = 0; j < 8; ++j) h[j] = b[j] - t[j];
@@ -278,6 +300,31 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         mm = __vimin3_u16x2(mm, h[5], h[6]);
         mm = __vimin3_u16x2(mm, h[7], h[7]);
         int hm = (int)min(mm & 0xffffu, mm >> 16);
+        if constexpr (TS != 0) {
+            for (int o = 1; o < Gp; o <<= 1) hm = min(hm, __shfl_xor_sync(FULL, hm, o, Gp));
+            const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
+            const uint32_t HM2 = (uint32_t)hm * 0x10001u;
+            if constexpr (TS == 1) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(h[j], CAP2, CAP2) - HM2;
+            } else {
+                // labels dbase - 1 (the previous lane's label 15) and dbase + 16 (the next lane's 0)
+                int left = __shfl_up_sync(FULL, (int)(h[7] >> 16), 1, Gp);
+                int right = __shfl_down_sync(FULL, (int)(h[0] & 0xffffu), 1, Gp);
+                if (g == 0) left = (int)BIG16;
+                if (g == Gp - 1) right = (int)BIG16;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    // register j holds labels (j, j+8): its neighbours sit in registers j-1 and j+1,
+                    // except across the lane edge and across the middle (labels 7 | 8)
+                    const uint32_t lft = j > 0 ? h[j - 1] : pk((uint32_t)left, h[7] & 0xffffu);
+                    const uint32_t rgt = j < 7 ? h[j + 1] : pk(h[0] >> 16, (uint32_t)right);
+                    m[j] = __vimin3_u16x2(__viaddmin_u16x2(lft, LAM2, h[j]), __viaddmin_u16x2(rgt, LAM2, CAP2), CAP2) -
+                           HM2;
+                }
+            }
+        } else {
+        uint32_t F[8], B[8];
         F[0] = h[0];
 #pragma unroll
         for (int j = 1; j < 8; ++j) F[j] = __viaddmin_u16x2(F[j - 1], LAM2, h[j]);
@@ -318,11 +365,12 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         }
         const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
         const uint32_t HM2 = (uint32_t)hm * 0x10001u;
-        uint32_t m[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            m[j] = __vimin3_u16x2(F[j], B[j], CAP2) - HM2;
-            if constexpr (PADDED)
+        for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(F[j], B[j], CAP2) - HM2;
+        }
+        if constexpr (PADDED) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
                 m[j] &= (dbase + j < D ? 0xffffu : 0u) | (dbase + 8 + j < D ? 0xffff0000u : 0u);
         }
         const uint4 out = pack_msg(m);
@@ -334,15 +382,30 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
                 diff = (old[q].x != out.x) | (old[q].y != out.y) | (old[q].z != out.z) | (old[q].w != out.w);
             const unsigned dm = __ballot_sync(FULL, diff);
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
+            bool append = false;
+            int64_t qs = 0;
             if (send && changed) {
                 if (lane_data) *dst[q] = out;
-                if (g == 0) dirty_out[slot_of(nbx[q], nby[q], lv.Wh)] = 1;
+                if (g == 0) {
+                    qs = slot_of(nbx[q], nby[q], lv.Wh);
+                    if constexpr (APPEND) append = atomicExch(dirty_out + qs, 1u) == 0u;
+                    else dirty_out[qs] = 1u;
+                }
+            }
+            if constexpr (APPEND) {
+                const unsigned am = __ballot_sync(FULL, append);
+                if (am) {
+                    unsigned base = 0;
+                    if (lane == __ffs(am) - 1) base = atomicAdd(al.n_out, (unsigned)__popc(am));
+                    base = __shfl_sync(FULL, base, __ffs(am) - 1);
+                    if (append) al.out[base + __popc(am & ((1u << lane) - 1u))] = (unsigned)qs;
+                }
             }
         } else if (send && lane_data) {
             *dst[q] = out;
         }
     }
-    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0;
+    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
 }
 
 

@@ -238,6 +238,45 @@ def test_batch_of_mixed_pairs(persistent, graph):
             st.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
+                                  (24, 6, 256, 3, 2, 3, 10, 2)], ids=lambda c: "x".join(map(str, c)))
+def test_every_sweep_variant_is_exact(case, variant):
+    # every kernel variant (stencil / distance transform, dense / active lists) forced on every
+    # scale, even tiny ones, must give the oracle's messages, trace and disparities
+    W, H, D, window, levels, iters, lam, trunc = case
+    pair = synth.make_pair(200 + W + D, W, H, D, 3, 2.0)
+    with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
+        for lvl in range(levels):
+            st.set_variant(lvl, variant)
+        assert st.variants() == [variant] * levels
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        st.bp_solve(iters, lam, trunc, skip=True)
+        msg = st.export_messages(0).cpu().numpy()
+        trace = st.get_trace()
+        disp = st.wta_disparity().cpu().numpy()
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+    ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True)
+    assert np.array_equal(msg, ref_msg) and np.array_equal(trace, ref_trace)
+    assert np.array_equal(disp, oracle.wta(c0, ref_msg))
+
+
+def test_autotuner_picks_exact_variants(tmp_path):
+    from paper_1709_06509_gb300 import autotune
+
+    pair = synth.make_pair(33, 120, 90, 32, 3, 2.0)
+    L, R = to_dev(pair.left), to_dev(pair.right)
+    cache = str(tmp_path / "variants.json")
+    with bps.Stereo(120, 90, 32, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        chosen = autotune.tune(st, L, R, 5, 20, 4, 10, 2, reps=1, cache=cache)
+        assert st.variants() == chosen and all(v in autotune.CANDIDATES for v in chosen)
+        d = st.stereo(L, R, 5, 20, 4, 10, 2, graph=True)
+        again = autotune.tune(st, L, R, 5, 20, 4, 10, 2, cache=cache)  # served from the cache
+        assert again == chosen
+    ref = oracle.stereo_int(pair.left, pair.right, 32, 5, 20, 3, 4, 10, 2)
+    assert np.array_equal(d.cpu().numpy(), ref["disp"])
+
+
 def test_argument_errors_on_a_live_context():
     with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_U8, device=DEV) as st:
         with pytest.raises(bps.BPSError) as e:
