@@ -292,7 +292,9 @@ def main():
 
     tuned = {}
     for (st, window), (L, R) in zip(ctxs, inputs):
-        tuned[f"{st.W}x{st.H}_D{st.D}"] = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3)
+        shape = autotune.tune_ncc(st, L, R, window, TRUNC_DATA)
+        variants = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3)
+        tuned[f"{st.W}x{st.H}_D{st.D}"] = {"ncc_shape": list(shape), "sweep_variants": variants}
 
     # one step = every pair of the workload as one batch: one CUDA graph whose branches are the
     # pairs' launch chains, so the pairs run concurrently
@@ -385,7 +387,7 @@ def main():
                        "trunc_data": TRUNC_DATA, "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC,
                        "fast_skip": True, "message_storage": "uint8 (exact: 0 <= m <= lambda*trunc)",
                        "cost_storage": "int16", "cuda_graph": True, "batch": "both pairs, concurrent graph branches",
-                       "sweep_variants": tuned, "l2": "flushed between timed steps (256 MiB write)",
+                       "autotuned": tuned, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_u8_kernel (all scales, both pairs)",

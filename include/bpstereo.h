@@ -267,6 +267,14 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
  * The autotuner (paper_1709_06509_gb300/autotune.py) picks them by measurement.
  */
+/*
+ * Shape of the NCC kernel's CTAs (windows up to 15): column_groups groups of 16 columns per
+ * CTA (column_groups * D rounded up to 16 threads, between 32 and 512) and `rows` image rows
+ * per strip (even).  0, 0 restores the default.  Results do not depend on it; the autotuner
+ * picks it by measurement.  Drops a graph recorded by bps_stereo.
+ */
+int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
+
 #define BPS_VARIANT_GENERAL_DT 1
 #define BPS_VARIANT_LISTS 2
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);

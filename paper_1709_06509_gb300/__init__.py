@@ -91,6 +91,7 @@ _SIGS = {
     "bps_batch_stereo_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "bps_set_sweep_variant": (_I, [_P, _I, _I]),
     "bps_get_sweep_variant": (_I, [_P, _I]),
+    "bps_set_ncc_shape": (_I, [_P, _I, _I]),
 }
 
 
@@ -255,6 +256,10 @@ def bps_set_sweep_variant(ctx, level: int, variant: int) -> None:
     _check(lib().bps_set_sweep_variant(ctx, level, variant), "bps_set_sweep_variant")
 
 
+def bps_set_ncc_shape(ctx, column_groups: int, rows: int) -> None:
+    _check(lib().bps_set_ncc_shape(ctx, column_groups, rows), "bps_set_ncc_shape")
+
+
 def bps_get_sweep_variant(ctx, level: int) -> int:
     return _check(lib().bps_get_sweep_variant(ctx, level), "bps_get_sweep_variant")
 
@@ -413,6 +418,9 @@ class Stereo:
 
     def set_variant(self, level: int, variant: int) -> None:
         bps_set_sweep_variant(self.ctx, level, variant)
+
+    def set_ncc_shape(self, column_groups: int, rows: int) -> None:
+        bps_set_ncc_shape(self.ctx, column_groups, rows)
 
     def variants(self) -> list[int]:
         return [bps_get_sweep_variant(self.ctx, l) for l in range(self.levels)]

@@ -1,4 +1,5 @@
-"""Autotuner of the red-black sweep: the kernel variant of every scale, picked by measurement.
+"""Autotuner: the NCC kernel's CTA shape and the red-black sweep's kernel variant of every
+scale, picked by measurement.
 
 Every variant computes the same messages (bit for bit); they differ in how fast they run at a
 given scale size and label count (see bps_set_sweep_variant in include/bpstereo.h):
@@ -70,3 +71,45 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
     for lvl, v in enumerate(chosen):
         st.set_variant(lvl, v)
     return chosen
+
+
+def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache: str | None = None):
+    """Pick and set the NCC CTA shape (column groups per CTA, rows per strip) of `st` for
+    windows up to 15; returns it.  Every shape computes the same costs."""
+    import torch
+
+    if window > 15:
+        return (0, 0)
+    gpu = torch.cuda.get_device_name(st.device)
+    Dp = (st.D + 15) // 16 * 16
+    key = f"{gpu}|ncc|{st.W}x{st.H}|Dp{Dp}|w{window}|form{st.msg_type}"
+    table = _load(cache)
+    if key in table:
+        best = tuple(table[key])
+    else:
+        xs_max = 1 if Dp >= 256 else 256 // Dp
+        cands = [(0, 0)]
+        xs = xs_max
+        while xs >= 1:
+            if 32 <= xs * Dp <= 512:
+                cands += [(xs, r) for r in (2, 4, 8, 16, 32, 64) if r <= max(2, st.H)]
+            xs //= 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        timed = {}
+        for c in cands:
+            st.set_ncc_shape(*c)
+            st.build_cost_volume(left, right, window, trunc_data)
+            e0.record()
+            for _ in range(reps):
+                st.build_cost_volume(left, right, window, trunc_data)
+            e1.record()
+            torch.cuda.synchronize()
+            timed[c] = e0.elapsed_time(e1)
+        best = min(timed, key=timed.get)
+        if cache:
+            table[key] = list(best)
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+    st.set_ncc_shape(*best)
+    return best

@@ -118,6 +118,7 @@ struct bps_ctx {
     unsigned *lists[2] = {nullptr, nullptr};  // active lists of the even / odd pixels
     unsigned *list_counts = nullptr;          // entries appended during each half-sweep
     int variant[BPS_MAX_LEVELS] = {};         // u8 sweep kernel variant per scale
+    int ncc_xs = 0, ncc_rows = 0;             // NCC CTA shape (0: default)
     int prof_launches = 0;  // finest-scale sweep launches of the last profiled solve
     int prof_all = 0;       // all sweep launches of the last profiled solve
     int prof_first_trace = 0;
@@ -325,7 +326,7 @@ static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitc
         // the row-streaming kernel also writes scale 1 in the integer forms
         const bool fuse = c->levels > 1 && c->cost_kind != COST_F32;
         CK(launch_ncc_rows(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0,
-                           fuse ? &c->lv[1] : nullptr, ncc_out, st));
+                           fuse ? &c->lv[1] : nullptr, ncc_out, st, c->ncc_xs, c->ncc_rows));
         if (fuse) first_pyramid = 2;
     } else {
         CK(launch_ncc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0.Wh, v0.cost[0],
@@ -925,4 +926,17 @@ extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
 extern "C" int bps_get_sweep_variant(bps_ctx *c, int level) {
     if (!c || level < 0 || level >= c->levels) return BPS_ERR_ARG;
     return c->variant[level];
+}
+
+extern "C" int bps_set_ncc_shape(bps_ctx *c, int column_groups, int rows) {
+    if (!c || column_groups < 0 || rows < 0 || (rows & 1) || column_groups * c->Dp > 512 ||
+        (column_groups > 0 && column_groups * c->Dp < 32))
+        return BPS_ERR_ARG;
+    c->ncc_xs = column_groups;
+    c->ncc_rows = rows;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BPS_OK;
 }

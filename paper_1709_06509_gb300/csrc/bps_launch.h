@@ -42,9 +42,10 @@ cudaError_t launch_pyramid(int cost_kind, const LevelView &fine, const LevelView
 // Row-streaming NCC for windows up to NCC_ROWS_MAX_WINDOW; with l1 != NULL (integer forms)
 // it also writes scale 1 of the pyramid.
 constexpr int NCC_ROWS_MAX_WINDOW = 15;
+// xs, tys: column groups of 16 per CTA and rows per strip (0: the default shape).
 cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int D, int Dp,
                             int window, int T, const LevelView &l0, const LevelView *l1, float *ncc_out,
-                            cudaStream_t st);
+                            cudaStream_t st, int xs = 0, int tys = 0);
 cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
 
 // Kernel variant of the u8 half-sweep at one scale (bit set; see bps_set_sweep_variant).

@@ -197,6 +197,7 @@ template <typename CostT, int R>
 __global__ void __launch_bounds__(512)
 ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Rimg, int pitch, int W, int H, int D,
                 int Dp, int T, int TYS, LevelView l0, LevelView l1, int write_l1, float *ncc_out) {
+    // blockDim.x = XS * Dp: XS column groups of 16, all labels
     using Num = typename NccInt<R>::type;
     pdl_enter();
     constexpr int WIN = 2 * R + 1, RING = 2 * R + 2, VN = NR_TX + 2 * R;
@@ -209,17 +210,15 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
     const int x0 = blockIdx.x * CW, y0 = blockIdx.y * TYS, y1 = min(H, y0 + TYS);
     const int N = WIN * WIN;
 
-    int *colA = reinterpret_cast<int *>(smem);   // [LW]  column sums of L over the window rows
+    // per-pixel and per-right-position records {S, N S_xx - S_x^2, its rsqrt, 0}: one 16-byte
+    // shared load each per output
+    int4 *PA = reinterpret_cast<int4 *>(smem);   // [CW]  left window at pixel x0 + i
+    int4 *PB = PA + CW;                          // [UW]  right window at u = x0 - (D-1) + i
+    int *colA = reinterpret_cast<int *>(PB + UW);  // [LW]  column sums of L over the window rows
     int *colAA = colA + LW;                      // [LW]
     int *colB = colAA + LW;                      // [RW]
     int *colBB = colB + RW;                      // [RW]
-    int *sA = colBB + RW;                        // [CW]  window sum of L at pixel x0 + i
-    unsigned *vA = reinterpret_cast<unsigned *>(sA + CW);  // [CW]  N S_aa - S_a^2
-    float *iA = reinterpret_cast<float *>(vA + CW);        // [CW]  its reciprocal square root
-    int *sB = reinterpret_cast<int *>(iA + CW);            // [UW]  window sum of R at u = x0 - (D-1) + i
-    unsigned *vB = reinterpret_cast<unsigned *>(sB + UW);  // [UW]
-    float *iB = reinterpret_cast<float *>(vB + UW);        // [UW]
-    uint8_t *Lr = reinterpret_cast<uint8_t *>(iB + UW);    // [RING][LW]
+    uint8_t *Lr = reinterpret_cast<uint8_t *>(colBB + RW);  // [RING][LW]
     uint8_t *Rr = Lr + RING * LW;                          // [RING][RW]
 
     for (int i = threadIdx.x; i < LW; i += blockDim.x) colA[i] = colAA[i] = 0;
@@ -275,9 +274,7 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 ss += colAA[i + k];
             }
             const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            sA[i] = s;
-            vA[i] = v;
-            iA[i] = v ? __frsqrt_rn((float)v) : 0.f;
+            PA[i] = make_int4(s, (int)v, __float_as_int(v ? __frsqrt_rn((float)v) : 0.f), 0);
         }
         for (int i = threadIdx.x; i < UW; i += blockDim.x) {
             int s = 0, ss = 0;
@@ -287,9 +284,7 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 ss += colBB[i + k];
             }
             const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            sB[i] = s;
-            vB[i] = v;
-            iB[i] = v ? __frsqrt_rn((float)v) : 0.f;
+            PB[i] = make_int4(s, (int)v, __float_as_int(v ? __frsqrt_rn((float)v) : 0.f), 0);
         }
         __syncthreads();
         int S = 0;
@@ -297,24 +292,34 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
         for (int i = 0; i < WIN; ++i) S += V[i];
         const int cy = y >> 1;
         const bool row_done = (y & 1) || y == H - 1;  // the coarse pixel of this row pair is complete
+        // destinations: x0 + lbase is even, so column j has colour (j + y) & 1 and slot
+        // row_slot + j / 2 in that colour's array
+        const int xb = x0 + lbase;
+        const int64_t row_slot = (int64_t)y * l0.Wh + (xb >> 1);
+        CostT *const base_even = reinterpret_cast<CostT *>((y & 1) ? l0.cost[1] : l0.cost[0]) + row_slot * Dp +
+                                 label_pos<CostT>(dl);
+        CostT *const base_odd = reinterpret_cast<CostT *>((y & 1) ? l0.cost[0] : l0.cost[1]) + row_slot * Dp +
+                                label_pos<CostT>(dl);
 #pragma unroll
         for (int j = 0; j < NR_TX; ++j) {
             if (j) S += V[j + 2 * R] - V[j - 1];
-            const int x = x0 + lbase + j;
-            const int pi = lbase + j, ui = lbase + j + D - 1 - d;
-            const unsigned va = vA[pi], vb = vB[ui];
-            const Num num = (Num)N * (Num)S - (Num)sA[pi] * (Num)sB[ui];
+            const int x = xb + j;
+            const int4 pa = PA[lbase + j];
+            const int4 pb = PB[lbase + j + D - 1 - d];
+            const unsigned va = (unsigned)pa.y, vb = (unsigned)pb.y;
+            const Num num = (Num)N * (Num)S - (Num)pa.x * (Num)pb.x;
             int c;
             float nccf;
             if constexpr (CostOut<CostT>::is_float) {
-                nccf = (va == 0u || vb == 0u) ? 0.f : __fmul_rn(__fmul_rn((float)num, iA[pi]), iB[ui]);
+                nccf = (va == 0u || vb == 0u) ? 0.f
+                                              : __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
                 c = 0;
             } else {
                 if (va == 0u || vb == 0u) {
                     nccf = 0.f;
                     c = T;
                 } else {
-                    nccf = __fmul_rn(__fmul_rn((float)num, iA[pi]), iB[ui]);
+                    nccf = __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
                     const float v = __fadd_rn(__fmul_rn((float)T, __fsub_rn(1.f, nccf)), 0.5f);
                     const float fl = floorf(v);
                     if (fminf(v - fl, fl + 1.f - v) > (float)(T + 1) * (1.f / 131072.f)) {
@@ -328,9 +333,7 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 }
             }
             if (x < W) {
-                const int colour = colour_of(x, y);
-                CostT *dst = reinterpret_cast<CostT *>(colour ? l0.cost[1] : l0.cost[0]) + slot_of(x, y, l0.Wh) * Dp +
-                             label_pos<CostT>(dl);
+                CostT *dst = ((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp;
                 if constexpr (CostOut<CostT>::is_float) {
                     const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
                     *dst = dl < D ? cf : 0.f;
@@ -362,29 +365,43 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
     }
 }
 
-size_t ncc_rows_smem_bytes(int D, int Dp, int window) {
+size_t ncc_rows_smem_bytes(int D, int XS, int window) {
     const int R = window / 2;
-    const int XS = Dp >= 256 ? 1 : 256 / Dp;
     const int CW = XS * NR_TX, LW = CW + 2 * R, RW = CW + 2 * R + D - 1, UW = CW + D - 1;
-    return (size_t)4 * (2 * LW + 2 * RW + 3 * CW + 3 * UW) + (size_t)(2 * R + 2) * (LW + RW);
+    return (size_t)16 * (CW + UW) + (size_t)4 * (2 * LW + 2 * RW) + (size_t)(2 * R + 2) * (LW + RW);
+}
+
+// Default CTA shape: every label of 256 / Dp column groups (256 threads), strips short
+// enough that the grid covers the GPU (each strip re-reads 2R + 1 rows to fill its window),
+// even for the 2x2 sums of scale 1.  bps_set_ncc_shape / the autotuner can replace it.
+static void ncc_rows_default_shape(int W, int H, int Dp, int *XS, int *tys) {
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int xs = Dp >= 256 ? 1 : 256 / Dp;
+    const int nx = (W + xs * NR_TX - 1) / (xs * NR_TX);
+    int rows = (int)(((int64_t)H * nx + sms - 1) / sms);
+    *XS = xs;
+    *tys = std::max(8, std::min(64, (rows + 1) & ~1));
 }
 
 template <typename CostT, int R>
 static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp, int T,
-                                 const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st, bool prep) {
-    const size_t smem = ncc_rows_smem_bytes(D, Dp, 2 * R + 1);
+                                 const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st, bool prep,
+                                 int xs_req = 0, int tys_req = 0) {
     if (prep) {
-        if ((int)smem > smem_optin()) return cudaErrorInvalidValue;
+        const int XSmax = Dp >= 256 ? 1 : 256 / Dp;
+        if ((int)ncc_rows_smem_bytes(D, XSmax, 2 * R + 1) > smem_optin()) return cudaErrorInvalidValue;
         return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     smem_optin());
     }
-    const int XS = Dp >= 256 ? 1 : 256 / Dp;
+    int XS = 1, tys = 16;
+    ncc_rows_default_shape(W, H, Dp, &XS, &tys);
+    if (xs_req > 0) XS = xs_req;
+    if (tys_req > 0) tys = tys_req;
+    const size_t smem = ncc_rows_smem_bytes(D, XS, 2 * R + 1);
     const int threads = XS * Dp;
     const int CW = XS * NR_TX;
     const int nx = (W + CW - 1) / CW;
-    // short strips when the image is small, so that every SM gets work; even for the 2x2 sums
-    int tys = (int)(((int64_t)H * nx + 151) / 152);
-    tys = std::max(8, std::min(64, (tys + 1) & ~1));
     const int ny = (H + tys - 1) / tys;
     LevelView none = l0;
     return launch_k(ncc_rows_kernel<CostT, R>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp, T,
@@ -394,27 +411,27 @@ static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch
 template <typename CostT>
 static cudaError_t launch_rows(int R, const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp,
                                int T, const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st,
-                               bool prep) {
+                               bool prep, int xs = 0, int tys = 0) {
     switch (R) {
-    case 0: return launch_rows_t<CostT, 0>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 1: return launch_rows_t<CostT, 1>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 2: return launch_rows_t<CostT, 2>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 3: return launch_rows_t<CostT, 3>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 4: return launch_rows_t<CostT, 4>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 5: return launch_rows_t<CostT, 5>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    case 6: return launch_rows_t<CostT, 6>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
-    default: return launch_rows_t<CostT, 7>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep);
+    case 0: return launch_rows_t<CostT, 0>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 1: return launch_rows_t<CostT, 1>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 2: return launch_rows_t<CostT, 2>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 3: return launch_rows_t<CostT, 3>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 4: return launch_rows_t<CostT, 4>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 5: return launch_rows_t<CostT, 5>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    case 6: return launch_rows_t<CostT, 6>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
+    default: return launch_rows_t<CostT, 7>(L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, prep, xs, tys);
     }
 }
 
 cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *Rim, int pitch, int W, int H, int D, int Dp,
                             int window, int T, const LevelView &l0, const LevelView *l1, float *ncc_out,
-                            cudaStream_t st) {
+                            cudaStream_t st, int xs, int tys) {
     const int R = window / 2;
     switch (cost_kind) {
-    case COST_I32: return launch_rows<int32_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false);
-    case COST_I16: return launch_rows<int16_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false);
-    default: return launch_rows<float>(R, L, Rim, pitch, W, H, D, Dp, T, l0, nullptr, ncc_out, st, false);
+    case COST_I32: return launch_rows<int32_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false, xs, tys);
+    case COST_I16: return launch_rows<int16_t>(R, L, Rim, pitch, W, H, D, Dp, T, l0, l1, ncc_out, st, false, xs, tys);
+    default: return launch_rows<float>(R, L, Rim, pitch, W, H, D, Dp, T, l0, nullptr, ncc_out, st, false, xs, tys);
     }
 }
 

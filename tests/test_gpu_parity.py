@@ -261,6 +261,17 @@ def test_every_sweep_variant_is_exact(case, variant):
     assert np.array_equal(disp, oracle.wta(c0, ref_msg))
 
 
+@pytest.mark.parametrize("shape", [(2, 2), (2, 8), (4, 4), (8, 64), (16, 2), (0, 0)])
+def test_ncc_shapes_are_exact(shape):
+    pair = synth.make_pair(44, 75, 41, 16, 3, 2.0)
+    with bps.Stereo(75, 41, 16, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        st.set_ncc_shape(*shape)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 7, 20)
+        costs = [st.export_cost(l).cpu().numpy() for l in range(2)]
+    want = oracle.pyramid(oracle.quantise(oracle.ncc(pair.left, pair.right, 16, 7), 20), 2)
+    assert np.array_equal(costs[0], want[0]) and np.array_equal(costs[1], want[1])
+
+
 def test_autotuner_picks_exact_variants(tmp_path):
     from paper_1709_06509_gb300 import autotune
 
@@ -268,6 +279,7 @@ def test_autotuner_picks_exact_variants(tmp_path):
     L, R = to_dev(pair.left), to_dev(pair.right)
     cache = str(tmp_path / "variants.json")
     with bps.Stereo(120, 90, 32, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        autotune.tune_ncc(st, L, R, 5, 20, reps=1, cache=cache)
         chosen = autotune.tune(st, L, R, 5, 20, 4, 10, 2, reps=1, cache=cache)
         assert st.variants() == chosen and all(v in autotune.CANDIDATES for v in chosen)
         d = st.stereo(L, R, 5, 20, 4, 10, 2, graph=True)
