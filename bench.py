@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the HBM-sized roofline_large measurement")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuned choices: read if present, else measured and written")
+    ap.add_argument("--batch-report", type=int, default=0, metavar="N",
+                    help="instead of the benchmark line: throughput of a batch of N mixed pairs (320-1280 x "
+                         "240-720, D in {32,64,96,128}) in every batch mode, one JSON line")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
     ap.add_argument("--workload", default=None,
@@ -250,10 +255,64 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def batch_report(args):
+    """Aggregate Mpix*disp/s of one batch of mixed pairs: a per-pair loop of bps_stereo graphs
+    against one bps_batch_stereo call (concurrent chains, or one persistent launch), each as a
+    CUDA graph, K timed repetitions after W warm-ups, L2 flushed between repetitions."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    specs = synth.batch_specs(args.batch_report)
+    pairs = [synth.make_pair(seed, W, H, D, 8, 3.0) for seed, W, H, D in specs]
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, LEVELS, bps.BPS_MSG_U8, device=dev) for p in pairs]
+    Ls = [torch.from_numpy(p.left).to(dev) for p in pairs]
+    Rs = [torch.from_numpy(p.right).to(dev) for p in pairs]
+    outs = [torch.empty(p.left.shape, dtype=torch.int32, device=dev) for p in pairs]
+    windows = [7] * len(pairs)
+    for st, L, R in zip(sts, Ls, Rs):
+        autotune.tune_ncc(st, L, R, 7, TRUNC_DATA, reps=2)
+        autotune.tune(st, L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    units = sum(p.left.size * p.D for p in pairs)
+    batch = bps.Batch(sts)
+    modes = {
+        "per_pair_loop": lambda: [st.stereo(L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=o)
+                                  for st, L, R, o in zip(sts, Ls, Rs, outs)],
+        "batch_concurrent_chains": lambda: batch.stereo(Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC, outs=outs),
+        "batch_persistent": lambda: batch.stereo(Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC, persistent=True,
+                                                 outs=outs),
+    }
+    res = {}
+    for name, fn in modes.items():
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        res[name] = {"value": units * args.steps / (total / 1e3) / 1e6, "ms_per_batch": total / args.steps}
+    batch.close()
+    for st in sts:
+        st.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": f"batch of {len(pairs)} mixed pairs",
+                      "pixels_x_labels": units, "steps": args.steps, "modes": res}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_report:
+        return batch_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     rank, world, local = dist_env()
     import torch
@@ -292,8 +351,8 @@ def main():
 
     tuned = {}
     for (st, window), (L, R) in zip(ctxs, inputs):
-        shape = autotune.tune_ncc(st, L, R, window, TRUNC_DATA)
-        variants = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3)
+        shape = autotune.tune_ncc(st, L, R, window, TRUNC_DATA, cache=args.tune_cache)
+        variants = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3, cache=args.tune_cache)
         tuned[f"{st.W}x{st.H}_D{st.D}"] = {"ncc_shape": list(shape), "sweep_variants": variants}
 
     # one step = every pair of the workload as one batch: one CUDA graph whose branches are the
