@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the HBM-sized roofline_large measurement")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned choices: read if present, else measured and written")
+    ap.add_argument("--warmstart-report", action="store_true",
+                    help="instead of the benchmark line: train the learned warm start on seeded 450x375 D64 "
+                         "pairs and report energy and throughput against the plain solve, one JSON line")
+    ap.add_argument("--train-pairs", type=int, default=2000)
+    ap.add_argument("--eval-pairs", type=int, default=200)
     ap.add_argument("--batch-report", type=int, default=0, metavar="N",
                     help="instead of the benchmark line: throughput of a batch of N mixed pairs (320-1280 x "
                          "240-720, D in {32,64,96,128}) in every batch mode, one JSON line")
@@ -307,12 +312,71 @@ def batch_report(args):
                       "pixels_x_labels": units, "steps": args.steps, "modes": res}))
 
 
+def warmstart_report(args):
+    """The learned warm start: trained on converged-BP labels of seeded 450x375 D64 pairs
+    (seeds 10000..), evaluated on held-out seeds (20000..) for the iterations it saves at equal
+    final energy, and timed against the plain solve at that energy."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import warmstart
+
+    W, H, D, window = 450, 375, 64, 7
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    train_imgs = warmstart.generate_pairs(range(10000, 10000 + args.train_pairs), W, H, D)
+    eval_imgs = warmstart.generate_pairs(range(20000, 20000 + args.eval_pairs), W, H, D)
+    t_gen = time.perf_counter() - t0
+    feats, targets = warmstart.make_dataset(None, W, H, D, window, TRUNC_DATA, LAM, TRUNC, label_iters=40,
+                                            device=dev, images=train_imgs)
+    net = warmstart.WarmNet(D, seed=0, device=dev)
+    t1 = time.perf_counter()
+    losses = warmstart.train(net, feats, targets, epochs=15, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    res = warmstart.evaluate(net, None, W, H, D, window, TRUNC_DATA, LAM, TRUNC, iters_list=(1, 2, 3, 4, 5, 6, 8, 10),
+                             device=dev, images=eval_imgs)
+    eq = warmstart.iterations_at_equal_energy(res, ITERS)
+    # throughput at equal energy: plain solve with ITERS iterations against the warm-started
+    # solve (network included) with the fewest iterations reaching the same total energy
+    units = W * H * D
+    timing = {}
+    with bps.Stereo(W, H, D, LEVELS, bps.BPS_MSG_U8, device=dev) as st:
+        Ls = [torch.from_numpy(l).to(dev) for l, _ in eval_imgs[:20]]
+        Rs = [torch.from_numpy(r).to(dev) for _, r in eval_imgs[:20]]
+        out = torch.empty((H, W), dtype=torch.int32, device=dev)
+        for form, k in (("plain", ITERS), ("warm", eq["warm"])):
+            if k is None:
+                continue
+            def run():
+                for L, R in zip(Ls, Rs):
+                    st.build_cost_volume(L, R, window, TRUNC_DATA)
+                    init = net.predict_messages(st, LAM, TRUNC) if form == "warm" else None
+                    st.bp_solve(k, LAM, TRUNC, init_msgs=init)
+                    st.wta_disparity(out)
+            run()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run()
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / len(Ls)
+            timing[form] = {"iters": k, "ms_per_pair": ms, "value": units / ms / 1e3}
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "learned warm start, 450x375 D64 pairs",
+                      "train_pairs": args.train_pairs, "eval_pairs": args.eval_pairs, "label_iters": 40,
+                      "loss_per_epoch": losses, "energy_sum_by_iters": res, "iters_at_equal_energy": eq,
+                      "timing_at_equal_energy": timing, "seconds": {"generate": t_gen, "train": t_train}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch_report:
         return batch_report(args)
+    if args.warmstart_report:
+        return warmstart_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     rank, world, local = dist_env()
     import torch

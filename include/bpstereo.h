@@ -281,6 +281,42 @@ int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 
 /*
+ * Learned warm start: kernels of a small convolutional network that predicts the coarsest
+ * scale's messages from the coarsest cost volume (the start messages of bps_bp_solve with
+ * BPS_FLAG_WARM_START).  The paper has no network; it is a way to start BP closer to its fixed
+ * point, judged by the BP energy it leads to.  Activations are [B][C][H][W], BF16 (bf16 != 0)
+ * or FP32; weights [Cout][Cin][3][3] BF16; biases and gradients FP32; every product is
+ * accumulated in FP32.  3x3 convolutions with zero padding keep H x W.  All asynchronous on
+ * `stream`; the caller owns every buffer.  Errors: BPS_ERR_ARG (NULL, sizes < 1), BPS_ERR_CUDA.
+ *
+ * bps_warmnet_conv3x3          out = conv(in, w) + bias, then max(., 0) when relu
+ * bps_warmnet_conv3x3_backward gradients of one such layer from d_gout (the gradient of its
+ *                              output; masked by d_relu_out > 0 when the layer had a ReLU):
+ *                              d_gw (and d_gb when not NULL) always, d_gin when not NULL
+ * bps_warmnet_mse              grad = 2 (pred - target) mask / n and per-block partial sums of
+ *                              the masked mean squared error (nparts blocks)
+ * bps_warmnet_adam             one Adam step (Kingma & Ba 2015) of FP32 master weights, also
+ *                              written as BF16 to d_w_bf16 when not NULL (step counts from 1)
+ * bps_warmnet_features         network input from a natural int32 cost volume [H][W][D]:
+ *                              channel g = (min of labels 8g..8g+7 - min of all labels) * scale,
+ *                              BF16 [ceil(D/8)][H][W]
+ * bps_warmnet_messages         start messages [4][H][W][D] int32 from the network output
+ *                              [4 * D][H][W] FP32: rounded, clamped to [0, cap], minimum
+ *                              shifted to 0, 0 for neighbours outside the image
+ */
+int bps_warmnet_conv3x3(const void *d_in, int in_bf16, int B, int Cin, int H, int W, const void *d_w,
+                        const float *d_bias, int Cout, int relu, void *d_out, int out_bf16, void *stream);
+int bps_warmnet_conv3x3_backward(const float *d_gout, const void *d_relu_out, const void *d_in, int in_bf16, int B,
+                                 int Cin, int H, int W, const void *d_w, int Cout, float *d_gin, float *d_gw,
+                                 float *d_gb, void *stream);
+int bps_warmnet_mse(const float *d_pred, const float *d_target, const float *d_mask, int64_t n, float *d_grad,
+                    float *d_loss_parts, int nparts, void *stream);
+int bps_warmnet_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64_t n, float lr, float beta1,
+                     float beta2, float eps, int step, void *d_w_bf16, void *stream);
+int bps_warmnet_features(const int32_t *d_cost, int H, int W, int D, float scale, void *d_feat, void *stream);
+int bps_warmnet_messages(const float *d_pred, int H, int W, int D, int cap, int32_t *d_init, void *stream);
+
+/*
  * Energy of a labelling without allocating any memory.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory when they need the
  * energy -- code running while a CUDA graph is being captured, real-time loops that may not

@@ -92,6 +92,13 @@ _SIGS = {
     "bps_set_sweep_variant": (_I, [_P, _I, _I]),
     "bps_get_sweep_variant": (_I, [_P, _I]),
     "bps_set_ncc_shape": (_I, [_P, _I, _I]),
+    "bps_warmnet_conv3x3": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P]),
+    "bps_warmnet_conv3x3_backward": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
+    "bps_warmnet_mse": (_I, [_P, _P, _P, _I64, _P, _P, _I, _P]),
+    "bps_warmnet_adam": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              _I, _P, _P]),
+    "bps_warmnet_features": (_I, [_P, _I, _I, _I, ctypes.c_float, _P, _P]),
+    "bps_warmnet_messages": (_I, [_P, _I, _I, _I, _I, _P, _P]),
 }
 
 
@@ -262,6 +269,35 @@ def bps_set_ncc_shape(ctx, column_groups: int, rows: int) -> None:
 
 def bps_get_sweep_variant(ctx, level: int) -> int:
     return _check(lib().bps_get_sweep_variant(ctx, level), "bps_get_sweep_variant")
+
+
+def bps_warmnet_conv3x3(x, x_bf16, B, Cin, H, W, w, bias, Cout, relu, out, out_bf16, stream=None):
+    _check(lib().bps_warmnet_conv3x3(_ptr(x), int(x_bf16), B, Cin, H, W, _ptr(w), _ptr(bias), Cout, int(relu), _ptr(out),
+                                     int(out_bf16), _stream(stream)), "bps_warmnet_conv3x3")
+
+
+def bps_warmnet_conv3x3_backward(gout, relu_out, x, x_bf16, B, Cin, H, W, w, Cout, gin, gw, gb, stream=None):
+    _check(lib().bps_warmnet_conv3x3_backward(_ptr(gout), _ptr(relu_out), _ptr(x), int(x_bf16), B, Cin, H, W, _ptr(w),
+                                              Cout, _ptr(gin), _ptr(gw), _ptr(gb), _stream(stream)),
+           "bps_warmnet_conv3x3_backward")
+
+
+def bps_warmnet_mse(pred, target, mask, n, grad, loss_parts, nparts, stream=None):
+    _check(lib().bps_warmnet_mse(_ptr(pred), _ptr(target), _ptr(mask), n, _ptr(grad), _ptr(loss_parts), nparts,
+                                 _stream(stream)), "bps_warmnet_mse")
+
+
+def bps_warmnet_adam(w, m, v, g, n, lr, beta1, beta2, eps, step, w_bf16=None, stream=None):
+    _check(lib().bps_warmnet_adam(_ptr(w), _ptr(m), _ptr(v), _ptr(g), n, lr, beta1, beta2, eps, step, _ptr(w_bf16),
+                                  _stream(stream)), "bps_warmnet_adam")
+
+
+def bps_warmnet_features(cost, H, W, D, scale, feat, stream=None):
+    _check(lib().bps_warmnet_features(_ptr(cost), H, W, D, scale, _ptr(feat), _stream(stream)), "bps_warmnet_features")
+
+
+def bps_warmnet_messages(pred, H, W, D, cap, init, stream=None):
+    _check(lib().bps_warmnet_messages(_ptr(pred), H, W, D, cap, _ptr(init), _stream(stream)), "bps_warmnet_messages")
 
 
 def bps_last_cuda_error() -> int:
