@@ -262,7 +262,15 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  *   BPS_VARIANT_GENERAL_DT  minimise with the forward/backward distance transform even
  *                           when trunc <= 2 allows the shorter stencil forms;
  *   BPS_VARIANT_LISTS       with the fast-converging skip, process only the listed dirty
- *                           pixels after the scale's first iteration.
+ *                           pixels after the scale's first iteration;
+ *   BPS_VARIANT_CLUSTER     run every iteration of the scale in one launch of one 16-CTA
+ *                           thread-block cluster (hardware cluster barrier between the
+ *                           half-sweeps); BPS_ERR_UNSUPPORTED where such a cluster does not fit;
+ *   BPS_VARIANT_EAGER       (dense launches) issue every load of a half-sweep at once, before
+ *                           the dirty flag is known, and the costs before the wait on the
+ *                           preceding kernel: one round trip to memory per half-sweep instead
+ *                           of two, at the price of loading clean pixels (small scales).
+ * With BPS_FLAG_PROFILE a cluster launch's time is shared out evenly over its half-sweeps.
  * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
  * The autotuner (paper_1709_06509_gb300/autotune.py) picks them by measurement.
@@ -277,6 +285,8 @@ int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
 
 #define BPS_VARIANT_GENERAL_DT 1
 #define BPS_VARIANT_LISTS 2
+#define BPS_VARIANT_CLUSTER 4
+#define BPS_VARIANT_EAGER 8
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 

@@ -3,31 +3,39 @@ scale, picked by measurement.
 
 Every variant computes the same messages (bit for bit); they differ in how fast they run at a
 given scale size and label count (see bps_set_sweep_variant in include/bpstereo.h):
-  0                          stencil form where trunc <= 2, dense launch over all pixels
-  LISTS                      ... with active lists after the scale's first iteration
-  GENERAL_DT                 distance-transform form, dense launch
-  GENERAL_DT | LISTS         distance-transform form with active lists
-For one context and one representative input, tune() runs the whole solve once per
-candidate with CUDA events around every half-sweep launch (BPS_FLAG_PROFILE), sums the
-launch times of each scale, and keeps each scale's fastest candidate.  Scales do not
-interact, so one solve per candidate times every scale at once.  Choices can be cached in
-a JSON file keyed by GPU, scale size, padded label count, numerical form, truncation class
-and skip, so later contexts of the same shapes skip the measurement.
+  0                  stencil form where trunc <= 2, dense launch over all pixels, the dirty
+                     flag read before the inputs
+  GENERAL_DT         distance-transform form instead of the stencil
+  LISTS              active lists after the scale's first iteration (large scales)
+  EAGER              every load of a half-sweep issued at once (small scales)
+  CLUSTER            every iteration of the scale in one thread-block-cluster launch
+and their combinations.  For one context and one representative input, tune() replays the
+whole pipeline from its CUDA graph (the way the variants run in production: consecutive
+launches overlap, which per-launch events would hide) and descends one scale at a time,
+coarsest first, keeping each scale's fastest candidate with the others fixed.  Choices can
+be cached in a JSON file keyed by GPU, scale size, padded label count, numerical form,
+truncation class and skip, so later contexts of the same shapes skip the measurement.
 """
 from __future__ import annotations
 
 import json
 import os
 
-from . import BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, level_dims
+from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_CLUSTER, BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT,
+               BPS_VARIANT_LISTS, BPSError, level_dims)
 
-CANDIDATES = (0, BPS_VARIANT_LISTS, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS)
+_G, _L, _E, _C = BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER
+# a cluster launch is only a candidate for scales of at most this many lanes (pixels x lanes per pixel)
+CLUSTER_MAX_LANES = 16 * 16 * 512
+SMALL_CANDIDATES = (0, _G, _E, _E | _G, _C, _C | _E, _C | _E | _G)
+LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L)
+CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
 
 
 def _key(gpu: str, w: int, h: int, D: int, msg_type: int, trunc: int, skip: bool) -> str:
     tclass = trunc if trunc <= 2 else 3  # the stencil forms exist for trunc 0, 1, 2 only
     Dp = (D + 15) // 16 * 16
-    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}"
+    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v2"
 
 
 def _load(path: str | None) -> dict:
@@ -37,8 +45,15 @@ def _load(path: str | None) -> dict:
     return {}
 
 
+def _lanes_per_pixel(D: int) -> int:
+    Gp = 1
+    while Gp * 16 < (D + 15) // 16 * 16:
+        Gp *= 2
+    return Gp
+
+
 def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, trunc: int, skip: bool = True,
-         reps: int = 3, cache: str | None = None) -> list[int]:
+         reps: int = 3, cache: str | None = None, target_ms: float = 10.0) -> list[int]:
     """Pick and set the variant of every scale of `st` (a Stereo); returns them per scale."""
     import torch
 
@@ -49,20 +64,48 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
     if all(k in table for k in keys):
         chosen = [int(table[k]) for k in keys]
     else:
-        per = 2 * iters
-        times = {v: [0.0] * st.levels for v in CANDIDATES}
-        st.build_cost_volume(left, right, window, trunc_data)
-        for v in CANDIDATES:
-            for lvl in range(st.levels):
+        Gp = _lanes_per_pixel(st.D)
+        small = [h * ((w + 1) // 2) * Gp <= CLUSTER_MAX_LANES for w, h in dims]
+        out = torch.empty((st.H, st.W), dtype=torch.int32, device=st.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def run():
+            st.stereo(left, right, window, trunc_data, iters, lam, trunc, graph=True, skip=skip, out=out)
+
+        def step_ms(vs) -> float:
+            for lvl, v in enumerate(vs):
                 st.set_variant(lvl, v)
-            st.bp_solve(iters, lam, trunc, skip=skip, profile=True)  # warm-up of this variant
+            run()  # records the graph
+            run()
+            e0.record()
+            run()
+            e1.record()
+            e1.synchronize()
+            n = max(2, min(200, int(target_ms / max(e0.elapsed_time(e1), 1e-3))))
+            best = float("inf")
             for _ in range(reps):
-                st.bp_solve(iters, lam, trunc, skip=skip, profile=True)
-                t = st.read_launch_times()
-                # launch order is coarsest scale first
-                for k in range(st.levels):
-                    times[v][st.levels - 1 - k] += float(t[k * per:(k + 1) * per].sum())
-        chosen = [min(CANDIDATES, key=lambda v: times[v][lvl]) for lvl in range(st.levels)]
+                e0.record()
+                for _ in range(n):
+                    run()
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / n)
+            return best
+
+        current = st.variants()
+        for lvl in reversed(range(st.levels)):
+            times = {}
+            for v in (SMALL_CANDIDATES if small[lvl] else LARGE_CANDIDATES):
+                trial = list(current)
+                trial[lvl] = v
+                try:
+                    times[v] = step_ms(trial)
+                except BPSError as e:
+                    if e.status == BPS_ERR_UNSUPPORTED:  # no room for the cluster on this GPU
+                        continue
+                    raise
+            current[lvl] = min(times, key=times.get)
+        chosen = current
         if cache:
             table.update({k: v for k, v in zip(keys, chosen)})
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)

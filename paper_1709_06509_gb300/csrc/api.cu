@@ -123,6 +123,8 @@ struct bps_ctx {
     int prof_all = 0;       // all sweep launches of the last profiled solve
     int prof_first_trace = 0;
     int prof_trace_n = 0;   // trace entries covered by the profiled launches
+    uint64_t config_version = 0;  // bumped when a kernel choice (variant, NCC shape) changes
+    std::vector<int> prof_span;  // half-sweeps each profiled launch covers (a cluster launch covers a scale)
 };
 
 namespace {
@@ -152,10 +154,12 @@ PairDesc make_desc(const bps_ctx *c) {
 // Defaults of the per-scale sweep variant, from measurements on GB300 (the autotuner may
 // replace them): the stencil forms win below about half a million pixels of a colour, the
 // distance transform above; active lists pay off from about 128 K pixels of a colour.
-int default_variant(int64_t slots) {
+int default_variant(int64_t slots, int Gp = 1) {
     int v = 0;
     if (slots >= 512 * 1024) v |= VARIANT_GENERAL_DT;
     if (slots >= 128 * 1024) v |= VARIANT_LISTS;
+    // a scale of at most four passes of a 16 x 512-thread cluster runs as one cluster launch
+    if (slots * Gp <= 4 * 16 * 512 && cluster_sweep_available()) v |= VARIANT_CLUSTER;
     return v;
 }
 
@@ -255,7 +259,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->lists[0] = reinterpret_cast<unsigned *>(c->ws + p.lists[0]);
     c->lists[1] = reinterpret_cast<unsigned *>(c->ws + p.lists[1]);
     c->list_counts = reinterpret_cast<unsigned *>(c->ws + p.list_counts);
-    for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l]);
+    for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l], c->Gp);
     PairDesc hd = make_desc(c);
     std::vector<int> prefix(2 * (levels + 1));
     for (int l = 0; l < levels; ++l) {
@@ -424,6 +428,7 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
     CK(launch_persistent(c->msg_kind, P, c->grid, st));
     if (prof) {
         CK(cudaEventRecord(c->ev[1], st));
+        c->prof_span.assign(1, 1);
         c->prof_all = 1;
         c->prof_launches = 1;
         c->prof_first_trace = 0;
@@ -442,6 +447,7 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     const int ntrace = levels * iters * 2;
     if (prof) {
         const size_t need = 2 * (size_t)levels * iters * 2;
+        c->prof_span.assign((size_t)levels * iters * 2 + 1, 1);
         while (c->ev.size() < need) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
@@ -467,6 +473,19 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         // only the even pixels' start messages are ever read: the first half-sweep overwrites every
         // existing incoming slot of the odd pixels (unless there is no sweep at all)
         if (l < top) CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, iters == 0 ? 1 : 0, c->Dp, skip ? 1 : 0, st));
+        if (iters > 0 && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_CLUSTER)) {
+            if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
+            CK(launch_sweep_level_cluster(v, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, iters,
+                                          c->variant[l], st));
+            if (prof) {
+                CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
+                c->prof_span[c->prof_all] = 2 * iters;
+                ++c->prof_all;
+                if (l == 0) c->prof_launches += 2 * iters;
+            }
+            t += 2 * iters;
+            continue;
+        }
         for (int it = 0; it < iters; ++it)
             for (int colour = 0; colour < 2; ++colour, ++t) {
                 if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
@@ -485,6 +504,7 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
                                 c->variant[l]));
                 if (prof) {
                     CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
+                    c->prof_span[c->prof_all] = 1;
                     ++c->prof_all;
                     if (l == 0) ++c->prof_launches;
                 }
@@ -632,11 +652,13 @@ extern "C" int bps_export_cost(bps_ctx *c, int level, void *d_out, void *stream)
 extern "C" int bps_read_profile(bps_ctx *c, int *h_launches, double *h_total_ms, int64_t *h_pixels) {
     if (!c || !h_launches || !h_total_ms || !h_pixels) return BPS_ERR_ARG;
     double total = 0.0;
-    for (int k = c->prof_all - c->prof_launches; k < c->prof_all; ++k) {
+    int covered = 0;
+    for (int k = c->prof_all - 1; k >= 0 && covered < c->prof_launches; --k) {
         CK(cudaEventSynchronize(c->ev[2 * k + 1]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
         total += ms;
+        covered += (int)c->prof_span.size() > k ? c->prof_span[k] : 1;
     }
     int64_t px = 0;
     if (c->prof_launches && c->prof_trace_n) {
@@ -653,12 +675,14 @@ extern "C" int bps_read_profile(bps_ctx *c, int *h_launches, double *h_total_ms,
 
 extern "C" int bps_read_launch_times(bps_ctx *c, double *h_ms, int cap) {
     if (!c || cap < 0 || (!h_ms && cap > 0)) return BPS_ERR_ARG;
-    const int n = std::min(cap, c->prof_all);
-    for (int k = 0; k < n; ++k) {
+    int n = 0;
+    for (int k = 0; k < c->prof_all; ++k) {
         CK(cudaEventSynchronize(c->ev[2 * k + 1]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
-        h_ms[k] = ms;
+        // a launch covering several half-sweeps (a cluster launch) is shared out evenly
+        const int span = (int)c->prof_span.size() > k ? c->prof_span[k] : 1;
+        for (int j = 0; j < span && n < cap; ++j) h_ms[n++] = ms / span;
     }
     return n;
 }
@@ -694,6 +718,7 @@ std::vector<intptr_t> batch_key(const bps_batch *b, const uint8_t *const *L, con
         k.push_back(pitches[i]);
         k.push_back(windows[i]);
         k.push_back((intptr_t)disps[i]);
+        k.push_back((intptr_t)b->ctxs[i]->config_version);  // a member's kernel choices changed
     }
     return k;
 }
@@ -913,9 +938,12 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
 }
 
 extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
-    if (!c || level < 0 || level >= c->levels || variant < -1 || variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS))
+    if (!c || level < 0 || level >= c->levels || variant < -1 ||
+        variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER))
         return BPS_ERR_ARG;
-    c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level]) : variant;
+    if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
+    c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp) : variant;
+    ++c->config_version;
     if (c->gexec) {  // a recorded graph holds the old kernels
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -934,6 +962,7 @@ extern "C" int bps_set_ncc_shape(bps_ctx *c, int column_groups, int rows) {
         return BPS_ERR_ARG;
     c->ncc_xs = column_groups;
     c->ncc_rows = rows;
+    ++c->config_version;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;

@@ -2,6 +2,8 @@
 // Converging BP" and "GPU Implementation"): one kernel launch per red-black half-sweep,
 // the coarse-to-fine start, and import / export of messages and costs in the natural
 // layout.  The per-pixel work lives in sweep_body.cuh.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -33,6 +35,17 @@ sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int la
         sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
 }
 
+// The same half-sweep with every load issued at once (see EAGER in sweep_group_u8): the first
+// block of each CTA loads its costs before waiting for the predecessor kernel.
+template <bool PADDED, int TS>
+__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+sweep_u8_eager_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                      unsigned long long *trace, int nblocks) {
+    sweep_group_u8<PADDED, false, TS, false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+    for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
+        sweep_group_u8<PADDED, false, TS, false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+}
+
 // The same half-sweep over the pixels of an active list; its length is read on the device
 // (a recorded graph keeps the launch shape, the list decides the work).
 template <bool PADDED, int TS>
@@ -47,11 +60,122 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
         sweep_group_u8<PADDED, true, TS>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n);
 }
 
+// Every iteration of one small scale in ONE launch of ONE thread-block cluster.  The CTAs of
+// a cluster are co-scheduled, so the hardware cluster barrier (release / acquire at cluster
+// scope, covering global memory) separates the half-sweeps: no software spin, no launch per
+// half-sweep.  Used where the whole scale is a few passes of the cluster's threads.
+constexpr int CLUSTER_CTAS = 16, CLUSTER_THREADS = 512;
+
+template <bool PADDED, int TS, int EAGER>
+__global__ void __launch_bounds__(CLUSTER_THREADS, 1)
+sweep_u8_cluster_kernel(LevelView lv, int D, int Dp, int Gp, int lam, int lamT, int skip, unsigned long long *trace,
+                        int iters, int nblocks) {
+    pdl_enter();
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    for (int it = 0; it < iters; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            unsigned long long *tr = trace ? trace + 2 * it + colour : nullptr;
+            for (int b = rank; b < nblocks; b += ncta)
+                sweep_group_u8<PADDED, false, TS, true, EAGER>(lv, colour, D, Dp, Gp, lam, lamT, skip, tr, b);
+            cl.sync();
+        }
+}
+
+template <bool PADDED, int TS, int EAGER>
+static cudaError_t launch_cluster_ts(const LevelView &lv, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                                     unsigned long long *trace, int iters, cudaStream_t st) {
+    const int groups = CLUSTER_THREADS / Gp;
+    const int nblocks = (int)(((int64_t)lv.H * lv.Wh + groups - 1) / groups);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLUSTER_CTAS);
+    cfg.blockDim = dim3(CLUSTER_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLUSTER_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, sweep_u8_cluster_kernel<PADDED, TS, EAGER>, lv, D, Dp, Gp, lam, lamT, skip, trace,
+                              iters, nblocks);
+}
+
+template <int EAGER>
+static cudaError_t launch_cluster_form(bool padded, int ts, const LevelView &lv, int D, int Dp, int Gp, int lam,
+                                       int lt, int skip, unsigned long long *trace, int iters, cudaStream_t st) {
+    if (padded) {
+        if (ts == 1) return launch_cluster_ts<true, 1, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+        if (ts == 2) return launch_cluster_ts<true, 2, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+        return launch_cluster_ts<true, 0, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+    }
+    if (ts == 1) return launch_cluster_ts<false, 1, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+    if (ts == 2) return launch_cluster_ts<false, 2, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+    return launch_cluster_ts<false, 0, EAGER>(lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+}
+
+cudaError_t launch_sweep_level_cluster(const LevelView &lv, int D, int Dp, int Gp, int lambda, int trunc, int skip,
+                                       unsigned long long *trace, int iters, int variant, cudaStream_t st) {
+    const int lam = trunc == 0 ? 0 : lambda;
+    const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
+    const int lt = lam * trunc;
+    const bool eager = (variant & VARIANT_EAGER) != 0;
+    if (eager) return launch_cluster_form<1>(D & 15, ts, lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+    return launch_cluster_form<0>(D & 15, ts, lv, D, Dp, Gp, lam, lt, skip, trace, iters, st);
+}
+
+template <bool PADDED, int TS, int EAGER> static cudaError_t prepare_cluster1() {
+    cudaError_t e = cudaFuncSetAttribute(sweep_u8_cluster_kernel<PADDED, TS, EAGER>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_cluster_kernel<PADDED, TS, EAGER>);
+    return e;
+}
+template <bool PADDED, int TS> static cudaError_t prepare_cluster() {
+    const cudaError_t e = prepare_cluster1<PADDED, TS, 0>();
+    return e == cudaSuccess ? prepare_cluster1<PADDED, TS, 1>() : e;
+}
+
+// Whether a 16-CTA cluster of the u8 sweep fits on this GPU (looked up once per process).
+bool cluster_sweep_available() {
+    static int state = -1;
+    if (state < 0) {
+        state = 0;
+        if (prepare_cluster<false, 0>() == cudaSuccess && prepare_cluster<false, 1>() == cudaSuccess &&
+            prepare_cluster<false, 2>() == cudaSuccess && prepare_cluster<true, 0>() == cudaSuccess &&
+            prepare_cluster<true, 1>() == cudaSuccess && prepare_cluster<true, 2>() == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(CLUSTER_CTAS);
+            cfg.blockDim = dim3(CLUSTER_THREADS);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CLUSTER_CTAS;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, sweep_u8_cluster_kernel<false, 0, 0>, &cfg) == cudaSuccess &&
+                clusters >= 1)
+                state = 1;
+        }
+        cudaGetLastError();
+    }
+    return state == 1;
+}
+
 // Kernel of one u8 half-sweep: padding variant x list / append mode x minimisation form.
 template <bool PADDED, int TS>
 static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                                cudaStream_t st) {
+                                bool eager, cudaStream_t st) {
+    if (eager && !al.in && !al.out)  // grid <= blocks: every CTA has a first block
+        return launch_k(sweep_u8_eager_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                        lamT, skip, trace, (int)blocks);
     if (skip && al.in)
         return launch_k(sweep_u8_list_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
                         lamT, trace, al);
@@ -66,11 +190,11 @@ static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, 
 template <bool PADDED>
 static cudaError_t launch_u8(int ts, const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                              unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                             cudaStream_t st) {
+                             bool eager, cudaStream_t st) {
     switch (ts) {
-    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
-    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
-    default: return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, st);
+    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
+    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
+    default: return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
     }
 }
 
@@ -111,8 +235,10 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_blocks(MSG_U8));
         const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
-        if (D & 15) return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, st);
-        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, st);
+        const bool eager = (variant & VARIANT_EAGER) != 0;
+        if (D & 15)
+            return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, st);
+        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, st);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -247,6 +373,7 @@ template <bool PADDED, int TS> static cudaError_t preload_u8() {
     cudaError_t e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, false, TS>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, true, TS>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_list_kernel<PADDED, TS>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_eager_kernel<PADDED, TS>);
     return e;
 }
 

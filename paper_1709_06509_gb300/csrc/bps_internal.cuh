@@ -136,6 +136,17 @@ __device__ inline void load16_rw(const __half *p, float (&v)[VEC]) {
     }
 }
 
+// Message loads of a kernel that may also have written them earlier in the same launch (a
+// cluster or persistent kernel, across its barriers) must take the coherent path.
+template <bool RW, typename T, typename V> __device__ inline void load16_msg(const T *p, V (&v)[VEC]) {
+    if constexpr (RW) load16_rw(p, v);
+    else load16(p, v);
+}
+template <bool RW> __device__ inline uint4 load_u4(const uint4 *p) {
+    if constexpr (RW) return *p;
+    else return __ldg(p);
+}
+
 // The value a message takes once stored (fp16 rounds; the integer forms are exact).
 template <typename MsgT> __device__ inline int stored_value(int v) { return v; }
 template <typename MsgT> __device__ inline float stored_value(float v) { return __half2float(__float2half_rn(v)); }

@@ -51,6 +51,8 @@ cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
 // Kernel variant of the u8 half-sweep at one scale (bit set; see bps_set_sweep_variant).
 constexpr int VARIANT_GENERAL_DT = 1;  // the distance transform even where a stencil form exists
 constexpr int VARIANT_LISTS = 2;       // active lists after the scale's first iteration (skip on)
+constexpr int VARIANT_CLUSTER = 4;     // every iteration of the scale in one thread-block-cluster launch
+constexpr int VARIANT_EAGER = 8;       // every load of a half-sweep issued at once (dense launches)
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {
@@ -65,6 +67,12 @@ struct SweepLists {
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
                          int trunc, int skip, unsigned long long *trace, cudaStream_t st,
                          const SweepLists &lists = SweepLists{nullptr, nullptr, nullptr, nullptr}, int variant = 0);
+// All iterations of one scale (u8 form) in one launch of one 16-CTA cluster; available only
+// where such a cluster fits (cluster_sweep_available).
+bool cluster_sweep_available();
+cudaError_t launch_sweep_level_cluster(const LevelView &lv, int D, int Dp, int Gp, int lambda, int trunc, int skip,
+                                       unsigned long long *trace, int iters, int variant, cudaStream_t st);
+
 // Coarse-to-fine start: copy parent messages into the fine pixels of `colour` (and of the
 // other colour too when both_colours), and mark every pixel of the fine scale dirty when
 // set_dirty (fast-converging skip).

@@ -173,34 +173,90 @@ static int smem_optin() {
 
 // ------------------------------------------------------------------ row-streaming NCC (windows up to 15)
 // ncc_rows_kernel: a CTA owns a strip of rows [y0, y0 + TYS) and XS * 16 columns; thread
-// (label d, column group xs) owns 16 consecutive columns at one label.  Walking down the
-// rows, each thread keeps the vertical window sums V of L(x') * R(x' - d) for its 16 + 2R
-// columns in registers (one row enters, one leaves: O(1) per row), and slides a horizontal
-// window over V for its 16 outputs.  Per row the CTA stages the entering row of L and R in
-// a shared ring of 2R + 2 rows, updates column sums of L, L^2, R, R^2 and forms, once per
-// pixel and once per right position, the window sums S, the variance term N S_xx - S_x^2
-// and its reciprocal square root (correctly rounded).  The data cost of each (pixel,
-// label) then needs one multiply-add for the numerator and two multiplies for the
-// correlation.  The 2x2 sum of the next scale is accumulated over row pairs in registers
-// and written directly (scale 1 of the pyramid).
+// (label d, column group xs) owns 16 consecutive columns at one label.
 //
-// Quantiser: the fp32 correlation num * rsqrt(va) * rsqrt(vb) has a relative error below
-// 6 * 2^-24 (six correctly rounded steps), so v = T (1 - ncc) + 1/2 is within (T + 1) * 2^-20
-// of its exact value; the FP64 sequence decides only where v lies within (T + 1) * 2^-17 of
-// an integer.
+// Every staged column (left: the CTA's columns and the horizontal window margin; right: the
+// positions those can match) keeps the 2R + 1 image bytes of its current window rows packed
+// in NW = ceil((2R + 1) / 4) 32-bit words, a shift register held by the thread that owns the
+// column: one byte enters per row.  The owner publishes the words to shared memory each row,
+// with the column's sum and sum of squares (4-way byte dot products with ones and with the
+// words themselves).  The vertical window sum of L(x') R(x' - d) of a column is then NW
+// byte dot products (dp4a) of the left and the right words, with no running state, so a
+// strip needs no per-label warm-up rows (only the owners shift in the 2R rows above the
+// strip).  Each thread slides the horizontal window over those column sums for its 16
+// outputs.  Per pixel and per right position the CTA forms once the window sum S, the
+// variance term N S_xx - S_x^2 and its reciprocal square root (correctly rounded).  The data
+// cost of each (pixel, label) then needs one multiply-add for the numerator and two
+// multiplies for the correlation.  The 2x2 sum of the next scale is accumulated over row
+// pairs in registers and written directly (scale 1 of the pyramid).
+//
+// Quantiser: one fused multiply-add forms v = T (1 - ncc) + 1/2 in fp32 within (T + 1) 2^-21
+// of its exact value (see quantise_fp32); the FP64 sequence decides only where v lies within
+// (T + 1) 2^-17 of an integer, after the row, for the few outputs that need it.
 constexpr int NR_TX = 16;
+constexpr int NR_ITEMS = 4;  // staged columns per thread at most (checked by the launcher)
+#ifndef NCC_ROWS_MAXNREG
+#define NCC_ROWS_MAXNREG 80  // registers a thread: 24 warps on an SM, CTAs of up to 512 threads
+#endif
 
 template <int R> struct NccInt { using type = int; };
 template <> struct NccInt<7> { using type = long long; };  // 15x15: N S_ab - S_a S_b needs 33 bits
 
-template <typename CostT, int R>
-__global__ void __launch_bounds__(512)
+// Words of a packed column window: (2R + 1) bytes, padded to 1, 2 or 4 words so that one
+// shared load fetches a column.
+template <int R> struct WinWords {
+    static constexpr int NW = (2 * R + 1 + 3) / 4;
+    static constexpr int NWP = NW <= 1 ? 1 : (NW <= 2 ? 2 : 4);
+};
+template <int NWP> struct alignas(4 * NWP) Win { uint32_t w[NWP]; };
+
+// The rare exact decision of the quantiser, out of line: the fp32 path is the hot one.
+template <typename Num>
+__device__ __noinline__ int quantise_fp64(Num num, unsigned va, unsigned vb, int T) {
+    const double den = __dmul_rn((double)va, (double)vb);
+    const double n64 = __ddiv_rn((double)num, __dsqrt_rn(den));
+    return (int)floor(__dadd_rn(__dmul_rn((double)T, __dadd_rn(1.0, -n64)), 0.5));
+}
+
+// A store under a predicate, without a branch around it.
+__device__ __forceinline__ void store_if(int16_t *p, int16_t v, bool pred) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.u16 [%0], %1;\n\t}" ::"l"(p),
+                 "h"(v), "r"((unsigned)pred)
+                 : "memory");
+}
+__device__ __forceinline__ void store_if(int32_t *p, int32_t v, bool pred) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.u32 [%0], %1;\n\t}" ::"l"(p),
+                 "r"(v), "r"((unsigned)pred)
+                 : "memory");
+}
+
+// The fp32 quantiser step of one (pixel, label): the level c = min(floor(v), T) of
+// v = (T + 1/2) - (T ra) rb num, one fused multiply-add, and whether v lies within the margin
+// m = (T + 1) 2^-17 of an integer (then only the FP64 sequence may decide).  ra, rb are the
+// correctly rounded reciprocal square roots of the two variance terms (each within 1.5 2^-24
+// relative of the exact value, the conversion to fp32 included) and T ra is rounded once more,
+// so the product carries at most 6 2^-24 relative error and v at most (T + 1) 2^-21 absolute
+// error: outside the margin the fp32 and the exact decision agree.  v >= 1/2 - (T + 1) 2^-21
+// > 0, so the lower clamp at 0 is never needed.  A zero variance has a zero reciprocal
+// square root, so v = T + 1/2 and c = T, the value the definition gives for ncc = 0.
+__device__ __forceinline__ int quantise_fp32(float numf, float tra, float rb, float T_half, float half_m, int T,
+                                             bool *near) {
+    const float v = __fmaf_rn(-__fmul_rn(tra, rb), numf, T_half);
+    const float fl = floorf(v);
+    *near = !(fabsf((v - fl) - 0.5f) < half_m);  // v - fl is exact
+    return min((int)fl, T);
+}
+
+template <typename CostT, int R, bool NCC_OUT>
+__global__ void __maxnreg__(NCC_ROWS_MAXNREG)
 ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Rimg, int pitch, int W, int H, int D,
                 int Dp, int T, int TYS, LevelView l0, LevelView l1, int write_l1, float *ncc_out) {
     // blockDim.x = XS * Dp: XS column groups of 16, all labels
     using Num = typename NccInt<R>::type;
-    pdl_enter();
-    constexpr int WIN = 2 * R + 1, RING = 2 * R + 2, VN = NR_TX + 2 * R;
+    constexpr int WIN = 2 * R + 1, VN = NR_TX + 2 * R;
+    constexpr int NW = WinWords<R>::NW, NWP = WinWords<R>::NWP;
+    constexpr bool FLOAT_COST = CostOut<CostT>::is_float;
+    using WinT = Win<NWP>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int XS = blockDim.x / Dp;
     const int CW = XS * NR_TX;
@@ -212,60 +268,100 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
 
     // per-pixel and per-right-position records {S, N S_xx - S_x^2, its rsqrt, 0}: one 16-byte
     // shared load each per output
-    int4 *PA = reinterpret_cast<int4 *>(smem);   // [CW]  left window at pixel x0 + i
-    int4 *PB = PA + CW;                          // [UW]  right window at u = x0 - (D-1) + i
-    int *colA = reinterpret_cast<int *>(PB + UW);  // [LW]  column sums of L over the window rows
-    int *colAA = colA + LW;                      // [LW]
-    int *colB = colAA + LW;                      // [RW]
-    int *colBB = colB + RW;                      // [RW]
-    uint8_t *Lr = reinterpret_cast<uint8_t *>(colBB + RW);  // [RING][LW]
-    uint8_t *Rr = Lr + RING * LW;                          // [RING][RW]
+    int4 *PA = reinterpret_cast<int4 *>(smem);       // [CW]  left window at pixel x0 + i
+    int4 *PB = PA + CW;                              // [UW]  right window at u = x0 - (D-1) + i
+    WinT *LWn = reinterpret_cast<WinT *>(PB + UW);   // [2][LW] packed left column windows (by row parity)
+    WinT *RWn = LWn + 2 * LW;                        // [2][RW] ... right
+    int *colA = reinterpret_cast<int *>(RWn + 2 * RW);  // [LW]  column sums of L over the window rows
+    int *colAA = colA + LW;                          // [LW]
+    int *colB = colAA + LW;                          // [RW]
+    int *colBB = colB + RW;                          // [RW]
 
-    for (int i = threadIdx.x; i < LW; i += blockDim.x) colA[i] = colAA[i] = 0;
-    for (int i = threadIdx.x; i < RW; i += blockDim.x) colB[i] = colBB[i] = 0;
-    int V[VN];
+    // the staged columns this thread owns: item k is column tid + k * blockDim of the left
+    // (index < LW) or the right (index - LW) image
+    const int items = LW + RW;
+    const int nk = (items - (int)threadIdx.x + (int)blockDim.x - 1) / (int)blockDim.x;  // items of this thread
+    uint32_t win[NR_ITEMS][NWP];
+    int col[NR_ITEMS];  // the item's clamped image column
 #pragma unroll
-    for (int i = 0; i < VN; ++i) V[i] = 0;
+    for (int k = 0; k < NR_ITEMS; ++k) {
+#pragma unroll
+        for (int w = 0; w < NWP; ++w) win[k][w] = 0u;
+        const int it = threadIdx.x + k * blockDim.x;
+        col[k] = it < LW ? clampi(x0 - R + it, 0, W - 1) : clampi(x0 - R - (D - 1) + (it - LW), 0, W - 1);
+    }
+    auto load_row = [&](int e, uint32_t (&bytes)[NR_ITEMS]) {
+        const int row = clampi(e, 0, H - 1) * pitch;
+#pragma unroll
+        for (int k = 0; k < NR_ITEMS; ++k) {
+            const int it = threadIdx.x + k * blockDim.x;
+            bytes[k] = k < nk ? (uint32_t)__ldg((it < LW ? Limg : Rimg) + row + col[k]) : 0u;
+        }
+    };
+    auto shift_in = [&](const uint32_t (&bytes)[NR_ITEMS]) {
+#pragma unroll
+        for (int k = 0; k < NR_ITEMS; ++k) {
+#pragma unroll
+            for (int w = 0; w < NWP; ++w) win[k][w] = __funnelshift_r(win[k][w], w + 1 < NWP ? win[k][w + 1] : 0u, 8);
+            win[k][(WIN - 1) / 4] |= bytes[k] << (8 * ((WIN - 1) % 4));
+        }
+    };
+
+    pdl_enter();
+    // the 2R rows above the strip enter the owners' windows first
+    uint32_t next[NR_ITEMS];
+    for (int e = y0 - R; e < y0 + R; ++e) {
+        load_row(e, next);
+        shift_in(next);
+    }
+    load_row(y0 + R, next);
+
     int acc[NR_TX / 2];
 #pragma unroll
     for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
-
     const int lbase = xs * NR_TX;               // this thread's first staged left column
     const int rbase = xs * NR_TX + D - 1 - d;   // ... and the right column matching it at label d
-    // rows y0-1-R .. y1-1+R enter in turn; a row leaves 2R+1 rows after it entered
-    for (int e = y0 - 1 - R; e < y1 + R; ++e) {
-        const int slot_e = (e - (y0 - 1 - R)) % RING;
-        const int lv = e - WIN;                 // the row leaving the window
-        const bool leave = lv >= y0 - 1 - R;
-        const int slot_l = leave ? (lv - (y0 - 1 - R)) % RING : 0;
-        __syncthreads();  // the ring slot about to be refilled is no longer read
+    const int xb = x0 + lbase;
+    const int nvalid = min(NR_TX, W - xb);      // columns of this thread inside the image
+    const bool lab = dl < D;
+    const float T_half = (float)T + 0.5f, half_m = 0.5f - (float)(T + 1) * (1.f / 131072.f);
+
+    for (int y = y0; y < y1; ++y) {
+        const int par = y & 1;
+        // phase 1: the owners shift row y + R in, publish the words and the column sums
         {
-            const size_t row = (size_t)clampi(e, 0, H - 1) * pitch;
-            for (int i = threadIdx.x; i < LW; i += blockDim.x)
-                Lr[slot_e * LW + i] = __ldg(Limg + row + clampi(x0 - R + i, 0, W - 1));
-            for (int i = threadIdx.x; i < RW; i += blockDim.x)
-                Rr[slot_e * RW + i] = __ldg(Rimg + row + clampi(x0 - R - (D - 1) + i, 0, W - 1));
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < LW; i += blockDim.x) {
-            const int a = Lr[slot_e * LW + i], o = leave ? Lr[slot_l * LW + i] : 0;
-            colA[i] += a - o;
-            colAA[i] += a * a - o * o;
-        }
-        for (int i = threadIdx.x; i < RW; i += blockDim.x) {
-            const int b = Rr[slot_e * RW + i], o = leave ? Rr[slot_l * RW + i] : 0;
-            colB[i] += b - o;
-            colBB[i] += b * b - o * o;
-        }
+            uint32_t cur[NR_ITEMS];
 #pragma unroll
-        for (int i = 0; i < VN; ++i) {
-            const int enter = (int)Lr[slot_e * LW + lbase + i] * (int)Rr[slot_e * RW + rbase + i];
-            const int out = leave ? (int)Lr[slot_l * LW + lbase + i] * (int)Rr[slot_l * RW + rbase + i] : 0;
-            V[i] += enter - out;
+            for (int k = 0; k < NR_ITEMS; ++k) cur[k] = next[k];
+            if (y + 1 < y1) load_row(y + 1 + R, next);  // in flight during this row
+            shift_in(cur);
+#pragma unroll
+            for (int k = 0; k < NR_ITEMS; ++k) {
+                if (k >= nk) break;
+                const int it = threadIdx.x + k * blockDim.x;
+                unsigned s = 0u, ss = 0u;
+                WinT wv;
+#pragma unroll
+                for (int w = 0; w < NWP; ++w) {
+                    wv.w[w] = win[k][w];
+                    if (w < NW) {
+                        s = __dp4a(win[k][w], 0x01010101u, s);
+                        ss = __dp4a(win[k][w], win[k][w], ss);
+                    }
+                }
+                if (it < LW) {
+                    LWn[par * LW + it] = wv;
+                    colA[it] = (int)s;
+                    colAA[it] = (int)ss;
+                } else {
+                    RWn[par * RW + it - LW] = wv;
+                    colB[it - LW] = (int)s;
+                    colBB[it - LW] = (int)ss;
+                }
+            }
         }
-        const int y = e - R;  // the row whose window is now complete
-        if (y < y0) continue;
         __syncthreads();
+        // phase 2: window records of every left pixel and every right position
         for (int i = threadIdx.x; i < CW; i += blockDim.x) {
             int s = 0, ss = 0;
 #pragma unroll
@@ -274,7 +370,8 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 ss += colAA[i + k];
             }
             const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            PA[i] = make_int4(s, (int)v, __float_as_int(v ? __frsqrt_rn((float)v) : 0.f), 0);
+            const float ra = v ? __frsqrt_rn((float)v) : 0.f;
+            PA[i] = make_int4(s, (int)v, __float_as_int(ra), __float_as_int(__fmul_rn((float)T, ra)));
         }
         for (int i = threadIdx.x; i < UW; i += blockDim.x) {
             int s = 0, ss = 0;
@@ -287,70 +384,92 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
             PB[i] = make_int4(s, (int)v, __float_as_int(v ? __frsqrt_rn((float)v) : 0.f), 0);
         }
         __syncthreads();
-        int S = 0;
+        // phase 3: this thread's 16 outputs at label dl
+        const WinT *Lrow = LWn + par * LW + lbase;
+        const WinT *Rrow = RWn + par * RW + rbase;
+        int V[VN];
 #pragma unroll
-        for (int i = 0; i < WIN; ++i) S += V[i];
-        const int cy = y >> 1;
-        const bool row_done = (y & 1) || y == H - 1;  // the coarse pixel of this row pair is complete
+        for (int i = 0; i < VN; ++i) {
+            const WinT a = Lrow[i], b = Rrow[i];
+            unsigned v = 0u;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
+            V[i] = (int)v;
+        }
         // destinations: x0 + lbase is even, so column j has colour (j + y) & 1 and slot
         // row_slot + j / 2 in that colour's array
-        const int xb = x0 + lbase;
         const int64_t row_slot = (int64_t)y * l0.Wh + (xb >> 1);
         CostT *const base_even = reinterpret_cast<CostT *>((y & 1) ? l0.cost[1] : l0.cost[0]) + row_slot * Dp +
                                  label_pos<CostT>(dl);
         CostT *const base_odd = reinterpret_cast<CostT *>((y & 1) ? l0.cost[0] : l0.cost[1]) + row_slot * Dp +
                                 label_pos<CostT>(dl);
+        if constexpr (!FLOAT_COST) {
+            if ((y & 1) == 0) {
+#pragma unroll
+                for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
+            }
+        }
+        unsigned near_mask = 0u;  // outputs whose level the FP64 sequence must decide
+        int S = 0;
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) S += V[i];
 #pragma unroll
         for (int j = 0; j < NR_TX; ++j) {
             if (j) S += V[j + 2 * R] - V[j - 1];
-            const int x = xb + j;
             const int4 pa = PA[lbase + j];
             const int4 pb = PB[lbase + j + D - 1 - d];
-            const unsigned va = (unsigned)pa.y, vb = (unsigned)pb.y;
             const Num num = (Num)N * (Num)S - (Num)pa.x * (Num)pb.x;
-            int c;
-            float nccf;
-            if constexpr (CostOut<CostT>::is_float) {
-                nccf = (va == 0u || vb == 0u) ? 0.f
-                                              : __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
-                c = 0;
+            bool near;
+            const int c = quantise_fp32((float)num, __int_as_float(pa.w), __int_as_float(pb.z), T_half, half_m, T, &near);
+            float nccf = 0.f;
+            if constexpr (NCC_OUT || FLOAT_COST)
+                nccf = __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
+            const bool inside = j < nvalid;
+            CostT *dst = ((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp;
+            if constexpr (FLOAT_COST) {
+                const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
+                if (inside) *dst = lab ? cf : 0.f;
             } else {
-                if (va == 0u || vb == 0u) {
-                    nccf = 0.f;
-                    c = T;
-                } else {
-                    nccf = __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
-                    const float v = __fadd_rn(__fmul_rn((float)T, __fsub_rn(1.f, nccf)), 0.5f);
-                    const float fl = floorf(v);
-                    if (fminf(v - fl, fl + 1.f - v) > (float)(T + 1) * (1.f / 131072.f)) {
-                        c = (int)fl;
-                    } else {
-                        const double den = __dmul_rn((double)va, (double)vb);
-                        const double n64 = __ddiv_rn((double)num, __dsqrt_rn(den));
-                        c = (int)floor(__dadd_rn(__dmul_rn((double)T, __dadd_rn(1.0, -n64)), 0.5));
-                    }
-                    c = c < 0 ? 0 : (c > T ? T : c);
-                }
+                const int cs = lab ? c : 0;
+                store_if(dst, (CostT)cs, inside);
+                acc[j >> 1] += inside ? cs : 0;
+                near_mask |= (near ? 1u : 0u) << j;
             }
-            if (x < W) {
-                CostT *dst = ((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp;
-                if constexpr (CostOut<CostT>::is_float) {
-                    const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
-                    *dst = dl < D ? cf : 0.f;
-                } else {
-                    *dst = dl < D ? (CostT)c : (CostT)0;
-                }
-                if (ncc_out && dl < D) ncc_out[((size_t)y * W + x) * D + dl] = nccf;
-            }
-            if constexpr (!CostOut<CostT>::is_float) {
-                if (write_l1) {
-                    if ((y & 1) == 0 && (j & 1) == 0) acc[j >> 1] = 0;
-                    if (x < W && dl < D) acc[j >> 1] += c;
-                }
+            if constexpr (NCC_OUT) {
+                if (inside && lab) ncc_out[((size_t)y * W + xb + j) * D + dl] = nccf;
             }
         }
-        if constexpr (!CostOut<CostT>::is_float) {
-            if (write_l1 && row_done) {
+        if constexpr (!FLOAT_COST) {
+            // rare: outputs whose fp32 value lies too near a level boundary are decided again
+            // in FP64, and their stores and scale-1 sums corrected
+            while (near_mask) {
+                const int j = __ffs(near_mask) - 1;
+                near_mask &= near_mask - 1;
+                int Sj = 0;
+                for (int i = j; i < j + WIN; ++i) {
+                    const WinT a = Lrow[i], b = Rrow[i];
+                    unsigned v = 0u;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
+                    Sj += (int)v;
+                }
+                const int4 pa = PA[lbase + j];
+                const int4 pb = PB[lbase + j + D - 1 - d];
+                const Num num = (Num)N * (Num)Sj - (Num)pa.x * (Num)pb.x;
+                bool near;
+                const int c32 = quantise_fp32((float)num, __int_as_float(pa.w), __int_as_float(pb.z), T_half, half_m, T,
+                                              &near);
+                int c = quantise_fp64<Num>(num, (unsigned)pa.y, (unsigned)pb.y, T);
+                c = c < 0 ? 0 : (c > T ? T : c);
+                if (j < nvalid && lab && c != c32) {
+                    (((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp)[0] = (CostT)c;
+#pragma unroll
+                    for (int i = 0; i < NR_TX / 2; ++i)
+                        if (i == (j >> 1)) acc[i] += c - c32;
+                }
+            }
+            if (write_l1 && ((y & 1) || y == H - 1)) {  // the coarse pixels of this row pair are complete
+                const int cy = y >> 1;
 #pragma unroll
                 for (int jj = 0; jj < NR_TX / 2; ++jj) {
                     const int cx = (x0 + lbase) / 2 + jj;
@@ -365,10 +484,21 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
     }
 }
 
+static int win_bytes(int window) {
+    const int nw = (window + 3) / 4;
+    return 4 * (nw <= 1 ? 1 : (nw <= 2 ? 2 : 4));
+}
+
 size_t ncc_rows_smem_bytes(int D, int XS, int window) {
     const int R = window / 2;
     const int CW = XS * NR_TX, LW = CW + 2 * R, RW = CW + 2 * R + D - 1, UW = CW + D - 1;
-    return (size_t)16 * (CW + UW) + (size_t)4 * (2 * LW + 2 * RW) + (size_t)(2 * R + 2) * (LW + RW);
+    return (size_t)16 * (CW + UW) + (size_t)2 * win_bytes(window) * (LW + RW) + (size_t)4 * (2 * LW + 2 * RW);
+}
+
+// Whether every staged column has an owner: at most NR_ITEMS per thread.
+static bool ncc_rows_shape_ok(int D, int Dp, int XS, int window) {
+    const int R = window / 2, CW = XS * NR_TX;
+    return (CW + 2 * R) + (CW + 2 * R + D - 1) <= NR_ITEMS * XS * Dp;
 }
 
 // Default CTA shape: every label of 256 / Dp column groups (256 threads), strips short
@@ -391,21 +521,28 @@ static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch
     if (prep) {
         const int XSmax = Dp >= 256 ? 1 : 256 / Dp;
         if ((int)ncc_rows_smem_bytes(D, XSmax, 2 * R + 1) > smem_optin()) return cudaErrorInvalidValue;
-        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        const cudaError_t e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     smem_optin());
     }
     int XS = 1, tys = 16;
     ncc_rows_default_shape(W, H, Dp, &XS, &tys);
     if (xs_req > 0) XS = xs_req;
     if (tys_req > 0) tys = tys_req;
+    if (!ncc_rows_shape_ok(D, Dp, XS, 2 * R + 1)) return cudaErrorInvalidConfiguration;
     const size_t smem = ncc_rows_smem_bytes(D, XS, 2 * R + 1);
     const int threads = XS * Dp;
     const int CW = XS * NR_TX;
     const int nx = (W + CW - 1) / CW;
     const int ny = (H + tys - 1) / tys;
     LevelView none = l0;
-    return launch_k(ncc_rows_kernel<CostT, R>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp, T,
-                    tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
+    if (ncc_out)
+        return launch_k(ncc_rows_kernel<CostT, R, true>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D,
+                        Dp, T, tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
+    return launch_k(ncc_rows_kernel<CostT, R, false>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp,
+                    T, tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
 }
 
 template <typename CostT>

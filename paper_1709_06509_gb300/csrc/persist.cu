@@ -111,16 +111,16 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
                     unsigned long long *trace = pd.trace ? pd.trace + t : nullptr;
                     if constexpr (FORM == MSG_U8) {
                         if (pd.D & 15)
-                            sweep_group_u8<true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
+                            sweep_group_u8<true, false, 0, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
                                                  P.skip, trace, b);
                         else
-                            sweep_group_u8<false>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
+                            sweep_group_u8<false, false, 0, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
                                                   P.skip, trace, b);
                     } else if constexpr (FORM == MSG_I32) {
-                        sweep_group<int32_t, int32_t>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam, P.lam * P.trunc,
+                        sweep_group<int32_t, int32_t, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam, P.lam * P.trunc,
                                                       P.skip, trace, b);
                     } else {
-                        sweep_group<float, __half>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, (float)P.lam,
+                        sweep_group<float, __half, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, (float)P.lam,
                                                    (float)P.lam * (float)P.trunc, P.skip, trace, b);
                     }
                 }
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
         const PairDesc &pd = P.pairs[p];
         int32_t *disp = (p == 0 && P.disp_override) ? P.disp_override : pd.disp;
         if (!disp) continue;
-        if constexpr (FORM == MSG_U8) wta_group<int16_t, uint8_t>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
-        else if constexpr (FORM == MSG_I32) wta_group<int32_t, int32_t>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
-        else wta_group<float, __half>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
+        if constexpr (FORM == MSG_U8) wta_group<int16_t, uint8_t, true>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
+        else if constexpr (FORM == MSG_I32) wta_group<int32_t, int32_t, true>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
+        else wta_group<float, __half, true>(pd.lv[0], pd.D, pd.Dp, pd.Gp, disp, vb - wp[p]);
     }
 }
 

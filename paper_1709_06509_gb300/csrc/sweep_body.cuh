@@ -72,7 +72,7 @@ __device__ inline void min_convolve(const Acc (&h)[VEC], Acc lam, Acc lamT, int 
     for (int k = 0; k < VEC; ++k) m[k] = A::mn(A::mn(F[k], B[k]), cap) - hm;
 }
 
-template <typename CostT, typename MsgT>
+template <typename CostT, typename MsgT, bool RW = false>
 __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int D, int Dp, int Gp,
                                             typename AccOf<MsgT>::type lam, typename AccOf<MsgT>::type lamT,
                                             int skip, unsigned long long *trace, int64_t block) {
@@ -108,7 +108,7 @@ __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (has[q]) {
-                load16(mp + q * Dp, in[q]);
+                load16_msg<RW>(mp + q * Dp, in[q]);
             } else {
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) in[q][k] = Acc(0);
@@ -208,7 +208,13 @@ struct ActiveList {
 //   TS = 2, trunc == 2: m(d) = min(h(d), h(d-1) + lambda, h(d+1) + lambda, min h + 2 lambda) - min h,
 //           the same function (a label two or more away costs the cap at least), needing only
 //           each label's immediate neighbours: no chains, no scan across the lanes.
-template <bool PADDED, bool APPEND = false, int TS = 0>
+// EAGER: 0, the dirty flag is read first and only pixels that need it load their inputs;
+//        1, every load of the half-sweep (cost, messages in, old messages out, flag) is issued at
+//           once, so a pixel waits for one round trip to memory instead of two (clean pixels load
+//           for nothing: for small, latency-bound scales);
+//        2, as 1, and the cost loads also precede the wait on the predecessor kernel (no BP
+//           kernel writes the cost volume); the caller then must not have called pdl_enter().
+template <bool PADDED, bool APPEND = false, int TS = 0, bool RW = false, int EAGER = 0>
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
                                                int lamT, int skip, unsigned long long *trace, int64_t block,
                                                const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
@@ -226,13 +232,6 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         valid = x < lv.W;
     }
     const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
-    const bool active = valid && (!skip || dirty_in[s] != 0u);
-    const unsigned act = __ballot_sync(FULL, active);
-    if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(Gp));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
     const int64_t sc = valid ? s : 0;
     const int dbase = g * VEC;
     const bool lane_data = dbase < Dp;
@@ -241,23 +240,56 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
     uint8_t *msg_out = reinterpret_cast<uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
     unsigned *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
+    const int nbx[4] = {x, x, x - 1, x + 1};
+    const int nby[4] = {y - 1, y + 1, y, y};
+    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
 
     uint32_t b[8];
     uint4 in[4];
-    if (lane_data) {
-        const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
-        const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
-        b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
-        b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+    // the old outgoing messages (the skip's change test) are loaded together with the inputs,
+    // so a recomputed pixel waits for one round trip to memory, not two
+    uint4 *dst[4];
+    uint4 old[4];
+    auto load_cost = [&]() {
+        if (lane_data) {
+            const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
+            const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
+            b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
+            b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
+        }
+    };
+    // `send`: whether this lane's pixel sends (the active pixels; all valid ones when eager)
+    auto load_messages = [&](bool send) {
         const uint8_t *mp = msg_in + sc * 4 * Dp + dbase;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            in[q] = has[q] ? __ldg(reinterpret_cast<const uint4 *>(mp + q * Dp)) : make_uint4(0u, 0u, 0u, 0u);
-    } else {
+            in[q] = (lane_data && has[q]) ? load_u4<RW>(reinterpret_cast<const uint4 *>(mp + q * Dp))
+                                          : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) in[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = 0; q < 4; ++q) {
+            const int64_t qs = (send && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+            dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
+            old[q] = (skip && send && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    if constexpr (EAGER != 0) {
+        load_cost();
+        if constexpr (EAGER == 2) pdl_enter();
+        load_messages(valid);
+    }
+    const bool active = valid && (!skip || dirty_in[s] != 0u);
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) return;
+    if (trace && lane == 0) {
+        const int n = __popc(act & leader_bits(Gp));
+        if (n) atomicAdd(trace, (unsigned long long)n);
+    }
+    if constexpr (EAGER == 0) {
+        load_cost();
+        load_messages(active);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -275,20 +307,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     }
 
     const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
-    const int nbx[4] = {x, x, x - 1, x + 1};
-    const int nby[4] = {y - 1, y + 1, y, y};
-    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
     const int gshift = lane & ~(Gp - 1);
-    // the old outgoing messages (the skip's change test) are loaded together with the inputs,
-    // so a recomputed pixel waits for one round trip to memory, not two
-    uint4 *dst[4];
-    uint4 old[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t qs = (active && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
-        dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
-        old[q] = (skip && active && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
-    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t t[8], h[8], m[8];
@@ -428,7 +447,7 @@ __device__ __forceinline__ void upsample_chunk(const LevelView &coarse, const Le
 // ------------------------------------------------------------------ winner-take-all
 // Pixels of block `block` in raster order, Gp lanes each: argmin of the belief, the lowest
 // label on ties (labels are compared through the storage order of the form).
-template <typename CostT, typename MsgT>
+template <typename CostT, typename MsgT, bool RW = false>
 __device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, int64_t block) {
     using Acc = typename AccOf<MsgT>::type;
     using A = Arith<Acc>;
@@ -449,7 +468,7 @@ __device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, in
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (!has[q]) continue;
-            load16(mp + q * Dp, t);
+            load16_msg<RW>(mp + q * Dp, t);
 #pragma unroll
             for (int k = 0; k < VEC; ++k) b[k] += t[k];
         }

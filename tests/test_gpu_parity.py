@@ -238,18 +238,29 @@ def test_batch_of_mixed_pairs(persistent, graph):
             st.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def set_all_variants(st, variant):
+    try:
+        for lvl in range(st.levels):
+            st.set_variant(lvl, variant)
+    except bps.BPSError as e:
+        if e.status == bps.BPS_ERR_UNSUPPORTED and variant & bps.BPS_VARIANT_CLUSTER:
+            pytest.skip("a 16-CTA cluster of the sweep kernel does not fit on this GPU")
+        raise
+    assert st.variants() == [variant] * st.levels
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
-                                  (24, 6, 256, 3, 2, 3, 10, 2)], ids=lambda c: "x".join(map(str, c)))
+                                  (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
+                         ids=lambda c: "x".join(map(str, c)))
 def test_every_sweep_variant_is_exact(case, variant):
-    # every kernel variant (stencil / distance transform, dense / active lists) forced on every
-    # scale, even tiny ones, must give the oracle's messages, trace and disparities
+    # every kernel variant (stencil / distance transform, dense / active lists, one cluster
+    # launch per scale) forced on every scale, even tiny ones, must give the oracle's
+    # messages, trace and disparities
     W, H, D, window, levels, iters, lam, trunc = case
     pair = synth.make_pair(200 + W + D, W, H, D, 3, 2.0)
     with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
-        for lvl in range(levels):
-            st.set_variant(lvl, variant)
-        assert st.variants() == [variant] * levels
+        set_all_variants(st, variant)
         st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
         st.bp_solve(iters, lam, trunc, skip=True)
         msg = st.export_messages(0).cpu().numpy()
@@ -259,6 +270,29 @@ def test_every_sweep_variant_is_exact(case, variant):
     ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True)
     assert np.array_equal(msg, ref_msg) and np.array_equal(trace, ref_trace)
     assert np.array_equal(disp, oracle.wta(c0, ref_msg))
+
+
+@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12])
+def test_cluster_and_eager_variants_without_skip_and_in_a_graph(variant):
+    # the cluster launch and the eager loads with every pixel recomputed (no skip), then
+    # captured in the cached graph of the whole pipeline; the profile shares a cluster
+    # launch's time out over its half-sweeps
+    W, H, D, window, levels, iters, lam, trunc = 130, 70, 24, 5, 3, 4, 10, 2
+    pair = synth.make_pair(61, W, H, D, 3, 2.0)
+    with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
+        set_all_variants(st, variant)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        st.bp_solve(iters, lam, trunc, skip=False, profile=True)
+        msg = st.export_messages(0).cpu().numpy()
+        times = st.read_launch_times()
+        assert len(times) == levels * iters * 2 and np.all(times > 0)
+        d = st.stereo(to_dev(pair.left), to_dev(pair.right), window, 20, iters, lam, trunc, graph=True)
+        d2 = st.stereo(to_dev(pair.left), to_dev(pair.right), window, 20, iters, lam, trunc, graph=True)
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+    ref_msg, _ = oracle.bp(c0, levels, iters, lam, trunc, skip=False)
+    assert np.array_equal(msg, ref_msg)
+    ref = oracle.stereo_int(pair.left, pair.right, D, window, 20, levels, iters, lam, trunc)
+    assert np.array_equal(d.cpu().numpy(), ref["disp"]) and np.array_equal(d2.cpu().numpy(), ref["disp"])
 
 
 @pytest.mark.parametrize("shape", [(2, 2), (2, 8), (4, 4), (8, 64), (16, 2), (0, 0)])
