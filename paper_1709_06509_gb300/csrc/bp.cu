@@ -53,11 +53,19 @@ __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
                      unsigned long long *trace, ActiveList al) {
     pdl_enter();
-    const int64_t n = *al.n_in;
     const int groups = blockDim.x / Gp;
-    const int64_t nblocks = (n + groups - 1) / groups;
-    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group_u8<PADDED, true, TS>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n);
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t stride = (int64_t)gridDim.x * groups;
+    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
+    // the list length and this thread's first entry are read together: an entry past the
+    // length is stale but inside the buffer, which holds a slot of every pixel of a colour
+    unsigned e = idx < nslot ? al.in[idx] : 0u;
+    const int64_t n = *al.n_in;
+    for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
+        const int64_t s = idx < n ? (int64_t)e : nslot;
+        if (idx + stride < n) e = al.in[idx + stride];
+        sweep_group_u8<PADDED, true, TS, false, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, s);
+    }
 }
 
 // Every iteration of one small scale in ONE launch of ONE thread-block cluster.  The CTAs of

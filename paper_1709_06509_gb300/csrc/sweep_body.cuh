@@ -214,16 +214,20 @@ struct ActiveList {
 //           for nothing: for small, latency-bound scales);
 //        2, as 1, and the cost loads also precede the wait on the predecessor kernel (no BP
 //           kernel writes the cost volume); the caller then must not have called pdl_enter().
-template <bool PADDED, bool APPEND = false, int TS = 0, bool RW = false, int EAGER = 0>
+// LISTED: the caller gives the slot (s_listed; nslot for none), an entry of the active list:
+//         a listed pixel is dirty by construction (it was appended when its flag flipped from
+//         0 to 1, and only its own update clears the flag), so its flag is not read.
+template <bool PADDED, bool APPEND = false, int TS = 0, bool RW = false, int EAGER = 0, bool LISTED = false>
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
                                                int lamT, int skip, unsigned long long *trace, int64_t block,
                                                const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
-                                               int64_t n_in = 0) {
+                                               int64_t n_in = 0, int64_t s_listed = 0) {
     const int lane = threadIdx.x & 31;
     const int g = threadIdx.x & (Gp - 1);
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
-    if (al.in) s = s < n_in ? (int64_t)al.in[s] : nslot;
+    if constexpr (LISTED) s = s_listed;
+    else if (al.in) s = s < n_in ? (int64_t)al.in[s] : nslot;
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
@@ -280,7 +284,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         if constexpr (EAGER == 2) pdl_enter();
         load_messages(valid);
     }
-    const bool active = valid && (!skip || dirty_in[s] != 0u);
+    const bool active = valid && (LISTED || !skip || dirty_in[s] != 0u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -308,6 +312,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 
     const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
     const int gshift = lane & ~(Gp - 1);
+    unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark dirty (APPEND)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t t[8], h[8], m[8];
@@ -401,27 +406,41 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
                 diff = (old[q].x != out.x) | (old[q].y != out.y) | (old[q].z != out.z) | (old[q].w != out.w);
             const unsigned dm = __ballot_sync(FULL, diff);
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
-            bool append = false;
-            int64_t qs = 0;
             if (send && changed) {
                 if (lane_data) *dst[q] = out;
                 if (g == 0) {
-                    qs = slot_of(nbx[q], nby[q], lv.Wh);
-                    if constexpr (APPEND) append = atomicExch(dirty_out + qs, 1u) == 0u;
+                    const unsigned qs = (unsigned)slot_of(nbx[q], nby[q], lv.Wh);
+                    if constexpr (APPEND) mark[q] = qs + 1u;
                     else dirty_out[qs] = 1u;
-                }
-            }
-            if constexpr (APPEND) {
-                const unsigned am = __ballot_sync(FULL, append);
-                if (am) {
-                    unsigned base = 0;
-                    if (lane == __ffs(am) - 1) base = atomicAdd(al.n_out, (unsigned)__popc(am));
-                    base = __shfl_sync(FULL, base, __ffs(am) - 1);
-                    if (append) al.out[base + __popc(am & ((1u << lane) - 1u))] = (unsigned)qs;
                 }
             }
         } else if (send && lane_data) {
             *dst[q] = out;
+        }
+    }
+    if constexpr (APPEND) {
+        // the flags of the marked neighbours flip together (one round trip), then the warp
+        // appends the ones that were clean with a single reservation
+        unsigned was[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) was[q] = mark[q] ? atomicExch(dirty_out + (mark[q] - 1u), 1u) : 1u;
+        unsigned am[4];
+        unsigned total = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            am[q] = __ballot_sync(FULL, was[q] == 0u);
+            total += __popc(am[q]);
+        }
+        if (total) {
+            unsigned base = 0u;
+            if (lane == 0) base = atomicAdd(al.n_out, total);
+            base = __shfl_sync(FULL, base, 0);
+            const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = mark[q] - 1u;
+                base += __popc(am[q]);
+            }
         }
     }
     if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
