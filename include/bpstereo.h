@@ -269,7 +269,10 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  *   BPS_VARIANT_EAGER       (dense launches) issue every load of a half-sweep at once, before
  *                           the dirty flag is known, and the costs before the wait on the
  *                           preceding kernel: one round trip to memory per half-sweep instead
- *                           of two, at the price of loading clean pixels (small scales).
+ *                           of two, at the price of loading clean pixels (small scales);
+ *   BPS_VARIANT_DPAR        one group of lanes per (pixel, direction) instead of per pixel:
+ *                           the four messages of a pixel side by side (up to 128 labels;
+ *                           ignored above), for scales whose time is the latency of few pixels.
  * With BPS_FLAG_PROFILE a cluster launch's time is shared out evenly over its half-sweeps.
  * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
@@ -287,6 +290,7 @@ int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
 #define BPS_VARIANT_LISTS 2
 #define BPS_VARIANT_CLUSTER 4
 #define BPS_VARIANT_EAGER 8
+#define BPS_VARIANT_DPAR 16
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 

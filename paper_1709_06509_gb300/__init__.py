@@ -49,6 +49,7 @@ BPS_VARIANT_GENERAL_DT = 1
 BPS_VARIANT_LISTS = 2
 BPS_VARIANT_CLUSTER = 4
 BPS_VARIANT_EAGER = 8
+BPS_VARIANT_DPAR = 16
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 

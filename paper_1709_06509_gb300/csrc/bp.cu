@@ -26,37 +26,46 @@ sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<Msg
 #define BPS_SWEEP_MIN_BLOCKS 3  // resident CTAs per SM the u8 sweep is compiled for
 #endif
 
-template <bool PADDED, bool APPEND, int TS>
+template <bool PADDED, bool APPEND, int TS, bool DP>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                 unsigned long long *trace, int nblocks, ActiveList al) {
     pdl_enter();
-    for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        if constexpr (DP) sweep_group_u8_dp<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+        else sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+    }
 }
 
 // The same half-sweep with every load issued at once (see EAGER in sweep_group_u8): the first
 // block of each CTA loads its costs before waiting for the predecessor kernel.
-template <bool PADDED, int TS>
+template <bool PADDED, int TS, bool DP>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_eager_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                       unsigned long long *trace, int nblocks) {
-    sweep_group_u8<PADDED, false, TS, false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
-    for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
-        sweep_group_u8<PADDED, false, TS, false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+    if constexpr (DP) {
+        sweep_group_u8_dp<PADDED, false, TS, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+        for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
+            sweep_group_u8_dp<PADDED, false, TS, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+    } else {
+        sweep_group_u8<PADDED, false, TS, false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+        for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
+            sweep_group_u8<PADDED, false, TS, false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+    }
 }
 
 // The same half-sweep over the pixels of an active list; its length is read on the device
 // (a recorded graph keeps the launch shape, the list decides the work).
-template <bool PADDED, int TS>
+template <bool PADDED, int TS, bool DP>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
                      unsigned long long *trace, ActiveList al) {
     pdl_enter();
-    const int groups = blockDim.x / Gp;
+    const int lpp = DP ? 4 * Gp : Gp;  // lanes a pixel
+    const int groups = blockDim.x / lpp;
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     const int64_t stride = (int64_t)gridDim.x * groups;
-    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
+    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / lpp;
     // the list length and this thread's first entry are read together: an entry past the
     // length is stale but inside the buffer, which holds a slot of every pixel of a colour
     unsigned e = idx < nslot ? al.in[idx] : 0u;
@@ -64,7 +73,8 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
         const int64_t s = idx < n ? (int64_t)e : nslot;
         if (idx + stride < n) e = al.in[idx + stride];
-        sweep_group_u8<PADDED, true, TS, false, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, s);
+        if constexpr (DP) sweep_group_u8_dp<PADDED, true, TS, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, s);
+        else sweep_group_u8<PADDED, true, TS, false, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, s);
     }
 }
 
@@ -177,32 +187,41 @@ bool cluster_sweep_available() {
 }
 
 // Kernel of one u8 half-sweep: padding variant x list / append mode x minimisation form.
-template <bool PADDED, int TS>
-static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+template <bool PADDED, int TS, bool DP>
+static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
                                 bool eager, cudaStream_t st) {
     if (eager && !al.in && !al.out)  // grid <= blocks: every CTA has a first block
-        return launch_k(sweep_u8_eager_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
-                        lamT, skip, trace, (int)blocks);
+        return launch_k(sweep_u8_eager_kernel<PADDED, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                        lam, lamT, skip, trace, (int)blocks);
     if (skip && al.in)
-        return launch_k(sweep_u8_list_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+        return launch_k(sweep_u8_list_kernel<PADDED, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
                         lamT, trace, al);
     const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
     if (al.out)
-        return launch_k(sweep_u8_kernel<PADDED, true, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
-                        lamT, skip, trace, (int)blocks, dense);
-    return launch_k(sweep_u8_kernel<PADDED, false, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam, lamT,
-                    skip, trace, (int)blocks, dense);
+        return launch_k(sweep_u8_kernel<PADDED, true, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                        lam, lamT, skip, trace, (int)blocks, dense);
+    return launch_k(sweep_u8_kernel<PADDED, false, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                    lamT, skip, trace, (int)blocks, dense);
+}
+
+template <bool PADDED, int TS>
+static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                                unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
+                                bool eager, bool dp, cudaStream_t st) {
+    if (dp) return launch_u8_dp<PADDED, TS, true>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
+    return launch_u8_dp<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
 }
 
 template <bool PADDED>
 static cudaError_t launch_u8(int ts, const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                              unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                             bool eager, cudaStream_t st) {
+                             bool eager, bool dp, cudaStream_t st) {
     switch (ts) {
-    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
-    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
-    default: return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
+    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
+    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
+    default:
+        return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
     }
 }
 
@@ -225,7 +244,7 @@ static int resident_blocks(int msg_kind) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 0>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 0, false>, 256, 0);
         cached[msg_kind] = std::max(1, sms * std::max(1, per_sm));
     }
     return cached[msg_kind];
@@ -236,7 +255,9 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
     switch (msg_kind) {
     case MSG_I32: return sweep_t<int32_t, int32_t>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     case MSG_U8: {
-        const int groups = 256 / Gp;
+        // direction-parallel lanes (4 Gp a pixel) fit a warp up to Gp = 8
+        const bool dp = (variant & VARIANT_DPAR) != 0 && Gp <= 8;
+        const int groups = 256 / (dp ? 4 * Gp : Gp);
         const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
         if (blocks == 0) return cudaSuccess;
         const int lam = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
@@ -245,8 +266,9 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
         const bool eager = (variant & VARIANT_EAGER) != 0;
         if (D & 15)
-            return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, st);
-        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, st);
+            return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
+                                   st);
+        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp, st);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -376,13 +398,17 @@ __global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
     }
 }
 
-template <bool PADDED, int TS> static cudaError_t preload_u8() {
+template <bool PADDED, int TS, bool DP> static cudaError_t preload_u8_dp() {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, false, TS>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, true, TS>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_list_kernel<PADDED, TS>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_eager_kernel<PADDED, TS>);
+    cudaError_t e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, false, TS, DP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, true, TS, DP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_list_kernel<PADDED, TS, DP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_eager_kernel<PADDED, TS, DP>);
     return e;
+}
+template <bool PADDED, int TS> static cudaError_t preload_u8() {
+    const cudaError_t e = preload_u8_dp<PADDED, TS, false>();
+    return e == cudaSuccess ? preload_u8_dp<PADDED, TS, true>() : e;
 }
 
 cudaError_t preload_bp_kernels(int msg_kind) {

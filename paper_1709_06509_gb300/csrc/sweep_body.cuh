@@ -187,6 +187,93 @@ __device__ inline uint4 pack_msg(const uint32_t (&v)[8]) {
                       __byte_perm(v[4], v[5], 0x6420), __byte_perm(v[6], v[7], 0x6420));
 }
 
+// The outgoing message of one direction from h = b - (message from that direction), for the
+// Gp lanes (segment of Gp lanes, 16 labels each in the u8 storage order) of one pixel: the
+// minimisation form TS (see sweep_group_u8), min h subtracted, padded labels zeroed.
+template <bool PADDED, int TS>
+__device__ __forceinline__ void u8_message(const uint32_t (&h)[8], int lam, int lamT, int g, int Gp, int D, int dbase,
+                                           uint32_t (&m)[8]) {
+    const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
+    uint32_t mm = __vimin3_u16x2(h[0], h[1], h[2]);
+    mm = __vimin3_u16x2(mm, h[3], h[4]);
+    mm = __vimin3_u16x2(mm, h[5], h[6]);
+    mm = __vimin3_u16x2(mm, h[7], h[7]);
+    int hm = (int)min(mm & 0xffffu, mm >> 16);
+    if constexpr (TS != 0) {
+        for (int o = 1; o < Gp; o <<= 1) hm = min(hm, __shfl_xor_sync(FULL, hm, o, Gp));
+        const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
+        const uint32_t HM2 = (uint32_t)hm * 0x10001u;
+        if constexpr (TS == 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(h[j], CAP2, CAP2) - HM2;
+        } else {
+            // labels dbase - 1 (the previous lane's label 15) and dbase + 16 (the next lane's 0)
+            int left = __shfl_up_sync(FULL, (int)(h[7] >> 16), 1, Gp);
+            int right = __shfl_down_sync(FULL, (int)(h[0] & 0xffffu), 1, Gp);
+            if (g == 0) left = (int)BIG16;
+            if (g == Gp - 1) right = (int)BIG16;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                // register j holds labels (j, j+8): its neighbours sit in registers j-1 and j+1,
+                // except across the lane edge and across the middle (labels 7 | 8)
+                const uint32_t lft = j > 0 ? h[j - 1] : pk((uint32_t)left, h[7] & 0xffffu);
+                const uint32_t rgt = j < 7 ? h[j + 1] : pk(h[0] >> 16, (uint32_t)right);
+                m[j] = __vimin3_u16x2(__viaddmin_u16x2(lft, LAM2, h[j]), __viaddmin_u16x2(rgt, LAM2, CAP2), CAP2) -
+                       HM2;
+            }
+        }
+    } else {
+    uint32_t F[8], B[8];
+    F[0] = h[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) F[j] = __viaddmin_u16x2(F[j - 1], LAM2, h[j]);
+    B[7] = h[7];
+#pragma unroll
+    for (int j = 6; j >= 0; --j) B[j] = __viaddmin_u16x2(B[j + 1], LAM2, h[j]);
+    const int fl = (int)(F[7] & 0xffffu), fh = (int)(F[7] >> 16);  // local forward at labels 7, 15
+    const int bl = (int)(B[0] & 0xffffu), bh = (int)(B[0] >> 16);  // local backward at labels 0, 8
+    int cf = (int)BIG16, cb = (int)BIG16;
+    if (Gp > 1) {
+        int fe = min(fh, fl + 8 * lam);  // forward value at this lane's last label
+        int bs = min(bl, bh + 8 * lam);  // backward value at this lane's first label
+        for (int o = 1; o < Gp; o <<= 1) {
+            const int tf = __shfl_up_sync(FULL, fe, o, Gp);
+            const int tb = __shfl_down_sync(FULL, bs, o, Gp);
+            const int th = __shfl_xor_sync(FULL, hm, o, Gp);
+            if (g >= o) fe = min(fe, tf + 16 * lam * o);
+            if (g + o < Gp) bs = min(bs, tb + 16 * lam * o);
+            hm = min(hm, th);
+        }
+        cf = __shfl_up_sync(FULL, fe, 1, Gp);
+        cb = __shfl_down_sync(FULL, bs, 1, Gp);
+        if (g == 0) cf = (int)BIG16;
+        if (g == Gp - 1) cb = (int)BIG16;
+        cf = min(cf, (int)BIG16);
+        cb = min(cb, (int)BIG16);
+    }
+    // forward: label j gets cf + lam*(j+1); label 8+j gets F(7) + lam*(j+1)
+    const int f7 = min(min(fl, cf + 8 * lam), (int)BIG16);
+    const uint32_t xF = pk((uint32_t)cf, (uint32_t)f7);
+    // backward: label 8+j gets cb + lam*(8-j); label j gets B(8) + lam*(8-j)
+    const int b8 = min(min(bh, cb + 8 * lam), (int)BIG16);
+    const uint32_t xB = pk((uint32_t)b8, (uint32_t)cb);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        F[j] = __viaddmin_u16x2(xF, (uint32_t)(lam * (j + 1)) * 0x10001u, F[j]);
+        B[j] = __viaddmin_u16x2(xB, (uint32_t)(lam * (8 - j)) * 0x10001u, B[j]);
+    }
+    const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
+    const uint32_t HM2 = (uint32_t)hm * 0x10001u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(F[j], B[j], CAP2) - HM2;
+    }
+    if constexpr (PADDED) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            m[j] &= (dbase + j < D ? 0xffffu : 0u) | (dbase + 8 + j < D ? 0xffff0000u : 0u);
+    }
+}
+
 // Active lists (fast-converging skip).  After the first two half-sweeps of a scale, a
 // half-sweep processes only the pixels listed for it, packed densely: a sender that flips a
 // neighbour's skip flag from 0 to 1 appends the neighbour to the other colour's list (one
@@ -310,7 +397,6 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         }
     }
 
-    const uint32_t LAM2 = pk((uint32_t)lam, (uint32_t)lam);
     const int gshift = lane & ~(Gp - 1);
     unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark dirty (APPEND)
 #pragma unroll
@@ -319,84 +405,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         unpack_msg(in[q], t);
 #pragma unroll
         for (int j = 0; j < 8; ++j) h[j] = b[j] - t[j];
-        uint32_t mm = __vimin3_u16x2(h[0], h[1], h[2]);
-        mm = __vimin3_u16x2(mm, h[3], h[4]);
-        mm = __vimin3_u16x2(mm, h[5], h[6]);
-        mm = __vimin3_u16x2(mm, h[7], h[7]);
-        int hm = (int)min(mm & 0xffffu, mm >> 16);
-        if constexpr (TS != 0) {
-            for (int o = 1; o < Gp; o <<= 1) hm = min(hm, __shfl_xor_sync(FULL, hm, o, Gp));
-            const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
-            const uint32_t HM2 = (uint32_t)hm * 0x10001u;
-            if constexpr (TS == 1) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(h[j], CAP2, CAP2) - HM2;
-            } else {
-                // labels dbase - 1 (the previous lane's label 15) and dbase + 16 (the next lane's 0)
-                int left = __shfl_up_sync(FULL, (int)(h[7] >> 16), 1, Gp);
-                int right = __shfl_down_sync(FULL, (int)(h[0] & 0xffffu), 1, Gp);
-                if (g == 0) left = (int)BIG16;
-                if (g == Gp - 1) right = (int)BIG16;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    // register j holds labels (j, j+8): its neighbours sit in registers j-1 and j+1,
-                    // except across the lane edge and across the middle (labels 7 | 8)
-                    const uint32_t lft = j > 0 ? h[j - 1] : pk((uint32_t)left, h[7] & 0xffffu);
-                    const uint32_t rgt = j < 7 ? h[j + 1] : pk(h[0] >> 16, (uint32_t)right);
-                    m[j] = __vimin3_u16x2(__viaddmin_u16x2(lft, LAM2, h[j]), __viaddmin_u16x2(rgt, LAM2, CAP2), CAP2) -
-                           HM2;
-                }
-            }
-        } else {
-        uint32_t F[8], B[8];
-        F[0] = h[0];
-#pragma unroll
-        for (int j = 1; j < 8; ++j) F[j] = __viaddmin_u16x2(F[j - 1], LAM2, h[j]);
-        B[7] = h[7];
-#pragma unroll
-        for (int j = 6; j >= 0; --j) B[j] = __viaddmin_u16x2(B[j + 1], LAM2, h[j]);
-        const int fl = (int)(F[7] & 0xffffu), fh = (int)(F[7] >> 16);  // local forward at labels 7, 15
-        const int bl = (int)(B[0] & 0xffffu), bh = (int)(B[0] >> 16);  // local backward at labels 0, 8
-        int cf = (int)BIG16, cb = (int)BIG16;
-        if (Gp > 1) {
-            int fe = min(fh, fl + 8 * lam);  // forward value at this lane's last label
-            int bs = min(bl, bh + 8 * lam);  // backward value at this lane's first label
-            for (int o = 1; o < Gp; o <<= 1) {
-                const int tf = __shfl_up_sync(FULL, fe, o, Gp);
-                const int tb = __shfl_down_sync(FULL, bs, o, Gp);
-                const int th = __shfl_xor_sync(FULL, hm, o, Gp);
-                if (g >= o) fe = min(fe, tf + 16 * lam * o);
-                if (g + o < Gp) bs = min(bs, tb + 16 * lam * o);
-                hm = min(hm, th);
-            }
-            cf = __shfl_up_sync(FULL, fe, 1, Gp);
-            cb = __shfl_down_sync(FULL, bs, 1, Gp);
-            if (g == 0) cf = (int)BIG16;
-            if (g == Gp - 1) cb = (int)BIG16;
-            cf = min(cf, (int)BIG16);
-            cb = min(cb, (int)BIG16);
-        }
-        // forward: label j gets cf + lam*(j+1); label 8+j gets F(7) + lam*(j+1)
-        const int f7 = min(min(fl, cf + 8 * lam), (int)BIG16);
-        const uint32_t xF = pk((uint32_t)cf, (uint32_t)f7);
-        // backward: label 8+j gets cb + lam*(8-j); label j gets B(8) + lam*(8-j)
-        const int b8 = min(min(bh, cb + 8 * lam), (int)BIG16);
-        const uint32_t xB = pk((uint32_t)b8, (uint32_t)cb);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            F[j] = __viaddmin_u16x2(xF, (uint32_t)(lam * (j + 1)) * 0x10001u, F[j]);
-            B[j] = __viaddmin_u16x2(xB, (uint32_t)(lam * (8 - j)) * 0x10001u, B[j]);
-        }
-        const uint32_t CAP2 = (uint32_t)(hm + lamT) * 0x10001u;
-        const uint32_t HM2 = (uint32_t)hm * 0x10001u;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) m[j] = __vimin3_u16x2(F[j], B[j], CAP2) - HM2;
-        }
-        if constexpr (PADDED) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                m[j] &= (dbase + j < D ? 0xffffu : 0u) | (dbase + 8 + j < D ? 0xffff0000u : 0u);
-        }
+        u8_message<PADDED, TS>(h, lam, lamT, g, Gp, D, dbase, m);
         const uint4 out = pack_msg(m);
 
         const bool send = active && has[q];
@@ -446,6 +455,139 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
 }
 
+
+// sweep_group_u8_dp: the same half-sweep with one group of Gp lanes per (pixel, direction),
+// 4 Gp lanes a pixel (Gp <= 8): every group forms the pixel's belief (the four incoming
+// message loads of a pixel are the same addresses across its groups, served once per warp)
+// and computes, compares and stores the one message of its direction.  The four messages of a
+// pixel are then computed side by side instead of one after another: a quarter of the
+// dependent work per lane, for scales whose time is the latency of few pixels.  Template
+// parameters as for sweep_group_u8; `block` counts blockDim / (4 Gp) pixels.
+template <bool PADDED, bool APPEND = false, int TS = 0, int EAGER = 0, bool LISTED = false>
+__device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
+                                                  int lamT, int skip, unsigned long long *trace, int64_t block,
+                                                  const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
+                                                  int64_t s_listed = 0) {
+    const int lane = threadIdx.x & 31;
+    const int LP = 4 * Gp;
+    const int g = threadIdx.x & (Gp - 1);
+    const int qo = (threadIdx.x / Gp) & 3;  // this group's direction
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    int64_t s = block * (blockDim.x / LP) + threadIdx.x / LP;
+    if constexpr (LISTED) s = s_listed;
+    int x = 0, y = 0;
+    bool valid = false;
+    if (s < nslot) {
+        y = (int)(s / lv.Wh);
+        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        valid = x < lv.W;
+    }
+    const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
+    const int64_t sc = valid ? s : 0;
+    const int dbase = g * VEC;
+    const bool lane_data = dbase < Dp;
+    const bool has[4] = {valid && y > 0, valid && y < lv.H - 1, valid && x > 0, valid && x < lv.W - 1};
+    const bool has_o = qo == 0 ? has[0] : (qo == 1 ? has[1] : (qo == 2 ? has[2] : has[3]));
+    const int nbx = qo == 2 ? x - 1 : (qo == 3 ? x + 1 : x);
+    const int nby = qo == 0 ? y - 1 : (qo == 1 ? y + 1 : y);
+    const int16_t *cost = reinterpret_cast<const int16_t *>(colour ? lv.cost[1] : lv.cost[0]);
+    const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
+    uint8_t *msg_out = reinterpret_cast<uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
+    unsigned *dirty_out = colour ? lv.dirty[0] : lv.dirty[1];
+
+    uint32_t b[8];
+    uint4 in[4];
+    uint4 *dst;
+    uint4 old;
+    auto load_cost = [&]() {
+        if (lane_data) {
+            const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
+            const uint4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
+            b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
+            b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
+        }
+    };
+    auto load_messages = [&](bool send) {
+        const uint8_t *mp = msg_in + sc * 4 * Dp + dbase;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            in[q] = (lane_data && has[q]) ? __ldg(reinterpret_cast<const uint4 *>(mp + q * Dp))
+                                          : make_uint4(0u, 0u, 0u, 0u);
+        const int64_t qs = (send && has_o) ? slot_of(nbx, nby, lv.Wh) : 0;
+        dst = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + (qo ^ 1)) * Dp + dbase);
+        old = (skip && send && has_o && lane_data) ? *dst : make_uint4(0u, 0u, 0u, 0u);
+    };
+    if constexpr (EAGER != 0) {
+        load_cost();
+        if constexpr (EAGER == 2) pdl_enter();
+        load_messages(valid);
+    }
+    const bool active = valid && (LISTED || !skip || dirty_in[s] != 0u);
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) return;
+    if (trace && lane == 0) {
+        const int n = __popc(act & leader_bits(LP));
+        if (n) atomicAdd(trace, (unsigned long long)n);
+    }
+    if constexpr (EAGER == 0) {
+        load_cost();
+        load_messages(active);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t t[8];
+        unpack_msg(in[q], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] += t[j];
+    }
+    if constexpr (PADDED) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool plo = dbase + j >= D, phi = dbase + 8 + j >= D;
+            b[j] = __vimax3_u16x2(b[j], pk(plo ? BIG16 : 0u, phi ? BIG16 : 0u), 0u);
+        }
+    }
+    const uint4 in_o = qo == 0 ? in[0] : (qo == 1 ? in[1] : (qo == 2 ? in[2] : in[3]));
+    uint32_t t[8], h[8], m[8];
+    unpack_msg(in_o, t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = b[j] - t[j];
+    u8_message<PADDED, TS>(h, lam, lamT, g, Gp, D, dbase, m);
+    const uint4 out = pack_msg(m);
+
+    const bool send = active && has_o;
+    unsigned mark = 0u;  // slot + 1 of the neighbour to mark dirty (APPEND)
+    if (skip) {
+        bool diff = false;
+        if (send && lane_data) diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
+        const unsigned dm = __ballot_sync(FULL, diff);
+        const bool changed = ((dm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
+        if (send && changed) {
+            if (lane_data) *dst = out;
+            if (g == 0) {
+                const unsigned qs = (unsigned)slot_of(nbx, nby, lv.Wh);
+                if constexpr (APPEND) mark = qs + 1u;
+                else dirty_out[qs] = 1u;
+            }
+        }
+    } else if (send && lane_data) {
+        *dst = out;
+    }
+    if constexpr (APPEND) {
+        const bool app = mark != 0u && atomicExch(dirty_out + (mark - 1u), 1u) == 0u;
+        const unsigned am = __ballot_sync(FULL, app);
+        if (am) {
+            unsigned base = 0u;
+            if (lane == 0) base = atomicAdd(al.n_out, (unsigned)__popc(am));
+            base = __shfl_sync(FULL, base, 0);
+            if (app) al.out[base + __popc(am & ((1u << lane) - 1u))] = mark - 1u;
+        }
+    }
+    if (skip && active && g == 0 && qo == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
+}
 
 // ------------------------------------------------------------------ coarse-to-fine start
 // Element k of the copy of parent records into the fine pixels of `colour` (16-byte chunks).

@@ -249,14 +249,14 @@ def set_all_variants(st, variant):
     assert st.variants() == [variant] * st.levels
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
                                   (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
                          ids=lambda c: "x".join(map(str, c)))
 def test_every_sweep_variant_is_exact(case, variant):
     # every kernel variant (stencil / distance transform, dense / active lists, one cluster
-    # launch per scale) forced on every scale, even tiny ones, must give the oracle's
-    # messages, trace and disparities
+    # launch per scale, eager loads, direction-parallel lanes) forced on every scale, even
+    # tiny ones, must give the oracle's messages, trace and disparities
     W, H, D, window, levels, iters, lam, trunc = case
     pair = synth.make_pair(200 + W + D, W, H, D, 3, 2.0)
     with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
@@ -272,7 +272,7 @@ def test_every_sweep_variant_is_exact(case, variant):
     assert np.array_equal(disp, oracle.wta(c0, ref_msg))
 
 
-@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12])
+@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25])
 def test_cluster_and_eager_variants_without_skip_and_in_a_graph(variant):
     # the cluster launch and the eager loads with every pixel recomputed (no skip), then
     # captured in the cached graph of the whole pipeline; the profile shares a cluster
