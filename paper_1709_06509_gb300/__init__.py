@@ -50,6 +50,7 @@ BPS_VARIANT_LISTS = 2
 BPS_VARIANT_CLUSTER = 4
 BPS_VARIANT_EAGER = 8
 BPS_VARIANT_DPAR = 16
+BPS_VARIANT_DPAR_LISTS = 32
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
@@ -417,14 +418,25 @@ class Stereo:
         import torch
 
         pin = h_left.is_pinned()
-        h_disp = h_disp if h_disp is not None else torch.empty((self.H, self.W), dtype=torch.int32).pin_memory() \
-            if pin else torch.empty((self.H, self.W), dtype=torch.int32)
-        ei = torch.zeros(1, dtype=torch.int64)
-        ef = torch.zeros(1, dtype=torch.float64)
+        own = h_disp is None
+        if pin:
+            # page-locked buffers kept across calls: the call replays as one recorded graph
+            # while its buffers stay the same
+            if getattr(self, "_host_bufs", None) is None:
+                self._host_bufs = (torch.empty((self.H, self.W), dtype=torch.int32).pin_memory(),
+                                   torch.zeros(1, dtype=torch.int64).pin_memory(),
+                                   torch.zeros(1, dtype=torch.float64).pin_memory())
+            d0, ei, ef = self._host_bufs
+            h_disp = d0 if own else h_disp
+        else:
+            h_disp = torch.empty((self.H, self.W), dtype=torch.int32) if own else h_disp
+            ei = torch.zeros(1, dtype=torch.int64)
+            ef = torch.zeros(1, dtype=torch.float64)
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
         bps_stereo_host(self.ctx, h_left, h_right, h_left.stride(0), window, trunc_data, iters, lam, trunc, flags,
                         h_disp, ei if self.msg_type != BPS_MSG_FP16 else None, ef, stream)
-        return h_disp, (int(ei.item()) if self.msg_type != BPS_MSG_FP16 else float(ef.item()))
+        energy = int(ei.item()) if self.msg_type != BPS_MSG_FP16 else float(ef.item())
+        return (h_disp.clone() if own and pin else h_disp), energy
 
     def get_trace(self):
         import numpy as np
@@ -516,11 +528,16 @@ class Batch:
         """Host tensors in; host disparities and int64 energies out (synchronous)."""
         import torch
 
-        if h_disps is None:
-            h_disps = [torch.empty((st.H, st.W), dtype=torch.int32).pin_memory() for st in self.stereos]
-        energies = torch.zeros(len(self.stereos), dtype=torch.int64)
+        # page-locked buffers kept across calls: the call replays as one recorded graph while
+        # its buffers stay the same
+        if getattr(self, "_host_bufs", None) is None:
+            self._host_bufs = ([torch.empty((st.H, st.W), dtype=torch.int32).pin_memory() for st in self.stereos],
+                               torch.zeros(len(self.stereos), dtype=torch.int64).pin_memory())
+        own = h_disps is None
+        h_disps = self._host_bufs[0] if own else h_disps
+        energies = self._host_bufs[1]
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
         flags |= BPS_FLAG_PERSISTENT if persistent else 0
         bps_batch_stereo_host(self.handle, h_lefts, h_rights, [t.stride(0) for t in h_lefts], windows, trunc_data,
                               iters, lam, trunc, flags, h_disps, energies, stream)
-        return h_disps, energies
+        return ([d.clone() for d in h_disps] if own else h_disps), energies.clone()

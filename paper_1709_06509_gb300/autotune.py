@@ -10,6 +10,7 @@ given scale size and label count (see bps_set_sweep_variant in include/bpstereo.
   EAGER              every load of a half-sweep issued at once (small scales)
   CLUSTER            every iteration of the scale in one thread-block-cluster launch
   DPAR               one lane group per (pixel, direction): the four messages side by side
+  DPAR_LISTS         ... on the list launches only
 and their combinations.  For one context and one representative input, tune() replays the
 whole pipeline from its CUDA graph (the way the variants run in production: consecutive
 launches overlap, which per-launch events would hide) and descends one scale at a time,
@@ -22,15 +23,16 @@ from __future__ import annotations
 import json
 import os
 
-from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR, BPS_VARIANT_EAGER,
-               BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPSError, level_dims)
+from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS,
+               BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPSError, level_dims)
 
-_G, _L, _E, _C, _P = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER,
-                      BPS_VARIANT_DPAR)
+_G, _L, _E, _C, _P, _PL = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER,
+                           BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS)
 # a cluster launch is only a candidate for scales of at most this many lanes (pixels x lanes per pixel)
 CLUSTER_MAX_LANES = 16 * 16 * 512
 SMALL_CANDIDATES = (0, _G, _E, _E | _G, _C, _C | _E, _C | _E | _G, _P, _P | _G, _P | _E, _P | _E | _G)
-LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, _P | _E, _P | _L, _P | _E | _L)
+LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, _P | _E, _P | _L, _P | _E | _L,
+                    _L | _PL, _E | _L | _PL, _G | _L | _PL, _E | _G | _L | _PL)
 CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
 DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
 
@@ -99,7 +101,7 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
         for lvl in reversed(range(st.levels)):
             times = {}
             for v in (SMALL_CANDIDATES if small[lvl] else LARGE_CANDIDATES):
-                if v & _P and Gp > DPAR_MAX_LANES_PER_PIXEL:
+                if v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL:
                     continue
                 trial = list(current)
                 trial[lvl] = v

@@ -91,6 +91,54 @@ struct GraphKey {
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
+// Page-locked host memory (registered or allocated pinned): copies from and to it can be
+// recorded in a CUDA graph.
+bool is_pinned(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// A recorded graph keyed by the arguments that shaped it: replayed while the key holds,
+// recorded again (on the capture stream `cap`) when it changes.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<intptr_t> key;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+};
+
+template <typename Enqueue>
+int replay_or_record(GraphSlot &g, const std::vector<intptr_t> &key, cudaStream_t cap, cudaStream_t st,
+                     Enqueue enqueue) {
+    if (!g.exec || key != g.key) {
+        g.reset();
+        if (cudaStreamSynchronize(cap) != cudaSuccess) return BPS_ERR_CUDA;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BPS_ERR_CUDA;
+        const int rc = enqueue(cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+        if (rc != BPS_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != BPS_OK ? rc : BPS_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            return BPS_ERR_CUDA;
+        }
+        g.key = key;
+    }
+    return cudaGraphLaunch(g.exec, st) == cudaSuccess ? BPS_OK : BPS_ERR_CUDA;
+}
+
 }  // namespace
 
 struct bps_ctx {
@@ -124,6 +172,7 @@ struct bps_ctx {
     int prof_first_trace = 0;
     int prof_trace_n = 0;   // trace entries covered by the profiled launches
     uint64_t config_version = 0;  // bumped when a kernel choice (variant, NCC shape) changes
+    GraphSlot host_graph;         // bps_stereo_host: copies in, pipeline, energy, copies out
     std::vector<int> prof_span;  // half-sweeps each profiled launch covers (a cluster launch covers a scale)
 };
 
@@ -295,6 +344,7 @@ extern "C" int bps_destroy(bps_ctx *c) {
     int rc = BPS_OK;
     if (c->cap && cudaStreamSynchronize(c->cap) != cudaSuccess) rc = BPS_ERR_CUDA;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->host_graph.reset();
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->owns_ws && c->ws) {
@@ -599,14 +649,14 @@ extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
     return BPS_OK;
 }
 
-extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR, int pitch, int window,
-                               int trunc_data, int iters, int lambda, int trunc, int flags, int32_t *h_disp,
-                               int64_t *h_e_i64, double *h_e_f64, void *stream) {
-    if (!c || !hL || !hR || !h_disp || pitch < c->W) return BPS_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
+// Host images in, pipeline, energy, host disparity (and energies) out, on stream st.
+static int enqueue_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR, int pitch, int window, int trunc_data,
+                               int iters, int lambda, int trunc, int flags, int32_t *h_disp, int64_t *h_e_i64,
+                               double *h_e_f64, cudaStream_t st) {
     CK(cudaMemcpy2DAsync(c->img[0], c->W, hL, pitch, c->W, c->H, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpy2DAsync(c->img[1], c->W, hR, pitch, c->W, c->H, cudaMemcpyHostToDevice, st));
-    int rc = bps_stereo(c, c->img[0], c->img[1], c->W, window, trunc_data, iters, lambda, trunc, flags, c->disp, stream);
+    const int rc = enqueue_stereo(c, c->img[0], c->img[1], c->W, window, trunc_data, iters, lambda, trunc, flags,
+                                  c->disp, st);
     if (rc != BPS_OK) return rc;
     if (h_e_i64 || h_e_f64) {
         CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, c->disp, lambda, trunc, c->partials,
@@ -615,8 +665,45 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
     CK(cudaMemcpyAsync(h_disp, c->disp, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, st));
     if (h_e_i64 && c->msg_type != BPS_MSG_FP16) CK(cudaMemcpyAsync(h_e_i64, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
     if (h_e_f64) CK(cudaMemcpyAsync(h_e_f64, c->e_f64, 8, cudaMemcpyDeviceToHost, st));
+    return BPS_OK;
+}
+
+extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR, int pitch, int window,
+                               int trunc_data, int iters, int lambda, int trunc, int flags, int32_t *h_disp,
+                               int64_t *h_e_i64, double *h_e_f64, void *stream) {
+    if (!c || !hL || !hR || !h_disp || pitch < c->W) return BPS_ERR_ARG;
+    int rc = check_cost_args(c, c->img[0], c->img[1], c->W, window, trunc_data);
+    if (rc != BPS_OK) return rc;
+    if (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT)) return BPS_ERR_ARG;
+    const bool had_cost = c->has_cost;
+    c->has_cost = true;  // the sequence builds the cost volume first
+    rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
+    if (rc != BPS_OK) {
+        c->has_cost = had_cost;
+        return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int f = flags & ~BPS_FLAG_GRAPH;
+    // with page-locked buffers (checked when the graph is recorded) the whole call, copies
+    // included, replays as one graph
+    const std::vector<intptr_t> key = {(intptr_t)hL, (intptr_t)hR, (intptr_t)h_disp, (intptr_t)h_e_i64,
+                                       (intptr_t)h_e_f64, pitch, window, trunc_data, iters, lambda, trunc, f,
+                                       (intptr_t)c->config_version};
+    const bool replay = (flags & BPS_FLAG_GRAPH) && c->host_graph.exec && key == c->host_graph.key;
+    if (replay || ((flags & BPS_FLAG_GRAPH) && is_pinned(hL) && is_pinned(hR) && is_pinned(h_disp) &&
+                   (!h_e_i64 || is_pinned(h_e_i64)) && (!h_e_f64 || is_pinned(h_e_f64)))) {
+        rc = replay_or_record(c->host_graph, key, c->cap, st, [&](cudaStream_t s) {
+            return enqueue_stereo_host(c, hL, hR, pitch, window, trunc_data, iters, lambda, trunc, f, h_disp, h_e_i64,
+                                       h_e_f64, s);
+        });
+    } else {
+        rc = enqueue_stereo_host(c, hL, hR, pitch, window, trunc_data, iters, lambda, trunc, f, h_disp, h_e_i64,
+                                 h_e_f64, st);
+    }
+    if (rc != BPS_OK) return rc;
     CK(cudaStreamSynchronize(st));
-    return bps_get_error(c);
+    // only the persistent kernel's barrier can time out
+    return (flags & BPS_FLAG_PERSISTENT) ? bps_get_error(c) : BPS_OK;
 }
 
 extern "C" int bps_get_error(bps_ctx *c) {
@@ -704,6 +791,7 @@ struct bps_batch {
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     std::vector<intptr_t> gkey;
+    GraphSlot host_graph;  // bps_batch_stereo_host: copies in, pipelines, energies, copies out
 };
 
 namespace {
@@ -725,6 +813,7 @@ std::vector<intptr_t> batch_key(const bps_batch *b, const uint8_t *const *L, con
 
 void batch_free(bps_batch *b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->host_graph.reset();
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -789,9 +878,36 @@ extern "C" int bps_batch_destroy(bps_batch *b) {
 }
 
 // Every pair's chain on its own branch stream, forked from and joined back into `st`.
+// Host buffers of a batch call: images copied in at the head of each pair's branch, the
+// disparity (and energy) copied out at its tail.
+struct BatchHostIO {
+    const uint8_t *const *lefts, *const *rights;
+    const int *pitches;
+    int32_t *const *disps;
+    int64_t *energies;
+};
+
+static int enqueue_pair_input(bps_ctx *c, const BatchHostIO *io, int i, cudaStream_t st) {
+    if (!io) return BPS_OK;
+    CK(cudaMemcpy2DAsync(c->img[0], c->W, io->lefts[i], io->pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpy2DAsync(c->img[1], c->W, io->rights[i], io->pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
+    return BPS_OK;
+}
+
+static int enqueue_pair_output(bps_ctx *c, const BatchHostIO *io, int i, int lambda, int trunc, cudaStream_t st) {
+    if (!io) return BPS_OK;
+    if (io->energies) {
+        CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, c->disp, lambda, trunc, c->partials,
+                         c->msg_type == BPS_MSG_FP16 ? nullptr : c->e_i64, c->e_f64, st));
+        CK(cudaMemcpyAsync(io->energies + i, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(io->disps[i], c->disp, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, st));
+    return BPS_OK;
+}
+
 static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *const *R, const int *pitches,
                          const int *windows, int trunc_data, int iters, int lambda, int trunc, int flags,
-                         int32_t *const *disps, cudaStream_t st) {
+                         int32_t *const *disps, cudaStream_t st, const BatchHostIO *io = nullptr) {
     const int n = (int)b->ctxs.size();
     if (flags & BPS_FLAG_PERSISTENT) {
         // costs of every pair on the branches, then one lockstep launch for all pairs
@@ -799,7 +915,8 @@ static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *c
         for (int i = 0; i < n; ++i) {
             bps_ctx *c = b->ctxs[i];
             CK(cudaStreamWaitEvent(b->streams[i], b->events[0], 0));
-            int rc = enqueue_cost(c, L[i], R[i], pitches[i], windows[i], trunc_data, nullptr, b->streams[i]);
+            int rc = enqueue_pair_input(c, io, i, b->streams[i]);
+            if (rc == BPS_OK) rc = enqueue_cost(c, L[i], R[i], pitches[i], windows[i], trunc_data, nullptr, b->streams[i]);
             if (rc == BPS_OK) rc = enqueue_start(c, b->levels - 1, 0, nullptr, b->streams[i]);
             if (rc != BPS_OK) return rc;
             if (iters) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * b->levels * iters * 2, b->streams[i]));
@@ -810,17 +927,23 @@ static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *c
         PersistParams P = persist_params(n, b->d_desc, b->d_prefix, b->d_prefix + (size_t)b->levels * (n + 1),
                                          b->d_barrier, b->levels, iters, lambda, trunc, flags);
         CK(launch_persistent(b->msg_kind, P, b->grid, st));
-        for (bps_ctx *c : b->ctxs) {
+        for (int i = 0; i < n; ++i) {
+            bps_ctx *c = b->ctxs[i];
             c->last_levels = b->levels;
             c->last_iters = iters;
+            const int rc = enqueue_pair_output(c, io, i, lambda, trunc, st);
+            if (rc != BPS_OK) return rc;
         }
         return BPS_OK;
     }
     CK(cudaEventRecord(b->events[0], st));
     for (int i = 0; i < n; ++i) {
         CK(cudaStreamWaitEvent(b->streams[i], b->events[0], 0));
-        const int rc = enqueue_stereo(b->ctxs[i], L[i], R[i], pitches[i], windows[i], trunc_data, iters, lambda, trunc,
-                                      flags & BPS_FLAG_FAST_SKIP, disps[i], b->streams[i]);
+        int rc = enqueue_pair_input(b->ctxs[i], io, i, b->streams[i]);
+        if (rc == BPS_OK)
+            rc = enqueue_stereo(b->ctxs[i], L[i], R[i], pitches[i], windows[i], trunc_data, iters, lambda, trunc,
+                                flags & BPS_FLAG_FAST_SKIP, disps[i], b->streams[i]);
+        if (rc == BPS_OK) rc = enqueue_pair_output(b->ctxs[i], io, i, lambda, trunc, b->streams[i]);
         if (rc != BPS_OK) return rc;
         CK(cudaEventRecord(b->events[i + 1], b->streams[i]));
         CK(cudaStreamWaitEvent(st, b->events[i + 1], 0));
@@ -828,9 +951,10 @@ static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *c
     return BPS_OK;
 }
 
-extern "C" int bps_batch_stereo(bps_batch *b, const uint8_t *const *d_lefts, const uint8_t *const *d_rights,
-                                const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
-                                int flags, int32_t *const *d_disps, void *stream) {
+// Argument checks of a batch call, and the persistent launch's read-out targets refreshed.
+static int batch_prepare(bps_batch *b, const uint8_t *const *d_lefts, const uint8_t *const *d_rights,
+                         const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
+                         int flags, int32_t *const *d_disps, void *stream) {
     if (!b || !d_lefts || !d_rights || !pitches || !windows || !d_disps ||
         (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT)))
         return BPS_ERR_ARG;
@@ -862,6 +986,15 @@ extern "C" int bps_batch_stereo(bps_batch *b, const uint8_t *const *d_lefts, con
             CK(cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice));
         }
     }
+    return BPS_OK;
+}
+
+extern "C" int bps_batch_stereo(bps_batch *b, const uint8_t *const *d_lefts, const uint8_t *const *d_rights,
+                                const int *pitches, const int *windows, int trunc_data, int iters, int lambda, int trunc,
+                                int flags, int32_t *const *d_disps, void *stream) {
+    const int prc = batch_prepare(b, d_lefts, d_rights, pitches, windows, trunc_data, iters, lambda, trunc, flags,
+                                  d_disps, stream);
+    if (prc != BPS_OK) return prc;
     cudaStream_t st = (cudaStream_t)stream;
     if (!(flags & BPS_FLAG_GRAPH))
         return enqueue_batch(b, d_lefts, d_rights, pitches, windows, trunc_data, iters, lambda, trunc, flags, d_disps, st);
@@ -914,25 +1047,48 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
     for (int i = 0; i < n; ++i) {
         bps_ctx *c = b->ctxs[i];
         if (!h_lefts[i] || !h_rights[i] || !h_disps[i] || pitches[i] < c->W) return BPS_ERR_ARG;
-        CK(cudaMemcpy2DAsync(c->img[0], c->W, h_lefts[i], pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpy2DAsync(c->img[1], c->W, h_rights[i], pitches[i], c->W, c->H, cudaMemcpyHostToDevice, st));
         L[i] = c->img[0];
         R[i] = c->img[1];
         pitch[i] = c->W;
         disp[i] = c->disp;
     }
-    int rc = bps_batch_stereo(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda, trunc, flags,
-                              disp.data(), stream);
-    if (rc != BPS_OK) return rc;
+    std::vector<intptr_t> key = batch_key(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda,
+                                          trunc, flags, disp.data());
+    key.push_back((intptr_t)h_energies);
     for (int i = 0; i < n; ++i) {
-        bps_ctx *c = b->ctxs[i];
-        if (h_energies) {
-            CK(launch_energy(c->cost_kind, c->lv[0], c->D, c->Dp, c->disp, lambda, trunc, c->partials,
-                             c->msg_type == BPS_MSG_FP16 ? nullptr : c->e_i64, c->e_f64, st));
-            CK(cudaMemcpyAsync(h_energies + i, c->e_i64, 8, cudaMemcpyDeviceToHost, st));
-        }
-        CK(cudaMemcpyAsync(h_disps[i], c->disp, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, st));
+        key.push_back((intptr_t)h_lefts[i]);
+        key.push_back((intptr_t)h_rights[i]);
+        key.push_back(pitches[i]);
+        key.push_back((intptr_t)h_disps[i]);
     }
+    // page-locked buffers (checked when the graph is recorded): the whole call, copies
+    // included, replays as one graph
+    bool pinned = (flags & BPS_FLAG_GRAPH) != 0;
+    if (pinned && !(b->host_graph.exec && key == b->host_graph.key)) {
+        pinned = !h_energies || is_pinned(h_energies);
+        for (int i = 0; i < n && pinned; ++i)
+            pinned = is_pinned(h_lefts[i]) && is_pinned(h_rights[i]) && is_pinned(h_disps[i]);
+    }
+    const BatchHostIO io{h_lefts, h_rights, pitches, h_disps, h_energies};
+    int rc;
+    if (pinned) {
+        rc = batch_prepare(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda, trunc, flags,
+                           disp.data(), stream);
+        if (rc != BPS_OK) return rc;
+        rc = replay_or_record(b->host_graph, key, b->cap, st, [&](cudaStream_t s) {
+            return enqueue_batch(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda, trunc, flags,
+                                 disp.data(), s, &io);
+        });
+    } else {
+        for (int i = 0; i < n; ++i) {
+            rc = enqueue_pair_input(b->ctxs[i], &io, i, st);
+            if (rc != BPS_OK) return rc;
+        }
+        rc = bps_batch_stereo(b, L.data(), R.data(), pitch.data(), windows, trunc_data, iters, lambda, trunc, flags,
+                              disp.data(), stream);
+        for (int i = 0; i < n && rc == BPS_OK; ++i) rc = enqueue_pair_output(b->ctxs[i], &io, i, lambda, trunc, st);
+    }
+    if (rc != BPS_OK) return rc;
     CK(cudaStreamSynchronize(st));
     return (flags & BPS_FLAG_PERSISTENT) ? bps_batch_get_error(b) : BPS_OK;
 }
@@ -940,7 +1096,7 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
 extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     if (!c || level < 0 || level >= c->levels || variant < -1 ||
         variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER |
-                   BPS_VARIANT_DPAR))
+                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp) : variant;

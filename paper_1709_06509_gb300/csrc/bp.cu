@@ -255,8 +255,10 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
     switch (msg_kind) {
     case MSG_I32: return sweep_t<int32_t, int32_t>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     case MSG_U8: {
-        // direction-parallel lanes (4 Gp a pixel) fit a warp up to Gp = 8
-        const bool dp = (variant & VARIANT_DPAR) != 0 && Gp <= 8;
+        // direction-parallel lanes (4 Gp a pixel) fit a warp up to Gp = 8: on every launch of
+        // the scale, or on its list launches only (few pixels each)
+        const bool list_launch = skip && lists.in;
+        const bool dp = Gp <= 8 && ((variant & VARIANT_DPAR) || (list_launch && (variant & VARIANT_DPAR_LISTS)));
         const int groups = 256 / (dp ? 4 * Gp : Gp);
         const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
         if (blocks == 0) return cudaSuccess;

@@ -54,6 +54,7 @@ constexpr int VARIANT_LISTS = 2;       // active lists after the scale's first i
 constexpr int VARIANT_CLUSTER = 4;     // every iteration of the scale in one thread-block-cluster launch
 constexpr int VARIANT_EAGER = 8;       // every load of a half-sweep issued at once (dense launches)
 constexpr int VARIANT_DPAR = 16;       // one lane group per (pixel, direction), up to 128 labels
+constexpr int VARIANT_DPAR_LISTS = 32; // ... on the list launches only
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {

@@ -193,6 +193,55 @@ def test_graph_replay_and_host_entry():
     assert np.array_equal(hd.numpy(), ref["disp"]) and he == ref["energy"]
 
 
+def test_host_entry_graph_reads_current_buffers():
+    # the recorded host graph copies from and to the same page-locked buffers every call: new
+    # image contents give new results, a new kernel choice records it again, and pageable
+    # buffers take the direct path
+    p1, p2 = synth.make_pair(8, 96, 72, 16, 3, 2.0), synth.make_pair(9, 96, 72, 16, 3, 2.0)
+    refs = [oracle.stereo_int(p.left, p.right, 16, 5, 20, 3, 6, 10, 2) for p in (p1, p2)]
+    with bps.Stereo(96, 72, 16, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        hl, hr = torch.from_numpy(p1.left).pin_memory(), torch.from_numpy(p1.right).pin_memory()
+        hd = torch.empty((72, 96), dtype=torch.int32).pin_memory()
+        got = []
+        d, e = st.stereo_host(hl, hr, 5, 20, 6, 10, 2, h_disp=hd)
+        got.append((d.clone(), e))
+        hl.copy_(torch.from_numpy(p2.left))
+        hr.copy_(torch.from_numpy(p2.right))
+        d, e = st.stereo_host(hl, hr, 5, 20, 6, 10, 2, h_disp=hd)
+        got.append((d.clone(), e))
+        st.set_variant(0, bps.BPS_VARIANT_GENERAL_DT | bps.BPS_VARIANT_EAGER)
+        d, e = st.stereo_host(hl, hr, 5, 20, 6, 10, 2, h_disp=hd)
+        got.append((d.clone(), e))
+        d, e = st.stereo_host(torch.from_numpy(p1.left), torch.from_numpy(p1.right), 5, 20, 6, 10, 2)
+        got.append((d, e))
+    for (d, e), ref in zip(got, [refs[0], refs[1], refs[1], refs[0]]):
+        assert np.array_equal(d.numpy(), ref["disp"]) and e == ref["energy"]
+
+
+def test_batch_host_entry_graph_reads_current_buffers():
+    shapes = [(70, 40, 16, 5), (45, 33, 64, 7)]
+    sets = [[synth.make_pair(70 + 10 * r + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+            for r in range(2)]
+    windows = [w for *_, w in shapes]
+    sts = [bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) for W, H, D, _ in shapes]
+    try:
+        with bps.Batch(sts) as batch:
+            hl = [torch.from_numpy(p.left).pin_memory() for p in sets[0]]
+            hr = [torch.from_numpy(p.right).pin_memory() for p in sets[0]]
+            for r in range(2):
+                for k, p in enumerate(sets[r]):
+                    hl[k].copy_(torch.from_numpy(p.left))
+                    hr[k].copy_(torch.from_numpy(p.right))
+                for rep in range(2):
+                    hd, he = batch.stereo_host(hl, hr, windows, 20, 5, 10, 2)
+                    for d, e, p, w in zip(hd, he.tolist(), sets[r], windows):
+                        ref = oracle.stereo_int(p.left, p.right, p.D, w, 20, 3, 5, 10, 2)
+                        assert np.array_equal(d.numpy(), ref["disp"]) and e == ref["energy"]
+    finally:
+        for st in sts:
+            st.close()
+
+
 def test_contexts_of_different_shapes_coexist():
     # kernel attributes are process-wide: creating a second context must not break the first
     pairs = [synth.make_pair(40 + k, W, H, D, 3, 2.0) for k, (W, H, D) in enumerate([(80, 40, 16), (60, 30, 64)])]
@@ -249,7 +298,7 @@ def set_all_variants(st, variant):
     assert st.variants() == [variant] * st.levels
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
                                   (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
                          ids=lambda c: "x".join(map(str, c)))
