@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--batch-report", type=int, default=0, metavar="N",
                     help="instead of the benchmark line: throughput of a batch of N mixed pairs (320-1280 x "
                          "240-720, D in {32,64,96,128}) in every batch mode, one JSON line")
+    ap.add_argument("--approx-report", action="store_true",
+                    help="instead of the benchmark line: the approximate skip rules (eps threshold, permanent "
+                         "freeze) on the benchmark pairs and the 960x540 D256 pair: time, work and energy gap "
+                         "against the exact skip, one JSON line")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
     ap.add_argument("--workload", default=None,
@@ -369,12 +373,81 @@ def warmstart_report(args):
                       "timing_at_equal_energy": timing, "seconds": {"generate": t_gen, "train": t_train}}))
 
 
+def approx_report(args):
+    """The approximate fast-converging rules against the exact skip: per rule, the benchmark step
+    (both pairs, one batch graph, L2 flushed between repetitions) and a 960x540 D256 pair (one
+    graph), with the recomputed pixels (trace) and the read-out energy of each pair."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rules = [(0, False), (1, False), (2, False), (4, False), (0, True), (1, True), (2, True)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def measure(sts, run, units):
+        for _ in range(max(3, args.warmup)):
+            run()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(5)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return units * args.steps / (total / 1e3) / 1e6, total / args.steps
+
+    out = {"metric": METRIC, "unit": UNIT, "report": "approximate skip rules", "rules": []}
+    groups = {"benchmark_pairs": [synth.workload_pair(n) for n in ("tsukuba_384x288_d16", "teddy_450x375_d64")],
+              "qhd_960x540_d256": [synth.workload_pair("qhd_960x540_d256")]}
+    ctx = {}
+    for gname, prs in groups.items():
+        sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, LEVELS, bps.BPS_MSG_U8, device=dev) for p, _ in prs]
+        Ls = [torch.from_numpy(p.left).to(dev) for p, _ in prs]
+        Rs = [torch.from_numpy(p.right).to(dev) for p, _ in prs]
+        outs = [torch.empty(p.left.shape, dtype=torch.int32, device=dev) for p, _ in prs]
+        ws = [w for _, w in prs]
+        for st, L, R, w in zip(sts, Ls, Rs, ws):
+            autotune.tune_ncc(st, L, R, w, TRUNC_DATA, reps=2)
+            autotune.tune(st, L, R, w, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+        ctx[gname] = (prs, sts, Ls, Rs, outs, ws, bps.Batch(sts))
+    for eps, freeze in rules:
+        row = {"eps": eps, "freeze": freeze}
+        for gname, (prs, sts, Ls, Rs, outs, ws, batch) in ctx.items():
+            for st in sts:
+                st.set_skip_rule(eps, freeze)
+            units = work_units(prs)
+            value, ms = measure(sts, lambda: batch.stereo(Ls, Rs, ws, TRUNC_DATA, ITERS, LAM, TRUNC, outs=outs), units)
+            energies, work = [], []
+            for st, L, R, w in zip(sts, Ls, Rs, ws):
+                st.build_cost_volume(L, R, w, TRUNC_DATA)
+                st.bp_solve(ITERS, LAM, TRUNC, skip=True)
+                energies.append(int(st.energy(st.wta_disparity(), LAM, TRUNC)[0].item()))
+                work.append(int(st.get_trace().sum()))
+            row[gname] = {"value": value, "ms": ms, "energy": energies, "recomputed_pixels": work}
+        out["rules"].append(row)
+    base = out["rules"][0]
+    for row in out["rules"]:
+        for gname in groups:
+            r, b = row[gname], base[gname]
+            r["energy_gap_rel"] = [(e - e0_) / e0_ for e, e0_ in zip(r["energy"], b["energy"])]
+            r["speedup"] = r["value"] / b["value"]
+            r["work_ratio"] = sum(r["recomputed_pixels"]) / sum(b["recomputed_pixels"])
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch_report:
         return batch_report(args)
+    if args.approx_report:
+        return approx_report(args)
     if args.warmstart_report:
         return warmstart_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps

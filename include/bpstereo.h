@@ -296,6 +296,17 @@ int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 
+/* The skip rule of the fast-converging variant (section "Fast Converging BP" does not fix the
+ * convergence test; the default, eps = 0 and freeze = 0, is the exact rule whose results equal
+ * those of no skip).  eps in [0, 255]: a recomputed pixel marks a receiver dirty only when the
+ * new message differs from the stored one by more than eps at some label (the message itself
+ * is always stored).  freeze = 1: a recomputed pixel that marked no receiver is frozen and not
+ * recomputed again at that scale, even when marked later.  Both make the skip approximate
+ * (judged by the energy gap).  u8 message form only: BPS_ERR_UNSUPPORTED otherwise for a
+ * non-exact rule; BPS_ERR_ARG out of range.  Applies to later solves of this context,
+ * including batches and persistent launches it takes part in. */
+int bps_set_skip_rule(bps_ctx *ctx, int eps, int freeze);
+
 /*
  * Learned warm start: kernels of a small convolutional network that predicts the coarsest
  * scale's messages from the coarsest cost volume (the start messages of bps_bp_solve with

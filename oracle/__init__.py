@@ -52,6 +52,8 @@ def lib() -> ctypes.CDLL:
             "oracle_message_f64": (None, [P, i, d, i, P]),
             "oracle_bp_i32": (i, [P, i, i, i, i, i, i, i, i, P, u64, P, P]),
             "oracle_bp_f64": (i, [P, i, i, i, i, i, d, i, i, P, u64, P, P]),
+            "oracle_bp_rule_i32": (i, [P, i, i, i, i, i, i, i, i, i, i, P, u64, P, P]),
+            "oracle_bp_rule_f64": (i, [P, i, i, i, i, i, d, i, i, d, i, P, u64, P, P]),
             "oracle_wta_i32": (i, [P, P, i, i, i, P]),
             "oracle_wta_f64": (i, [P, P, i, i, i, P]),
             "oracle_energy_i32": (i64, [P, P, i, i, i, i, i]),
@@ -136,8 +138,9 @@ def message(h: np.ndarray, lam, trunc: int) -> np.ndarray:
 
 
 def bp(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool = True,
-       init_coarsest: np.ndarray | None = None, order_seed: int = 0):
-    """Hierarchical min-sum BP.  Returns (finest messages [4][H][W][D], trace per half-sweep)."""
+       init_coarsest: np.ndarray | None = None, order_seed: int = 0, eps=0, freeze: bool = False):
+    """Hierarchical min-sum BP.  Returns (finest messages [4][H][W][D], trace per half-sweep).
+    eps / freeze: the approximate skip rule (0 / False: the exact skip)."""
     H, W, D = cost0.shape
     ntrace = levels * iters * 2
     trace = np.zeros(max(ntrace, 1), dtype=np.int64)
@@ -145,14 +148,14 @@ def bp(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool =
         a = np.ascontiguousarray(cost0)
         out = np.empty((4, H, W, D), dtype=np.int32)
         init = None if init_coarsest is None else np.ascontiguousarray(init_coarsest, dtype=np.int32)
-        rc = lib().oracle_bp_i32(_p(a), W, H, D, levels, iters, int(lam), trunc, int(skip),
-                                 _p(init), order_seed, _p(out), _p(trace))
+        rc = lib().oracle_bp_rule_i32(_p(a), W, H, D, levels, iters, int(lam), trunc, int(skip), int(eps),
+                                      int(freeze), _p(init), order_seed, _p(out), _p(trace))
     else:
         a = np.ascontiguousarray(cost0, dtype=np.float64)
         out = np.empty((4, H, W, D), dtype=np.float64)
         init = None if init_coarsest is None else np.ascontiguousarray(init_coarsest, dtype=np.float64)
-        rc = lib().oracle_bp_f64(_p(a), W, H, D, levels, iters, float(lam), trunc, int(skip),
-                                 _p(init), order_seed, _p(out), _p(trace))
+        rc = lib().oracle_bp_rule_f64(_p(a), W, H, D, levels, iters, float(lam), trunc, int(skip), float(eps),
+                                      int(freeze), _p(init), order_seed, _p(out), _p(trace))
     _check(rc, "oracle_bp")
     return out, trace[:ntrace]
 

@@ -194,15 +194,22 @@ static uint64_t sm64(uint64_t *s)
     return z ^ (z >> 31);
 }
 
-/* One scale of red-black min-sum BP.  M: [4][H][W][D] incoming messages, updated in place. */
+/* One scale of red-black min-sum BP.  M: [4][H][W][D] incoming messages, updated in place.
+ * Skip rule (with skip on): a pixel is recomputed while it is dirty.  A recomputed pixel
+ * stores every outgoing message, and marks the receiver dirty when the new message differs
+ * from the stored one by more than eps at some label (eps = 0: any change, the exact skip).
+ * With freeze, a recomputed pixel that marked no receiver is frozen: it is not recomputed
+ * again at this scale, dirty or not.  eps > 0 or freeze make the skip approximate. */
 static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int iters,
-                         double lambda, int trunc, int skip, uint64_t order_seed, int64_t *trace)
+                         double lambda, int trunc, int skip, double eps, int freeze,
+                         uint64_t order_seed, int64_t *trace)
 {
     const size_t plane = (size_t)H * W * D;
     double *b = malloc(sizeof(double) * (size_t)D);
     double *h = malloc(sizeof(double) * (size_t)D);
     double *m = malloc(sizeof(double) * (size_t)D);
     unsigned char *dirty = malloc((size_t)W * H);
+    unsigned char *frozen = calloc((size_t)W * H, 1);
     int *order = malloc(sizeof(int) * ((size_t)W * H + 1));
     memset(dirty, 1, (size_t)W * H);
     uint64_t rng = order_seed;
@@ -225,9 +232,10 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
             for (int k = 0; k < n; ++k) {
                 const int x = order[k] % W, y = order[k] / W;
                 const size_t p = (size_t)y * W + x;
-                if (skip && !dirty[p])
+                if (skip && (!dirty[p] || frozen[p]))
                     continue;
                 ++updated;
+                int marked = 0;
                 const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
                 /* belief: data term plus every incoming message */
                 for (int d = 0; d < D; ++d) {
@@ -254,14 +262,18 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
                     double *dst = M + slot * plane + ((size_t)qy * W + qx) * D;
                     int changed = 0;
                     for (int d = 0; d < D; ++d) {
-                        if (dst[d] != m[d])
+                        if (fabs(dst[d] - m[d]) > eps)
                             changed = 1;
                         dst[d] = m[d];
                     }
-                    if (changed)
+                    if (changed) {
                         dirty[(size_t)qy * W + qx] = 1;
+                        marked = 1;
+                    }
                 }
                 dirty[p] = 0;
+                if (freeze && !marked)
+                    frozen[p] = 1;
             }
             if (trace)
                 *trace++ = updated;
@@ -270,6 +282,7 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
     free(h);
     free(m);
     free(dirty);
+    free(frozen);
     free(order);
     return trace;
 }
@@ -277,6 +290,14 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
 int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
                   int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
                   double *msg0_out, int64_t *trace)
+{
+    return oracle_bp_rule_f64(cost0, W, H, D, levels, iters, lambda, trunc, skip, 0.0, 0, init_coarsest,
+                              order_seed, msg0_out, trace);
+}
+
+int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                       int trunc, int skip, double eps, int freeze, const double *init_coarsest,
+                       uint64_t order_seed, double *msg0_out, int64_t *trace)
 {
     int Ws[32], Hs[32];
     if (!cost0 || !msg0_out || D < 1 || levels > 32 || iters < 0 || trunc < 0 ||
@@ -316,7 +337,7 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
                                sizeof(double) * D);
         }
         free(parent);
-        tr = bp_level(pyr + off[l], M, w, h, D, iters, lambda, trunc, skip, order_seed, tr);
+        tr = bp_level(pyr + off[l], M, w, h, D, iters, lambda, trunc, skip, eps, freeze, order_seed, tr);
         parent = M;
     }
     memcpy(msg0_out, parent, sizeof(double) * 4 * (size_t)W * H * D);
@@ -328,6 +349,14 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
 int oracle_bp_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
                   int trunc, int skip, const int32_t *init_coarsest, uint64_t order_seed,
                   int32_t *msg0_out, int64_t *trace)
+{
+    return oracle_bp_rule_i32(cost0, W, H, D, levels, iters, lambda, trunc, skip, 0, 0, init_coarsest,
+                              order_seed, msg0_out, trace);
+}
+
+int oracle_bp_rule_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                       int trunc, int skip, int eps, int freeze, const int32_t *init_coarsest,
+                       uint64_t order_seed, int32_t *msg0_out, int64_t *trace)
 {
     int Ws[32], Hs[32];
     if (!cost0 || !msg0_out || D < 1 || levels > 32 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
@@ -348,8 +377,8 @@ int oracle_bp_i32(const int32_t *cost0, int W, int H, int D, int levels, int ite
     if (init)
         for (size_t k = 0; k < 4 * nc; ++k)
             init[k] = init_coarsest[k];
-    const int rc = oracle_bp_f64(c, W, H, D, levels, iters, (double)lambda, trunc, skip, init,
-                                 order_seed, m, trace);
+    const int rc = oracle_bp_rule_f64(c, W, H, D, levels, iters, (double)lambda, trunc, skip, (double)eps,
+                                      freeze, init, order_seed, m, trace);
     for (size_t k = 0; k < 4 * n0; ++k)
         msg0_out[k] = (int32_t)m[k];
     free(c);

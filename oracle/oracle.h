@@ -73,6 +73,17 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
                   int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
                   double *msg0_out, int64_t *trace);
 
+/* The same with an approximate skip rule (section "Fast Converging BP" leaves the convergence
+ * test open): a receiver is marked dirty only when its new message differs from the stored one
+ * by more than eps at some label, and with freeze a recomputed pixel that marked no receiver
+ * is not recomputed again at that scale.  eps = 0, freeze = 0 is the exact skip above. */
+int oracle_bp_rule_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                       int trunc, int skip, int eps, int freeze, const int32_t *init_coarsest,
+                       uint64_t order_seed, int32_t *msg0_out, int64_t *trace);
+int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                       int trunc, int skip, double eps, int freeze, const double *init_coarsest,
+                       uint64_t order_seed, double *msg0_out, int64_t *trace);
+
 /* d*(p) = argmin_d [cost(p, d) + sum of incoming messages], lowest d on ties. */
 int oracle_wta_i32(const int32_t *cost, const int32_t *msg, int W, int H, int D, int32_t *disp);
 int oracle_wta_f64(const double *cost, const double *msg, int W, int H, int D, int32_t *disp);

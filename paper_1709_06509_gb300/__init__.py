@@ -95,6 +95,7 @@ _SIGS = {
     "bps_batch_stereo_host": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "bps_set_sweep_variant": (_I, [_P, _I, _I]),
     "bps_get_sweep_variant": (_I, [_P, _I]),
+    "bps_set_skip_rule": (_I, [_P, _I, _I]),
     "bps_set_ncc_shape": (_I, [_P, _I, _I]),
     "bps_warmnet_conv3x3": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P]),
     "bps_warmnet_conv3x3_backward": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
@@ -273,6 +274,10 @@ def bps_set_ncc_shape(ctx, column_groups: int, rows: int) -> None:
 
 def bps_get_sweep_variant(ctx, level: int) -> int:
     return _check(lib().bps_get_sweep_variant(ctx, level), "bps_get_sweep_variant")
+
+
+def bps_set_skip_rule(ctx, eps: int, freeze: bool) -> None:
+    _check(lib().bps_set_skip_rule(ctx, int(eps), int(freeze)), "bps_set_skip_rule")
 
 
 def bps_warmnet_conv3x3(x, x_bf16, B, Cin, H, W, w, bias, Cout, relu, out, out_bf16, stream=None):
@@ -469,6 +474,10 @@ class Stereo:
 
     def set_variant(self, level: int, variant: int) -> None:
         bps_set_sweep_variant(self.ctx, level, variant)
+
+    def set_skip_rule(self, eps: int = 0, freeze: bool = False) -> None:
+        """Approximate fast-converging skip: eps threshold on message changes, permanent freeze."""
+        bps_set_skip_rule(self.ctx, eps, freeze)
 
     def set_ncc_shape(self, column_groups: int, rows: int) -> None:
         bps_set_ncc_shape(self.ctx, column_groups, rows)

@@ -289,6 +289,8 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.W = p.Ws[l];
         v.H = p.Hs[l];
         v.Wh = p.Whs[l];
+        v.eps = 0;  // the exact skip rule
+        v.freeze = 0;
         for (int k = 0; k < 2; ++k) {
             v.cost[k] = c->ws + p.cost[l][k];
             v.msg[k] = c->ws + p.msg[l][k];
@@ -522,7 +524,11 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         const LevelView &v = c->lv[l];
         // only the even pixels' start messages are ever read: the first half-sweep overwrites every
         // existing incoming slot of the odd pixels (unless there is no sweep at all)
-        if (l < top) CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, iters == 0 ? 1 : 0, c->Dp, skip ? 1 : 0, st));
+        // the odd pixels' start messages are read only without sweeps, or under the freeze rule
+        // (its first half-sweep compares the even pixels' new messages with them)
+        if (l < top)
+            CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, (iters == 0 || v.freeze) ? 1 : 0, c->Dp, skip ? 1 : 0,
+                               st));
         if (iters > 0 && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_CLUSTER)) {
             if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
             CK(launch_sweep_level_cluster(v, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, iters,
@@ -975,11 +981,17 @@ static int batch_prepare(bps_batch *b, const uint8_t *const *d_lefts, const uint
     if (flags & BPS_FLAG_PERSISTENT) {
         // the read-out targets live in the device descriptors: refresh them when they change
         bool changed = false;
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
             if (b->h_desc[i].disp != d_disps[i]) {
                 b->h_desc[i].disp = d_disps[i];
                 changed = true;
             }
+            const bps_ctx *c = b->ctxs[i];
+            if (b->h_desc[i].lv[0].eps != c->lv[0].eps || b->h_desc[i].lv[0].freeze != c->lv[0].freeze) {
+                for (int l = 0; l < c->levels; ++l) b->h_desc[i].lv[l] = c->lv[l];  // the skip rule changed
+                changed = true;
+            }
+        }
         if (changed) {
             for (cudaStream_t s : b->streams) CK(cudaStreamSynchronize(s));
             CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1102,6 +1114,24 @@ extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp) : variant;
     ++c->config_version;
     if (c->gexec) {  // a recorded graph holds the old kernels
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BPS_OK;
+}
+
+extern "C" int bps_set_skip_rule(bps_ctx *c, int eps, int freeze) {
+    if (!c || eps < 0 || eps > 255 || (freeze != 0 && freeze != 1)) return BPS_ERR_ARG;
+    if ((eps || freeze) && c->msg_kind != MSG_U8) return BPS_ERR_UNSUPPORTED;
+    for (int l = 0; l < c->levels; ++l) {
+        c->lv[l].eps = eps;
+        c->lv[l].freeze = freeze;
+    }
+    // this context's own descriptor (the persistent form) carries the level views
+    PairDesc hd = make_desc(c);
+    CK(cudaMemcpy(c->d_desc, &hd, sizeof(hd), cudaMemcpyHostToDevice));
+    ++c->config_version;
+    if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }

@@ -30,7 +30,9 @@ struct LevelView {
     int W, H, Wh;
     void *cost[2];
     void *msg[2];
-    unsigned *dirty[2];  // 32-bit words so a sender can flip them atomically
+    unsigned *dirty[2];  // 32-bit words so a sender can flip them atomically: bit 0 dirty, bit 1 frozen
+    int eps;             // skip rule: a receiver is marked when its message moves by more than eps
+    int freeze;          // skip rule: a recomputed pixel that marked no receiver is frozen
 };
 
 // Programmatic dependent launch: every kernel of the stereo chain is launched so that it may

@@ -90,7 +90,9 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
             if (l < top) {
                 const int rec_chunks = 4 * pd.Dp * (FORM == MSG_I32 ? 4 : FORM == MSG_U8 ? 1 : 2) / 16;
                 const int64_t n = (int64_t)v.H * v.Wh * rec_chunks;
-                for (int colour = 0; colour < (P.iters == 0 ? 2 : 1); ++colour)
+                // the odd pixels' start messages matter only without sweeps, or under the freeze
+                // rule, whose first half-sweep compares the even pixels' messages with them
+                for (int colour = 0; colour < ((P.iters == 0 || v.freeze) ? 2 : 1); ++colour)
                     for (int64_t k = tid; k < n; k += nthreads) upsample_chunk(pd.lv[l + 1], v, colour, rec_chunks, k);
             }
             if (P.skip) {

@@ -371,7 +371,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         if constexpr (EAGER == 2) pdl_enter();
         load_messages(valid);
     }
-    const bool active = valid && (LISTED || !skip || dirty_in[s] != 0u);
+    // dirty and not frozen (flags are 0 / 1 under the exact skip rule)
+    const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -399,6 +400,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 
     const int gshift = lane & ~(Gp - 1);
     unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark dirty (APPEND)
+    const uint32_t EPS4 = (uint32_t)lv.eps * 0x01010101u;
+    bool marked = false;                  // this pixel marked some receiver (skip rule freeze)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t t[8], h[8], m[8];
@@ -410,16 +413,23 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 
         const bool send = active && has[q];
         if (skip) {
-            bool diff = false;
-            if (send && lane_data)
+            bool diff = false, big = false;
+            if (send && lane_data) {
                 diff = (old[q].x != out.x) | (old[q].y != out.y) | (old[q].z != out.z) | (old[q].w != out.w);
+                big = (__vcmpgtu4(__vabsdiffu4(old[q].x, out.x), EPS4) | __vcmpgtu4(__vabsdiffu4(old[q].y, out.y), EPS4) |
+                       __vcmpgtu4(__vabsdiffu4(old[q].z, out.z), EPS4) | __vcmpgtu4(__vabsdiffu4(old[q].w, out.w), EPS4)) != 0u;
+            }
             const unsigned dm = __ballot_sync(FULL, diff);
+            const unsigned bm = __ballot_sync(FULL, big);
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
-            if (send && changed) {
-                if (lane_data) *dst[q] = out;
+            const bool significant = ((bm >> gshift) & group_bits(Gp)) != 0u;  // = changed when eps = 0
+            if (send && changed && lane_data) *dst[q] = out;
+            if (send && significant) {
+                marked = true;
                 if (g == 0) {
                     const unsigned qs = (unsigned)slot_of(nbx[q], nby[q], lv.Wh);
                     if constexpr (APPEND) mark[q] = qs + 1u;
+                    else if (lv.freeze) atomicOr(dirty_out + qs, 1u);  // keeps the frozen bit
                     else dirty_out[qs] = 1u;
                 }
             }
@@ -432,7 +442,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         // appends the ones that were clean with a single reservation
         unsigned was[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) was[q] = mark[q] ? atomicExch(dirty_out + (mark[q] - 1u), 1u) : 1u;
+        for (int q = 0; q < 4; ++q) was[q] = mark[q] ? atomicOr(dirty_out + (mark[q] - 1u), 1u) : 1u;
         unsigned am[4];
         unsigned total = 0u;
 #pragma unroll
@@ -452,7 +462,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             }
         }
     }
-    if (skip && active && g == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
+    if (skip && active && g == 0)
+        (colour ? lv.dirty[1] : lv.dirty[0])[s] = (lv.freeze && !marked) ? 2u : 0u;  // frozen: bit 1
 }
 
 
@@ -525,7 +536,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         if constexpr (EAGER == 2) pdl_enter();
         load_messages(valid);
     }
-    const bool active = valid && (LISTED || !skip || dirty_in[s] != 0u);
+    const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -560,16 +571,26 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
 
     const bool send = active && has_o;
     unsigned mark = 0u;  // slot + 1 of the neighbour to mark dirty (APPEND)
+    bool marked = false;  // this group marked its receiver (skip rule freeze)
     if (skip) {
-        bool diff = false;
-        if (send && lane_data) diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
+        bool diff = false, big = false;
+        if (send && lane_data) {
+            const uint32_t EPS4 = (uint32_t)lv.eps * 0x01010101u;
+            diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
+            big = (__vcmpgtu4(__vabsdiffu4(old.x, out.x), EPS4) | __vcmpgtu4(__vabsdiffu4(old.y, out.y), EPS4) |
+                   __vcmpgtu4(__vabsdiffu4(old.z, out.z), EPS4) | __vcmpgtu4(__vabsdiffu4(old.w, out.w), EPS4)) != 0u;
+        }
         const unsigned dm = __ballot_sync(FULL, diff);
+        const unsigned bm = __ballot_sync(FULL, big);
         const bool changed = ((dm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
-        if (send && changed) {
-            if (lane_data) *dst = out;
+        const bool significant = ((bm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
+        if (send && changed && lane_data) *dst = out;
+        if (send && significant) {
+            marked = true;
             if (g == 0) {
                 const unsigned qs = (unsigned)slot_of(nbx, nby, lv.Wh);
                 if constexpr (APPEND) mark = qs + 1u;
+                else if (lv.freeze) atomicOr(dirty_out + qs, 1u);  // keeps the frozen bit
                 else dirty_out[qs] = 1u;
             }
         }
@@ -577,7 +598,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         *dst = out;
     }
     if constexpr (APPEND) {
-        const bool app = mark != 0u && atomicExch(dirty_out + (mark - 1u), 1u) == 0u;
+        const bool app = mark != 0u && atomicOr(dirty_out + (mark - 1u), 1u) == 0u;
         const unsigned am = __ballot_sync(FULL, app);
         if (am) {
             unsigned base = 0u;
@@ -586,7 +607,11 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
             if (app) al.out[base + __popc(am & ((1u << lane) - 1u))] = mark - 1u;
         }
     }
-    if (skip && active && g == 0 && qo == 0) (colour ? lv.dirty[1] : lv.dirty[0])[s] = 0u;
+    // the pixel's four direction groups: did any mark its receiver?
+    const unsigned mk = __ballot_sync(FULL, marked && g == 0);
+    const unsigned pix_dirs = (1u | (1u << Gp) | (1u << (2 * Gp)) | (1u << (3 * Gp))) << (lane & ~(LP - 1));
+    if (skip && active && g == 0 && qo == 0)
+        (colour ? lv.dirty[1] : lv.dirty[0])[s] = (lv.freeze && (mk & pix_dirs) == 0u) ? 2u : 0u;
 }
 
 // ------------------------------------------------------------------ coarse-to-fine start

