@@ -1108,7 +1108,7 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
 extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     if (!c || level < 0 || level >= c->levels || variant < -1 ||
         variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER |
-                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS))
+                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp) : variant;

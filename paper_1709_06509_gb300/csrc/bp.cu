@@ -54,6 +54,35 @@ sweep_u8_eager_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, 
     }
 }
 
+// The same half-sweep with staged inputs (see stage_u8): each thread copies the next block's
+// inputs into its shared-memory stage while it computes the current block (two stages, so a
+// stage is refilled only after the block that read it has been computed).
+#ifndef BPS_SWEEP_STAGED_MIN_BLOCKS
+#define BPS_SWEEP_STAGED_MIN_BLOCKS 2  // 2 x 256 threads x 2 stages x 11 chunks x 16 B = 180 KB a SM
+#endif
+template <bool PADDED, bool APPEND, int TS>
+__global__ void __launch_bounds__(256, BPS_SWEEP_STAGED_MIN_BLOCKS)
+sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                       unsigned long long *trace, int nblocks, ActiveList al) {
+    extern __shared__ uint4 stage_mem[];  // [2][STAGE_CHUNKS][blockDim.x]
+    pdl_enter();
+    const int stage_len = STAGE_CHUNKS * blockDim.x;
+    int buf = 0;
+    if (blockIdx.x < (unsigned)nblocks) stage_u8(lv, colour, Dp, Gp, skip, blockIdx.x, stage_mem);
+    cp_async_commit();
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x, buf ^= 1) {
+        if (b + (int)gridDim.x < nblocks)
+            stage_u8(lv, colour, Dp, Gp, skip, b + gridDim.x, stage_mem + (buf ^ 1) * stage_len);
+        cp_async_commit();
+        cp_async_wait<1>();  // block b's copies have landed; the next block's may be in flight
+        sweep_group_u8<PADDED, APPEND, TS, false, 3>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al, 0, 0,
+                                                     stage_mem + buf * stage_len);
+    }
+    cp_async_wait<0>();
+}
+
+static size_t staged_smem_bytes() { return (size_t)2 * STAGE_CHUNKS * 256 * sizeof(uint4); }
+
 // The same half-sweep over the pixels of an active list; its length is read on the device
 // (a recorded graph keeps the launch shape, the list decides the work).
 template <bool PADDED, int TS, bool DP>
@@ -187,10 +216,35 @@ bool cluster_sweep_available() {
 }
 
 // Kernel of one u8 half-sweep: padding variant x list / append mode x minimisation form.
+// CTAs of the staged sweep that fit on the GPU at once (looked up once per process).
+static int resident_staged_blocks() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_staged_kernel<false, false, 0>, 256,
+                                                      staged_smem_bytes());
+        cached = std::max(1, sms * std::max(1, per_sm));
+    }
+    return cached;
+}
+
 template <bool PADDED, int TS, bool DP>
 static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                                bool eager, cudaStream_t st) {
+                                bool eager, cudaStream_t st, bool staged = false) {
+    if constexpr (!DP) {
+        if (staged && !al.in) {  // dense launches only
+            const unsigned g = (unsigned)std::min<int64_t>(blocks, resident_staged_blocks());
+            const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
+            if (al.out)
+                return launch_k(sweep_u8_staged_kernel<PADDED, true, TS>, dim3(g), dim3(256), staged_smem_bytes(), st,
+                                lv, colour, D, Dp, Gp, lam, lamT, skip, trace, (int)blocks, dense);
+            return launch_k(sweep_u8_staged_kernel<PADDED, false, TS>, dim3(g), dim3(256), staged_smem_bytes(), st, lv,
+                            colour, D, Dp, Gp, lam, lamT, skip, trace, (int)blocks, dense);
+        }
+    }
     if (eager && !al.in && !al.out)  // grid <= blocks: every CTA has a first block
         return launch_k(sweep_u8_eager_kernel<PADDED, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
                         lam, lamT, skip, trace, (int)blocks);
@@ -208,20 +262,26 @@ static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, 
 template <bool PADDED, int TS>
 static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                                bool eager, bool dp, cudaStream_t st) {
+                                bool eager, bool dp, bool staged, cudaStream_t st) {
     if (dp) return launch_u8_dp<PADDED, TS, true>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
-    return launch_u8_dp<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
+    return launch_u8_dp<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st,
+                                           staged);
 }
 
 template <bool PADDED>
 static cudaError_t launch_u8(int ts, const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                              unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                             bool eager, bool dp, cudaStream_t st) {
+                             bool eager, bool dp, bool staged, cudaStream_t st) {
     switch (ts) {
-    case 1: return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
-    case 2: return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
+    case 1:
+        return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
+                                       staged, st);
+    case 2:
+        return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
+                                       staged, st);
     default:
-        return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp, st);
+        return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
+                                       staged, st);
     }
 }
 
@@ -267,10 +327,12 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
         const bool eager = (variant & VARIANT_EAGER) != 0;
+        const bool staged = (variant & VARIANT_STAGED) != 0 && !dp;
         if (D & 15)
             return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
-                                   st);
-        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp, st);
+                                   staged, st);
+        return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
+                                staged, st);
     }
     default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
@@ -409,8 +471,15 @@ template <bool PADDED, int TS, bool DP> static cudaError_t preload_u8_dp() {
     return e;
 }
 template <bool PADDED, int TS> static cudaError_t preload_u8() {
-    const cudaError_t e = preload_u8_dp<PADDED, TS, false>();
-    return e == cudaSuccess ? preload_u8_dp<PADDED, TS, true>() : e;
+    cudaError_t e = preload_u8_dp<PADDED, TS, false>();
+    if (e == cudaSuccess) e = preload_u8_dp<PADDED, TS, true>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_staged_kernel<PADDED, false, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)staged_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_staged_kernel<PADDED, true, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)staged_smem_bytes());
+    return e;
 }
 
 cudaError_t preload_bp_kernels(int msg_kind) {

@@ -55,6 +55,7 @@ constexpr int VARIANT_CLUSTER = 4;     // every iteration of the scale in one th
 constexpr int VARIANT_EAGER = 8;       // every load of a half-sweep issued at once (dense launches)
 constexpr int VARIANT_DPAR = 16;       // one lane group per (pixel, direction), up to 128 labels
 constexpr int VARIANT_DPAR_LISTS = 32; // ... on the list launches only
+constexpr int VARIANT_STAGED = 64;     // dense launches stage the next block's inputs in shared memory
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {

@@ -286,6 +286,71 @@ struct ActiveList {
     unsigned *n_out;
 };
 
+// ------------------------------------------------------------------ staged inputs (cp.async)
+// A staged sweep keeps every input of a pixel block in a per-thread shared-memory stage, filled
+// by asynchronous 16-byte copies one block ahead, so the loads of the next block are in flight
+// while the current one computes and memory parallelism does not cost registers.  Stage chunk k
+// of thread t is stage[k * blockDim.x + t]: 0-1 cost, 2-5 incoming, 6-9 old outgoing, 10 flag.
+// Chunks of absent inputs are zero-filled by the copy (source size 0, an in-bounds address).
+constexpr int STAGE_CHUNKS = 11;
+
+__device__ __forceinline__ void cp_async16(uint4 *smem, const void *gmem, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint4 *smem, const void *gmem, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// every committed group but the newest `n` has landed in shared memory
+template <int n> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// Issue the copies of block `block`'s inputs (eager: old messages of every valid pixel) into
+// `stage` (this thread's chunks).
+__device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp, int Gp, int skip, int64_t block,
+                                         uint4 *stage) {
+    const int T = blockDim.x, t = threadIdx.x;
+    const int g = threadIdx.x & (Gp - 1);
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    int x = 0, y = 0;
+    bool valid = false;
+    if (s < nslot) {
+        y = (int)(s / lv.Wh);
+        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        valid = x < lv.W;
+    }
+    const int64_t sc = valid ? s : 0;
+    const int dbase = g * VEC;
+    const bool lane_data = dbase < Dp;
+    const bool has[4] = {valid && y > 0, valid && y < lv.H - 1, valid && x > 0, valid && x < lv.W - 1};
+    const int16_t *cost = reinterpret_cast<const int16_t *>(colour ? lv.cost[1] : lv.cost[0]);
+    const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
+    const uint8_t *msg_out = reinterpret_cast<const uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
+    const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
+    const int nbx[4] = {x, x, x - 1, x + 1};
+    const int nby[4] = {y - 1, y + 1, y, y};
+    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
+    const uint4 *cp = reinterpret_cast<const uint4 *>(cost + (lane_data ? sc * Dp + dbase : 0));
+    cp_async16(stage + 0 * T + t, cp, lane_data);
+    cp_async16(stage + 1 * T + t, cp + (lane_data ? 1 : 0), lane_data);
+    const uint8_t *mp = msg_in + (lane_data ? sc * 4 * Dp + dbase : 0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool hq = lane_data && has[q];
+        cp_async16(stage + (2 + q) * T + t, mp + (hq ? q * Dp : 0), hq);
+        const bool oq = skip && hq;
+        const int64_t qs = oq ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+        cp_async16(stage + (6 + q) * T + t, msg_out + (oq ? (qs * 4 + opp[q]) * Dp + dbase : 0), oq);
+    }
+    cp_async4(stage + 10 * T + t, dirty_in + sc, valid);
+}
+
 // PADDED: D is not a multiple of 16, so the last lane holds labels >= D that must stay out
 // of every minimum and be stored as 0.
 // APPEND: newly dirty neighbours are appended to the other colour's active list.
@@ -301,6 +366,7 @@ struct ActiveList {
 //           for nothing: for small, latency-bound scales);
 //        2, as 1, and the cost loads also precede the wait on the predecessor kernel (no BP
 //           kernel writes the cost volume); the caller then must not have called pdl_enter().
+//        3, the inputs were staged by the caller (stage_u8, waited for): read from `stage`.
 // LISTED: the caller gives the slot (s_listed; nslot for none), an entry of the active list:
 //         a listed pixel is dirty by construction (it was appended when its flag flipped from
 //         0 to 1, and only its own update clears the flag), so its flag is not read.
@@ -308,7 +374,7 @@ template <bool PADDED, bool APPEND = false, int TS = 0, bool RW = false, int EAG
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
                                                int lamT, int skip, unsigned long long *trace, int64_t block,
                                                const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
-                                               int64_t n_in = 0, int64_t s_listed = 0) {
+                                               int64_t n_in = 0, int64_t s_listed = 0, const uint4 *stage = nullptr) {
     const int lane = threadIdx.x & 31;
     const int g = threadIdx.x & (Gp - 1);
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
@@ -366,13 +432,32 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             old[q] = (skip && send && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
         }
     };
-    if constexpr (EAGER != 0) {
+    unsigned flag_staged = 0u;
+    if constexpr (EAGER == 3) {
+        const int T = blockDim.x, t = threadIdx.x;
+        const uint4 c0 = stage[0 * T + t], c1 = stage[1 * T + t];
+        b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
+        b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+        if (!lane_data) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            in[q] = stage[(2 + q) * T + t];
+            old[q] = stage[(6 + q) * T + t];
+            const int64_t qs = (valid && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+            dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
+        }
+        flag_staged = stage[10 * T + t].x;
+    } else if constexpr (EAGER != 0) {
         load_cost();
         if constexpr (EAGER == 2) pdl_enter();
         load_messages(valid);
     }
     // dirty and not frozen (flags are 0 / 1 under the exact skip rule)
-    const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
+    const bool active =
+        valid && (LISTED || !skip || (EAGER == 3 ? flag_staged : dirty_in[s]) == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {

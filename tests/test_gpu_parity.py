@@ -298,7 +298,7 @@ def set_all_variants(st, variant):
     assert st.variants() == [variant] * st.levels
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43, 64, 65, 66, 67])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
                                   (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
                          ids=lambda c: "x".join(map(str, c)))
@@ -321,7 +321,7 @@ def test_every_sweep_variant_is_exact(case, variant):
     assert np.array_equal(disp, oracle.wta(c0, ref_msg))
 
 
-@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25])
+@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25, 64, 65])
 def test_cluster_and_eager_variants_without_skip_and_in_a_graph(variant):
     # the cluster launch and the eager loads with every pixel recomputed (no skip), then
     # captured in the cached graph of the whole pipeline; the profile shares a cluster
@@ -493,7 +493,7 @@ def test_fp16_energy_gap(name):
     assert (d != ref["disp"]).mean() < 0.02
 
 
-@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24])
+@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66])
 @pytest.mark.parametrize("eps,freeze", [(1, False), (3, False), (0, True), (2, True)])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (60, 44, 40, 5, 3, 5, 8, 3)],
                          ids=lambda c: "x".join(map(str, c)))
