@@ -58,6 +58,12 @@ def parse():
                     help="instead of the benchmark line: the approximate skip rules (eps threshold, permanent "
                          "freeze) on the benchmark pairs and the 960x540 D256 pair: time, work and energy gap "
                          "against the exact skip, one JSON line")
+    ap.add_argument("--forms-report", action="store_true",
+                    help="instead of the benchmark line: every message form (int32, u8, fp16) on the benchmark "
+                         "pairs and the 1920x1080 D256 pair: throughput, energy, fp16 energy gap against the FP64 "
+                         "oracle and bad-pixel rates, one JSON line")
+    ap.add_argument("--batch-form", choices=["u8", "fp16"], default="u8",
+                    help="message form of --batch-report")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
     ap.add_argument("--workload", default=None,
@@ -276,14 +282,16 @@ def batch_report(args):
     dev = torch.device("cuda", 0)
     specs = synth.batch_specs(args.batch_report)
     pairs = [synth.make_pair(seed, W, H, D, 8, 3.0) for seed, W, H, D in specs]
-    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, LEVELS, bps.BPS_MSG_U8, device=dev) for p in pairs]
+    form = bps.BPS_MSG_FP16 if args.batch_form == "fp16" else bps.BPS_MSG_U8
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, LEVELS, form, device=dev) for p in pairs]
     Ls = [torch.from_numpy(p.left).to(dev) for p in pairs]
     Rs = [torch.from_numpy(p.right).to(dev) for p in pairs]
     outs = [torch.empty(p.left.shape, dtype=torch.int32, device=dev) for p in pairs]
     windows = [7] * len(pairs)
-    for st, L, R in zip(sts, Ls, Rs):
-        autotune.tune_ncc(st, L, R, 7, TRUNC_DATA, reps=2)
-        autotune.tune(st, L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+    if form == bps.BPS_MSG_U8:  # the sweep variants and NCC shapes exist for the u8 form
+        for st, L, R in zip(sts, Ls, Rs):
+            autotune.tune_ncc(st, L, R, 7, TRUNC_DATA, reps=2)
+            autotune.tune(st, L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     units = sum(p.left.size * p.D for p in pairs)
     batch = bps.Batch(sts)
@@ -312,7 +320,7 @@ def batch_report(args):
     batch.close()
     for st in sts:
         st.close()
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": f"batch of {len(pairs)} mixed pairs",
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": f"batch of {len(pairs)} mixed pairs", "form": args.batch_form,
                       "pixels_x_labels": units, "steps": args.steps, "modes": res}))
 
 
@@ -440,12 +448,86 @@ def approx_report(args):
     print(json.dumps(out))
 
 
+def bad_pixel_rate(disp, pair) -> float:
+    """Share of visible (non-occluded) pixels whose disparity is off the generator's truth by more than 1."""
+    import numpy as np
+
+    vis = ~pair.occluded
+    return float((np.abs(disp.astype(np.int64) - pair.disparity)[vis] > 1).mean())
+
+
+def forms_report(args):
+    """The message forms side by side: int32 messages, u8 messages (the same integer method, bit-exact),
+    fp16 messages on the unquantised float cost (judged by its energy gap against the FP64 oracle of
+    the float form, scored by the oracle's own energy).  One graph per pair, L2 flushed between
+    repetitions; the 1920x1080 pair has no oracle run (hours on one core)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    forms = {"int32": bps.BPS_MSG_INT32, "u8": bps.BPS_MSG_U8, "fp16": bps.BPS_MSG_FP16}
+    out = {"metric": METRIC, "unit": UNIT, "report": "message forms", "pairs": {}}
+    for name in ("tsukuba_384x288_d16", "teddy_450x375_d64", "hd_1920x1080_d256"):
+        pair, window = synth.workload_pair(name)
+        H, W = pair.left.shape
+        L = torch.from_numpy(pair.left).to(dev)
+        R = torch.from_numpy(pair.right).to(dev)
+        disp = torch.empty((H, W), dtype=torch.int32, device=dev)
+        row = {}
+        ref = None
+        if not name.startswith("hd"):
+            ref = oracle.stereo_f64(pair.left, pair.right, pair.D, window, TRUNC_DATA, LEVELS, ITERS, float(LAM), TRUNC)
+        for fname, form in forms.items():
+            with bps.Stereo(W, H, pair.D, LEVELS, form, device=dev) as st:
+                if form == bps.BPS_MSG_U8:
+                    autotune.tune_ncc(st, L, R, window, TRUNC_DATA, reps=2)
+                    autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+                steps = max(3, args.steps if not name.startswith("hd") else min(args.steps, 10))
+                for _ in range(3):
+                    st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=disp)
+                torch.cuda.synchronize()
+                total = 0.0
+                for _ in range(steps):
+                    flush.fill_(7)
+                    e0.record()
+                    st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=disp)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    total += e0.elapsed_time(e1)
+                ei, ef = st.energy(disp, LAM, TRUNC)
+                d = disp.cpu().numpy()
+                r = {"value": W * H * pair.D * steps / (total / 1e3) / 1e6, "ms": total / steps,
+                     "bad_pixel_rate": bad_pixel_rate(d, pair)}
+                if form == bps.BPS_MSG_FP16:
+                    r["energy_fp64_gpu"] = float(ef.item())
+                    if ref is not None:
+                        e_gpu = oracle.energy(ref["cost"], d, float(LAM), TRUNC)  # GPU labels, oracle's scoring
+                        r["energy_gap_rel"] = (e_gpu - ref["energy"]) / ref["energy"]
+                        r["label_disagreement"] = float((d != ref["disp"]).mean())
+                        r["oracle_bad_pixel_rate"] = bad_pixel_rate(ref["disp"], pair)
+                else:
+                    r["energy_int64"] = int(ei.item())
+                row[fname] = r
+        row["fp16_vs_int32"] = row["fp16"]["value"] / row["int32"]["value"]
+        row["u8_vs_int32"] = row["u8"]["value"] / row["int32"]["value"]
+        out["pairs"][name] = row
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch_report:
         return batch_report(args)
+    if args.forms_report:
+        return forms_report(args)
     if args.approx_report:
         return approx_report(args)
     if args.warmstart_report:
@@ -497,6 +579,11 @@ def main():
     batch = bps.Batch([st for st, _ in ctxs])
     windows = [w for _, w in ctxs]
     Ls, Rs = [L for L, _ in inputs], [R for _, R in inputs]
+    # the pairs share the GPU: refine the choices jointly on the batch step (untimed)
+    joint = autotune.tune_batch(batch, [st for st, _ in ctxs], Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC,
+                                cache=args.tune_cache)
+    for (st, _), vs in zip(ctxs, joint):
+        tuned[f"{st.W}x{st.H}_D{st.D}"]["sweep_variants"] = vs
 
     def step():
         batch.stereo(Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, outs=outs)

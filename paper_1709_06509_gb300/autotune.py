@@ -165,3 +165,84 @@ def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache
                 json.dump(table, fh, indent=1, sort_keys=True)
     st.set_ncc_shape(*best)
     return best
+
+
+def tune_batch(batch, sts, lefts, rights, windows, trunc_data: int, iters: int, lam: int, trunc: int,
+               skip: bool = True, reps: int = 3, cache: str | None = None, target_ms: float = 20.0,
+               margin: float = 0.005) -> list[list[int]]:
+    """Refine the sweep variants of every member of a batch jointly and set them; returns them.
+
+    The members' launch chains run side by side on one GPU, so the variant that is fastest for a
+    member alone may take SMs from another member's critical path.  Starting from the current
+    choices (normally each member's own tuning), one pass of coordinate descent over (member,
+    scale) times the whole batch graph; a candidate replaces the current choice only when it
+    makes the batch faster by more than `margin`.  Cached under the members' keys together."""
+    import torch
+
+    gpu = torch.cuda.get_device_name(sts[0].device)
+    member_keys = []
+    for st in sts:
+        dims = level_dims(st.W, st.H, st.levels)
+        member_keys.append([_key(gpu, w, h, st.D, st.msg_type, trunc, skip) for w, h in dims])
+    key = "batch[" + ";".join(",".join(k) for k in member_keys) + "]"
+    table = _load(cache)
+    if key in table:
+        chosen = [list(map(int, v)) for v in table[key]]
+        for st, vs in zip(sts, chosen):
+            for lvl, v in enumerate(vs):
+                st.set_variant(lvl, v)
+        return chosen
+    outs = [torch.empty((st.H, st.W), dtype=torch.int32, device=st.device) for st in sts]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run():
+        batch.stereo(lefts, rights, windows, trunc_data, iters, lam, trunc, skip=skip, graph=True, outs=outs)
+
+    def step_ms() -> float:
+        run()  # records the graph
+        run()
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        n = max(2, min(400, int(target_ms / max(e0.elapsed_time(e1), 1e-3))))
+        best = float("inf")
+        for _ in range(reps):
+            e0.record()
+            for _ in range(n):
+                run()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / n)
+        return best
+
+    base = step_ms()
+    for st in sts:
+        Gp = _lanes_per_pixel(st.D)
+        dims = level_dims(st.W, st.H, st.levels)
+        for lvl in reversed(range(st.levels)):
+            w, h = dims[lvl]
+            small = h * ((w + 1) // 2) * Gp <= CLUSTER_MAX_LANES
+            current = st.variants()[lvl]
+            best_v, best_t = current, base
+            for v in (SMALL_CANDIDATES if small else LARGE_CANDIDATES):
+                if v == current or (v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL):
+                    continue
+                try:
+                    st.set_variant(lvl, v)
+                except BPSError as e:
+                    if e.status == BPS_ERR_UNSUPPORTED:
+                        continue
+                    raise
+                t = step_ms()
+                if t < best_t * (1.0 - margin):
+                    best_v, best_t = v, t
+            st.set_variant(lvl, best_v)
+            base = best_t
+    chosen = [st.variants() for st in sts]
+    if cache:
+        table[key] = chosen
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+    return chosen

@@ -372,6 +372,36 @@ def test_autotuner_picks_exact_variants(tmp_path):
     assert np.array_equal(d.cpu().numpy(), ref["disp"])
 
 
+def test_batch_autotuner_keeps_results_exact(tmp_path):
+    from paper_1709_06509_gb300 import autotune
+
+    shapes = [(80, 60, 16, 5), (64, 48, 48, 5)]
+    pairs = [synth.make_pair(120 + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+    windows = [w for *_, w in shapes]
+    sts = [bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) for W, H, D, _ in shapes]
+    cache = str(tmp_path / "joint.json")
+    try:
+        with bps.Batch(sts) as batch:
+            Ls = [to_dev(p.left) for p in pairs]
+            Rs = [to_dev(p.right) for p in pairs]
+            chosen = autotune.tune_batch(batch, sts, Ls, Rs, windows, 20, 4, 10, 2, reps=1, target_ms=2.0,
+                                         cache=cache)
+            assert [st.variants() for st in sts] == chosen
+            outs = batch.stereo(Ls, Rs, windows, 20, 4, 10, 2)
+            torch.cuda.synchronize()
+            for out, p, w in zip(outs, pairs, windows):
+                ref = oracle.stereo_int(p.left, p.right, p.D, w, 20, 3, 4, 10, 2)
+                assert np.array_equal(out.cpu().numpy(), ref["disp"])
+            for st in sts:
+                for lvl in range(st.levels):
+                    st.set_variant(lvl, 0)
+            again = autotune.tune_batch(batch, sts, Ls, Rs, windows, 20, 4, 10, 2, cache=cache)  # from the cache
+            assert again == chosen and [st.variants() for st in sts] == chosen
+    finally:
+        for st in sts:
+            st.close()
+
+
 def test_argument_errors_on_a_live_context():
     with bps.Stereo(16, 8, 4, 2, bps.BPS_MSG_U8, device=DEV) as st:
         with pytest.raises(bps.BPSError) as e:
