@@ -54,6 +54,9 @@ def lib() -> ctypes.CDLL:
             "oracle_bp_f64": (i, [P, i, i, i, i, i, d, i, i, P, u64, P, P]),
             "oracle_bp_rule_i32": (i, [P, i, i, i, i, i, i, i, i, i, i, P, u64, P, P]),
             "oracle_bp_rule_f64": (i, [P, i, i, i, i, i, d, i, i, d, i, P, u64, P, P]),
+            "oracle_candidates": (i, [P, i, i, i, i, P]),
+            "oracle_bp_sparse_i32": (i, [P, i, i, i, i, i, i, i, i, i, P, P, P]),
+            "oracle_wta_sparse_i32": (i, [P, P, P, i, i, i, i, P]),
             "oracle_wta_i32": (i, [P, P, i, i, i, P]),
             "oracle_wta_f64": (i, [P, P, i, i, i, P]),
             "oracle_energy_i32": (i64, [P, P, i, i, i, i, i]),
@@ -158,6 +161,39 @@ def bp(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool =
                                       int(freeze), _p(init), order_seed, _p(out), _p(trace))
     _check(rc, "oracle_bp")
     return out, trace[:ntrace]
+
+
+def candidates(cost0: np.ndarray, K: int) -> np.ndarray:
+    """The K labels of lowest cost per pixel, in increasing label order, int32 [H][W][K]."""
+    H, W, D = cost0.shape
+    out = np.empty((H, W, K), dtype=np.int32)
+    _check(lib().oracle_candidates(_p(np.ascontiguousarray(cost0, dtype=np.int32)), W, H, D, K, _p(out)),
+           "oracle_candidates")
+    return out
+
+
+def bp_sparse(cost0: np.ndarray, levels: int, iters: int, lam: int, trunc: int, K: int, skip: bool = True):
+    """Hierarchical BP with K candidates per pixel at the finest scale.  Returns (candidates
+    [H][W][K], finest messages [4][H][W][K], trace per half-sweep)."""
+    H, W, D = cost0.shape
+    ntrace = levels * iters * 2
+    trace = np.zeros(max(ntrace, 1), dtype=np.int64)
+    cand = np.empty((H, W, K), dtype=np.int32)
+    msg = np.empty((4, H, W, K), dtype=np.int32)
+    _check(lib().oracle_bp_sparse_i32(_p(np.ascontiguousarray(cost0, dtype=np.int32)), W, H, D, levels, iters,
+                                      int(lam), trunc, int(skip), K, _p(cand), _p(msg), _p(trace)), "oracle_bp_sparse")
+    return cand, msg, trace[:ntrace]
+
+
+def wta_sparse(cost0: np.ndarray, cand: np.ndarray, msg: np.ndarray) -> np.ndarray:
+    H, W, D = cost0.shape
+    K = cand.shape[2]
+    out = np.empty((H, W), dtype=np.int32)
+    _check(lib().oracle_wta_sparse_i32(_p(np.ascontiguousarray(cost0, dtype=np.int32)),
+                                       _p(np.ascontiguousarray(cand, dtype=np.int32)),
+                                       _p(np.ascontiguousarray(msg, dtype=np.int32)), W, H, D, K, _p(out)),
+           "oracle_wta_sparse")
+    return out
 
 
 def wta(cost0: np.ndarray, msg0: np.ndarray) -> np.ndarray:

@@ -387,6 +387,218 @@ int oracle_bp_rule_i32(const int32_t *cost0, int W, int H, int D, int levels, in
     return rc;
 }
 
+/* ---------------------------------------------------------------- sparse candidates */
+
+int oracle_candidates(const int32_t *cost0, int W, int H, int D, int K, int32_t *cand)
+{
+    if (!cost0 || !cand || W < 1 || H < 1 || K < 1 || K > D)
+        return -1;
+    unsigned char *taken = malloc((size_t)D);
+    if (!taken)
+        return -1;
+    for (size_t p = 0; p < (size_t)W * H; ++p) {
+        const int32_t *c = cost0 + p * D;
+        int32_t *out = cand + p * K;
+        memset(taken, 0, (size_t)D);
+        /* the K smallest costs, the lower label first among equal costs */
+        for (int k = 0; k < K; ++k) {
+            int best = -1;
+            for (int d = 0; d < D; ++d)
+                if (!taken[d] && (best < 0 || c[d] < c[best]))
+                    best = d;
+            taken[best] = 1;
+            out[k] = best;
+        }
+        /* listed in increasing label order */
+        for (int a = 1; a < K; ++a)
+            for (int b = a; b > 0 && out[b - 1] > out[b]; --b) {
+                const int32_t t = out[b];
+                out[b] = out[b - 1];
+                out[b - 1] = t;
+            }
+    }
+    free(taken);
+    return 0;
+}
+
+/* The finest scale over candidate sets.  M: [4][H][W][K] incoming messages, indexed like the
+ * candidates of the receiving pixel. */
+static int64_t *bp_sparse_level(const double *C, const int32_t *cand, double *M, int W, int H, int D,
+                                int K, int iters, double lambda, int trunc, int skip, int64_t *trace)
+{
+    const size_t plane = (size_t)H * W * K;
+    double *b = malloc(sizeof(double) * (size_t)K);
+    double *h = malloc(sizeof(double) * (size_t)K);
+    double *m = malloc(sizeof(double) * (size_t)K);
+    unsigned char *dirty = malloc((size_t)W * H);
+    memset(dirty, 1, (size_t)W * H);
+    for (int it = 0; it < iters; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            int64_t updated = 0;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    if (((x + y) & 1) != colour)
+                        continue;
+                    const size_t p = (size_t)y * W + x;
+                    if (skip && !dirty[p])
+                        continue;
+                    ++updated;
+                    const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
+                    const int32_t *cp = cand + p * K;
+                    for (int i = 0; i < K; ++i) {
+                        double s = C[p * D + cp[i]];
+                        for (int q = 0; q < 4; ++q)
+                            if (has[q])
+                                s += M[q * plane + p * K + i];
+                        b[i] = s;
+                    }
+                    for (int q = 0; q < 4; ++q) {
+                        if (!has[q])
+                            continue;
+                        int qx = x, qy = y, slot;
+                        switch (q) {
+                        case UP: qy = y - 1; slot = DOWN; break;
+                        case DOWN: qy = y + 1; slot = UP; break;
+                        case LEFT: qx = x - 1; slot = RIGHT; break;
+                        default: qx = x + 1; slot = LEFT; break;
+                        }
+                        const size_t r = (size_t)qy * W + qx;
+                        const int32_t *cr = cand + r * K;
+                        for (int i = 0; i < K; ++i)
+                            h[i] = b[i] - M[q * plane + p * K + i];
+                        /* m(j) = min over p's candidates i of h(i) + lambda*min(|label_i - label_j|, T) */
+                        double mn = INFINITY;
+                        for (int j = 0; j < K; ++j) {
+                            double v = INFINITY;
+                            for (int i = 0; i < K; ++i) {
+                                const int dd = abs(cp[i] - cr[j]);
+                                const double t = h[i] + lambda * (double)(dd < trunc ? dd : trunc);
+                                if (t < v)
+                                    v = t;
+                            }
+                            m[j] = v;
+                            if (v < mn)
+                                mn = v;
+                        }
+                        double *dst = M + slot * plane + r * K;
+                        int changed = 0;
+                        for (int j = 0; j < K; ++j) {
+                            const double v = m[j] - mn;
+                            if (dst[j] != v)
+                                changed = 1;
+                            dst[j] = v;
+                        }
+                        if (changed)
+                            dirty[r] = 1;
+                    }
+                    dirty[p] = 0;
+                }
+            if (trace)
+                *trace++ = updated;
+        }
+    free(b);
+    free(h);
+    free(m);
+    free(dirty);
+    return trace;
+}
+
+int oracle_bp_sparse_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                         int trunc, int skip, int K, int32_t *cand_out, int32_t *msg_out, int64_t *trace)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !cand_out || !msg_out || D < 1 || K < 1 || K > D || levels < 1 || levels > 32 || iters < 0 ||
+        trunc < 0 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    if (oracle_candidates(cost0, W, H, D, K, cand_out) != 0)
+        return -1;
+    size_t off[33];
+    off[0] = 0;
+    for (int l = 0; l < levels; ++l)
+        off[l + 1] = off[l] + (size_t)Ws[l] * Hs[l] * D;
+    const size_t n0 = (size_t)W * H * D;
+    double *c = malloc(sizeof(double) * n0);
+    double *pyr = malloc(sizeof(double) * off[levels]);
+    if (!c || !pyr) {
+        free(c);
+        free(pyr);
+        return -1;
+    }
+    for (size_t k = 0; k < n0; ++k)
+        c[k] = cost0[k];
+    oracle_pyramid_f64(c, W, H, D, levels, pyr);
+    /* scales levels-1 .. 1: the dense hierarchical solve */
+    double *parent = NULL;
+    int64_t *tr = trace;
+    for (int l = levels - 1; l >= 1; --l) {
+        const int w = Ws[l], h = Hs[l];
+        const size_t plane = (size_t)w * h * D;
+        double *M = calloc(4 * plane, sizeof(double));
+        if (l < levels - 1) {
+            const int pw = Ws[l + 1], ph = Hs[l + 1];
+            const size_t pplane = (size_t)pw * ph * D;
+            for (int q = 0; q < 4; ++q)
+                for (int y = 0; y < h; ++y)
+                    for (int x = 0; x < w; ++x)
+                        memcpy(M + q * plane + ((size_t)y * w + x) * D,
+                               parent + q * pplane + ((size_t)(y / 2) * pw + x / 2) * D, sizeof(double) * D);
+        }
+        free(parent);
+        tr = bp_level(pyr + off[l], M, w, h, D, iters, (double)lambda, trunc, skip, 0.0, 0, 0, tr);
+        parent = M;
+    }
+    /* the finest scale: each candidate starts from the parent's message at its label */
+    const size_t splane = (size_t)W * H * K;
+    double *M = calloc(4 * splane, sizeof(double));
+    if (parent) {
+        const int pw = Ws[1], ph = Hs[1];
+        const size_t pplane = (size_t)pw * ph * D;
+        for (int q = 0; q < 4; ++q)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    for (int j = 0; j < K; ++j) {
+                        const size_t p = (size_t)y * W + x;
+                        M[q * splane + p * K + j] =
+                            parent[q * pplane + ((size_t)(y / 2) * pw + x / 2) * D + cand_out[p * K + j]];
+                    }
+    }
+    free(parent);
+    bp_sparse_level(pyr, cand_out, M, W, H, D, K, iters, (double)lambda, trunc, skip, tr);
+    for (size_t k = 0; k < 4 * splane; ++k)
+        msg_out[k] = (int32_t)M[k];
+    free(M);
+    free(pyr);
+    free(c);
+    return 0;
+}
+
+int oracle_wta_sparse_i32(const int32_t *cost0, const int32_t *cand, const int32_t *msg, int W, int H, int D,
+                          int K, int32_t *disp)
+{
+    if (!cost0 || !cand || !msg || !disp || W < 1 || H < 1 || K < 1 || K > D)
+        return -1;
+    const size_t plane = (size_t)W * H * K;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
+            int64_t best = INT64_MAX;
+            int arg = 0;
+            for (int j = 0; j < K; ++j) { /* increasing labels: the lowest label wins ties */
+                int64_t s = cost0[p * D + cand[p * K + j]];
+                for (int q = 0; q < 4; ++q)
+                    if (has[q])
+                        s += msg[q * plane + p * K + j];
+                if (s < best) {
+                    best = s;
+                    arg = cand[p * K + j];
+                }
+            }
+            disp[p] = arg;
+        }
+    return 0;
+}
+
 /* ---------------------------------------------------------------- read-out and energy */
 
 int oracle_wta_f64(const double *cost, const double *msg, int W, int H, int D, int32_t *disp)

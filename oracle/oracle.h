@@ -84,6 +84,20 @@ int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int
                        int trunc, int skip, double eps, int freeze, const double *init_coarsest,
                        uint64_t order_seed, double *msg0_out, int64_t *trace);
 
+/* Sparse candidates (the abstract: NCC retrieves a sparse set of candidate matches and BP chooses
+ * among them).  oracle_candidates: per pixel the K labels of lowest cost (the lower label first
+ * among equal costs), listed in increasing label order, cand [H][W][K].  oracle_bp_sparse_i32:
+ * scales levels-1 .. 1 run the dense solve above; at the finest scale each candidate starts from
+ * the parent's message at its label, and red-black min-sum BP runs over the candidate sets:
+ * m(j) = min over the sender's candidates i of h(i) + lambda*min(|label_i - label_j|, trunc),
+ * minus its minimum, for each receiver candidate j.  msg_out [4][H][W][K]; trace as above.
+ * oracle_wta_sparse_i32: the candidate of least belief (lowest label on ties). */
+int oracle_candidates(const int32_t *cost0, int W, int H, int D, int K, int32_t *cand);
+int oracle_bp_sparse_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,
+                         int trunc, int skip, int K, int32_t *cand_out, int32_t *msg_out, int64_t *trace);
+int oracle_wta_sparse_i32(const int32_t *cost0, const int32_t *cand, const int32_t *msg, int W, int H, int D,
+                          int K, int32_t *disp);
+
 /* d*(p) = argmin_d [cost(p, d) + sum of incoming messages], lowest d on ties. */
 int oracle_wta_i32(const int32_t *cost, const int32_t *msg, int W, int H, int D, int32_t *disp);
 int oracle_wta_f64(const double *cost, const double *msg, int W, int H, int D, int32_t *disp);

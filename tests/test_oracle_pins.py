@@ -505,3 +505,72 @@ def test_skip_rule_keeps_messages_normalised_and_removes_work(eps, freeze):
     e_exact = oracle.energy(cost, oracle.wta(cost, m_exact), 10, 2)
     e = oracle.energy(cost, oracle.wta(cost, m), 10, 2)
     assert abs(e - e_exact) <= 0.05 * e_exact
+
+
+# ---------------------------------------------------------------- sparse candidates
+# (the abstract: NCC retrieves a sparse set of candidate matches, BP chooses among them)
+
+def test_candidates_are_the_k_lowest_costs():
+    rng = np.random.default_rng(31)
+    cost = random_cost(rng, 5, 7, 12, 6)  # many ties: the lower label must win them
+    for K in (1, 3, 12):
+        cand = oracle.candidates(cost, K)
+        for y in range(5):
+            for x in range(7):
+                order = np.lexsort((np.arange(12), cost[y, x]))  # by cost, then by label
+                assert cand[y, x].tolist() == sorted(order[:K].tolist())
+
+
+def test_sparse_with_every_label_is_the_dense_solve():
+    p = synth.make_pair(33, 40, 30, 12, 3, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 12, 5), 20)
+    for skip in (False, True):
+        m, t = oracle.bp(cost, 3, 5, 10, 2, skip=skip)
+        cand, ms, ts = oracle.bp_sparse(cost, 3, 5, 10, 2, 12, skip=skip)
+        assert np.array_equal(cand, np.broadcast_to(np.arange(12), cand.shape))
+        assert np.array_equal(ms, m) and np.array_equal(ts, t)
+        assert np.array_equal(oracle.wta_sparse(cost, cand, ms), oracle.wta(cost, m))
+
+
+def test_sparse_with_one_candidate_is_the_argmin():
+    rng = np.random.default_rng(34)
+    cost = random_cost(rng, 8, 9, 7)
+    cand, ms, _ = oracle.bp_sparse(cost, 2, 4, 10, 2, 1)
+    assert not ms.any()
+    assert np.array_equal(oracle.wta_sparse(cost, cand, ms), cost.argmin(axis=2))
+
+
+def test_sparse_chain_equals_viterbi_over_the_candidates():
+    # on a chain BP over candidate sets is exact: its read-out is the MAP labelling restricted to
+    # the candidates, found by Viterbi with every other label priced out of reach
+    rng = np.random.default_rng(35)
+    done = 0
+    while done < 12:
+        n, D = int(rng.integers(3, 25)), int(rng.integers(3, 10))
+        K = int(rng.integers(2, D))
+        lam, T = int(rng.integers(1, 8)), int(rng.integers(1, D + 1))
+        c = rng.integers(0, 25, (n, D)).astype(np.int64)
+        cost = c.astype(np.int32).reshape(1, n, D)
+        cand = oracle.candidates(cost, K).reshape(n, K)
+        masked = np.full_like(c, 10 ** 6)
+        np.put_along_axis(masked, cand, np.take_along_axis(c, cand, axis=1), axis=1)
+        marg, emin = viterbi(masked, lam, T)
+        mc = np.take_along_axis(marg, cand, axis=1)
+        srt = np.sort(mc, axis=1)
+        if np.any(srt[:, 0] == srt[:, 1]):
+            continue
+        cs, ms, _ = oracle.bp_sparse(cost, 1, n + 2, lam, T, K, skip=bool(done % 2))
+        d = oracle.wta_sparse(cost, cs, ms)
+        assert np.array_equal(d.ravel(), np.take_along_axis(cand, mc.argmin(axis=1)[:, None], axis=1).ravel())
+        assert oracle.energy(cost, d, lam, T) == emin
+        belief = np.take_along_axis(c, cand, axis=1) + ms.reshape(4, n, K).sum(axis=0)
+        assert np.array_equal(belief - belief.min(axis=1, keepdims=True), mc - mc.min(axis=1, keepdims=True))
+        done += 1
+
+
+def test_sparse_messages_stay_normalised():
+    p = synth.make_pair(36, 48, 36, 32, 4, 2.0)
+    cost = oracle.quantise(oracle.ncc(p.left, p.right, 32, 5), 20)
+    cand, ms, t = oracle.bp_sparse(cost, 3, 6, 10, 2, 6)
+    interior = ms[:, 1:-1, 1:-1]
+    assert np.all(interior.min(axis=3) == 0) and ms.max() <= 10 * 2 and ms.min() >= 0
