@@ -311,6 +311,24 @@ int bps_get_sweep_variant(bps_ctx *ctx, int level);
  * including batches and persistent launches it takes part in. */
 int bps_set_skip_rule(bps_ctx *ctx, int eps, int freeze);
 
+/* Sparse candidates (the abstract: normalised cross correlation retrieves a sparse set of
+ * candidate matches and belief propagation then chooses among them).  K = 0 (the default): the
+ * dense solve.  1 <= K <= min(D, BPS_MAX_CANDIDATES): later solves of this context run the
+ * scales above the finest densely; at the finest scale each pixel keeps the K labels of lowest
+ * data cost (the lower label first among equal costs), each candidate starts from the parent's
+ * message at its label, and messages are vectors over the receiver's candidates,
+ *   m(j) = min over the sender's candidates i of h(i) + lambda*min(|label_i - label_j|, trunc),
+ * minus their minimum.  bps_wta_disparity then picks the candidate of least belief (lowest
+ * label on ties); bps_energy scores the labels with the dense cost.  K = D gives the dense
+ * solve's results.  u8 form only, exact skip rule only (BPS_ERR_UNSUPPORTED otherwise, and for
+ * BPS_FLAG_PERSISTENT, or BPS_FLAG_WARM_START with one scale); BPS_ERR_ARG out of range.
+ * After a sparse solve bps_export_messages(level 0) returns BPS_ERR_STATE; read the finest
+ * scale with bps_export_sparse: d_cand int32 [H][W][K] labels in increasing order, d_msgs
+ * int32 [4][H][W][K] (direction as in bps_export_messages), both caller-owned device buffers. */
+#define BPS_MAX_CANDIDATES 32
+int bps_set_candidates(bps_ctx *ctx, int K);
+int bps_export_sparse(bps_ctx *ctx, int32_t *d_cand, int32_t *d_msgs, void *stream);
+
 /*
  * Learned warm start: kernels of a small convolutional network that predicts the coarsest
  * scale's messages from the coarsest cost volume (the start messages of bps_bp_solve with

@@ -97,6 +97,8 @@ _SIGS = {
     "bps_set_sweep_variant": (_I, [_P, _I, _I]),
     "bps_get_sweep_variant": (_I, [_P, _I]),
     "bps_set_skip_rule": (_I, [_P, _I, _I]),
+    "bps_set_candidates": (_I, [_P, _I]),
+    "bps_export_sparse": (_I, [_P, _P, _P, _P]),
     "bps_set_ncc_shape": (_I, [_P, _I, _I]),
     "bps_warmnet_conv3x3": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P]),
     "bps_warmnet_conv3x3_backward": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
@@ -279,6 +281,14 @@ def bps_get_sweep_variant(ctx, level: int) -> int:
 
 def bps_set_skip_rule(ctx, eps: int, freeze: bool) -> None:
     _check(lib().bps_set_skip_rule(ctx, int(eps), int(freeze)), "bps_set_skip_rule")
+
+
+def bps_set_candidates(ctx, K: int) -> None:
+    _check(lib().bps_set_candidates(ctx, int(K)), "bps_set_candidates")
+
+
+def bps_export_sparse(ctx, d_cand, d_msgs, stream=None) -> None:
+    _check(lib().bps_export_sparse(ctx, _ptr(d_cand), _ptr(d_msgs), _stream(stream)), "bps_export_sparse")
 
 
 def bps_warmnet_conv3x3(x, x_bf16, B, Cin, H, W, w, bias, Cout, relu, out, out_bf16, stream=None):
@@ -479,6 +489,21 @@ class Stereo:
     def set_skip_rule(self, eps: int = 0, freeze: bool = False) -> None:
         """Approximate fast-converging skip: eps threshold on message changes, permanent freeze."""
         bps_set_skip_rule(self.ctx, eps, freeze)
+
+    def set_candidates(self, K: int) -> None:
+        """K sparse candidate labels per pixel at the finest scale (0: the dense solve)."""
+        bps_set_candidates(self.ctx, K)
+        self.K = K
+
+    def export_sparse(self, stream=None):
+        """Finest-scale candidates int32 [H][W][K] and messages int32 [4][H][W][K] of a sparse solve."""
+        import torch
+
+        K = getattr(self, "K", 0)
+        cand = torch.empty((self.H, self.W, K), dtype=torch.int32, device=self.device)
+        msgs = torch.empty((4, self.H, self.W, K), dtype=torch.int32, device=self.device)
+        bps_export_sparse(self.ctx, cand, msgs, stream)
+        return cand, msgs
 
     def set_ncc_shape(self, column_groups: int, rows: int) -> None:
         bps_set_ncc_shape(self.ctx, column_groups, rows)

@@ -20,7 +20,7 @@ struct Plan {
     int levels = 0;
     int Ws[BPS_MAX_LEVELS], Hs[BPS_MAX_LEVELS], Whs[BPS_MAX_LEVELS];
     size_t cost[BPS_MAX_LEVELS][2], msg[BPS_MAX_LEVELS][2], dirty[BPS_MAX_LEVELS][2];
-    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, lists[2], list_counts, total;
+    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, lists[2], list_counts, sparse[2], total;
 };
 
 int cost_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? COST_I32 : msg_type == BPS_MSG_U8 ? COST_I16 : COST_F32; }
@@ -80,6 +80,11 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
     }
     p.list_counts = off;
     off += up((size_t)levels * BPS_MAX_ITERS * 2 * sizeof(unsigned));
+    // sparse candidates of the finest scale (u8 form): labels then costs, BPS_MAX_CANDIDATES a slot
+    for (int c = 0; c < 2; ++c) {
+        p.sparse[c] = off;
+        if (msg_type == BPS_MSG_U8) off += up((size_t)p.Hs[0] * p.Whs[0] * BPS_MAX_CANDIDATES * 4);
+    }
     p.total = off;
     return true;
 }
@@ -172,6 +177,8 @@ struct bps_ctx {
     int prof_first_trace = 0;
     int prof_trace_n = 0;   // trace entries covered by the profiled launches
     uint64_t config_version = 0;  // bumped when a kernel choice (variant, NCC shape) changes
+    SparseView sv{};              // sparse candidates of the finest scale (K = 0: dense)
+    int last_sparse_k = 0;        // K of the last solve (0: dense)
     GraphSlot host_graph;         // bps_stereo_host: copies in, pipeline, energy, copies out
     std::vector<int> prof_span;  // half-sweeps each profiled launch covers (a cluster launch covers a scale)
 };
@@ -310,6 +317,9 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->lists[0] = reinterpret_cast<unsigned *>(c->ws + p.lists[0]);
     c->lists[1] = reinterpret_cast<unsigned *>(c->ws + p.lists[1]);
     c->list_counts = reinterpret_cast<unsigned *>(c->ws + p.list_counts);
+    c->sv.cand[0] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[0]);
+    c->sv.cand[1] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[1]);
+    c->sv.K = c->sv.Kp = 0;
     for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l], c->Gp);
     PairDesc hd = make_desc(c);
     std::vector<int> prefix(2 * (levels + 1));
@@ -327,6 +337,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     ok = ok && ncc_rows_prepare(c->cost_kind, D, c->Dp) == cudaSuccess;
     ok = ok && preload_cost_kernels(c->cost_kind) == cudaSuccess;
     ok = ok && preload_bp_kernels(c->msg_kind) == cudaSuccess;
+    ok = ok && (c->msg_kind != MSG_U8 || preload_sparse_kernels() == cudaSuccess);
     ok = ok && preload_readout_kernels(c->msg_kind) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->ws, 0, p.total, c->cap) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->d_desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->cap) == cudaSuccess;
@@ -411,6 +422,9 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
         ((flags & BPS_FLAG_WARM_START) && !init))
         return BPS_ERR_ARG;
     if (c->msg_type == BPS_MSG_U8 && (int64_t)lambda * trunc > 255) return BPS_ERR_UNSUPPORTED;
+    // sparse candidates: chained launches only; a warm start needs a dense coarser scale
+    if (c->sv.K > 0 && ((flags & BPS_FLAG_PERSISTENT) || ((flags & BPS_FLAG_WARM_START) && levels == 1)))
+        return BPS_ERR_UNSUPPORTED;
     return BPS_OK;
 }
 
@@ -454,11 +468,15 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
                       cudaStream_t st, int32_t *disp = nullptr) {
     if (!(flags & BPS_FLAG_PERSISTENT)) {
         const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st);
-        if (rc == BPS_OK && disp) CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+        if (rc == BPS_OK && disp) {
+            if (c->last_sparse_k) CK(launch_sparse_wta(c->lv[0], c->sv, disp, st));
+            else CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+        }
         return rc;
     }
     const int top = levels - 1;
     const int ntrace = levels * iters * 2;
+    c->last_sparse_k = 0;
     if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
     const int rc = enqueue_start(c, top, flags, init, st);
     if (rc != BPS_OK) return rc;
@@ -520,8 +538,27 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     // predecessor built (entry count list_counts[t - 1]).  Small scales are latency-bound and
     // keep the dense launch, whose clean warps exit after one flag load.
     int t = 0;
+    c->last_sparse_k = c->sv.K;
     for (int l = top; l >= 0; --l) {
         const LevelView &v = c->lv[l];
+        if (l == 0 && c->sv.K > 0) {
+            // the finest scale over sparse candidates: selection, start from the parent's messages
+            // at each candidate's label, then the half-sweeps
+            CK(launch_sparse_candidates(v, c->sv, c->D, c->Dp, c->Gp, st));
+            CK(launch_sparse_start(v, top > 0 ? &c->lv[1] : nullptr, c->sv, c->Dp, st));
+            for (int it = 0; it < iters; ++it)
+                for (int colour = 0; colour < 2; ++colour, ++t) {
+                    if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
+                    CK(launch_sparse_sweep(v, c->sv, colour, lambda, trunc, skip ? 1 : 0, c->trace + t, st));
+                    if (prof) {
+                        CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
+                        c->prof_span[c->prof_all] = 1;
+                        ++c->prof_all;
+                        ++c->prof_launches;
+                    }
+                }
+            continue;
+        }
         // only the even pixels' start messages are ever read: the first half-sweep overwrites every
         // existing incoming slot of the odd pixels (unless there is no sweep at all)
         // the odd pixels' start messages are read only without sweeps, or under the freeze rule
@@ -581,7 +618,8 @@ extern "C" int bps_bp_solve(bps_ctx *c, int levels, int iters, int lambda, int t
 extern "C" int bps_wta_disparity(bps_ctx *c, int32_t *disp, void *stream) {
     if (!c || !disp) return BPS_ERR_ARG;
     if (!c->has_cost) return BPS_ERR_STATE;
-    CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, (cudaStream_t)stream));
+    if (c->last_sparse_k) CK(launch_sparse_wta(c->lv[0], c->sv, disp, (cudaStream_t)stream));
+    else CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, (cudaStream_t)stream));
     return BPS_OK;
 }
 
@@ -731,6 +769,7 @@ extern "C" int bps_get_trace(bps_ctx *c, int64_t *h_counts, int cap) {
 
 extern "C" int bps_export_messages(bps_ctx *c, int level, void *d_out, void *stream) {
     if (!c || !d_out || level < 0 || level >= c->levels) return BPS_ERR_ARG;
+    if (level == 0 && c->last_sparse_k) return BPS_ERR_STATE;  // the finest scale holds sparse messages
     CK(launch_export_msgs(c->msg_kind, c->lv[level], c->D, c->Dp, d_out, (cudaStream_t)stream));
     return BPS_OK;
 }
@@ -972,7 +1011,8 @@ static int batch_prepare(bps_batch *b, const uint8_t *const *d_lefts, const uint
         if (!d_disps[i]) return BPS_ERR_ARG;
         const bool had = c->has_cost;
         c->has_cost = true;
-        rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
+        rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PERSISTENT),
+                           nullptr);
         if (rc != BPS_OK) {
             c->has_cost = had;
             return rc;
@@ -1120,9 +1160,32 @@ extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     return BPS_OK;
 }
 
+extern "C" int bps_set_candidates(bps_ctx *c, int K) {
+    if (!c || K < 0 || K > BPS_MAX_CANDIDATES || K > c->D) return BPS_ERR_ARG;
+    if (K > 0 && (c->msg_kind != MSG_U8 || c->lv[0].eps || c->lv[0].freeze)) return BPS_ERR_UNSUPPORTED;
+    int Kp = 1;
+    while (Kp < K) Kp *= 2;
+    c->sv.K = K;
+    c->sv.Kp = K ? Kp : 0;
+    ++c->config_version;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BPS_OK;
+}
+
+extern "C" int bps_export_sparse(bps_ctx *c, int32_t *d_cand, int32_t *d_msgs, void *stream) {
+    if (!c || !d_cand || !d_msgs) return BPS_ERR_ARG;
+    if (!c->last_sparse_k || c->last_sparse_k != c->sv.K) return BPS_ERR_STATE;
+    CK(launch_sparse_export(c->lv[0], c->sv, d_cand, d_msgs, (cudaStream_t)stream));
+    return BPS_OK;
+}
+
 extern "C" int bps_set_skip_rule(bps_ctx *c, int eps, int freeze) {
     if (!c || eps < 0 || eps > 255 || (freeze != 0 && freeze != 1)) return BPS_ERR_ARG;
     if ((eps || freeze) && c->msg_kind != MSG_U8) return BPS_ERR_UNSUPPORTED;
+    if ((eps || freeze) && c->sv.K) return BPS_ERR_UNSUPPORTED;  // the sparse solve keeps the exact rule
     for (int l = 0; l < c->levels; ++l) {
         c->lv[l].eps = eps;
         c->lv[l].freeze = freeze;

@@ -119,6 +119,22 @@ cudaError_t preload_readout_kernels(int msg_kind);
 
 // Winner-take-all disparity at the finest scale.
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);
+
+// Sparse candidates of the finest scale (sparse.cu): per colour, Kp uint16 labels a slot, then
+// Kp int16 costs a slot (K candidates, Kp = K rounded up to a power of two).
+struct SparseView {
+    uint16_t *cand[2];
+    int K, Kp;
+};
+cudaError_t launch_sparse_candidates(const LevelView &lv, const SparseView &sv, int D, int Dp, int Gp, cudaStream_t st);
+cudaError_t launch_sparse_start(const LevelView &fine, const LevelView *coarse, const SparseView &sv, int Dp,
+                                cudaStream_t st);
+cudaError_t launch_sparse_sweep(const LevelView &lv, const SparseView &sv, int colour, int lambda, int trunc, int skip,
+                                unsigned long long *trace, cudaStream_t st);
+cudaError_t launch_sparse_wta(const LevelView &lv, const SparseView &sv, int32_t *disp, cudaStream_t st);
+cudaError_t launch_sparse_export(const LevelView &lv, const SparseView &sv, int32_t *cand, int32_t *msg,
+                                 cudaStream_t st);
+cudaError_t preload_sparse_kernels();
 // Energy: per-block partial sums into `partials` (nblocks entries of 8 bytes), then one
 // block sums them in a fixed order.
 int energy_blocks(int W, int H);

@@ -603,3 +603,89 @@ def test_approximate_skip_energy_gap_on_a_full_size_pair():
             e = int(st.energy(st.wta_disparity(), 10, 2)[0].item())
             assert abs(e - e0) <= (0.02 if freeze else 0.005) * e0, (eps, freeze, e, e0)
             assert int(st.get_trace().sum()) < w0
+
+
+# ------------------------------------------------------------------ sparse candidates
+
+@pytest.mark.parametrize("skip", [True, False])
+@pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2, 4), (96, 72, 16, 5, 3, 5, 10, 2, 16),
+                                  (45, 19, 33, 7, 3, 4, 7, 3, 6), (60, 44, 64, 5, 2, 5, 8, 2, 8),
+                                  (40, 30, 64, 5, 1, 6, 10, 2, 32), (37, 21, 20, 5, 3, 4, 10, 2, 1)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_sparse_candidates_match_the_oracle(case, skip):
+    W, H, D, window, levels, iters, lam, trunc, K = case
+    pair = synth.make_pair(400 + W + D + K, W, H, D, 4, 2.0)
+    with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
+        st.set_candidates(K)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        st.bp_solve(iters, lam, trunc, skip=skip)
+        cand, msg = (t.cpu().numpy() for t in st.export_sparse())
+        trace = st.get_trace()
+        disp = st.wta_disparity().cpu().numpy()
+        with pytest.raises(bps.BPSError) as e:
+            st.export_messages(0)  # the finest scale holds sparse messages
+        assert e.value.status == bps.BPS_ERR_STATE
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+    rc, rm, rt = oracle.bp_sparse(c0, levels, iters, lam, trunc, K, skip=skip)
+    assert np.array_equal(cand, rc)
+    assert np.array_equal(msg, rm) and np.array_equal(trace, rt)
+    assert np.array_equal(disp, oracle.wta_sparse(c0, rc, rm))
+
+
+def test_sparse_in_a_graph_and_a_batch_and_back_to_dense():
+    shapes = [(70, 40, 16, 5, 6), (45, 33, 64, 7, 12)]
+    pairs = [synth.make_pair(130 + k, W, H, D, 3, 2.0) for k, (W, H, D, _, _) in enumerate(shapes)]
+    windows = [s[3] for s in shapes]
+    sts = [bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) for W, H, D, _, _ in shapes]
+    try:
+        for st, (_, _, _, _, K) in zip(sts, shapes):
+            st.set_candidates(K)
+        refs = []
+        for p, w, (_, _, D, _, K) in zip(pairs, windows, shapes):
+            c0 = oracle.quantise(oracle.ncc(p.left, p.right, D, w), 20)
+            rc, rm, _ = oracle.bp_sparse(c0, 3, 5, 10, 2, K)
+            refs.append(oracle.wta_sparse(c0, rc, rm))
+        for rep in range(2):  # recorded, then replayed
+            for st, p, w, ref in zip(sts, pairs, windows, refs):
+                d = st.stereo(to_dev(p.left), to_dev(p.right), w, 20, 5, 10, 2, graph=True)
+                assert np.array_equal(d.cpu().numpy(), ref)
+        with bps.Batch(sts) as batch:
+            outs = batch.stereo([to_dev(p.left) for p in pairs], [to_dev(p.right) for p in pairs], windows, 20, 5,
+                                10, 2)
+            torch.cuda.synchronize()
+            for out, ref in zip(outs, refs):
+                assert np.array_equal(out.cpu().numpy(), ref)
+            with pytest.raises(bps.BPSError) as e:
+                batch.stereo([to_dev(p.left) for p in pairs], [to_dev(p.right) for p in pairs], windows, 20, 5,
+                             10, 2, persistent=True)
+            assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+        # back to the dense solve
+        st, p, w = sts[0], pairs[0], windows[0]
+        st.set_candidates(0)
+        d = st.stereo(to_dev(p.left), to_dev(p.right), w, 20, 5, 10, 2, graph=True)
+        ref = oracle.stereo_int(p.left, p.right, 16, w, 20, 3, 5, 10, 2)
+        assert np.array_equal(d.cpu().numpy(), ref["disp"])
+    finally:
+        for st in sts:
+            st.close()
+
+
+def test_sparse_arguments():
+    with bps.Stereo(16, 8, 8, 2, bps.BPS_MSG_INT32, device=DEV) as st:
+        with pytest.raises(bps.BPSError) as e:
+            st.set_candidates(4)
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+    with bps.Stereo(16, 8, 40, 2, bps.BPS_MSG_U8, device=DEV) as st:
+        for K in (-1, 33, 41):
+            with pytest.raises(bps.BPSError) as e:
+                st.set_candidates(K)
+            assert e.value.status == bps.BPS_ERR_ARG
+        st.set_skip_rule(1, False)
+        with pytest.raises(bps.BPSError) as e:
+            st.set_candidates(4)
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+        st.set_skip_rule(0, False)
+        st.set_candidates(4)
+        with pytest.raises(bps.BPSError) as e:
+            st.set_skip_rule(0, True)
+        assert e.value.status == bps.BPS_ERR_UNSUPPORTED
