@@ -58,6 +58,10 @@ def parse():
                     help="instead of the benchmark line: the approximate skip rules (eps threshold, permanent "
                          "freeze) on the benchmark pairs and the 960x540 D256 pair: time, work and energy gap "
                          "against the exact skip, one JSON line")
+    ap.add_argument("--sparse-report", action="store_true",
+                    help="instead of the benchmark line: the finest scale over K sparse candidates against the "
+                         "dense solve on the benchmark pairs and the 1920x1080 D256 pair: throughput, energy gap, "
+                         "bad pixels, one JSON line")
     ap.add_argument("--forms-report", action="store_true",
                     help="instead of the benchmark line: every message form (int32, u8, fp16) on the benchmark "
                          "pairs and the 1920x1080 D256 pair: throughput, energy, fp16 energy gap against the FP64 "
@@ -520,10 +524,63 @@ def forms_report(args):
     print(json.dumps(out))
 
 
+def sparse_report(args):
+    """The finest scale over K candidate labels per pixel (the abstract's sparse set of NCC matches)
+    against the exact dense solve: one graph per pair, L2 flushed between repetitions; the energy
+    gap is relative to the dense solve's energy on the same integer cost."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"metric": METRIC, "unit": UNIT, "report": "sparse candidates", "pairs": {}}
+    for name, ks in (("tsukuba_384x288_d16", (2, 4, 8)), ("teddy_450x375_d64", (4, 8, 16, 32)),
+                     ("hd_1920x1080_d256", (4, 8, 16, 32))):
+        pair, window = synth.workload_pair(name)
+        H, W = pair.left.shape
+        L = torch.from_numpy(pair.left).to(dev)
+        R = torch.from_numpy(pair.right).to(dev)
+        disp = torch.empty((H, W), dtype=torch.int32, device=dev)
+        rows = {}
+        with bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev) as st:
+            autotune.tune_ncc(st, L, R, window, TRUNC_DATA, reps=2)
+            autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+            steps = max(3, args.steps if not name.startswith("hd") else min(args.steps, 10))
+            for K in (0,) + ks:
+                st.set_candidates(K)
+                for _ in range(3):
+                    st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=disp)
+                torch.cuda.synchronize()
+                total = 0.0
+                for _ in range(steps):
+                    flush.fill_(9)
+                    e0.record()
+                    st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=disp)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    total += e0.elapsed_time(e1)
+                e = int(st.energy(disp, LAM, TRUNC)[0].item())
+                rows["dense" if K == 0 else f"K{K}"] = {
+                    "value": W * H * pair.D * steps / (total / 1e3) / 1e6, "ms": total / steps, "energy": e,
+                    "bad_pixel_rate": bad_pixel_rate(disp.cpu().numpy(), pair)}
+            st.set_candidates(0)
+        base = rows["dense"]
+        for r in rows.values():
+            r["speedup"] = r["value"] / base["value"]
+            r["energy_gap_rel"] = (r["energy"] - base["energy"]) / base["energy"]
+        out["pairs"][name] = rows
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sparse_report:
+        return sparse_report(args)
     if args.batch_report:
         return batch_report(args)
     if args.forms_report:
