@@ -12,12 +12,16 @@
 
 namespace bps {
 
+// Grid-stride over the pixel blocks: the grid is capped at the CTAs resident at once, so a
+// large scale does not pay for scheduling tens of thousands of CTAs that mostly find clean
+// pixels.
 template <typename CostT, typename MsgT>
 __global__ void __launch_bounds__(256)
 sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<MsgT>::type lam,
-             typename AccOf<MsgT>::type lamT, int skip, unsigned long long *trace) {
+             typename AccOf<MsgT>::type lamT, int skip, unsigned long long *trace, int nblocks) {
     pdl_enter();
-    sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
+        sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
 }
 
 // Grid-stride over the colour's pixel blocks: the grid is capped at what is resident at
@@ -289,12 +293,21 @@ template <typename CostT, typename MsgT>
 static cudaError_t sweep_t(const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc, int skip,
                            unsigned long long *trace, cudaStream_t st) {
     using Acc = typename AccOf<MsgT>::type;
+    static int resident = 0;  // CTAs of this kernel resident at once (looked up once per process)
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<CostT, MsgT>, 256, 0);
+        resident = std::max(1, sms * std::max(1, per_sm));
+    }
     const int groups = 256 / Gp;
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     const int64_t blocks = (nslot + groups - 1) / groups;
     if (blocks == 0) return cudaSuccess;
-    return launch_k(sweep_kernel<CostT, MsgT>, dim3((unsigned)blocks), dim3(256), 0, st, lv, colour, D, Dp, Gp,
-                    (Acc)lambda, (Acc)lambda * (Acc)trunc, skip, trace);
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident);
+    return launch_k(sweep_kernel<CostT, MsgT>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, (Acc)lambda,
+                    (Acc)lambda * (Acc)trunc, skip, trace, (int)blocks);
 }
 
 // CTAs of the u8 sweep that fit on the GPU at once (looked up once per process).
