@@ -703,14 +703,29 @@ def main():
     for _ in range(3):
         batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
     torch.cuda.synchronize()
+    # every call synchronous (the host waits for each step's results)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
+    e2e_sync_s = time.perf_counter() - t0
+    # queued: one call per step returns once its copies and work are on the stream (BPS_FLAG_ASYNC),
+    # the host synchronises once after the last step; each step still copies its images in and its
+    # disparities and energies out
+    for d in host_out:
+        d.fill_(-1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out, sync=False)
+    torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
+    for d, o in zip(host_out, outs):  # the host results are the device path's
+        if not torch.equal(d, o.cpu()):
+            raise RuntimeError("host-entry disparities differ from the device entry's")
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
+        t = torch.tensor([e2e_s, e2e_sync_s], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s, e2e_sync_s = (float(v) for v in t.tolist())
     h2d = sum(2 * p.left.size for p, _ in pairs)
     d2h = sum(4 * p.left.size + 8 for p, _ in pairs)
 
@@ -733,7 +748,10 @@ def main():
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_u8_kernel (all scales, both pairs)",
                          "peak_kind": peak_kind, "launches_timed": prof_launches},
             "e2e": {"value": units * args.steps / e2e_s / 1e6, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "mode": "bps_batch_stereo_host once per step from pinned host buffers, queued on one "
+                            "stream (BPS_FLAG_ASYNC), one synchronisation after the last step",
+                    "value_synchronous": units * args.steps / e2e_sync_s / 1e6},
             "gpu_launches": launches_per_pair * len(pairs) * args.steps,
             "clocks": clocks,
         }

@@ -68,6 +68,12 @@ typedef struct bps_ctx bps_ctx;
 #define BPS_FLAG_TEST_TIMEOUT 32 /* test hook (with BPS_FLAG_PERSISTENT): the grid barrier waits for one
                                     block more than it has, gives up after 2 ms and the solve
                                     reports BPS_ERR_TIMEOUT through bps_get_error */
+#define BPS_FLAG_ASYNC 64 /* bps_stereo_host / bps_batch_stereo_host: return once the work (copies
+                             included) is queued on the stream instead of waiting for it; the host
+                             outputs are valid, and the host inputs may be rewritten, only after
+                             the stream has been synchronised (calls on one stream run in order).
+                             With BPS_FLAG_PERSISTENT read the status with bps_get_error /
+                             bps_batch_get_error after that synchronisation. */
 
 /* Limits of this build. */
 #define BPS_MAX_LEVELS 8

@@ -39,6 +39,7 @@ BPS_FLAG_GRAPH = 4
 BPS_FLAG_PROFILE = 8
 BPS_FLAG_PERSISTENT = 16
 BPS_FLAG_TEST_TIMEOUT = 32
+BPS_FLAG_ASYNC = 64
 
 BPS_MAX_LEVELS = 8
 BPS_MAX_D = 512
@@ -559,8 +560,9 @@ class Batch:
         return bps_batch_get_error(self.handle)
 
     def stereo_host(self, h_lefts, h_rights, windows, trunc_data, iters, lam, trunc, skip=True, graph=True,
-                    persistent=False, h_disps=None, stream=None):
-        """Host tensors in; host disparities and int64 energies out (synchronous)."""
+                    persistent=False, h_disps=None, stream=None, sync=True):
+        """Host tensors in; host disparities and int64 energies out.  sync=False: return once the
+        work is queued (copies included); the outputs are valid after the stream is synchronised."""
         import torch
 
         # page-locked buffers kept across calls: the call replays as one recorded graph while
@@ -572,7 +574,9 @@ class Batch:
         h_disps = self._host_bufs[0] if own else h_disps
         energies = self._host_bufs[1]
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_GRAPH if graph else 0)
-        flags |= BPS_FLAG_PERSISTENT if persistent else 0
+        flags |= (BPS_FLAG_PERSISTENT if persistent else 0) | (0 if sync else BPS_FLAG_ASYNC)
         bps_batch_stereo_host(self.handle, h_lefts, h_rights, [t.stride(0) for t in h_lefts], windows, trunc_data,
                               iters, lam, trunc, flags, h_disps, energies, stream)
+        if not sync:
+            return h_disps, energies  # valid after the stream is synchronised
         return ([d.clone() for d in h_disps] if own else h_disps), energies.clone()

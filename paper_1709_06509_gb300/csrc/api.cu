@@ -718,10 +718,12 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
     if (!c || !hL || !hR || !h_disp || pitch < c->W) return BPS_ERR_ARG;
     int rc = check_cost_args(c, c->img[0], c->img[1], c->W, window, trunc_data);
     if (rc != BPS_OK) return rc;
-    if (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT)) return BPS_ERR_ARG;
+    if (flags & ~(BPS_FLAG_FAST_SKIP | BPS_FLAG_GRAPH | BPS_FLAG_PERSISTENT | BPS_FLAG_ASYNC)) return BPS_ERR_ARG;
+    const bool async = (flags & BPS_FLAG_ASYNC) != 0;
+    flags &= ~BPS_FLAG_ASYNC;
     const bool had_cost = c->has_cost;
     c->has_cost = true;  // the sequence builds the cost volume first
-    rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & BPS_FLAG_FAST_SKIP, nullptr);
+    rc = check_bp_args(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PERSISTENT), nullptr);
     if (rc != BPS_OK) {
         c->has_cost = had_cost;
         return rc;
@@ -745,6 +747,7 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
                                  h_e_f64, st);
     }
     if (rc != BPS_OK) return rc;
+    if (async) return BPS_OK;
     CK(cudaStreamSynchronize(st));
     // only the persistent kernel's barrier can time out
     return (flags & BPS_FLAG_PERSISTENT) ? bps_get_error(c) : BPS_OK;
@@ -1091,6 +1094,8 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
                                      int trunc, int flags, int32_t *const *h_disps, int64_t *h_energies,
                                      void *stream) {
     if (!b || !h_lefts || !h_rights || !pitches || !windows || !h_disps) return BPS_ERR_ARG;
+    const bool async = (flags & BPS_FLAG_ASYNC) != 0;
+    flags &= ~BPS_FLAG_ASYNC;
     const int n = (int)b->ctxs.size();
     std::vector<const uint8_t *> L(n), R(n);
     std::vector<int> pitch(n);
@@ -1141,6 +1146,7 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
         for (int i = 0; i < n && rc == BPS_OK; ++i) rc = enqueue_pair_output(b->ctxs[i], &io, i, lambda, trunc, st);
     }
     if (rc != BPS_OK) return rc;
+    if (async) return BPS_OK;
     CK(cudaStreamSynchronize(st));
     return (flags & BPS_FLAG_PERSISTENT) ? bps_batch_get_error(b) : BPS_OK;
 }

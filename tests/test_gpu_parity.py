@@ -242,6 +242,29 @@ def test_batch_host_entry_graph_reads_current_buffers():
             st.close()
 
 
+def test_queued_host_calls_give_the_same_results():
+    # BPS_FLAG_ASYNC: calls return once queued; after one synchronisation the host outputs of the
+    # last call are those of a synchronous call
+    shapes = [(70, 40, 16, 5), (45, 33, 64, 7)]
+    pairs = [synth.make_pair(150 + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+    windows = [w for *_, w in shapes]
+    sts = [bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) for W, H, D, _ in shapes]
+    try:
+        with bps.Batch(sts) as batch:
+            hl = [torch.from_numpy(p.left).pin_memory() for p in pairs]
+            hr = [torch.from_numpy(p.right).pin_memory() for p in pairs]
+            hd = [torch.full((p.left.shape[0], p.left.shape[1]), -1, dtype=torch.int32).pin_memory() for p in pairs]
+            for _ in range(3):
+                _, he = batch.stereo_host(hl, hr, windows, 20, 5, 10, 2, h_disps=hd, sync=False)
+            torch.cuda.current_stream().synchronize()
+            for d, e, p, w in zip(hd, he.tolist(), pairs, windows):
+                ref = oracle.stereo_int(p.left, p.right, p.D, w, 20, 3, 5, 10, 2)
+                assert np.array_equal(d.numpy(), ref["disp"]) and e == ref["energy"]
+    finally:
+        for st in sts:
+            st.close()
+
+
 def test_contexts_of_different_shapes_coexist():
     # kernel attributes are process-wide: creating a second context must not break the first
     pairs = [synth.make_pair(40 + k, W, H, D, 3, 2.0) for k, (W, H, D) in enumerate([(80, 40, 16), (60, 30, 64)])]
