@@ -274,6 +274,18 @@ __device__ __forceinline__ void u8_message(const uint32_t (&h)[8], int lam, int 
     }
 }
 
+// Stores under a predicate, without a branch around them.
+__device__ __forceinline__ void st_v4_if(uint4 *p, const uint4 &v, bool pred) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t@p st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((unsigned)pred)
+                 : "memory");
+}
+__device__ __forceinline__ void st_u32_if(unsigned *p, unsigned v, bool pred) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.u32 [%0], %1;\n\t}" ::"l"(p), "r"(v),
+                 "r"((unsigned)pred)
+                 : "memory");
+}
+
 // Active lists (fast-converging skip).  After the first two half-sweeps of a scale, a
 // half-sweep processes only the pixels listed for it, packed densely: a sender that flips a
 // neighbour's skip flag from 0 to 1 appends the neighbour to the other colour's list (one
@@ -407,6 +419,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     // so a recomputed pixel waits for one round trip to memory, not two
     uint4 *dst[4];
     uint4 old[4];
+    unsigned qsv[4];  // the neighbours' slots (0 where there is none)
     auto load_cost = [&]() {
         if (lane_data) {
             const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
@@ -428,6 +441,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t qs = (send && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+            qsv[q] = (unsigned)qs;
             dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
             old[q] = (skip && send && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
         }
@@ -447,6 +461,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             in[q] = stage[(2 + q) * T + t];
             old[q] = stage[(6 + q) * T + t];
             const int64_t qs = (valid && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+            qsv[q] = (unsigned)qs;
             dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
         }
         flag_staged = stage[10 * T + t].x;
@@ -497,29 +512,33 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         const uint4 out = pack_msg(m);
 
         const bool send = active && has[q];
+        const bool mine = send && lane_data;
         if (skip) {
-            bool diff = false, big = false;
-            if (send && lane_data) {
-                diff = (old[q].x != out.x) | (old[q].y != out.y) | (old[q].z != out.z) | (old[q].w != out.w);
-                big = (__vcmpgtu4(__vabsdiffu4(old[q].x, out.x), EPS4) | __vcmpgtu4(__vabsdiffu4(old[q].y, out.y), EPS4) |
-                       __vcmpgtu4(__vabsdiffu4(old[q].z, out.z), EPS4) | __vcmpgtu4(__vabsdiffu4(old[q].w, out.w), EPS4)) != 0u;
-            }
+            const bool diff =
+                mine && ((old[q].x ^ out.x) | (old[q].y ^ out.y) | (old[q].z ^ out.z) | (old[q].w ^ out.w)) != 0u;
+            bool big = false;
+            if (lv.eps)  // uniform: the exact rule (eps = 0) marks exactly the changed messages
+                big = mine && (__vcmpgtu4(__vabsdiffu4(old[q].x, out.x), EPS4) |
+                               __vcmpgtu4(__vabsdiffu4(old[q].y, out.y), EPS4) |
+                               __vcmpgtu4(__vabsdiffu4(old[q].z, out.z), EPS4) |
+                               __vcmpgtu4(__vabsdiffu4(old[q].w, out.w), EPS4)) != 0u;
             const unsigned dm = __ballot_sync(FULL, diff);
-            const unsigned bm = __ballot_sync(FULL, big);
+            const unsigned bm = lv.eps ? __ballot_sync(FULL, big) : dm;
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             const bool significant = ((bm >> gshift) & group_bits(Gp)) != 0u;  // = changed when eps = 0
-            if (send && changed && lane_data) *dst[q] = out;
-            if (send && significant) {
-                marked = true;
-                if (g == 0) {
-                    const unsigned qs = (unsigned)slot_of(nbx[q], nby[q], lv.Wh);
-                    if constexpr (APPEND) mark[q] = qs + 1u;
-                    else if (lv.freeze) atomicOr(dirty_out + qs, 1u);  // keeps the frozen bit
-                    else dirty_out[qs] = 1u;
-                }
+            st_v4_if(dst[q], out, mine && changed);
+            const bool mk = send && significant;
+            marked = marked || mk;
+            const bool lead = mk && g == 0;  // one mark per pixel group
+            if constexpr (APPEND) {
+                mark[q] = lead ? qsv[q] + 1u : 0u;
+            } else if (lv.freeze) {
+                if (lead) atomicOr(dirty_out + qsv[q], 1u);  // keeps the frozen bit
+            } else {
+                st_u32_if(dirty_out + qsv[q], 1u, lead);
             }
-        } else if (send && lane_data) {
-            *dst[q] = out;
+        } else {
+            st_v4_if(dst[q], out, mine);
         }
     }
     if constexpr (APPEND) {
@@ -595,6 +614,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     uint4 in[4];
     uint4 *dst;
     uint4 old;
+    unsigned qs_o = 0u;  // the receiver's slot
     auto load_cost = [&]() {
         if (lane_data) {
             const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
@@ -613,6 +633,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
             in[q] = (lane_data && has[q]) ? __ldg(reinterpret_cast<const uint4 *>(mp + q * Dp))
                                           : make_uint4(0u, 0u, 0u, 0u);
         const int64_t qs = (send && has_o) ? slot_of(nbx, nby, lv.Wh) : 0;
+        qs_o = (unsigned)qs;
         dst = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + (qo ^ 1)) * Dp + dbase);
         old = (skip && send && has_o && lane_data) ? *dst : make_uint4(0u, 0u, 0u, 0u);
     };
@@ -657,30 +678,31 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     const bool send = active && has_o;
     unsigned mark = 0u;  // slot + 1 of the neighbour to mark dirty (APPEND)
     bool marked = false;  // this group marked its receiver (skip rule freeze)
+    const bool mine = send && lane_data;
     if (skip) {
-        bool diff = false, big = false;
-        if (send && lane_data) {
+        const bool diff = mine && ((old.x ^ out.x) | (old.y ^ out.y) | (old.z ^ out.z) | (old.w ^ out.w)) != 0u;
+        bool big = false;
+        if (lv.eps) {
             const uint32_t EPS4 = (uint32_t)lv.eps * 0x01010101u;
-            diff = (old.x != out.x) | (old.y != out.y) | (old.z != out.z) | (old.w != out.w);
-            big = (__vcmpgtu4(__vabsdiffu4(old.x, out.x), EPS4) | __vcmpgtu4(__vabsdiffu4(old.y, out.y), EPS4) |
-                   __vcmpgtu4(__vabsdiffu4(old.z, out.z), EPS4) | __vcmpgtu4(__vabsdiffu4(old.w, out.w), EPS4)) != 0u;
+            big = mine && (__vcmpgtu4(__vabsdiffu4(old.x, out.x), EPS4) | __vcmpgtu4(__vabsdiffu4(old.y, out.y), EPS4) |
+                           __vcmpgtu4(__vabsdiffu4(old.z, out.z), EPS4) | __vcmpgtu4(__vabsdiffu4(old.w, out.w), EPS4)) != 0u;
         }
         const unsigned dm = __ballot_sync(FULL, diff);
-        const unsigned bm = __ballot_sync(FULL, big);
+        const unsigned bm = lv.eps ? __ballot_sync(FULL, big) : dm;
         const bool changed = ((dm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
         const bool significant = ((bm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
-        if (send && changed && lane_data) *dst = out;
-        if (send && significant) {
-            marked = true;
-            if (g == 0) {
-                const unsigned qs = (unsigned)slot_of(nbx, nby, lv.Wh);
-                if constexpr (APPEND) mark = qs + 1u;
-                else if (lv.freeze) atomicOr(dirty_out + qs, 1u);  // keeps the frozen bit
-                else dirty_out[qs] = 1u;
-            }
+        st_v4_if(dst, out, mine && changed);
+        marked = send && significant;
+        const bool lead = marked && g == 0;
+        if constexpr (APPEND) {
+            mark = lead ? qs_o + 1u : 0u;
+        } else if (lv.freeze) {
+            if (lead) atomicOr(dirty_out + qs_o, 1u);  // keeps the frozen bit
+        } else {
+            st_u32_if(dirty_out + qs_o, 1u, lead);
         }
-    } else if (send && lane_data) {
-        *dst = out;
+    } else {
+        st_v4_if(dst, out, mine);
     }
     if constexpr (APPEND) {
         const bool app = mark != 0u && atomicOr(dirty_out + (mark - 1u), 1u) == 0u;
