@@ -298,6 +298,9 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.Wh = p.Whs[l];
         v.eps = 0;  // the exact skip rule
         v.freeze = 0;
+        v.start = 0;
+        v.pWh = 0;
+        v.pmsg[0] = v.pmsg[1] = nullptr;
         for (int k = 0; k < 2; ++k) {
             v.cost[k] = c->ws + p.cost[l][k];
             v.msg[k] = c->ws + p.msg[l][k];
@@ -562,10 +565,23 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         // only the even pixels' start messages are ever read: the first half-sweep overwrites every
         // existing incoming slot of the odd pixels (unless there is no sweep at all)
         // the odd pixels' start messages are read only without sweeps, or under the freeze rule
-        // (its first half-sweep compares the even pixels' new messages with them)
-        if (l < top)
+        // (its first half-sweep compares the even pixels' new messages with them).
+        // u8 form: the first iteration reads the parent's records itself and recomputes every
+        // pixel (the skip flags need no setting), so no copy is launched, except under the freeze
+        // rule or for a one-launch (cluster) scale
+        const bool fused_start = l < top && iters > 0 && c->msg_kind == MSG_U8 && !v.freeze &&
+                                 !(c->variant[l] & VARIANT_CLUSTER);
+        if (l < top && !fused_start)
             CK(launch_upsample(c->msg_kind, c->lv[l + 1], v, (iters == 0 || v.freeze) ? 1 : 0, c->Dp, skip ? 1 : 0,
                                st));
+        LevelView first = v, second = v;  // the views of the scale's first two half-sweeps
+        if (fused_start) {
+            first.start = 1;
+            first.pWh = c->lv[l + 1].Wh;
+            first.pmsg[0] = c->lv[l + 1].msg[0];
+            first.pmsg[1] = c->lv[l + 1].msg[1];
+            second.start = 2;
+        }
         if (iters > 0 && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_CLUSTER)) {
             if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
             CK(launch_sweep_level_cluster(v, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, iters,
@@ -593,7 +609,8 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
                     sl.in = c->lists[colour];
                     sl.n_in = c->list_counts + t - 1;
                 }
-                CK(launch_sweep(c->msg_kind, v, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st, sl,
+                const LevelView &vv = it > 0 ? v : (colour == 0 ? first : second);
+                CK(launch_sweep(c->msg_kind, vv, colour, c->D, c->Dp, c->Gp, lambda, trunc, skip, c->trace + t, st, sl,
                                 c->variant[l]));
                 if (prof) {
                     CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));

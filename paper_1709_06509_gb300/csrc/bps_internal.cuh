@@ -33,6 +33,13 @@ struct LevelView {
     unsigned *dirty[2];  // 32-bit words so a sender can flip them atomically: bit 0 dirty, bit 1 frozen
     int eps;             // skip rule: a receiver is marked when its message moves by more than eps
     int freeze;          // skip rule: a recomputed pixel that marked no receiver is frozen
+    // A scale's first iteration without a separate coarse-to-fine copy (u8 sweeps): start = 1, the
+    // first half-sweep reads each even pixel's start messages straight from its parent's record
+    // (pmsg, pWh: the parent scale's message arrays and slots per row) and recomputes every
+    // pixel; start = 2, the second half-sweep recomputes every pixel.  0 otherwise.
+    int start;
+    int pWh;
+    const void *pmsg[2];
 };
 
 // Programmatic dependent launch: every kernel of the stereo chain is launched so that it may

@@ -352,6 +352,11 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
     cp_async16(stage + 0 * T + t, cp, lane_data);
     cp_async16(stage + 1 * T + t, cp + (lane_data ? 1 : 0), lane_data);
     const uint8_t *mp = msg_in + (lane_data ? sc * 4 * Dp + dbase : 0);
+    if (lv.start == 1) {  // a scale's first half-sweep: the parent's record holds the start messages
+        const int px = x >> 1, py = y >> 1;
+        mp = reinterpret_cast<const uint8_t *>(colour_of(px, py) ? lv.pmsg[1] : lv.pmsg[0]) +
+             (lane_data ? slot_of(px, py, lv.pWh) * 4 * Dp + dbase : 0);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const bool hq = lane_data && has[q];
@@ -434,6 +439,11 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     // `send`: whether this lane's pixel sends (the active pixels; all valid ones when eager)
     auto load_messages = [&](bool send) {
         const uint8_t *mp = msg_in + sc * 4 * Dp + dbase;
+        if (lv.start == 1) {  // a scale's first half-sweep: the parent's record holds the start messages
+            const int px = x >> 1, py = y >> 1;
+            mp = reinterpret_cast<const uint8_t *>(colour_of(px, py) ? lv.pmsg[1] : lv.pmsg[0]) +
+                 slot_of(px, py, lv.pWh) * 4 * Dp + dbase;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             in[q] = (lane_data && has[q]) ? load_u4<RW>(reinterpret_cast<const uint4 *>(mp + q * Dp))
@@ -472,7 +482,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     }
     // dirty and not frozen (flags are 0 / 1 under the exact skip rule)
     const bool active =
-        valid && (LISTED || !skip || (EAGER == 3 ? flag_staged : dirty_in[s]) == 1u);
+        valid && (LISTED || !skip || lv.start != 0 || (EAGER == 3 ? flag_staged : dirty_in[s]) == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -489,6 +499,14 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         unpack_msg(in[q], t);
 #pragma unroll
         for (int j = 0; j < 8; ++j) b[j] += t[j];
+    }
+    if (lv.start == 1) {
+        // the start messages read from the parent become this pixel's records: the second
+        // half-sweep's change test compares the new messages with them
+        uint4 *own = reinterpret_cast<uint4 *>(const_cast<uint8_t *>(msg_in) + sc * 4 * Dp + dbase);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st_v4_if(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(own) + q * Dp), in[q],
+                                             active && lane_data && has[q]);
     }
     if constexpr (PADDED) {
 #pragma unroll
@@ -628,6 +646,11 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     };
     auto load_messages = [&](bool send) {
         const uint8_t *mp = msg_in + sc * 4 * Dp + dbase;
+        if (lv.start == 1) {  // a scale's first half-sweep: the parent's record holds the start messages
+            const int px = x >> 1, py = y >> 1;
+            mp = reinterpret_cast<const uint8_t *>(colour_of(px, py) ? lv.pmsg[1] : lv.pmsg[0]) +
+                 slot_of(px, py, lv.pWh) * 4 * Dp + dbase;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             in[q] = (lane_data && has[q]) ? __ldg(reinterpret_cast<const uint4 *>(mp + q * Dp))
@@ -642,7 +665,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         if constexpr (EAGER == 2) pdl_enter();
         load_messages(valid);
     }
-    const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
+    const bool active = valid && (LISTED || !skip || lv.start != 0 || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -668,6 +691,9 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         }
     }
     const uint4 in_o = qo == 0 ? in[0] : (qo == 1 ? in[1] : (qo == 2 ? in[2] : in[3]));
+    if (lv.start == 1)  // the start message read from the parent becomes this pixel's record
+        st_v4_if(reinterpret_cast<uint4 *>(const_cast<uint8_t *>(msg_in) + sc * 4 * Dp + qo * Dp + dbase), in_o,
+                 active && lane_data && has_o);
     uint32_t t[8], h[8], m[8];
     unpack_msg(in_o, t);
 #pragma unroll
