@@ -731,7 +731,16 @@ def main():
 
     # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the solve-start
     # kernel, one upsample kernel per scale below the coarsest, 2 * ITERS sweeps per scale, WTA
-    launches_per_pair = 1 + max(0, LEVELS - 2) + 1 + (LEVELS - 1) + LEVELS * ITERS * 2 + 1
+    # (the pyramid kernel forms two scales a launch; a scale's first half-sweep starts from its
+    # parent's messages itself, except for a one-launch cluster scale, which keeps the copy kernel)
+    def pair_launches(st):
+        vs = st.variants()
+        cluster_scales = [lvl for lvl in range(LEVELS) if vs[lvl] & bps.BPS_VARIANT_CLUSTER]
+        sweeps = sum(1 if lvl in cluster_scales else 2 * ITERS for lvl in range(LEVELS))
+        copies = sum(1 for lvl in cluster_scales if lvl < LEVELS - 1)
+        return 1 + (max(0, LEVELS - 2) + 1) // 2 + 1 + copies + sweeps + 1
+
+    launches_per_step = sum(pair_launches(st) for st, _ in ctxs)
     large = large_roofline(dev, flush) if rank == 0 and not args.no_large else None
     if rank == 0:
         line = {
@@ -752,7 +761,7 @@ def main():
                     "mode": "bps_batch_stereo_host once per step from pinned host buffers, queued on one "
                             "stream (BPS_FLAG_ASYNC), one synchronisation after the last step",
                     "value_synchronous": units * args.steps / e2e_sync_s / 1e6},
-            "gpu_launches": launches_per_pair * len(pairs) * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
         if large:

@@ -402,7 +402,11 @@ static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitc
         CK(launch_ncc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0.Wh, v0.cost[0],
                       v0.cost[1], ncc_out, st));
     }
-    for (int l = first_pyramid; l < c->levels; ++l) CK(launch_pyramid(c->cost_kind, c->lv[l - 1], c->lv[l], c->Dp, st));
+    // two scales a launch, then a last single one
+    int l = first_pyramid;
+    for (; l + 1 < c->levels; l += 2)
+        CK(launch_pyramid2(c->cost_kind, c->lv[l - 1], c->lv[l], c->lv[l + 1], c->Dp, st));
+    if (l < c->levels) CK(launch_pyramid(c->cost_kind, c->lv[l - 1], c->lv[l], c->Dp, st));
     return BPS_OK;
 }
 

@@ -38,6 +38,9 @@ cudaError_t ncc_prepare(int cost_kind, int D, int max_window);
 cudaError_t launch_ncc(int cost_kind, const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int D, int Dp,
                        int window, int T, int Wh, void *c0, void *c1, float *ncc_out, cudaStream_t st);
 cudaError_t launch_pyramid(int cost_kind, const LevelView &fine, const LevelView &coarse, int Dp, cudaStream_t st);
+// Scales l and l+1 from scale l-1 in one launch.
+cudaError_t launch_pyramid2(int cost_kind, const LevelView &fine, const LevelView &mid, const LevelView &coarse, int Dp,
+                            cudaStream_t st);
 
 // Row-streaming NCC for windows up to NCC_ROWS_MAX_WINDOW; with l1 != NULL (integer forms)
 // it also writes scale 1 of the pyramid.

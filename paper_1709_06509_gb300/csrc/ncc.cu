@@ -649,12 +649,65 @@ __global__ void pyramid_kernel(LevelView fine, LevelView coarse, int Dp) {
     }
 }
 
+// Two scales in one launch: a thread per (pixel of scale l+1, label) forms its four children
+// at scale l from their 2x2 blocks at scale l-1, writes them, and writes their sum.  Every
+// pixel of scale l has its parent at scale l+1 (ceil halving), so each is written once.
+template <typename CostT>
+__global__ void pyramid2_kernel(LevelView fine, LevelView mid, LevelView coarse, int Dp) {
+    pdl_enter();
+    using Acc = typename std::conditional<CostOut<CostT>::is_float, float, int>::type;
+    const int64_t n = (int64_t)coarse.H * coarse.W * Dp;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(k % Dp);
+        const int64_t p = k / Dp;
+        const int X = (int)(p % coarse.W), Y = (int)(p / coarse.W);
+        Acc S = Acc(0);
+        for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa) {
+                const int mx = 2 * X + aa, my = 2 * Y + bb;
+                if (mx >= mid.W || my >= mid.H) continue;
+                Acc s = Acc(0);
+                for (int b = 0; b < 2; ++b)
+                    for (int a = 0; a < 2; ++a) {
+                        const int fx = 2 * mx + a, fy = 2 * my + b;
+                        if (fx < fine.W && fy < fine.H) {
+                            const CostT *src = (const CostT *)fine.cost[(a + b) & 1];
+                            s += (Acc)src[((int64_t)fy * fine.Wh + mx) * Dp + d];
+                        }
+                    }
+                ((CostT *)mid.cost[colour_of(mx, my)])[slot_of(mx, my, mid.Wh) * Dp + d] = (CostT)s;
+                S += s;
+            }
+        ((CostT *)coarse.cost[colour_of(X, Y)])[slot_of(X, Y, coarse.Wh) * Dp + d] = (CostT)S;
+    }
+}
+
 cudaError_t preload_cost_kernels(int cost_kind) {
     cudaFuncAttributes a;
     switch (cost_kind) {
-    case COST_I32: return cudaFuncGetAttributes(&a, pyramid_kernel<int32_t>);
-    case COST_I16: return cudaFuncGetAttributes(&a, pyramid_kernel<int16_t>);
-    default: return cudaFuncGetAttributes(&a, pyramid_kernel<float>);
+    case COST_I32:
+        return cudaFuncGetAttributes(&a, pyramid_kernel<int32_t>) == cudaSuccess
+                   ? cudaFuncGetAttributes(&a, pyramid2_kernel<int32_t>)
+                   : cudaErrorUnknown;
+    case COST_I16:
+        return cudaFuncGetAttributes(&a, pyramid_kernel<int16_t>) == cudaSuccess
+                   ? cudaFuncGetAttributes(&a, pyramid2_kernel<int16_t>)
+                   : cudaErrorUnknown;
+    default:
+        return cudaFuncGetAttributes(&a, pyramid_kernel<float>) == cudaSuccess
+                   ? cudaFuncGetAttributes(&a, pyramid2_kernel<float>)
+                   : cudaErrorUnknown;
+    }
+}
+
+cudaError_t launch_pyramid2(int cost_kind, const LevelView &fine, const LevelView &mid, const LevelView &coarse, int Dp,
+                            cudaStream_t st) {
+    const int64_t n = (int64_t)coarse.H * coarse.W * Dp;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    switch (cost_kind) {
+    case COST_I32: return launch_k(pyramid2_kernel<int32_t>, dim3(blocks), dim3(256), 0, st, fine, mid, coarse, Dp);
+    case COST_I16: return launch_k(pyramid2_kernel<int16_t>, dim3(blocks), dim3(256), 0, st, fine, mid, coarse, Dp);
+    default: return launch_k(pyramid2_kernel<float>, dim3(blocks), dim3(256), 0, st, fine, mid, coarse, Dp);
     }
 }
 
