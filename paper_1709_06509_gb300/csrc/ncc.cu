@@ -190,7 +190,7 @@ static int smem_optin() {
 // multiplies for the correlation.  The 2x2 sum of the next scale is accumulated over row
 // pairs in registers and written directly (scale 1 of the pyramid).
 //
-// Quantiser: one fused multiply-add forms v = T (1 - ncc) + 1/2 in fp32 within (T + 1) 2^-21
+// Quantiser: one fused multiply-add forms v = T (1 - ncc) + 1/2 in fp32 within (T + 1) 2^-20
 // of its exact value (see quantise_fp32); the FP64 sequence decides only where v lies within
 // (T + 1) 2^-17 of an integer, after the row, for the few outputs that need it.
 constexpr int NR_TX = 16;
@@ -233,11 +233,12 @@ __device__ __forceinline__ void store_if(int32_t *p, int32_t v, bool pred) {
 // The fp32 quantiser step of one (pixel, label): the level c = min(floor(v), T) of
 // v = (T + 1/2) - (T ra) rb num, one fused multiply-add, and whether v lies within the margin
 // m = (T + 1) 2^-17 of an integer (then only the FP64 sequence may decide).  ra, rb are the
-// correctly rounded reciprocal square roots of the two variance terms (each within 1.5 2^-24
-// relative of the exact value, the conversion to fp32 included) and T ra is rounded once more,
-// so the product carries at most 6 2^-24 relative error and v at most (T + 1) 2^-21 absolute
-// error: outside the margin the fp32 and the exact decision agree.  v >= 1/2 - (T + 1) 2^-21
-// > 0, so the lower clamp at 0 is never needed.  A zero variance has a zero reciprocal
+// reciprocal square roots of the two variance terms (rsqrtf, at most 2 ulp = 4 2^-24 relative
+// error, plus half the conversion's 2^-24), T ra is rounded once more, the product once more
+// and the numerator's conversion once: at most 12 2^-24 relative error in the product, and with
+// the fused multiply-add's rounding v is within (T + 1) 14 2^-24 < (T + 1) 2^-20 of its exact
+// value: outside the margin (8 times wider) the fp32 and the exact decision agree.
+// v >= 1/2 - (T + 1) 2^-20 > 0, so the lower clamp at 0 is never needed.  A zero variance has a zero reciprocal
 // square root, so v = T + 1/2 and c = T, the value the definition gives for ncc = 0.
 __device__ __forceinline__ int quantise_fp32(float numf, float tra, float rb, float T_half, float half_m, int T,
                                              bool *near) {
@@ -370,7 +371,7 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 ss += colAA[i + k];
             }
             const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            const float ra = v ? __frsqrt_rn((float)v) : 0.f;
+            const float ra = v ? rsqrtf((float)v) : 0.f;
             PA[i] = make_int4(s, (int)v, __float_as_int(ra), __float_as_int(__fmul_rn((float)T, ra)));
         }
         for (int i = threadIdx.x; i < UW; i += blockDim.x) {
@@ -381,7 +382,7 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
                 ss += colBB[i + k];
             }
             const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            PB[i] = make_int4(s, (int)v, __float_as_int(v ? __frsqrt_rn((float)v) : 0.f), 0);
+            PB[i] = make_int4(s, (int)v, __float_as_int(v ? rsqrtf((float)v) : 0.f), 0);
         }
         __syncthreads();
         // phase 3: this thread's 16 outputs at label dl
