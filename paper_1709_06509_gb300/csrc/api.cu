@@ -341,6 +341,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     ok = ok && preload_cost_kernels(c->cost_kind) == cudaSuccess;
     ok = ok && preload_bp_kernels(c->msg_kind) == cudaSuccess;
     ok = ok && (c->msg_kind != MSG_U8 || preload_sparse_kernels() == cudaSuccess);
+    ok = ok && (c->msg_kind != MSG_F16 || preload_f16_kernels() == cudaSuccess);
     ok = ok && preload_readout_kernels(c->msg_kind) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->ws, 0, p.total, c->cap) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->d_desc, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->cap) == cudaSuccess;

@@ -347,7 +347,13 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
                                 staged, st);
     }
-    default: return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
+    default:
+        // packed half2 arithmetic where the stencil forms apply (the GENERAL_DT variant keeps the
+        // generic kernel)
+        if (sweep_f16_applies(trunc) && !(variant & VARIANT_GENERAL_DT))
+            return launch_sweep_f16(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, (variant & VARIANT_EAGER) != 0,
+                                    st);
+        return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
 }
 

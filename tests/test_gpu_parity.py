@@ -712,3 +712,31 @@ def test_sparse_arguments():
         with pytest.raises(bps.BPSError) as e:
             st.set_skip_rule(0, True)
         assert e.value.status == bps.BPS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("skip", [True, False])
+@pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 8, 10, 2), (60, 44, 33, 5, 3, 6, 10, 1), (64, 48, 64, 7, 3, 6, 8, 2)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_fp16_packed_kernel_agrees_with_the_generic_one_and_the_oracle(case, skip):
+    # the packed half2 half-sweep (default for T <= 2) against the generic float-arithmetic one
+    # (the GENERAL_DT variant) and the FP64 oracle of the float form: the same labels up to
+    # rounding, energies within 0.5%
+    W, H, D, window, levels, iters, lam, trunc = case
+    pair = synth.make_pair(500 + W + D, W, H, D, 4, 2.0)
+    res = {}
+    for name, variant, eager in (("packed", 0, False), ("packed_eager", bps.BPS_VARIANT_EAGER, True),
+                                 ("generic", bps.BPS_VARIANT_GENERAL_DT, False)):
+        with bps.Stereo(W, H, D, levels, bps.BPS_MSG_FP16, device=DEV) as st:
+            for lvl in range(levels):
+                st.set_variant(lvl, variant)
+            st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+            st.bp_solve(iters, lam, trunc, skip=skip)
+            d = st.wta_disparity().cpu().numpy()
+        res[name] = d
+    ref = oracle.stereo_f64(pair.left, pair.right, D, window, 20, levels, iters, float(lam), trunc)
+    for name, d in res.items():
+        e = oracle.energy(ref["cost"], d, float(lam), trunc)
+        assert abs(e - ref["energy"]) <= 0.005 * ref["energy"], (name, e, ref["energy"])
+        assert (d != ref["disp"]).mean() < 0.02, name
+    assert (res["packed"] != res["generic"]).mean() < 0.02
+    assert np.array_equal(res["packed"], res["packed_eager"])  # loading order changes nothing
