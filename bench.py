@@ -491,6 +491,7 @@ def forms_report(args):
             with bps.Stereo(W, H, pair.D, LEVELS, form, device=dev) as st:
                 if form == bps.BPS_MSG_U8:
                     autotune.tune_ncc(st, L, R, window, TRUNC_DATA, reps=2)
+                if form != bps.BPS_MSG_INT32:  # the int32 form has the generic kernel only
                     autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
                 steps = max(3, args.steps if not name.startswith("hd") else min(args.steps, 10))
                 for _ in range(3):

@@ -208,15 +208,23 @@ PairDesc make_desc(const bps_ctx *c) {
 }
 
 // Defaults of the per-scale sweep variant, from measurements on GB300 (the autotuner may
-// replace them): the stencil forms win below about half a million pixels of a colour, the
-// distance transform above; active lists pay off from about 128 K pixels of a colour.
-int default_variant(int64_t slots, int Gp = 1) {
+// replace them): in the u8 form the stencil forms win below about half a million pixels of a
+// colour, the distance transform above (the fp16 form's packed stencil kernel wins at every
+// size); active lists pay off from about 128 K pixels of a colour.
+int default_variant(int64_t slots, int Gp, int msg_kind) {
     int v = 0;
-    if (slots >= 512 * 1024) v |= VARIANT_GENERAL_DT;
+    if (slots >= 512 * 1024 && msg_kind == MSG_U8) v |= VARIANT_GENERAL_DT;
     if (slots >= 128 * 1024) v |= VARIANT_LISTS;
     // a scale of at most four passes of a 16 x 512-thread cluster runs as one cluster launch
     if (slots * Gp <= 4 * 16 * 512 && cluster_sweep_available()) v |= VARIANT_CLUSTER;
     return v;
+}
+
+// Whether a half-sweep of this form and variant builds and reads active lists: the u8 form's
+// kernels and the fp16 form's packed one do; the generic kernels sweep densely.
+bool sweep_takes_lists(int msg_kind, int variant, int trunc) {
+    return msg_kind == MSG_U8 ||
+           (msg_kind == MSG_F16 && sweep_f16_applies(trunc) && !(variant & VARIANT_GENERAL_DT));
 }
 
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 4000000000ull;  // 4 s: far above any phase
@@ -323,7 +331,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->sv.cand[0] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[0]);
     c->sv.cand[1] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[1]);
     c->sv.K = c->sv.Kp = 0;
-    for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l], c->Gp);
+    for (int l = 0; l < levels; ++l) c->variant[l] = default_variant((int64_t)p.Hs[l] * p.Whs[l], c->Gp, c->msg_kind);
     PairDesc hd = make_desc(c);
     std::vector<int> prefix(2 * (levels + 1));
     for (int l = 0; l < levels; ++l) {
@@ -604,7 +612,8 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
             for (int colour = 0; colour < 2; ++colour, ++t) {
                 if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
                 SweepLists sl{nullptr, nullptr, nullptr, nullptr};
-                const bool lists = skip && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_LISTS);
+                const bool lists =
+                    skip && (c->variant[l] & VARIANT_LISTS) && sweep_takes_lists(c->msg_kind, c->variant[l], trunc);
                 // the scale's first half-sweep cannot grow a list: every flag is still set
                 if (lists && (it > 0 || colour == 1)) {
                     sl.out = c->lists[colour ^ 1];
@@ -1179,7 +1188,8 @@ extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
                    BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
-    c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp) : variant;
+    c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp, c->msg_kind)
+                                       : variant;
     ++c->config_version;
     if (c->gexec) {  // a recorded graph holds the old kernels
         cudaGraphExecDestroy(c->gexec);

@@ -352,7 +352,7 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         // generic kernel)
         if (sweep_f16_applies(trunc) && !(variant & VARIANT_GENERAL_DT))
             return launch_sweep_f16(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, (variant & VARIANT_EAGER) != 0,
-                                    st);
+                                    lists, st);
         return sweep_t<float, __half>(lv, colour, D, Dp, Gp, lambda, trunc, skip, trace, st);
     }
 }

@@ -142,7 +142,7 @@ cudaError_t preload_sparse_kernels();
 // The fp16-message form's half-sweep in packed half2 arithmetic (sweep_f16.cu), for T <= 2.
 bool sweep_f16_applies(int trunc);
 cudaError_t launch_sweep_f16(const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc, int skip,
-                             unsigned long long *trace, bool eager, cudaStream_t st);
+                             unsigned long long *trace, bool eager, const SweepLists &lists, cudaStream_t st);
 cudaError_t preload_f16_kernels();
 // Energy: per-block partial sums into `partials` (nblocks entries of 8 bytes), then one
 // block sums them in a fixed order.

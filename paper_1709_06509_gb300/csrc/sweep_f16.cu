@@ -3,11 +3,13 @@
 // generic form: float costs, fp16 messages, labels 2j and 2j+1 in one half2 register j of a
 // lane's 16.  Per pixel the belief is formed from the costs minus their minimum over the
 // pixel's labels: a constant per pixel changes no message and no read-out, and it keeps every
-// value that can decide a message small (the minimum of h is at most three messages, 3 lambda T,
-// above zero), so half precision resolves it to 1/32 or better.  The truncated-linear
+// value that can decide a message small: the minimum of h is at most three messages, 3 lambda T,
+// above zero, so those values lie below 4 lambda T (80 at lambda T = 20, where half precision
+// steps by 1/16 at most; a message itself, at most lambda T, by 1/64).  The truncated-linear
 // minimisation is the stencil of the u8 form: m(d) = min(h(d), h(d±1) + lambda, min h + lambda T)
 // - min h for T = 2, min(h(d), min h + lambda T) - min h for T <= 1.  Skip and trace as in the
-// other forms; the flag and every input may be loaded at once (EAGER).
+// other forms; the flag and every input may be loaded at once (EAGER); with the skip on, the
+// active lists of the u8 form (a dense launch that appends, then launches over the lists).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -24,13 +26,18 @@ __device__ __forceinline__ uint32_t word(const uint4 (&v)[2], int j) {
     return (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
 }
 
-template <bool PADDED, int TS, bool EAGER>
+// APPEND: newly dirty neighbours are appended to the other colour's active list (one
+// reservation a warp).  LISTED: the slot is the caller's list entry (nslot for none); a listed
+// pixel is dirty by construction, so its flag is not read.
+template <bool PADDED, int TS, bool EAGER, bool APPEND = false, bool LISTED = false>
 __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour, int D, int Dp, int Gp, float lam,
-                                                float lamT, int skip, unsigned long long *trace, int64_t block) {
+                                                float lamT, int skip, unsigned long long *trace, int64_t block,
+                                                const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
+                                                int64_t s_listed = 0) {
     const int lane = threadIdx.x & 31;
     const int g = threadIdx.x & (Gp - 1);
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
-    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const int64_t s = LISTED ? s_listed : block * (blockDim.x / Gp) + threadIdx.x / Gp;
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
@@ -83,7 +90,7 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
         load_cost();
         load_messages(valid);
     }
-    const bool active = valid && (!skip || dirty_in[s] == 1u);
+    const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
     if (trace && lane == 0) {
@@ -111,6 +118,7 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
     }
     const __half2 L2 = __float2half2_rn(lam), LT2 = __float2half2_rn(lamT);
     const int gshift = lane & ~(Gp - 1);
+    unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark (APPEND)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         __half2 h[8], m[8];
@@ -161,68 +169,125 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             st_v4_if(dst[q], o0, mine && changed);
             st_v4_if(dst[q] + 1, o1, mine && changed);
-            st_u32_if(dirty_out + qsv[q], 1u, send && changed && g == 0);
+            const bool lead = send && changed && g == 0;
+            if constexpr (APPEND) mark[q] = lead ? qsv[q] + 1u : 0u;
+            else st_u32_if(dirty_out + qsv[q], 1u, lead);
         } else {
             st_v4_if(dst[q], o0, mine);
             st_v4_if(dst[q] + 1, o1, mine);
         }
     }
+    if constexpr (APPEND) {
+        // the marked neighbours' flags flip together, then the warp appends the ones that were
+        // clean with a single reservation
+        unsigned was[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) was[q] = mark[q] ? atomicOr(dirty_out + (mark[q] - 1u), 1u) : 1u;
+        unsigned am[4];
+        unsigned total = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            am[q] = __ballot_sync(FULL, was[q] == 0u);
+            total += __popc(am[q]);
+        }
+        if (total) {
+            unsigned base = 0u;
+            if (lane == 0) base = atomicAdd(al.n_out, total);
+            base = __shfl_sync(FULL, base, 0);
+            const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = mark[q] - 1u;
+                base += __popc(am[q]);
+            }
+        }
+    }
     if (skip && active && g == 0) dirty_in[s] = 0u;
 }
 
-template <bool PADDED, int TS, bool EAGER>
+template <bool PADDED, int TS, bool EAGER, bool APPEND>
 __global__ void __launch_bounds__(256, 2)
 sweep_f16_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam, float lamT, int skip,
-                 unsigned long long *trace, int nblocks) {
+                 unsigned long long *trace, int nblocks, ActiveList al) {
     pdl_enter();
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group_f16<PADDED, TS, EAGER>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+        sweep_group_f16<PADDED, TS, EAGER, APPEND>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
 }
 
-template <bool PADDED, int TS, bool EAGER>
-static cudaError_t launch_f16_t(const LevelView &lv, int colour, int D, int Dp, int Gp, float lam, float lamT, int skip,
-                                unsigned long long *trace, cudaStream_t st) {
+// Over the pixels of an active list (its length read on the device), like the u8 list sweep.
+template <bool PADDED, int TS>
+__global__ void __launch_bounds__(256, 2)
+sweep_f16_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam, float lamT,
+                      unsigned long long *trace, ActiveList al) {
+    pdl_enter();
+    const int groups = blockDim.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t stride = (int64_t)gridDim.x * groups;
+    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
+    unsigned e = idx < nslot ? al.in[idx] : 0u;
+    const int64_t n = *al.n_in;
+    for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
+        const int64_t s = idx < n ? (int64_t)e : nslot;
+        if (idx + stride < n) e = al.in[idx + stride];
+        sweep_group_f16<PADDED, TS, false, true, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, s);
+    }
+}
+
+static int resident_f16() {  // CTAs of the fp16 sweep resident at once (looked up once per process)
     static int resident = 0;
     if (!resident) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_f16_kernel<PADDED, TS, EAGER>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_f16_kernel<false, 2, false, false>, 256, 0);
         resident = std::max(1, sms * std::max(1, per_sm));
     }
-    const int groups = 256 / Gp;
-    const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
-    if (blocks == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident);
-    return launch_k(sweep_f16_kernel<PADDED, TS, EAGER>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam, lamT,
-                    skip, trace, (int)blocks);
+    return resident;
 }
 
 template <bool PADDED, int TS>
-static cudaError_t launch_f16_e(bool eager, const LevelView &lv, int colour, int D, int Dp, int Gp, float lam,
-                                float lamT, int skip, unsigned long long *trace, cudaStream_t st) {
-    if (eager) return launch_f16_t<PADDED, TS, true>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
-    return launch_f16_t<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
+static cudaError_t launch_f16_t(const LevelView &lv, int colour, int D, int Dp, int Gp, float lam, float lamT, int skip,
+                                unsigned long long *trace, bool eager, const SweepLists &lists, cudaStream_t st) {
+    const int groups = 256 / Gp;
+    const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
+    if (blocks == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_f16());
+    const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
+    if (skip && al.in)
+        return launch_k(sweep_f16_list_kernel<PADDED, TS>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
+                        lamT, trace, al);
+    const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
+    if (al.out)
+        return launch_k(sweep_f16_kernel<PADDED, TS, false, true>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                        lam, lamT, skip, trace, (int)blocks, dense);
+    if (eager)
+        return launch_k(sweep_f16_kernel<PADDED, TS, true, false>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                        lam, lamT, skip, trace, (int)blocks, dense);
+    return launch_k(sweep_f16_kernel<PADDED, TS, false, false>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
+                    lam, lamT, skip, trace, (int)blocks, dense);
 }
 
 bool sweep_f16_applies(int trunc) { return trunc <= 2; }
 
 cudaError_t launch_sweep_f16(const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc, int skip,
-                             unsigned long long *trace, bool eager, cudaStream_t st) {
+                             unsigned long long *trace, bool eager, const SweepLists &lists, cudaStream_t st) {
     const float lam = trunc == 0 ? 0.f : (float)lambda, lamT = lam * (float)trunc;
     const bool padded = (D & 15) != 0;
     if (trunc <= 1) {
-        if (padded) return launch_f16_e<true, 1>(eager, lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
-        return launch_f16_e<false, 1>(eager, lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
+        if (padded) return launch_f16_t<true, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, eager, lists, st);
+        return launch_f16_t<false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, eager, lists, st);
     }
-    if (padded) return launch_f16_e<true, 2>(eager, lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
-    return launch_f16_e<false, 2>(eager, lv, colour, D, Dp, Gp, lam, lamT, skip, trace, st);
+    if (padded) return launch_f16_t<true, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, eager, lists, st);
+    return launch_f16_t<false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, eager, lists, st);
 }
 
 template <bool PADDED, int TS> static cudaError_t preload_f16_t() {
     cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, sweep_f16_kernel<PADDED, TS, false>);
-    return e == cudaSuccess ? cudaFuncGetAttributes(&a, sweep_f16_kernel<PADDED, TS, true>) : e;
+    cudaError_t e = cudaFuncGetAttributes(&a, sweep_f16_kernel<PADDED, TS, false, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_f16_kernel<PADDED, TS, true, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_f16_kernel<PADDED, TS, false, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_f16_list_kernel<PADDED, TS>);
+    return e;
 }
 
 cudaError_t preload_f16_kernels() {

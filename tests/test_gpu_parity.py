@@ -740,3 +740,33 @@ def test_fp16_packed_kernel_agrees_with_the_generic_one_and_the_oracle(case, ski
         assert (d != ref["disp"]).mean() < 0.02, name
     assert (res["packed"] != res["generic"]).mean() < 0.02
     assert np.array_equal(res["packed"], res["packed_eager"])  # loading order changes nothing
+
+
+@pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 8, 10, 2), (60, 44, 33, 5, 3, 6, 10, 1), (64, 48, 64, 7, 3, 6, 8, 2)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_fp16_active_lists_reproduce_the_dense_packed_sweep(case):
+    # with the skip on, the active lists only enumerate the pixels whose flag is set, so the
+    # packed fp16 sweep over lists must leave the same messages, trace and labels bit for bit,
+    # launched directly and replayed from a graph
+    W, H, D, window, levels, iters, lam, trunc = case
+    pair = synth.make_pair(700 + W + D, W, H, D, 4, 2.0)
+    res = {}
+    for name, variant in (("dense", 0), ("lists", bps.BPS_VARIANT_LISTS), ("lists_eager", bps.BPS_VARIANT_LISTS | 8)):
+        with bps.Stereo(W, H, D, levels, bps.BPS_MSG_FP16, device=DEV) as st:
+            for lvl in range(levels):
+                st.set_variant(lvl, variant)
+            out = torch.empty((H, W), dtype=torch.int32, device=DEV)
+            for graph in (False, True, True):
+                st.stereo(to_dev(pair.left), to_dev(pair.right), window, 20, iters, lam, trunc, graph=graph, out=out)
+                torch.cuda.synchronize()
+                got = (out.cpu().numpy().copy(), st.get_trace().copy(),
+                       [st.export_messages(lvl).cpu().numpy().copy() for lvl in range(levels)])
+                if name in res:
+                    prev = res[name]
+                    assert np.array_equal(prev[0], got[0]) and np.array_equal(prev[1], got[1])
+                    assert all(np.array_equal(a, b) for a, b in zip(prev[2], got[2]))
+                res[name] = got
+    for name in ("lists", "lists_eager"):
+        assert np.array_equal(res[name][0], res["dense"][0]), name
+        assert np.array_equal(res[name][1], res["dense"][1]), name
+        assert all(np.array_equal(a, b) for a, b in zip(res[name][2], res["dense"][2])), name
