@@ -108,6 +108,21 @@ def cpu_baseline(pairs) -> dict:
                       f"single-threaded C oracle with the skip on, {t:.1f} s"}
 
 
+def cpu_baseline_parallel(pairs) -> dict | None:
+    """The same pass on the oracle's OpenMP build (NCC rows and the pixels of one colour split
+    over every host core; the same results bit for bit); None where gcc has no OpenMP."""
+    import oracle
+
+    if not oracle.openmp_available():
+        return None
+    with oracle.openmp(os.cpu_count() or 1) as n:
+        oracle_pass(pairs[:1])
+        t = oracle_pass(pairs)
+    return {"value": work_units(pairs) / t / 1e6, "unit": UNIT, "cores": n, "kind": "oracle (OpenMP build)",
+            "sample": "one pass of both workload pairs (384x288 D16 + 450x375 D64) through the "
+                      f"C oracle built with OpenMP, {n} threads, skip on, {t:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -769,6 +784,9 @@ def main():
             line["roofline_large"] = large
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pairs)
+            par = cpu_baseline_parallel(pairs)
+            if par:
+                line["cpu_baseline_parallel"] = par
         print(json.dumps(line))
     batch.close()
     for st, _ in ctxs:

@@ -8,6 +8,7 @@ up, down, left, right).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -17,28 +18,58 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, a second or two)."""
-    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, a second or two); with `openmp`, the
+    timing build liboracle_omp.so (same source and results, threads over pixels)."""
+    out = _LIB_OMP if openmp else _LIB
+    stale = (not os.path.exists(out)) or os.path.getmtime(out) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
     if force or stale:
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = out + f".{os.getpid()}.tmp"
+        flags = CFLAGS + (["-fopenmp"] if openmp else [])
+        subprocess.check_call(["gcc", *flags, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs: dict[bool, ctypes.CDLL] = {}
+_use_openmp = False
+
+
+def openmp_available() -> bool:
+    """Whether the OpenMP build compiles and loads here."""
+    try:
+        _load(True)
+        return True
+    except (OSError, subprocess.CalledProcessError):
+        return False
+
+
+@contextlib.contextmanager
+def openmp(threads: int = 0):
+    """Inside the block every oracle call runs on the OpenMP build with `threads` threads (0:
+    the OpenMP default); yields the thread count in use."""
+    global _use_openmp
+    n = _load(True).oracle_threads(threads)
+    prev, _use_openmp = _use_openmp, True
+    try:
+        yield n
+    finally:
+        _use_openmp = prev
 
 
 def lib() -> ctypes.CDLL:
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+    return _load(_use_openmp)
+
+
+def _load(openmp_build: bool) -> ctypes.CDLL:
+    if openmp_build not in _libs:
+        _lib = ctypes.CDLL(build(openmp=openmp_build))
         P = ctypes.c_void_p
         i, i64, u64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         sig = {
@@ -61,12 +92,14 @@ def lib() -> ctypes.CDLL:
             "oracle_wta_f64": (i, [P, P, i, i, i, P]),
             "oracle_energy_i32": (i64, [P, P, i, i, i, i, i]),
             "oracle_energy_f64": (d, [P, P, i, i, i, d, i]),
+            "oracle_threads": (i, [i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
             f.restype = res
             f.argtypes = args
-    return _lib
+        _libs[openmp_build] = _lib
+    return _libs[openmp_build]
 
 
 def _p(a: np.ndarray | None):

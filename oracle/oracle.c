@@ -7,7 +7,11 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC oracle.c -lm
  * (-ffp-contract=off keeps every FP64 multiply and add separately rounded; gcc would
- * otherwise fuse them on aarch64.)
+ * otherwise fuse them on aarch64.)  A second build adds -fopenmp, for timing only: the NCC
+ * rows and the pixels of one colour in a half-sweep are then split over threads.  Every
+ * output element is computed by the same operations either way (the pixels of one colour
+ * are independent within a half-sweep, which the shuffled-order pin checks), so both builds
+ * return the same bits.
  *
  * The message passing runs in FP64 for both forms.  With integer costs, lambda and trunc
  * every value stays an integer far below 2^53, so FP64 min/+/- are exact and the integer
@@ -18,10 +22,27 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { UP = 0, DOWN = 1, LEFT = 2, RIGHT = 3 };
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* The OpenMP build's thread count (set when n > 0); returns the count in use, 1 in the
+ * serial build. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------- NCC (Correlation volume) */
 
@@ -31,6 +52,7 @@ int oracle_ncc(const uint8_t *L, const uint8_t *R, int W, int H, int D, int wind
         return -1;
     const int r = window / 2;
     const int64_t N = (int64_t)window * window;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             for (int d = 0; d < D; ++d) {
@@ -205,9 +227,6 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
                          uint64_t order_seed, int64_t *trace)
 {
     const size_t plane = (size_t)H * W * D;
-    double *b = malloc(sizeof(double) * (size_t)D);
-    double *h = malloc(sizeof(double) * (size_t)D);
-    double *m = malloc(sizeof(double) * (size_t)D);
     unsigned char *dirty = malloc((size_t)W * H);
     unsigned char *frozen = calloc((size_t)W * H, 1);
     int *order = malloc(sizeof(int) * ((size_t)W * H + 1));
@@ -229,6 +248,7 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
                     order[j] = t;
                 }
             int64_t updated = 0;
+#pragma omp parallel for schedule(static) reduction(+ : updated)
             for (int k = 0; k < n; ++k) {
                 const int x = order[k] % W, y = order[k] / W;
                 const size_t p = (size_t)y * W + x;
@@ -236,6 +256,7 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
                     continue;
                 ++updated;
                 int marked = 0;
+                double b[D], h[D], m[D]; /* belief, message input, message */
                 const int has[4] = {y > 0, y < H - 1, x > 0, x < W - 1};
                 /* belief: data term plus every incoming message */
                 for (int d = 0; d < D; ++d) {
@@ -267,6 +288,8 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
                         dst[d] = m[d];
                     }
                     if (changed) {
+                        /* q is of the other colour; several senders may mark it */
+#pragma omp atomic write
                         dirty[(size_t)qy * W + qx] = 1;
                         marked = 1;
                     }
@@ -278,9 +301,6 @@ static int64_t *bp_level(const double *C, double *M, int W, int H, int D, int it
             if (trace)
                 *trace++ = updated;
         }
-    free(b);
-    free(h);
-    free(m);
     free(dirty);
     free(frozen);
     free(order);

@@ -41,6 +41,10 @@
 extern "C" {
 #endif
 
+/* Threads of the OpenMP build (a timing build; same results): sets the count when n > 0 and
+ * returns the count in use (1 in the serial build). */
+int oracle_threads(int n);
+
 /* ncc[H][W][D] in FP64.  window odd >= 1. */
 int oracle_ncc(const uint8_t *L, const uint8_t *R, int W, int H, int D, int window, double *ncc);
 

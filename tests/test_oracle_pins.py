@@ -574,3 +574,22 @@ def test_sparse_messages_stay_normalised():
     cand, ms, t = oracle.bp_sparse(cost, 3, 6, 10, 2, 6)
     interior = ms[:, 1:-1, 1:-1]
     assert np.all(interior.min(axis=3) == 0) and ms.max() <= 10 * 2 and ms.min() >= 0
+
+
+def test_openmp_build_of_the_oracle_returns_the_same_bits():
+    # the OpenMP timing build splits NCC rows and the pixels of one colour over threads; the
+    # pixels of a colour are independent within a half-sweep, so every output must be identical
+    if not oracle.openmp_available():
+        pytest.skip("gcc without OpenMP")
+    pair = synth.make_pair(31, 40, 30, 12, 4, 2.0)
+    serial = oracle.stereo_int(pair.left, pair.right, 12, 5, 20, 3, 6, 10, 2)
+    rules = oracle.bp(serial["cost"], 3, 6, 10, 2, eps=2, freeze=True)
+    with oracle.openmp(4) as n:
+        assert n == 4
+        par = oracle.stereo_int(pair.left, pair.right, 12, 5, 20, 3, 6, 10, 2)
+        par_rules = oracle.bp(serial["cost"], 3, 6, 10, 2, eps=2, freeze=True)
+    for k in ("cost", "msg", "trace", "disp"):
+        assert np.array_equal(serial[k], par[k]), k
+    assert serial["energy"] == par["energy"]
+    for a, b in zip(rules, par_rules):
+        assert np.array_equal(a, b)
