@@ -307,10 +307,10 @@ def batch_report(args):
     Rs = [torch.from_numpy(p.right).to(dev) for p in pairs]
     outs = [torch.empty(p.left.shape, dtype=torch.int32, device=dev) for p in pairs]
     windows = [7] * len(pairs)
-    if form == bps.BPS_MSG_U8:  # the sweep variants and NCC shapes exist for the u8 form
-        for st, L, R in zip(sts, Ls, Rs):
+    for st, L, R in zip(sts, Ls, Rs):
+        if form == bps.BPS_MSG_U8:  # the NCC shapes are tuned on the u8 form's int16 costs
             autotune.tune_ncc(st, L, R, 7, TRUNC_DATA, reps=2)
-            autotune.tune(st, L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
+        autotune.tune(st, L, R, 7, TRUNC_DATA, ITERS, LAM, TRUNC, reps=1)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     units = sum(p.left.size * p.D for p in pairs)
     batch = bps.Batch(sts)

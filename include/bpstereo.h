@@ -282,7 +282,9 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  *   BPS_VARIANT_DPAR_LISTS  the same on the list launches only (with BPS_VARIANT_LISTS);
  *   BPS_VARIANT_STAGED      dense launches: each thread copies the next pixel block's inputs
  *                           into shared memory (cp.async) while it computes the current one,
- *                           for HBM-bound scales (not combined with BPS_VARIANT_DPAR).
+ *                           for HBM-bound scales (not combined with BPS_VARIANT_DPAR);
+ *   BPS_VARIANT_STAGED_LISTS the same on the list launches (with BPS_VARIANT_LISTS; not
+ *                           combined with BPS_VARIANT_DPAR_LISTS).
  * With BPS_FLAG_PROFILE a cluster launch's time is shared out evenly over its half-sweeps.
  * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
@@ -303,6 +305,7 @@ int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
 #define BPS_VARIANT_DPAR 16
 #define BPS_VARIANT_DPAR_LISTS 32
 #define BPS_VARIANT_STAGED 64
+#define BPS_VARIANT_STAGED_LISTS 128
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 

@@ -53,6 +53,7 @@ BPS_VARIANT_EAGER = 8
 BPS_VARIANT_DPAR = 16
 BPS_VARIANT_DPAR_LISTS = 32
 BPS_VARIANT_STAGED = 64
+BPS_VARIANT_STAGED_LISTS = 128
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 

@@ -12,6 +12,7 @@ given scale size and label count (see bps_set_sweep_variant in include/bpstereo.
   DPAR               one lane group per (pixel, direction): the four messages side by side
   DPAR_LISTS         ... on the list launches only
   STAGED             dense launches prefetch the next block's inputs into shared memory (large scales)
+  STAGED_LISTS       ... list launches
 and their combinations.  For one context and one representative input, tune() replays the
 whole pipeline from its CUDA graph (the way the variants run in production: consecutive
 launches overlap, which per-launch events would hide) and descends one scale at a time,
@@ -25,16 +26,19 @@ import json
 import os
 
 from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS,
-               BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_STAGED, BPSError, level_dims)
+               BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_STAGED,
+               BPS_VARIANT_STAGED_LISTS, BPSError, level_dims)
 
-_G, _L, _E, _C, _P, _PL, _S = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER,
-                               BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_STAGED)
+_G, _L, _E, _C, _P, _PL, _S, _SL = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER,
+                                    BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_STAGED,
+                                    BPS_VARIANT_STAGED_LISTS)
 # a cluster launch is only a candidate for scales of at most this many lanes (pixels x lanes per pixel)
 CLUSTER_MAX_LANES = 16 * 16 * 512
 SMALL_CANDIDATES = (0, _G, _E, _E | _G, _C, _C | _E, _C | _E | _G, _P, _P | _G, _P | _E, _P | _E | _G)
 LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, _P | _E, _P | _L, _P | _E | _L,
                     _L | _PL, _E | _L | _PL, _G | _L | _PL, _E | _G | _L | _PL, _S, _S | _G, _S | _L, _S | _G | _L,
-                    _S | _L | _PL, _S | _G | _L | _PL)
+                    _S | _L | _PL, _S | _G | _L | _PL, _L | _SL, _G | _L | _SL, _E | _L | _SL, _E | _G | _L | _SL,
+                    _S | _L | _SL, _S | _G | _L | _SL)
 CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
 DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
 
@@ -42,7 +46,7 @@ DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
 def _key(gpu: str, w: int, h: int, D: int, msg_type: int, trunc: int, skip: bool) -> str:
     tclass = trunc if trunc <= 2 else 3  # the stencil forms exist for trunc 0, 1, 2 only
     Dp = (D + 15) // 16 * 16
-    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v3"
+    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v4"
 
 
 def _load(path: str | None) -> dict:

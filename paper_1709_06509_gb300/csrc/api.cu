@@ -208,13 +208,13 @@ PairDesc make_desc(const bps_ctx *c) {
 }
 
 // Defaults of the per-scale sweep variant, from measurements on GB300 (the autotuner may
-// replace them): in the u8 form the stencil forms win below about half a million pixels of a
-// colour, the distance transform above (the fp16 form's packed stencil kernel wins at every
-// size); active lists pay off from about 128 K pixels of a colour.
+// replace them): active lists pay off from about 128 K pixels of a colour, and there the u8
+// form's staged launches (dense and list) beat the plain ones (960x540 and 1920x1080 at 256
+// labels: 1.53 ms against 1.79 ms, and 4.15 ms against 5.50 ms, for the finest scale's 20
+// half-sweeps); the stencil forms stay ahead of the distance transform at every size.
 int default_variant(int64_t slots, int Gp, int msg_kind) {
     int v = 0;
-    if (slots >= 512 * 1024 && msg_kind == MSG_U8) v |= VARIANT_GENERAL_DT;
-    if (slots >= 128 * 1024) v |= VARIANT_LISTS;
+    if (slots >= 128 * 1024) v |= VARIANT_LISTS | (msg_kind == MSG_U8 ? VARIANT_STAGED | VARIANT_STAGED_LISTS : 0);
     // a scale of at most four passes of a 16 x 512-thread cluster runs as one cluster launch
     if (slots * Gp <= 4 * 16 * 512 && cluster_sweep_available()) v |= VARIANT_CLUSTER;
     return v;
@@ -1185,7 +1185,8 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
 extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     if (!c || level < 0 || level >= c->levels || variant < -1 ||
         variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER |
-                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED))
+                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED |
+                    BPS_VARIANT_STAGED_LISTS))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp, c->msg_kind)

@@ -85,6 +85,44 @@ sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam,
     cp_async_wait<0>();
 }
 
+// The staged half-sweep over the pixels of an active list: the entries of a thread's current
+// and next block are read one block ahead of their copies, the copies one block ahead of the
+// computation.
+template <bool PADDED, int TS>
+__global__ void __launch_bounds__(256, BPS_SWEEP_STAGED_MIN_BLOCKS)
+sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
+                            unsigned long long *trace, ActiveList al) {
+    extern __shared__ uint4 stage_mem[];  // [2][STAGE_CHUNKS][blockDim.x]
+    pdl_enter();
+    const int stage_len = STAGE_CHUNKS * blockDim.x;
+    const int groups = blockDim.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t stride = (int64_t)gridDim.x * groups;
+    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
+    // the length and the first two entries are read together: an entry past the length is
+    // stale but inside the buffer, which holds a slot of every pixel of a colour
+    const unsigned e0 = idx < nslot ? al.in[idx] : 0u;
+    const unsigned e1 = idx + stride < nslot ? al.in[idx + stride] : 0u;
+    const int64_t n = *al.n_in;
+    int64_t cur = idx < n ? (int64_t)e0 : nslot;
+    int64_t nxt = idx + stride < n ? (int64_t)e1 : nslot;
+    int buf = 0;
+    if ((int64_t)blockIdx.x * groups < n) stage_u8<true>(lv, colour, Dp, Gp, 1, blockIdx.x, stage_mem, cur);
+    cp_async_commit();
+    for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride, buf ^= 1) {
+        if ((b + gridDim.x) * groups < n)
+            stage_u8<true>(lv, colour, Dp, Gp, 1, b + gridDim.x, stage_mem + (buf ^ 1) * stage_len, nxt);
+        cp_async_commit();
+        const int64_t after = idx + 2 * stride < n ? (int64_t)al.in[idx + 2 * stride] : nslot;
+        cp_async_wait<1>();  // block b's copies have landed; the next block's may be in flight
+        sweep_group_u8<PADDED, true, TS, false, 3, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, cur,
+                                                         stage_mem + buf * stage_len);
+        cur = nxt;
+        nxt = after;
+    }
+    cp_async_wait<0>();
+}
+
 static size_t staged_smem_bytes() { return (size_t)2 * STAGE_CHUNKS * 256 * sizeof(uint4); }
 
 // The same half-sweep over the pixels of an active list; its length is read on the device
@@ -239,7 +277,11 @@ static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, 
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
                                 bool eager, cudaStream_t st, bool staged = false) {
     if constexpr (!DP) {
-        if (staged && !al.in) {  // dense launches only
+        if (staged && skip && al.in)
+            return launch_k(sweep_u8_staged_list_kernel<PADDED, TS>,
+                            dim3((unsigned)std::min<int64_t>(blocks, resident_staged_blocks())), dim3(256),
+                            staged_smem_bytes(), st, lv, colour, D, Dp, Gp, lam, lamT, trace, al);
+        if (staged && !al.in) {
             const unsigned g = (unsigned)std::min<int64_t>(blocks, resident_staged_blocks());
             const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
             if (al.out)
@@ -340,7 +382,7 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
         const bool eager = (variant & VARIANT_EAGER) != 0;
-        const bool staged = (variant & VARIANT_STAGED) != 0 && !dp;
+        const bool staged = (variant & (list_launch ? VARIANT_STAGED_LISTS : VARIANT_STAGED)) != 0 && !dp;
         if (D & 15)
             return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
                                    staged, st);
@@ -497,6 +539,9 @@ template <bool PADDED, int TS> static cudaError_t preload_u8() {
                                  (int)staged_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_u8_staged_kernel<PADDED, true, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)staged_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_staged_list_kernel<PADDED, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)staged_smem_bytes());
     return e;
 }

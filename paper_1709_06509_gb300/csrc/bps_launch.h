@@ -59,6 +59,7 @@ constexpr int VARIANT_EAGER = 8;       // every load of a half-sweep issued at o
 constexpr int VARIANT_DPAR = 16;       // one lane group per (pixel, direction), up to 128 labels
 constexpr int VARIANT_DPAR_LISTS = 32; // ... on the list launches only
 constexpr int VARIANT_STAGED = 64;     // dense launches stage the next block's inputs in shared memory
+constexpr int VARIANT_STAGED_LISTS = 128; // ... list launches
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {

@@ -323,13 +323,15 @@ template <int n> __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Issue the copies of block `block`'s inputs (eager: old messages of every valid pixel) into
-// `stage` (this thread's chunks).
+// `stage` (this thread's chunks).  LISTED: the slot is the caller's list entry s_listed (nslot
+// for none), and no flag is copied (a listed pixel is dirty by construction).
+template <bool LISTED = false>
 __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp, int Gp, int skip, int64_t block,
-                                         uint4 *stage) {
+                                         uint4 *stage, int64_t s_listed = 0) {
     const int T = blockDim.x, t = threadIdx.x;
     const int g = threadIdx.x & (Gp - 1);
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
-    const int64_t s = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const int64_t s = LISTED ? s_listed : block * (blockDim.x / Gp) + threadIdx.x / Gp;
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
@@ -365,7 +367,7 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
         const int64_t qs = oq ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
         cp_async16(stage + (6 + q) * T + t, msg_out + (oq ? (qs * 4 + opp[q]) * Dp + dbase : 0), oq);
     }
-    cp_async4(stage + 10 * T + t, dirty_in + sc, valid);
+    if constexpr (!LISTED) cp_async4(stage + 10 * T + t, dirty_in + sc, valid);
 }
 
 // PADDED: D is not a multiple of 16, so the last lane holds labels >= D that must stay out

@@ -321,7 +321,8 @@ def set_all_variants(st, variant):
     assert st.variants() == [variant] * st.levels
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43, 64, 65, 66, 67])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43, 64, 65, 66, 67,
+                                     130, 131, 138, 194, 195, 162])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
                                   (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
                          ids=lambda c: "x".join(map(str, c)))
@@ -342,6 +343,34 @@ def test_every_sweep_variant_is_exact(case, variant):
     ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True)
     assert np.array_equal(msg, ref_msg) and np.array_equal(trace, ref_trace)
     assert np.array_equal(disp, oracle.wta(c0, ref_msg))
+
+
+_STAGED_REF = {}
+
+
+@pytest.mark.parametrize("variant", [64, 66, 130, 194])
+@pytest.mark.parametrize("case", [(160, 72, 256, 5, 1, 4, 10, 2), (520, 330, 16, 5, 3, 5, 10, 2), (400, 64, 100, 5, 2, 4, 7, 3)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_staged_variants_exact_where_every_cta_loops(case, variant):
+    # sizes whose finest scale has more pixel blocks than the staged kernels have resident CTAs
+    # (2 a SM), so CTAs stage their next block while they compute the current one (dense and
+    # list launches): messages, trace and disparities must be the oracle's
+    W, H, D, window, levels, iters, lam, trunc = case
+    pair = synth.make_pair(900 + W + D, W, H, D, 4, 2.0)
+    with bps.Stereo(W, H, D, levels, bps.BPS_MSG_U8, device=DEV) as st:
+        set_all_variants(st, variant)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        st.bp_solve(iters, lam, trunc, skip=True)
+        msg = st.export_messages(0).cpu().numpy()
+        trace = st.get_trace()
+        disp = st.wta_disparity().cpu().numpy()
+    if case not in _STAGED_REF:
+        c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+        ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True)
+        _STAGED_REF[case] = (ref_msg, ref_trace, oracle.wta(c0, ref_msg))
+    ref_msg, ref_trace, ref_disp = _STAGED_REF[case]
+    assert np.array_equal(msg, ref_msg) and np.array_equal(trace, ref_trace)
+    assert np.array_equal(disp, ref_disp)
 
 
 @pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25, 64, 65])
@@ -546,7 +575,7 @@ def test_fp16_energy_gap(name):
     assert (d != ref["disp"]).mean() < 0.02
 
 
-@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66])
+@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66, 130, 194])
 @pytest.mark.parametrize("eps,freeze", [(1, False), (3, False), (0, True), (2, True)])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (60, 44, 40, 5, 3, 5, 8, 3)],
                          ids=lambda c: "x".join(map(str, c)))
