@@ -41,12 +41,23 @@ LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, 
                     _S | _L | _SL, _S | _G | _L | _SL)
 CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
 DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
+# the list and staged candidates are tried on every scale of at least this many lanes (a scale
+# small enough for the cluster launch may still have enough pixels for active lists to pay)
+LIST_MIN_LANES = 8 * 1024
+
+
+def _candidates(lanes: int, Gp: int) -> list[int]:
+    """The variants tried on a scale of `lanes` lanes (pixels of a colour x lanes a pixel)."""
+    cands = list(SMALL_CANDIDATES) if lanes <= CLUSTER_MAX_LANES else []
+    if lanes > CLUSTER_MAX_LANES or lanes >= LIST_MIN_LANES:
+        cands += [v for v in LARGE_CANDIDATES if v not in cands]
+    return [v for v in cands if not (v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL)]
 
 
 def _key(gpu: str, w: int, h: int, D: int, msg_type: int, trunc: int, skip: bool) -> str:
     tclass = trunc if trunc <= 2 else 3  # the stencil forms exist for trunc 0, 1, 2 only
     Dp = (D + 15) // 16 * 16
-    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v4"
+    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v5"
 
 
 def _load(path: str | None) -> dict:
@@ -76,7 +87,7 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
         chosen = [int(table[k]) for k in keys]
     else:
         Gp = _lanes_per_pixel(st.D)
-        small = [h * ((w + 1) // 2) * Gp <= CLUSTER_MAX_LANES for w, h in dims]
+        lanes = [h * ((w + 1) // 2) * Gp for w, h in dims]
         out = torch.empty((st.H, st.W), dtype=torch.int32, device=st.device)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -106,9 +117,7 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
         current = st.variants()
         for lvl in reversed(range(st.levels)):
             times = {}
-            for v in (SMALL_CANDIDATES if small[lvl] else LARGE_CANDIDATES):
-                if v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL:
-                    continue
+            for v in _candidates(lanes[lvl], Gp):
                 trial = list(current)
                 trial[lvl] = v
                 try:
@@ -226,11 +235,10 @@ def tune_batch(batch, sts, lefts, rights, windows, trunc_data: int, iters: int, 
         dims = level_dims(st.W, st.H, st.levels)
         for lvl in reversed(range(st.levels)):
             w, h = dims[lvl]
-            small = h * ((w + 1) // 2) * Gp <= CLUSTER_MAX_LANES
             current = st.variants()[lvl]
             best_v, best_t = current, base
-            for v in (SMALL_CANDIDATES if small else LARGE_CANDIDATES):
-                if v == current or (v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL):
+            for v in _candidates(h * ((w + 1) // 2) * Gp, Gp):
+                if v == current:
                     continue
                 try:
                     st.set_variant(lvl, v)
