@@ -125,28 +125,48 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
 
 static size_t staged_smem_bytes() { return (size_t)2 * STAGE_CHUNKS * 256 * sizeof(uint4); }
 
-// The same half-sweep over the pixels of an active list; its length is read on the device
-// (a recorded graph keeps the launch shape, the list decides the work).
+// A list launch's loop over the entries with one group of Gp lanes a pixel, or with 4 Gp lanes
+// a pixel (DP: one group per direction); `e` is this thread's first entry, read by the caller
+// together with the list length n.
 template <bool PADDED, int TS, bool DP>
-__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
-sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
-                     unsigned long long *trace, ActiveList al) {
-    pdl_enter();
+__device__ __forceinline__ void list_loop(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
+                                          unsigned long long *trace, const ActiveList &al, int64_t n, unsigned e) {
     const int lpp = DP ? 4 * Gp : Gp;  // lanes a pixel
     const int groups = blockDim.x / lpp;
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     const int64_t stride = (int64_t)gridDim.x * groups;
     int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / lpp;
-    // the list length and this thread's first entry are read together: an entry past the
-    // length is stale but inside the buffer, which holds a slot of every pixel of a colour
-    unsigned e = idx < nslot ? al.in[idx] : 0u;
-    const int64_t n = *al.n_in;
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
         const int64_t s = idx < n ? (int64_t)e : nslot;
         if (idx + stride < n) e = al.in[idx + stride];
         if constexpr (DP) sweep_group_u8_dp<PADDED, true, TS, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, s);
         else sweep_group_u8<PADDED, true, TS, false, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, s);
     }
+}
+
+// The same half-sweep over the pixels of an active list; its length is read on the device
+// (a recorded graph keeps the launch shape, the list decides the work).  DP: direction-parallel
+// lanes while the list has at most dp_max entries (short lists: a quarter of the dependent work
+// per lane), one group a pixel on longer ones (fewer passes of the resident CTAs).
+template <bool PADDED, int TS, bool DP>
+__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
+                     unsigned long long *trace, ActiveList al, int64_t dp_max) {
+    pdl_enter();
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    // the list length and this thread's first entry (of either lane mapping) are read together:
+    // an entry past the length is stale but inside the buffer, which holds a slot of every
+    // pixel of a colour
+    const int64_t i_pix = (int64_t)blockIdx.x * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const unsigned e_pix = i_pix < nslot ? al.in[i_pix] : 0u;
+    unsigned e_dp = 0u;
+    if constexpr (DP) {
+        const int64_t i_dp = (int64_t)blockIdx.x * (blockDim.x / (4 * Gp)) + threadIdx.x / (4 * Gp);
+        e_dp = i_dp < nslot ? al.in[i_dp] : 0u;
+    }
+    const int64_t n = *al.n_in;
+    if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_dp);
+    else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_pix);
 }
 
 // Every iteration of one small scale in ONE launch of ONE thread-block cluster.  The CTAs of
@@ -294,9 +314,12 @@ static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, 
     if (eager && !al.in && !al.out)  // grid <= blocks: every CTA has a first block
         return launch_k(sweep_u8_eager_kernel<PADDED, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
                         lam, lamT, skip, trace, (int)blocks);
-    if (skip && al.in)
+    if (skip && al.in) {
+        // direction-parallel lanes up to about one and a half passes of the launch's CTAs
+        const int64_t dp_max = DP ? (int64_t)grid * (256 / (4 * Gp)) * 3 / 2 : 0;
         return launch_k(sweep_u8_list_kernel<PADDED, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp, lam,
-                        lamT, trace, al);
+                        lamT, trace, al, dp_max);
+    }
     const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
     if (al.out)
         return launch_k(sweep_u8_kernel<PADDED, true, TS, DP>, dim3(grid), dim3(256), 0, st, lv, colour, D, Dp, Gp,
