@@ -424,9 +424,12 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     uint4 in[4];
     // the old outgoing messages (the skip's change test) are loaded together with the inputs,
     // so a recomputed pixel waits for one round trip to memory, not two
-    uint4 *dst[4];
     uint4 old[4];
     unsigned qsv[4];  // the neighbours' slots (0 where there is none)
+    // the slot a message to neighbour q goes to (recomputed where it is stored: fewer live registers)
+    auto dst = [&](int q) {
+        return reinterpret_cast<uint4 *>(msg_out + ((int64_t)qsv[q] * 4 + opp[q]) * Dp + dbase);
+    };
     auto load_cost = [&]() {
         if (lane_data) {
             const uint4 *cp = reinterpret_cast<const uint4 *>(cost + sc * Dp + dbase);
@@ -454,8 +457,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         for (int q = 0; q < 4; ++q) {
             const int64_t qs = (send && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
             qsv[q] = (unsigned)qs;
-            dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
-            old[q] = (skip && send && has[q] && lane_data) ? *dst[q] : make_uint4(0u, 0u, 0u, 0u);
+            old[q] = (skip && send && has[q] && lane_data) ? *dst(q) : make_uint4(0u, 0u, 0u, 0u);
         }
     };
     unsigned flag_staged = 0u;
@@ -474,7 +476,6 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             old[q] = stage[(6 + q) * T + t];
             const int64_t qs = (valid && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
             qsv[q] = (unsigned)qs;
-            dst[q] = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + opp[q]) * Dp + dbase);
         }
         flag_staged = stage[10 * T + t].x;
     } else if constexpr (EAGER != 0) {
@@ -519,7 +520,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     }
 
     const int gshift = lane & ~(Gp - 1);
-    unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark dirty (APPEND)
+    unsigned marks = 0u;  // bit q: this group marks neighbour q dirty (APPEND)
     const uint32_t EPS4 = (uint32_t)lv.eps * 0x01010101u;
     bool marked = false;                  // this pixel marked some receiver (skip rule freeze)
 #pragma unroll
@@ -546,19 +547,19 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             const unsigned bm = lv.eps ? __ballot_sync(FULL, big) : dm;
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             const bool significant = ((bm >> gshift) & group_bits(Gp)) != 0u;  // = changed when eps = 0
-            st_v4_if(dst[q], out, mine && changed);
+            st_v4_if(dst(q), out, mine && changed);
             const bool mk = send && significant;
             marked = marked || mk;
             const bool lead = mk && g == 0;  // one mark per pixel group
             if constexpr (APPEND) {
-                mark[q] = lead ? qsv[q] + 1u : 0u;
+                marks |= (lead ? 1u : 0u) << q;
             } else if (lv.freeze) {
                 if (lead) atomicOr(dirty_out + qsv[q], 1u);  // keeps the frozen bit
             } else {
                 st_u32_if(dirty_out + qsv[q], 1u, lead);
             }
         } else {
-            st_v4_if(dst[q], out, mine);
+            st_v4_if(dst(q), out, mine);
         }
     }
     if constexpr (APPEND) {
@@ -566,7 +567,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         // appends the ones that were clean with a single reservation
         unsigned was[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) was[q] = mark[q] ? atomicOr(dirty_out + (mark[q] - 1u), 1u) : 1u;
+        for (int q = 0; q < 4; ++q) was[q] = ((marks >> q) & 1u) ? atomicOr(dirty_out + qsv[q], 1u) : 1u;
         unsigned am[4];
         unsigned total = 0u;
 #pragma unroll
@@ -581,7 +582,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             const unsigned below = (1u << lane) - 1u;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = mark[q] - 1u;
+                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = qsv[q];
                 base += __popc(am[q]);
             }
         }
