@@ -127,17 +127,18 @@ static size_t staged_smem_bytes() { return (size_t)2 * STAGE_CHUNKS * 256 * size
 
 // A list launch's loop over the entries with one group of Gp lanes a pixel, or with 4 Gp lanes
 // a pixel (DP: one group per direction); `e` is this thread's first entry, read by the caller
-// together with the list length n.
+// together with the list length n.  Indexes are 32-bit: a colour has at most 2^30 pixels
+// (bps_create admits at most 2^31 pixels), so n, idx + stride and b * groups stay below 2^31.
 template <bool PADDED, int TS, bool DP>
 __device__ __forceinline__ void list_loop(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
-                                          unsigned long long *trace, const ActiveList &al, int64_t n, unsigned e) {
-    const int lpp = DP ? 4 * Gp : Gp;  // lanes a pixel
-    const int groups = blockDim.x / lpp;
-    const int64_t nslot = (int64_t)lv.H * lv.Wh;
-    const int64_t stride = (int64_t)gridDim.x * groups;
-    int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / lpp;
-    for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
-        const int64_t s = idx < n ? (int64_t)e : nslot;
+                                          unsigned long long *trace, const ActiveList &al, unsigned n, unsigned e) {
+    const unsigned lpp = DP ? 4 * Gp : Gp;  // lanes a pixel
+    const unsigned groups = blockDim.x / lpp;
+    const unsigned nslot = (unsigned)lv.H * (unsigned)lv.Wh;
+    const unsigned stride = gridDim.x * groups;
+    unsigned idx = blockIdx.x * groups + threadIdx.x / lpp;
+    for (unsigned b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
+        const unsigned s = idx < n ? e : nslot;
         if (idx + stride < n) e = al.in[idx + stride];
         if constexpr (DP) sweep_group_u8_dp<PADDED, true, TS, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, s);
         else sweep_group_u8<PADDED, true, TS, false, 0, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, s);
@@ -164,7 +165,7 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
         const int64_t i_dp = (int64_t)blockIdx.x * (blockDim.x / (4 * Gp)) + threadIdx.x / (4 * Gp);
         e_dp = i_dp < nslot ? al.in[i_dp] : 0u;
     }
-    const int64_t n = *al.n_in;
+    const unsigned n = *al.n_in;
     if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_dp);
     else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_pix);
 }

@@ -120,8 +120,9 @@ sparse_sweep_kernel(LevelView lv, SparseView sv, int colour, int lam, int lamT, 
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
-        y = (int)(s / lv.Wh);
-        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
+        y = (int)(su / wh);
+        x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
     const int64_t sc = valid ? s : 0;

@@ -85,8 +85,9 @@ __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
-        y = (int)(s / lv.Wh);
-        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
+        y = (int)(su / wh);
+        x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
     const bool active = valid && (!skip || (colour ? lv.dirty[1] : lv.dirty[0])[s] != 0u);
@@ -335,8 +336,9 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
-        y = (int)(s / lv.Wh);
-        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
+        y = (int)(su / wh);
+        x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
     const int64_t sc = valid ? s : 0;
@@ -403,8 +405,9 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
-        y = (int)(s / lv.Wh);
-        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
+        y = (int)(su / wh);
+        x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
     const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
@@ -614,8 +617,9 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     int x = 0, y = 0;
     bool valid = false;
     if (s < nslot) {
-        y = (int)(s / lv.Wh);
-        x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+        const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
+        y = (int)(su / wh);
+        x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
         valid = x < lv.W;
     }
     const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
