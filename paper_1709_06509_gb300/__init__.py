@@ -44,6 +44,7 @@ BPS_FLAG_ASYNC = 64
 BPS_MAX_LEVELS = 8
 BPS_MAX_D = 512
 BPS_MAX_ITERS = 1024
+BPS_MAX_CANDIDATES = 32
 BPS_MAX_WINDOW = 31
 BPS_MAX_BATCH = 256
 BPS_VARIANT_GENERAL_DT = 1

@@ -87,3 +87,29 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.bps_bp_solve(None, 1, 1, 1, 1, 0, None, None) == bps.BPS_ERR_ARG
     assert lib.bps_wta_disparity(None, None, None) == bps.BPS_ERR_ARG
     assert lib.bps_energy(None, None, 1, 1, None, None, None) == bps.BPS_ERR_ARG
+
+
+def test_binding_constants_match_the_header():
+    # every #define of the header has the same value in the binding
+    text = open(HEADER).read()
+    for name, value in re.findall(r"#define\s+(BPS_\w+)\s+(-?\d+)\b", text):
+        assert getattr(bps, name) == int(value), name
+
+
+def test_autotuner_candidate_sets():
+    # scales small enough for the cluster launch get the small-scale set, scales of at least
+    # LIST_MIN_LANES lanes also get the list and staged forms, and direction-parallel variants
+    # are dropped where a pixel needs more than 8 lane groups (more than 128 labels)
+    from paper_1709_06509_gb300 import autotune as at
+
+    tiny = at._candidates(1000, 4)
+    assert set(tiny) == set(at.SMALL_CANDIDATES)
+    mid = at._candidates(at.LIST_MIN_LANES, 4)
+    assert set(mid) == set(at.SMALL_CANDIDATES) | set(at.LARGE_CANDIDATES) and len(mid) == len(set(mid))
+    big = at._candidates(at.CLUSTER_MAX_LANES + 1, 4)
+    assert set(big) == set(at.LARGE_CANDIDATES)
+    wide = at._candidates(at.CLUSTER_MAX_LANES + 1, 16)
+    dp = bps.BPS_VARIANT_DPAR | bps.BPS_VARIANT_DPAR_LISTS
+    assert wide and all(not (v & dp) for v in wide)
+    assert all(v & bps.BPS_VARIANT_LISTS for v in at.LARGE_CANDIDATES if v & bps.BPS_VARIANT_STAGED_LISTS)
+    assert set(at.CANDIDATES) == set(at.SMALL_CANDIDATES) | set(at.LARGE_CANDIDATES)
