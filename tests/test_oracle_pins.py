@@ -593,3 +593,16 @@ def test_openmp_build_of_the_oracle_returns_the_same_bits():
     assert serial["energy"] == par["energy"]
     for a, b in zip(rules, par_rules):
         assert np.array_equal(a, b)
+
+
+def test_generator_bytes_are_pinned():
+    # the seeded generator is integer-only, so the benchmark's inputs are the same bytes on
+    # every machine; these digests were taken from it and must not drift
+    import hashlib
+
+    def digest(p):
+        return hashlib.sha256(p.left.tobytes() + p.right.tobytes()).hexdigest()[:16]
+
+    assert digest(synth.workload_pair("tsukuba_384x288_d16")[0]) == "7dd0f5782c4c5075"
+    assert digest(synth.workload_pair("teddy_450x375_d64")[0]) == "949f63d01e46de04"
+    assert digest(synth.make_pair(11, 40, 30, 8, 3, 2.0)) == "b01b5c87e18b3021"
