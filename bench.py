@@ -1,14 +1,22 @@
 """Throughput of the stereo hot path (NCC cost volume + 4-scale min-sum BP with the
 fast-converging skip + WTA) in Mpix*disp/s, one JSON line on stdout.
 
-Workload (per GPU): the two single-pair configurations of the paper's test-set shapes,
-a 384x288 pair with D=16 and a 450x375 pair with D=64, 7x7 NCC window, data costs
-quantised with trunc 20, 4 scales, 10 iterations per scale, lambda=10, trunc=2, the
-fast-converging skip on, integer messages in uint8 storage (bit-exact with the int32
-method).  Seeded synthetic pairs stand in for the Middlebury images.  One step = both
-pairs as one bps_batch_stereo call (one CUDA graph replay whose branches are the pairs'
-launch chains, running concurrently).  The working set is smaller than
-L2, so a 256 MiB buffer is written between timed steps to flush it.
+Workload (per GPU): the full-HD configuration, one seeded synthetic 1920x1080 pair with
+D = 256 labels, 9x9 NCC window, data costs quantised with trunc 20, 4 scales, 10 iterations
+per scale, lambda = 10, trunc = 2, the exact fast-converging skip, integer messages in uint8
+storage (bit-exact with the int32 method).  One step = one bps_stereo graph replay of the
+whole path (cost volume, solve, read-out).  Its working set (4.3 GB) is far above L2; a
+256 MiB buffer is also written between timed steps.
+
+Beside the headline the line carries:
+  roofline       the red-black half-sweeps (every sweep launch of a solve), algorithmic bytes
+                 from the live skip trace over the graph-timed solve;
+  fp16           the fp16-message form on the same pair, with its energy gap and label
+                 disagreement against the FP64 oracle's result (tests/golden);
+  c2             the 384x288 D16 + 450x375 D64 pairs as one batch graph, checked against the
+                 oracle;
+  e2e            bps_stereo_host from pinned host buffers, copies inside the timed region;
+  cpu_baseline   the C oracle on a bounded crop of the same pair, which the GPU must match.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,19 +39,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpix·disp/s (cost vol + BP) at equal energy; plain int32 vs FP16/learned/batched"
 UNIT = "Mpix·disp/s"
-WORKLOAD = ["tsukuba_384x288_d16", "teddy_450x375_d64"]
+HEADLINE = "hd_1920x1080_d256"
+C2_PAIRS = ["tsukuba_384x288_d16", "teddy_450x375_d64"]
 TRUNC_DATA, LEVELS, ITERS, LAM, TRUNC = 20, 4, 10, 10, 2
 FLUSH_BYTES = 256 << 20
+# the bounded CPU sample: a central 384x216 crop of the full-HD pair (1/25 of its pixels), all
+# 256 labels, the same window and solve parameters
+CROP = (768, 432, 384, 216)  # x0, y0, width, height
+GOLDEN = os.path.join(ROOT, "tests", "golden", HEADLINE + ".json")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-large", action="store_true", help="skip the HBM-sized roofline_large measurement")
+    ap.add_argument("--no-extras", action="store_true", help="headline only: no fp16 and c2 keys")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned choices: read if present, else measured and written")
     ap.add_argument("--warmstart-report", action="store_true",
@@ -66,12 +79,17 @@ def parse():
                     help="instead of the benchmark line: every message form (int32, u8, fp16) on the benchmark "
                          "pairs and the 1920x1080 D256 pair: throughput, energy, fp16 energy gap against the FP64 "
                          "oracle and bad-pixel rates, one JSON line")
+    ap.add_argument("--launch-report", action="store_true",
+                    help="instead of the benchmark line: per-launch times (profile mode) and recomputed pixels of "
+                         "every sweep launch of the headline pair, one JSON line")
     ap.add_argument("--batch-form", choices=["u8", "fp16"], default="u8",
                     help="message form of --batch-report")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only run warm-up + steps of the workload (no timing, no JSON): the command to profile")
+    ap.add_argument("--form", choices=["u8", "fp16"], default="u8", help="with --ncu-case: the message form")
     ap.add_argument("--workload", default=None,
-                    help="with --ncu-case: one named pair of paper_1709_06509_gb300.synth.WORKLOADS instead of the default two")
+                    help="with --ncu-case: one named pair of paper_1709_06509_gb300.synth.WORKLOADS instead of "
+                         "the full-HD pair")
     return ap.parse_args()
 
 
@@ -83,70 +101,110 @@ def work_units(pairs) -> int:
     return sum(p.left.shape[0] * p.left.shape[1] * p.D for p, _ in pairs)
 
 
-def load_pairs(rank: int):
-    from paper_1709_06509_gb300 import shard, synth
+def crop_pair(pair):
+    """The bounded CPU sample of the full-HD pair (a StereoPair of the crop)."""
+    from paper_1709_06509_gb300 import synth
 
-    return [synth.workload_pair(name, shard.seed_offset(rank)) for name in WORKLOAD]
+    x0, y0, w, h = CROP
+    sl = (slice(y0, y0 + h), slice(x0, x0 + w))
+    return synth.StereoPair(pair.left[sl].copy(), pair.right[sl].copy(), pair.disparity[sl].copy(),
+                            pair.occluded[sl].copy(), pair.D, pair.seed)
+
+
+def golden() -> dict | None:
+    try:
+        with open(GOLDEN) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def sha(a) -> str:
+    import numpy as np
+
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
 
-def oracle_pass(pairs) -> float:
+def oracle_run(pair, window):
+    """The whole integer path through the oracle: disparities, energy and trace."""
     import oracle
 
+    c = oracle.quantise(oracle.ncc(pair.left, pair.right, pair.D, window), TRUNC_DATA)
+    d, tr = oracle.bp_wta(c, LEVELS, ITERS, LAM, TRUNC, skip=True)
+    return {"disp": d, "trace": tr, "energy": oracle.energy(c, d, LAM, TRUNC)}
+
+
+def timed_oracle_run(pair, window):
     t0 = time.perf_counter()
-    for pair, window in pairs:
-        oracle.stereo_int(pair.left, pair.right, pair.D, window, TRUNC_DATA, LEVELS, ITERS, LAM, TRUNC, skip=True)
-    return time.perf_counter() - t0
+    r = oracle_run(pair, window)
+    return r, time.perf_counter() - t0
 
 
-def cpu_baseline(pairs) -> dict:
-    oracle_pass(pairs[:1])  # load / build the library outside the timing
-    t = oracle_pass(pairs)
-    return {"value": work_units(pairs) / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one pass of both workload pairs (384x288 D16 + 450x375 D64) through the "
-                      f"single-threaded C oracle with the skip on, {t:.1f} s"}
-
-
-def cpu_baseline_parallel(pairs) -> dict | None:
-    """The same pass on the oracle's OpenMP build (NCC rows and the pixels of one colour split
-    over every host core; the same results bit for bit); None where gcc has no OpenMP."""
+def cpu_baselines(crop, window) -> tuple[dict, dict | None, dict]:
+    """The oracle as it stands on the crop: single-threaded, and its OpenMP build over every host
+    core (same bits).  Returns (cpu_baseline, cpu_baseline_parallel or None, oracle result)."""
     import oracle
 
-    if not oracle.openmp_available():
-        return None
-    with oracle.openmp(os.cpu_count() or 1) as n:
-        oracle_pass(pairs[:1])
-        t = oracle_pass(pairs)
-    return {"value": work_units(pairs) / t / 1e6, "unit": UNIT, "cores": n, "kind": "oracle (OpenMP build)",
-            "sample": "one pass of both workload pairs (384x288 D16 + 450x375 D64) through the "
-                      f"C oracle built with OpenMP, {n} threads, skip on, {t:.1f} s"}
+    from paper_1709_06509_gb300 import synth
+
+    tiny, w = synth.workload_pair("tiny_96x72_d16")
+    oracle_run(tiny, w)  # load / build the library outside the timing
+    units = crop.left.size * crop.D
+    ref, t = timed_oracle_run(crop, window)
+    what = (f"a central {CROP[2]}x{CROP[3]} crop of the 1920x1080 D256 pair (1/25 of its pixels, all 256 labels, "
+            "9x9 window, 4 scales, 10 iterations, skip on) through the C oracle")
+    base = {"value": units / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{what}, single-threaded, {t:.1f} s"}
+    par = None
+    if oracle.openmp_available():
+        with oracle.openmp(os.cpu_count() or 1) as n:
+            r2, t2 = timed_oracle_run(crop, window)
+        if not (r2["disp"] == ref["disp"]).all() or r2["energy"] != ref["energy"]:
+            raise RuntimeError("the OpenMP build of the oracle disagrees with the serial build")
+        par = {"value": units / t2 / 1e6, "unit": UNIT, "cores": n, "kind": "oracle (OpenMP build)",
+               "sample": f"{what}, {n} threads, {t2:.1f} s"}
+    return base, par, ref
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands (OpenMP build, every host core) on the bounded
+    crop of the headline pair, one crop per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle
+
     from paper_1709_06509_gb300 import synth
 
-    pair = synth.workload_pair(WORKLOAD[0])
-    sample = [pair]
-    for _ in range(args.warmup):
-        oracle_pass(sample)
-    times = [oracle_pass(sample) for _ in range(args.steps)]
+    pair, window = synth.workload_pair(HEADLINE)
+    crop = crop_pair(pair)
+    units = crop.left.size * crop.D
+    cores = 1
+    ctx = oracle.openmp(os.cpu_count() or 1) if oracle.openmp_available() else None
+    if ctx:
+        cores = ctx.__enter__()
+    try:
+        for _ in range(args.warmup):
+            oracle_run(crop, window)
+        times = [timed_oracle_run(crop, window)[1] for _ in range(args.steps)]
+    finally:
+        if ctx:
+            ctx.__exit__(None, None, None)
     total = sum(times)
-    units = work_units(sample)
     value = units * args.steps / total / 1e6
+    sample = (f"a central {CROP[2]}x{CROP[3]} crop of the 1920x1080 D256 pair per step (1/25 of its pixels, all "
+              f"256 labels), the C oracle's OpenMP build on {cores} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "tsukuba_384x288_d16 (one pair per step: the smaller pair of the "
-                               "384x288 D16 + 450x375 D64 workload)", "window": 7, "trunc_data": TRUNC_DATA,
-                   "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC, "fast_skip": True},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "the 384x288 D16 pair per step, single-threaded C oracle"},
+        "config": {"workload": "1920x1080 D256 pair (bounded sample: a central crop per step)", "window": 9,
+                   "trunc_data": TRUNC_DATA, "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC,
+                   "fast_skip": True, "crop": list(CROP)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -226,52 +284,10 @@ def ncu_traffic(profile_name: str):
         return None
 
 
-def sweep_bytes(st, trace) -> float:
-    """Algorithmic bytes of the half-sweeps of one solve of the u8 form, given its trace
-    (recomputed pixels per half-sweep, coarsest scale first): per recomputed pixel its int16
-    cost, 4 incoming and 4 old outgoing uint8 messages read (the old ones for the skip's
-    change test) and 4 uint8 messages written, Dp labels each; plus the 1-byte skip flag of
-    every slot of the scale per launch."""
-    from paper_1709_06509_gb300 import level_dims
-
+def pixel_labels_recomputed(st, trace) -> float:
+    """Sum over the half-sweeps of a solve of (recomputed pixels) x Dp (labels a pixel moves)."""
     Dp = (st.D + 15) // 16 * 16
-    per = ITERS * 2
-    total = 0.0
-    for k, (w, h) in enumerate(level_dims(st.W, st.H, st.levels)[::-1]):
-        total += float(trace[k * per:(k + 1) * per].sum()) * Dp * (2 + 12 * 1) + per * h * ((w + 1) // 2)
-    return total
-
-
-def large_roofline(dev, flush) -> dict:
-    """The same sweep kernel on an HBM-sized working set: the 960x540 pair with D=256 (9x9
-    window; 1.1 GB of state, far above L2).  Per-launch CUDA events over every finest-scale
-    half-sweep of three solves; algorithmic bytes from the live trace as in sweep_bytes()."""
-    import paper_1709_06509_gb300 as bps
-    from paper_1709_06509_gb300 import level_dims, synth
-
-    pair, window = synth.workload_pair("qhd_960x540_d256")
-    H, W = pair.left.shape
-    st = bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev)
-    L = torch_from(pair.left, dev)
-    R = torch_from(pair.right, dev)
-    Dp = (st.D + 15) // 16 * 16
-    w0, h0 = level_dims(W, H, LEVELS)[0]
-    slots = h0 * ((w0 + 1) // 2)
-    ms, nbytes = 0.0, 0.0
-    for _ in range(3):
-        flush.fill_(2)
-        st.build_cost_volume(L, R, window, TRUNC_DATA)
-        st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
-        t = st.read_launch_times()[-2 * ITERS:]
-        tr = st.get_trace()[-2 * ITERS:]
-        ms += float(t.sum())
-        nbytes += float(tr.sum()) * Dp * (2 + 12) + len(t) * slots
-    st.close()
-    hbm, kind = peaks()
-    achieved = nbytes / (ms / 1e3) / 1e9
-    return {"workload": "960x540 D256 pair, 9x9 window, finest-scale half-sweeps", "bound": "hbm",
-            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "sweep_u8_kernel", "peak_kind": kind}
+    return float(trace.sum()) * Dp
 
 
 def torch_from(a, dev):
@@ -287,6 +303,36 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def time_region(fn, steps, flush, stream, flush_value=1) -> list[float]:
+    """CUDA-event time (ms) of each of `steps` calls of fn on `stream`; L2 flushed before each,
+    outside the events."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_((flush_value + k) & 0xFF)
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def pair_launches(bps, st) -> int:
+    """Kernels one bps_stereo call of a context launches: the NCC kernel (scale 1 fused), the
+    pyramid kernels of scales 2.. (two scales a launch), the solve-start kernel, one copy kernel
+    per scale that does not start from its parent's records itself, 2 * ITERS half-sweeps per
+    scale (one launch for a cluster scale), and the read-out."""
+    if st.msg_type == bps.BPS_MSG_FP16:
+        # float costs: scale 1 is not fused into the NCC kernel; every finer scale's start is copied
+        return 1 + LEVELS // 2 + 1 + (LEVELS - 1) + 2 * ITERS * LEVELS + 1
+    vs = st.variants()
+    cluster_scales = [lvl for lvl in range(LEVELS) if vs[lvl] & bps.BPS_VARIANT_CLUSTER]
+    sweeps = sum(1 if lvl in cluster_scales else 2 * ITERS for lvl in range(LEVELS))
+    copies = sum(1 for lvl in cluster_scales if lvl < LEVELS - 1)
+    return 1 + (max(0, LEVELS - 2) + 1) // 2 + 1 + copies + sweeps + 1
 
 
 def batch_report(args):
@@ -591,6 +637,181 @@ def sparse_report(args):
     print(json.dumps(out))
 
 
+def setup_ctx(bps, autotune, pair, window, form, dev, tune_cache):
+    """A context for `pair` in message form `form`, its kernel choices autotuned (untimed)."""
+    H, W = pair.left.shape
+    st = bps.Stereo(W, H, pair.D, LEVELS, form, device=dev)
+    L, R = torch_from(pair.left, dev), torch_from(pair.right, dev)
+    tuned = {}
+    if form == bps.BPS_MSG_U8:  # the NCC shapes are tuned on the u8 form's int16 costs
+        tuned["ncc_shape"] = list(autotune.tune_ncc(st, L, R, window, TRUNC_DATA, cache=tune_cache))
+    tuned["sweep_variants"] = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3, cache=tune_cache)
+    return st, L, R, tuned
+
+
+def solve_roofline(st, L, R, window, steps, flush, stream, per_label: int, per_label_change: int) -> dict:
+    """The red-black half-sweeps of one solve as the dominant kernel: every sweep launch of the
+    4 scales.  Time: graph replays of bps_bp_solve (CUDA events on the launching stream, L2
+    flushed before each).  Bytes: (8s + c) per recomputed pixel-label from the live trace."""
+    st.build_cost_volume(L, R, window, TRUNC_DATA)
+    solve = lambda: st.bp_solve(ITERS, LAM, TRUNC, skip=True, graph=True)
+    for _ in range(3):
+        solve()
+    ms = time_region(solve, steps, flush, stream, flush_value=11)
+    trace = st.get_trace()
+    launches = 2 * ITERS * LEVELS
+    solve_ms = statistics.median(ms)
+    pl = pixel_labels_recomputed(st, trace)
+    hbm, kind = peaks()
+    achieved = pl * per_label / (solve_ms / 1e3) / 1e9
+    return {"achieved": achieved, "peak": hbm, "frac": achieved / hbm, "peak_kind": kind,
+            "solve_ms": solve_ms, "launches_per_solve": launches, "avg_launch_us": 1e3 * solve_ms / launches,
+            "algorithmic_bytes_per_launch": pl * per_label / launches,
+            "pixel_labels_recomputed_per_solve": pl,
+            "frac_with_change_test": pl * per_label_change / (solve_ms / 1e3) / 1e9 / hbm}
+
+
+def stage_times(st, L, R, window, disp, flush, stream, reps=10) -> dict:
+    """Median CUDA-event time of the cost-volume stage (NCC + pyramid launches)."""
+    cost = time_region(lambda: st.build_cost_volume(L, R, window, TRUNC_DATA), reps, flush, stream, 21)
+    return {"cost_volume_ms": statistics.median(cost)}
+
+
+def check_headline(st, disp, gold) -> dict:
+    """The timed pair's results against the oracle's (tests/golden, written by a script that calls
+    only the oracle): disparity digest, int64 energy, skip trace.  Raises on a mismatch."""
+    import numpy as np
+
+    d = disp.cpu().numpy().astype("<i4")
+    e = int(st.energy(disp, LAM, TRUNC)[0].item())
+    tr = st.get_trace()
+    g = gold["int"]
+    ok = sha(d) == g["disp_sha256"] and e == g["energy"] and [int(v) for v in tr] == g["trace"]
+    if not ok:
+        raise RuntimeError(f"full-HD results differ from the oracle's: energy {e} vs {g['energy']}, "
+                           f"digest {sha(d)[:16]} vs {g['disp_sha256'][:16]}")
+    return {"disp_sha256": sha(d), "energy": e, "oracle_energy": g["energy"], "trace_equal": True,
+            "source": "tests/golden/" + HEADLINE + ".json"}
+
+
+def fp16_key(bps, autotune, pair, window, dev, args, flush, stream, gold) -> dict:
+    """The fp16-message form on the headline pair: throughput, and its energy gap and label
+    disagreement against the FP64 oracle's result."""
+    import numpy as np
+    import torch
+
+    st, L, R, tuned = setup_ctx(bps, autotune, pair, window, bps.BPS_MSG_FP16, dev, args.tune_cache)
+    disp = torch.empty(pair.left.shape, dtype=torch.int32, device=dev)
+    step = lambda: st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True, out=disp)
+    for _ in range(args.warmup):
+        step()
+    ms = time_region(step, args.steps, flush, stream, flush_value=41)
+    total = sum(ms)
+    units = pair.left.size * pair.D
+    _, ef = st.energy(disp, LAM, TRUNC)
+    e = float(ef.item())
+    d = disp.cpu().numpy()
+    out = {"value": units * len(ms) / (total / 1e3) / 1e6, "unit": UNIT, "ms_per_step": total / len(ms),
+           "dtype": "fp16 messages, fp32 costs and arithmetic, FP64 energy", "energy_fp64": e,
+           "autotuned": tuned}
+    if gold:
+        g = gold["f64"]
+        ref = float.fromhex(g["energy_hex"])
+        out["energy_gap_rel"] = (e - ref) / ref
+        path = os.path.join(ROOT, "tests", "golden", g["disp_file"])
+        if os.path.exists(path):
+            ref_d = np.load(path)["disp"].astype(np.int32)
+            out["label_disagreement"] = float((d != ref_d).mean())
+        out["oracle"] = "FP64 oracle of the float-message form (tests/golden/" + HEADLINE + ".json)"
+    roof = solve_roofline(st, L, R, window, max(3, min(args.steps, 20)), flush, stream, 2 * 8 + 4, 2 * 12 + 4)
+    out["roofline"] = {"bound": "hbm", "achieved": roof["achieved"], "peak": roof["peak"], "unit": "GB/s",
+                       "frac": roof["frac"], "bytes_model": "(8s + c) = 20 B per recomputed pixel-label "
+                       "(s = 2 B fp16 message, c = 4 B fp32 cost)", "solve_ms": roof["solve_ms"]}
+    out["gpu_launches_per_step"] = pair_launches(bps, st)
+    st.close()
+    return out
+
+
+def c2_key(bps, autotune, dev, args, flush, stream, rank) -> dict:
+    """The 384x288 D16 + 450x375 D64 pairs as one batch graph (concurrent chains), L2 flushed
+    between steps, results checked against the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1709_06509_gb300 import shard, synth
+
+    pairs = [synth.workload_pair(n, shard.seed_offset(rank)) for n in C2_PAIRS]
+    ctxs, tuned = [], {}
+    for pair, window in pairs:
+        st, L, R, t = setup_ctx(bps, autotune, pair, window, bps.BPS_MSG_U8, dev, args.tune_cache)
+        ctxs.append((st, L, R, window))
+        tuned[f"{st.W}x{st.H}_D{st.D}"] = t
+    sts = [c[0] for c in ctxs]
+    Ls, Rs, ws = [c[1] for c in ctxs], [c[2] for c in ctxs], [c[3] for c in ctxs]
+    outs = [torch.empty(p.left.shape, dtype=torch.int32, device=dev) for p, _ in pairs]
+    batch = bps.Batch(sts)
+    joint = autotune.tune_batch(batch, sts, Ls, Rs, ws, TRUNC_DATA, ITERS, LAM, TRUNC, cache=args.tune_cache)
+    for st, vs in zip(sts, joint):
+        tuned[f"{st.W}x{st.H}_D{st.D}"]["sweep_variants"] = vs
+    step = lambda: batch.stereo(Ls, Rs, ws, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, outs=outs)
+    for _ in range(args.warmup):
+        step()
+    steps = max(args.steps, 20)
+    ms = time_region(step, steps, flush, stream, flush_value=51)
+    total = sum(ms)
+    units = work_units(pairs)
+    res = {"workload": "384x288 D16 + 450x375 D64 pairs (7x7 window; one step = both, one batch graph)",
+           "value": units * steps / (total / 1e3) / 1e6, "unit": UNIT, "ms_per_step": total / steps,
+           "l2": "flushed between timed steps (256 MiB write)", "autotuned": tuned}
+    if rank == 0:
+        import oracle
+
+        ctx = oracle.openmp(os.cpu_count() or 1) if oracle.openmp_available() else None
+        if ctx:
+            ctx.__enter__()
+        try:
+            for (pair, window), (st, _, _, _), o in zip(pairs, ctxs, outs):
+                ref = oracle_run(pair, window)
+                e = int(st.energy(o, LAM, TRUNC)[0].item())
+                if not np.array_equal(o.cpu().numpy(), ref["disp"]) or e != ref["energy"] or \
+                        not np.array_equal(st.get_trace(), ref["trace"]):
+                    raise RuntimeError(f"{st.W}x{st.H} D{st.D}: the timed batch's results differ from the oracle's")
+        finally:
+            if ctx:
+                ctx.__exit__(None, None, None)
+        res["oracle_match"] = "disparities, int64 energies and skip traces equal to the oracle's"
+    batch.close()
+    for st in sts:
+        st.close()
+    return res
+
+
+def launch_report(args):
+    """Per-launch CUDA-event times (profile mode) of every sweep launch of the headline pair, with
+    the pixels each recomputed."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    name = args.workload or HEADLINE
+    pair, window = synth.workload_pair(name)
+    form = bps.BPS_MSG_FP16 if args.form == "fp16" else bps.BPS_MSG_U8
+    st, L, R, tuned = setup_ctx(bps, autotune, pair, window, form, dev, args.tune_cache)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    runs = []
+    for _ in range(3):
+        flush.fill_(3)
+        st.build_cost_volume(L, R, window, TRUNC_DATA)
+        st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
+        runs.append(st.read_launch_times())
+    t = [min(r[k] for r in runs) for k in range(len(runs[0]))]
+    print(json.dumps({"workload": name, "form": args.form, "autotuned": tuned, "trace": [int(v) for v in st.get_trace()],
+                      "launch_ms": t, "total_ms": sum(t)}))
+    st.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -605,12 +826,14 @@ def main():
         return approx_report(args)
     if args.warmstart_report:
         return warmstart_report(args)
+    if args.launch_report:
+        return launch_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     rank, world, local = dist_env()
     import torch
 
     import paper_1709_06509_gb300 as bps
-    from paper_1709_06509_gb300 import _build
+    from paper_1709_06509_gb300 import _build, autotune, shard, synth
 
     if not os.path.exists(bps.LIB_PATH) or _build.is_stale():
         if rank == 0 or world == 1:
@@ -624,42 +847,16 @@ def main():
         dist.barrier()
         _build.build()  # no-op once rank 0 has built
 
-    pairs = load_pairs(rank)
-    if args.ncu_case and args.workload:
-        from paper_1709_06509_gb300 import synth
-
-        pairs = [synth.workload_pair(args.workload)]
-    ctxs, inputs, outs = [], [], []
-    for pair, window in pairs:
-        H, W = pair.left.shape
-        st = bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev)
-        ctxs.append((st, window))
-        inputs.append((torch.from_numpy(pair.left).to(dev), torch.from_numpy(pair.right).to(dev)))
-        outs.append(torch.empty((H, W), dtype=torch.int32, device=dev))
+    name = args.workload if (args.ncu_case and args.workload) else HEADLINE
+    pair, window = synth.workload_pair(name, shard.seed_offset(rank))
+    form = bps.BPS_MSG_FP16 if (args.ncu_case and args.form == "fp16") else bps.BPS_MSG_U8
+    st, L, R, tuned = setup_ctx(bps, autotune, pair, window, form, dev, args.tune_cache)
+    disp = torch.empty(pair.left.shape, dtype=torch.int32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    # pick each scale's sweep kernel variant by measurement (untimed; results are identical)
-    from paper_1709_06509_gb300 import autotune
-
-    tuned = {}
-    for (st, window), (L, R) in zip(ctxs, inputs):
-        shape = autotune.tune_ncc(st, L, R, window, TRUNC_DATA, cache=args.tune_cache)
-        variants = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3, cache=args.tune_cache)
-        tuned[f"{st.W}x{st.H}_D{st.D}"] = {"ncc_shape": list(shape), "sweep_variants": variants}
-
-    # one step = every pair of the workload as one batch: one CUDA graph whose branches are the
-    # pairs' launch chains, so the pairs run concurrently
-    batch = bps.Batch([st for st, _ in ctxs])
-    windows = [w for _, w in ctxs]
-    Ls, Rs = [L for L, _ in inputs], [R for _, R in inputs]
-    # the pairs share the GPU: refine the choices jointly on the batch step (untimed)
-    joint = autotune.tune_batch(batch, [st for st, _ in ctxs], Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC,
-                                cache=args.tune_cache)
-    for (st, _), vs in zip(ctxs, joint):
-        tuned[f"{st.W}x{st.H}_D{st.D}"]["sweep_variants"] = vs
 
     def step():
-        batch.stereo(Ls, Rs, windows, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, outs=outs)
+        st.stereo(L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, skip=True, graph=True, out=disp)
 
     for _ in range(args.warmup):
         step()
@@ -669,7 +866,6 @@ def main():
             step()
         torch.cuda.synchronize()
         return
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", "") or "")
     sampler = ClockSampler(("GPU-" + uuid if uuid and not uuid.startswith("GPU-") else uuid) or str(local))
@@ -678,119 +874,120 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.2)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)  # evict the previous step's working set from L2 (outside the events)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    ms = time_region(step, args.steps, flush, stream)
     clocks = sampler.stop()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    total_ms = sum(ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    units = work_units(pairs) * world
+    units = pair.left.size * pair.D * world
     value = units * args.steps / (total_ms / 1e3) / 1e6
 
-    # dominant kernel: the red-black sweep (every launch of a step, all scales, both pairs).
-    # CUDA events around each launch, on the launching stream, with the same L2 flush per pair
-    prof_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
-    for _ in range(max(3, min(args.steps, 20))):
-        for (st, window), (L, R), out in zip(ctxs, inputs, outs):
-            flush.fill_(1)
-            st.build_cost_volume(L, R, window, TRUNC_DATA)
-            st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
-            times = st.read_launch_times()
-            prof_bytes += sweep_bytes(st, st.get_trace())
-            prof_ms += float(times.sum())
-            prof_launches += len(times)
-    hbm, peak_kind = peaks()
-    achieved = prof_bytes / (prof_ms / 1e3) / 1e9
-    traffic = ncu_traffic("sweep_u8_tsukuba_teddy_pairs.txt")
+    # the timed step's results: against the oracle's (rank 0 holds the golden pair's seeds)
+    gold = golden() if rank == 0 else None
+    verified = check_headline(st, disp, gold) if gold else {"oracle_match": "no golden file"}
 
-    # end to end through the public API with host buffers (pinned): bps_batch_stereo_host copies
-    # both pairs' images in, runs the batch, and copies disparities and energies out, every step
-    host_in_l = [torch.from_numpy(p.left).pin_memory() for p, _ in pairs]
-    host_in_r = [torch.from_numpy(p.right).pin_memory() for p, _ in pairs]
-    host_out = [torch.empty(p.left.shape, dtype=torch.int32).pin_memory() for p, _ in pairs]
+    # dominant kernel: the red-black half-sweeps of the solve, graph-timed, algorithmic bytes
+    # (8s + c) = 10 B per recomputed pixel-label of the u8 form (1 B messages, 2 B costs); the
+    # change test of the skip reads the 4 old outgoing messages too: (12s + c) = 14 B
+    roof = solve_roofline(st, L, R, window, max(3, min(args.steps, 20)), flush, stream, 10, 14)
+    stages = stage_times(st, L, R, window, disp, flush, stream)
+    traffic = ncu_traffic(f"sweep_u8_{HEADLINE}.txt")
+    ncc_bytes = pair.left.size * ((pair.D + 15) // 16 * 16) * 2 * 1.25  # int16 costs of scale 0, plus scale 1
+
+    # end to end through the public API from pinned host buffers: every step copies the images in
+    # and the disparities and energy out (bps_stereo_host, one recorded graph per call)
+    hL = torch.from_numpy(pair.left).pin_memory()
+    hR = torch.from_numpy(pair.right).pin_memory()
+    hD = torch.empty(pair.left.shape, dtype=torch.int32).pin_memory()
+    hE = torch.zeros(1, dtype=torch.int64).pin_memory()
+    flags = bps.BPS_FLAG_FAST_SKIP | bps.BPS_FLAG_GRAPH
+    host = lambda f: bps.bps_stereo_host(st.ctx, hL, hR, pair.left.shape[1], window, TRUNC_DATA, ITERS, LAM, TRUNC,
+                                         f, hD, hE, None, stream)
     for _ in range(3):
-        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
+        host(flags)
     torch.cuda.synchronize()
-    # every call synchronous (the host waits for each step's results)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out)
+        host(flags)
     e2e_sync_s = time.perf_counter() - t0
-    # queued: one call per step returns once its copies and work are on the stream (BPS_FLAG_ASYNC),
-    # the host synchronises once after the last step; each step still copies its images in and its
-    # disparities and energies out
-    for d in host_out:
-        d.fill_(-1)
+    hD.fill_(-1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        batch.stereo_host(host_in_l, host_in_r, windows, TRUNC_DATA, ITERS, LAM, TRUNC, h_disps=host_out, sync=False)
-    torch.cuda.current_stream().synchronize()
+        host(flags | bps.BPS_FLAG_ASYNC)
+    stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    for d, o in zip(host_out, outs):  # the host results are the device path's
-        if not torch.equal(d, o.cpu()):
-            raise RuntimeError("host-entry disparities differ from the device entry's")
+    if not torch.equal(hD, disp.cpu()):
+        raise RuntimeError("host-entry disparities differ from the device entry's")
     if world > 1:
         t = torch.tensor([e2e_s, e2e_sync_s], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s, e2e_sync_s = (float(v) for v in t.tolist())
-    h2d = sum(2 * p.left.size for p, _ in pairs)
-    d2h = sum(4 * p.left.size + 8 for p, _ in pairs)
-
-    # per pair: the NCC kernel (scale 1 fused), the pyramid kernels of scales 2.., the solve-start
-    # kernel, one upsample kernel per scale below the coarsest, 2 * ITERS sweeps per scale, WTA
-    # (the pyramid kernel forms two scales a launch; a scale's first half-sweep starts from its
-    # parent's messages itself, except for a one-launch cluster scale, which keeps the copy kernel)
-    def pair_launches(st):
-        vs = st.variants()
-        cluster_scales = [lvl for lvl in range(LEVELS) if vs[lvl] & bps.BPS_VARIANT_CLUSTER]
-        sweeps = sum(1 if lvl in cluster_scales else 2 * ITERS for lvl in range(LEVELS))
-        copies = sum(1 for lvl in cluster_scales if lvl < LEVELS - 1)
-        return 1 + (max(0, LEVELS - 2) + 1) // 2 + 1 + copies + sweeps + 1
-
-    launches_per_step = sum(pair_launches(st) for st, _ in ctxs)
-    large = large_roofline(dev, flush) if rank == 0 and not args.no_large else None
+    h2d = 2 * pair.left.size
+    d2h = 4 * pair.left.size + 8
+    launches_per_step = pair_launches(bps, st)
+    extras = {}
+    if not args.no_extras:
+        extras["fp16"] = fp16_key(bps, autotune, pair, window, dev, args, flush, stream, gold)
+        extras["c2"] = c2_key(bps, autotune, dev, args, flush, stream, rank)
     if rank == 0:
+        hbm, kind = roof["peak"], roof["peak_kind"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "384x288 D16 + 450x375 D64 pairs (one step = both)", "window": 7,
+            "config": {"workload": "1920x1080 D256 pair (one step = one pair)", "window": window,
                        "trunc_data": TRUNC_DATA, "levels": LEVELS, "iters": ITERS, "lambda": LAM, "trunc": TRUNC,
                        "fast_skip": True, "message_storage": "uint8 (exact: 0 <= m <= lambda*trunc)",
-                       "cost_storage": "int16", "cuda_graph": True, "batch": "both pairs, concurrent graph branches",
-                       "autotuned": tuned, "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "kernel": "sweep_u8_kernel (all scales, both pairs)",
-                         "peak_kind": peak_kind, "launches_timed": prof_launches},
+                       "cost_storage": "int16", "cuda_graph": True, "autotuned": tuned,
+                       "l2": "working set 4.3 GB, far above L2; a 256 MiB buffer is also written between timed "
+                             "steps", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": roof["achieved"], "peak": hbm, "unit": "GB/s",
+                         "frac": roof["frac"], "traffic": traffic,
+                         "kernel": "red-black half-sweep (sweep_u8_* kernels, every launch of the 4 scales)",
+                         "bytes_model": "(8s + c) = 10 B per recomputed pixel-label (s = 1 B uint8 message, "
+                                        "c = 2 B int16 cost), pixels from the live skip trace",
+                         "timing": "graph replays of bps_bp_solve, CUDA events on the launching stream, median",
+                         "peak_kind": kind, **{k: roof[k] for k in ("solve_ms", "launches_per_solve", "avg_launch_us",
+                                                                    "algorithmic_bytes_per_launch",
+                                                                    "frac_with_change_test")}},
+            "roofline_ncc": {"bound": "hbm", "achieved": ncc_bytes / (stages["cost_volume_ms"] / 1e3) / 1e9,
+                             "peak": hbm, "unit": "GB/s",
+                             "frac": ncc_bytes / (stages["cost_volume_ms"] / 1e3) / 1e9 / hbm,
+                             "bytes_model": "int16 data costs written: scale 0 plus the fused scale 1 (x1.25)",
+                             **stages},
             "e2e": {"value": units * args.steps / e2e_s / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "mode": "bps_batch_stereo_host once per step from pinned host buffers, queued on one "
-                            "stream (BPS_FLAG_ASYNC), one synchronisation after the last step",
+                    "mode": "bps_stereo_host once per step from pinned host buffers, queued on one stream "
+                            "(BPS_FLAG_ASYNC), one synchronisation after the last step",
                     "value_synchronous": units * args.steps / e2e_sync_s / 1e6},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
+            "verified": verified,
+            **extras,
         }
-        if large:
-            line["roofline_large"] = large
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(pairs)
-            par = cpu_baseline_parallel(pairs)
+            crop = crop_pair(pair)
+            base, par, ref = cpu_baselines(crop, window)
+            with bps.Stereo(CROP[2], CROP[3], pair.D, LEVELS, bps.BPS_MSG_U8, device=dev) as sc:
+                cd = sc.stereo(torch_from(crop.left, dev), torch_from(crop.right, dev), window, TRUNC_DATA, ITERS,
+                               LAM, TRUNC, graph=True)
+                ce = int(sc.energy(cd, LAM, TRUNC)[0].item())
+                import numpy as np
+
+                if not np.array_equal(cd.cpu().numpy(), ref["disp"]) or ce != ref["energy"] or \
+                        not np.array_equal(sc.get_trace(), ref["trace"]):
+                    raise RuntimeError("GPU results on the CPU sample differ from the oracle's")
+            base["gpu_match"] = "the GPU's disparities, energy and trace on the sample equal the oracle's"
+            line["cpu_baseline"] = base
             if par:
                 line["cpu_baseline_parallel"] = par
         print(json.dumps(line))
-    batch.close()
-    for st, _ in ctxs:
-        st.close()
+    st.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

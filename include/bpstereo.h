@@ -58,8 +58,9 @@ typedef struct bps_ctx bps_ctx;
 /* flags for bps_bp_solve / bps_stereo */
 #define BPS_FLAG_FAST_SKIP 1  /* fast-converging BP: skip pixels whose inputs did not change */
 #define BPS_FLAG_WARM_START 2 /* start the coarsest scale from d_init_msgs instead of zeros */
-#define BPS_FLAG_GRAPH 4      /* bps_stereo*: record the launch sequence once as a CUDA graph
-                                 and replay it while the arguments stay the same */
+#define BPS_FLAG_GRAPH 4      /* bps_stereo*, bps_bp_solve: record the launch sequence once as a
+                                 CUDA graph and replay it while the arguments and the kernel
+                                 choices (variants, skip rule, candidates) stay the same */
 #define BPS_FLAG_PROFILE 8    /* bps_bp_solve: time the BP launches with CUDA events (read with
                                  bps_read_profile / bps_read_launch_times); not with BPS_FLAG_GRAPH */
 #define BPS_FLAG_PERSISTENT 16 /* run the whole solve as one persistent cooperative launch instead
@@ -110,7 +111,10 @@ size_t bps_workspace_bytes(int W, int H, int D, int levels, int msg_type);
 int bps_create(bps_ctx **out, int W, int H, int D, int levels, int msg_type, void *d_workspace,
                size_t workspace_bytes);
 
-/* Destroy a context (synchronises its internal stream; frees what it allocated). NULL is a no-op. */
+/* Destroy a context: synchronises its internal stream and frees what it allocated (cudaFree of
+ * a context-owned workspace waits for the work in flight on the device; a caller-owned
+ * workspace must not be reused before the context's work on the caller's streams is done).
+ * NULL is a no-op. */
 int bps_destroy(bps_ctx *ctx);
 
 /*
@@ -142,7 +146,9 @@ int bps_build_cost_volume(bps_ctx *ctx, const uint8_t *d_left, const uint8_t *d_
  * float for BPS_MSG_FP16, direction = neighbour the message comes from: up, down, left,
  * right); every finer pixel starts from its parent's messages.  With BPS_FLAG_FAST_SKIP a
  * pixel is recomputed only if one of its incoming messages changed since its last update;
- * the result is identical to running without the skip.
+ * the result is identical to running without the skip.  With BPS_FLAG_GRAPH (not with
+ * BPS_FLAG_PROFILE) the solve is recorded once as a CUDA graph and replayed while its
+ * arguments (d_init_msgs included, as a pointer) and the context's kernel choices hold.
  * Errors: BPS_ERR_STATE (no cost volume yet), BPS_ERR_ARG (levels, iters > BPS_MAX_ITERS,
  * lambda < 0, trunc < 0, lambda*(D+trunc) >= 2^24, warm start without d_init_msgs),
  * BPS_ERR_UNSUPPORTED (BPS_MSG_U8 with lambda*trunc > 255).
@@ -377,8 +383,9 @@ int bps_warmnet_messages(const float *d_pred, int H, int W, int D, int cap, int3
 /*
  * Energy of a labelling without allocating any memory.  The paper has no counterpart:
  * this entry point serves callers that cannot allocate device memory when they need the
- * energy -- code running while a CUDA graph is being captured, real-time loops that may not
- * wait on an allocator, programs whose allocator this library cannot reach.
+ * energy -- real-time loops that may not wait on an allocator (cudaMalloc and cudaFree may
+ * synchronise the whole device), programs whose device memory belongs to an allocator this
+ * library cannot reach, code under a fixed memory budget where a new allocation may fail.
  *
  * Computes E(d) = sum_p cost(p, d_p) + sum over right and down grid edges of
  * lambda * min(|d_p - d_q|, trunc), exactly, in int64, from
@@ -392,7 +399,8 @@ int bps_warmnet_messages(const float *d_pred, int H, int W, int D, int cap, int3
  * called.  Images with more than BPS_NOALLOC_MAX_PIXELS pixels are rejected with
  * BPS_ERR_UNSUPPORTED before anything is launched.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current: make that first
- * call before any stream capture.  All calls share the array: calls whose kernels overlap on
+ * call before any stream capture.  cudaDeviceReset invalidates the looked-up address; a call
+ * whose launch fails forgets it, and the next call looks it up again.  All calls share the array: calls whose kernels overlap on
  * the GPU (other streams, other host threads) race on it; calls in order on one stream are
  * safe.  Errors: BPS_ERR_ARG (NULL pointer, sizes < 1, lambda or trunc < 0),
  * BPS_ERR_UNSUPPORTED (too many pixels), BPS_ERR_CUDA.

@@ -85,6 +85,8 @@ def _load(openmp_build: bool) -> ctypes.CDLL:
             "oracle_bp_f64": (i, [P, i, i, i, i, i, d, i, i, P, u64, P, P]),
             "oracle_bp_rule_i32": (i, [P, i, i, i, i, i, i, i, i, i, i, P, u64, P, P]),
             "oracle_bp_rule_f64": (i, [P, i, i, i, i, i, d, i, i, d, i, P, u64, P, P]),
+            "oracle_bp_wta_i32": (i, [P, i, i, i, i, i, i, i, i, P, P]),
+            "oracle_bp_wta_f64": (i, [P, i, i, i, i, i, d, i, i, P, P]),
             "oracle_candidates": (i, [P, i, i, i, i, P]),
             "oracle_bp_sparse_i32": (i, [P, i, i, i, i, i, i, i, i, i, P, P, P]),
             "oracle_wta_sparse_i32": (i, [P, P, P, i, i, i, i, P]),
@@ -194,6 +196,23 @@ def bp(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool =
                                       int(freeze), _p(init), order_seed, _p(out), _p(trace))
     _check(rc, "oracle_bp")
     return out, trace[:ntrace]
+
+
+def bp_wta(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool = True):
+    """Hierarchical BP (exact skip, zero start) and the read-out, without the messages: the same
+    results as bp() then wta() in half the host memory.  Returns (disparities [H][W], trace)."""
+    H, W, D = cost0.shape
+    ntrace = levels * iters * 2
+    trace = np.zeros(max(ntrace, 1), dtype=np.int64)
+    disp = np.empty((H, W), dtype=np.int32)
+    if cost0.dtype == np.int32:
+        rc = lib().oracle_bp_wta_i32(_p(np.ascontiguousarray(cost0)), W, H, D, levels, iters, int(lam), trunc,
+                                     int(skip), _p(disp), _p(trace))
+    else:
+        rc = lib().oracle_bp_wta_f64(_p(np.ascontiguousarray(cost0, dtype=np.float64)), W, H, D, levels, iters,
+                                     float(lam), trunc, int(skip), _p(disp), _p(trace))
+    _check(rc, "oracle_bp_wta")
+    return disp, trace[:ntrace]
 
 
 def candidates(cost0: np.ndarray, K: int) -> np.ndarray:

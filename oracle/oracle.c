@@ -315,21 +315,24 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
                               order_seed, msg0_out, trace);
 }
 
-int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
-                       int trunc, int skip, double eps, int freeze, const double *init_coarsest,
-                       uint64_t order_seed, double *msg0_out, int64_t *trace)
+/* The hierarchy of scales (section "GPU Implementation"): the cost pyramid, then every scale
+ * coarsest first, each starting from its parent's messages.  Returns the finest scale's
+ * messages [4][H][W][D] in a buffer the caller frees, or NULL on bad arguments or allocation
+ * failure. */
+static double *bp_hierarchy(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                            int trunc, int skip, double eps, int freeze, const double *init_coarsest,
+                            uint64_t order_seed, int64_t *trace)
 {
     int Ws[32], Hs[32];
-    if (!cost0 || !msg0_out || D < 1 || levels > 32 || iters < 0 || trunc < 0 ||
-        oracle_level_dims(W, H, levels, Ws, Hs) < 0)
-        return -1;
+    if (!cost0 || D < 1 || levels > 32 || iters < 0 || trunc < 0 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return NULL;
     size_t off[33];
     off[0] = 0;
     for (int l = 0; l < levels; ++l)
         off[l + 1] = off[l] + (size_t)Ws[l] * Hs[l] * D;
     double *pyr = malloc(sizeof(double) * off[levels]);
     if (!pyr)
-        return -1;
+        return NULL;
     oracle_pyramid_f64(cost0, W, H, D, levels, pyr);
     double *parent = NULL;
     int64_t *tr = trace;
@@ -340,7 +343,7 @@ int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int
         if (!M) {
             free(pyr);
             free(parent);
-            return -1;
+            return NULL;
         }
         if (l == levels - 1) {
             if (init_coarsest)
@@ -360,10 +363,54 @@ int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int
         tr = bp_level(pyr + off[l], M, w, h, D, iters, lambda, trunc, skip, eps, freeze, order_seed, tr);
         parent = M;
     }
-    memcpy(msg0_out, parent, sizeof(double) * 4 * (size_t)W * H * D);
-    free(parent);
     free(pyr);
+    return parent;
+}
+
+int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+                       int trunc, int skip, double eps, int freeze, const double *init_coarsest,
+                       uint64_t order_seed, double *msg0_out, int64_t *trace)
+{
+    if (!msg0_out)
+        return -1;
+    double *M = bp_hierarchy(cost0, W, H, D, levels, iters, lambda, trunc, skip, eps, freeze, init_coarsest,
+                             order_seed, trace);
+    if (!M)
+        return -1;
+    memcpy(msg0_out, M, sizeof(double) * 4 * (size_t)W * H * D);
+    free(M);
     return 0;
+}
+
+int oracle_bp_wta_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda, int trunc,
+                      int skip, int32_t *disp, int64_t *trace)
+{
+    if (!disp)
+        return -1;
+    double *M = bp_hierarchy(cost0, W, H, D, levels, iters, lambda, trunc, skip, 0.0, 0, NULL, 0, trace);
+    if (!M)
+        return -1;
+    const int rc = oracle_wta_f64(cost0, M, W, H, D, disp);
+    free(M);
+    return rc;
+}
+
+int oracle_bp_wta_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda, int trunc,
+                      int skip, int32_t *disp, int64_t *trace)
+{
+    if (!cost0 || !disp || W < 1 || H < 1 || D < 1)
+        return -1;
+    const size_t n0 = (size_t)W * H * D;
+    double *c = malloc(sizeof(double) * n0);
+    if (!c)
+        return -1;
+    for (size_t k = 0; k < n0; ++k)
+        c[k] = cost0[k];
+    /* every value is an exact integer in FP64, so the FP64 argmin (lowest d on ties) is the
+     * integer read-out */
+    const int rc = oracle_bp_wta_f64(c, W, H, D, levels, iters, (double)lambda, trunc, skip, disp, trace);
+    free(c);
+    return rc;
 }
 
 int oracle_bp_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda,

@@ -77,6 +77,15 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
                   int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
                   double *msg0_out, int64_t *trace);
 
+/* Hierarchical BP (exact skip rule, zero start messages, raster order) followed by the
+ * winner-take-all read-out, without handing the messages back: disp [H][W]; trace as above.
+ * Same results as oracle_bp_* then oracle_wta_*, in half the host memory (for full-HD pairs
+ * with many labels). */
+int oracle_bp_wta_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda, int trunc,
+                      int skip, int32_t *disp, int64_t *trace);
+int oracle_bp_wta_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda, int trunc,
+                      int skip, int32_t *disp, int64_t *trace);
+
 /* The same with an approximate skip rule (section "Fast Converging BP" leaves the convergence
  * test open): a receiver is marked dirty only when its new message differs from the stored one
  * by more than eps at some label, and with freeze a recomputed pixel that marked no receiver

@@ -400,10 +400,10 @@ class Stereo:
 
     def bp_solve(self, iters: int, lam: int, trunc: int, levels: int | None = None, skip: bool = True,
                  init_msgs=None, profile: bool = False, persistent: bool = False, test_timeout: bool = False,
-                 stream=None):
+                 graph: bool = False, stream=None):
         flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_WARM_START if init_msgs is not None else 0)
         flags |= (BPS_FLAG_PROFILE if profile else 0) | (BPS_FLAG_PERSISTENT if persistent else 0)
-        flags |= BPS_FLAG_TEST_TIMEOUT if test_timeout else 0
+        flags |= (BPS_FLAG_TEST_TIMEOUT if test_timeout else 0) | (BPS_FLAG_GRAPH if graph else 0)
         bps_bp_solve(self.ctx, levels or self.levels, iters, lam, trunc, flags, init_msgs, stream)
 
     def wta_disparity(self, out=None, stream=None):

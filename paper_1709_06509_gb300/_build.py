@@ -1,6 +1,6 @@
 """Build the CUDA library libbpstereo.so in-tree with nvcc (sm_103a only).
 
-The four translation units compile in parallel, then nvcc links them into a shared
+Every translation unit (SOURCES) compiles in parallel, then nvcc links them into a shared
 library next to this file.  Nothing is installed anywhere else.
 """
 from __future__ import annotations

@@ -180,6 +180,7 @@ struct bps_ctx {
     SparseView sv{};              // sparse candidates of the finest scale (K = 0: dense)
     int last_sparse_k = 0;        // K of the last solve (0: dense)
     GraphSlot host_graph;         // bps_stereo_host: copies in, pipeline, energy, copies out
+    GraphSlot solve_graph;        // bps_bp_solve with BPS_FLAG_GRAPH
     std::vector<int> prof_span;  // half-sweeps each profiled launch covers (a cluster launch covers a scale)
 };
 
@@ -204,6 +205,9 @@ PairDesc make_desc(const bps_ctx *c) {
     d.Gp = c->Gp;
     d.trace = c->trace;
     d.disp = nullptr;
+    d.lists[0] = c->lists[0];
+    d.lists[1] = c->lists[1];
+    d.list_counts = c->list_counts;
     return d;
 }
 
@@ -309,6 +313,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.start = 0;
         v.pWh = 0;
         v.pmsg[0] = v.pmsg[1] = nullptr;
+        v.disp = nullptr;
         for (int k = 0; k < 2; ++k) {
             v.cost[k] = c->ws + p.cost[l][k];
             v.msg[k] = c->ws + p.msg[l][k];
@@ -341,7 +346,8 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     prefix[2 * levels] = 0;
     prefix[2 * levels + 1] = wta_blocks(c);
     bool ok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && persistent_grid(c->msg_kind, &c->grid) == cudaSuccess;
+    // every persistent kernel (one per minimisation form) is loaded and sized now, outside any capture
+    for (int T = 1; ok && T <= 3; ++T) ok = persistent_grid(c->msg_kind, T, &c->grid) == cudaSuccess;
     // the NCC kernel's shared memory depends on D and the window; allow the largest window now so
     // that no attribute call happens while a launch sequence is being captured
     ok = ok && ncc_prepare(c->cost_kind, D, BPS_MAX_WINDOW) == cudaSuccess;
@@ -370,12 +376,11 @@ extern "C" int bps_destroy(bps_ctx *c) {
     if (c->cap && cudaStreamSynchronize(c->cap) != cudaSuccess) rc = BPS_ERR_CUDA;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->host_graph.reset();
+    c->solve_graph.reset();
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->owns_ws && c->ws) {
-        cudaDeviceSynchronize();
-        if (cudaFree(c->ws) != cudaSuccess) rc = BPS_ERR_CUDA;
-    }
+    // cudaFree waits for the work in flight on the device before it releases the memory
+    if (c->owns_ws && c->ws && cudaFree(c->ws) != cudaSuccess) rc = BPS_ERR_CUDA;
     delete c;
     return rc;
 }
@@ -445,7 +450,7 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
 }
 
 static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
-                             cudaStream_t st);
+                             cudaStream_t st, int32_t *readout = nullptr);
 
 // The start messages of the coarsest scale: zero, or imported from the caller.
 static int enqueue_start(bps_ctx *c, int top, int flags, const void *init, cudaStream_t st) {
@@ -483,17 +488,34 @@ static PersistParams persist_params(int npairs, const PairDesc *pairs, const int
 static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
                       cudaStream_t st, int32_t *disp = nullptr) {
     if (!(flags & BPS_FLAG_PERSISTENT)) {
-        const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st);
+        // u8 form, exact skip rule: the finest scale's half-sweeps read out every pixel they
+        // recompute, and only the even pixels the last half-sweep dirtied are read out after it
+        const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
+        const bool fused = disp && c->msg_kind == MSG_U8 && c->sv.K == 0 && c->lv[0].eps == 0 && !c->lv[0].freeze &&
+                           iters > 0;
+        const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st, fused ? disp : nullptr);
         if (rc == BPS_OK && disp) {
-            if (c->last_sparse_k) CK(launch_sparse_wta(c->lv[0], c->sv, disp, st));
-            else CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+            if (c->last_sparse_k) {
+                CK(launch_sparse_wta(c->lv[0], c->sv, disp, st));
+            } else if (fused) {
+                // the last half-sweep's list of newly dirty even pixels, where the scale keeps lists
+                const bool listed = skip && (c->variant[0] & VARIANT_LISTS) && !(c->variant[0] & VARIANT_CLUSTER);
+                const int t_last = levels * iters * 2 - 1;
+                CK(launch_wta_rest(c->lv[0], c->D, c->Dp, c->Gp, skip ? 1 : 0, listed ? c->lists[0] : nullptr,
+                                   listed ? c->list_counts + t_last : nullptr, disp, st));
+            } else {
+                CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
+            }
         }
         return rc;
     }
     const int top = levels - 1;
     const int ntrace = levels * iters * 2;
     c->last_sparse_k = 0;
-    if (ntrace) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
+    if (ntrace) {
+        CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * ntrace, st));
+        CK(cudaMemsetAsync(c->list_counts, 0, sizeof(unsigned) * ntrace, st));
+    }
     const int rc = enqueue_start(c, top, flags, init, st);
     if (rc != BPS_OK) return rc;
     CK(cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), st));
@@ -511,7 +533,7 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
         }
         CK(cudaEventRecord(c->ev[0], st));
     }
-    CK(launch_persistent(c->msg_kind, P, c->grid, st));
+    CK(launch_persistent(c->msg_kind, P, st));
     if (prof) {
         CK(cudaEventRecord(c->ev[1], st));
         c->prof_span.assign(1, 1);
@@ -526,7 +548,7 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
 }
 
 static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
-                             cudaStream_t st) {
+                             cudaStream_t st, int32_t *readout) {
     const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
     const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
     const int top = levels - 1;
@@ -556,7 +578,8 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     int t = 0;
     c->last_sparse_k = c->sv.K;
     for (int l = top; l >= 0; --l) {
-        const LevelView &v = c->lv[l];
+        LevelView v = c->lv[l];
+        if (l == 0) v.disp = readout;  // the finest scale's half-sweeps read out what they recompute
         if (l == 0 && c->sv.K > 0) {
             // the finest scale over sparse candidates: selection, start from the parent's messages
             // at each candidate's label, then the half-sweeps
@@ -589,11 +612,16 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
                                st));
         LevelView first = v, second = v;  // the views of the scale's first two half-sweeps
         if (fused_start) {
+            // the first half-sweep reads the even pixels' start messages from their parents'
+            // records; the second compares its messages with the odd pixels' receivers' start
+            // messages there (the receivers' own records are written whole only then)
             first.start = 1;
-            first.pWh = c->lv[l + 1].Wh;
-            first.pmsg[0] = c->lv[l + 1].msg[0];
-            first.pmsg[1] = c->lv[l + 1].msg[1];
             second.start = 2;
+            for (LevelView *fs : {&first, &second}) {
+                fs->pWh = c->lv[l + 1].Wh;
+                fs->pmsg[0] = c->lv[l + 1].msg[0];
+                fs->pmsg[1] = c->lv[l + 1].msg[1];
+            }
         }
         if (iters > 0 && c->msg_kind == MSG_U8 && (c->variant[l] & VARIANT_CLUSTER)) {
             if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
@@ -643,7 +671,20 @@ extern "C" int bps_bp_solve(bps_ctx *c, int levels, int iters, int lambda, int t
                             void *stream) {
     const int rc = check_bp_args(c, levels, iters, lambda, trunc, flags & ~BPS_FLAG_GRAPH, init);
     if (rc != BPS_OK) return rc;
-    return enqueue_bp(c, levels, iters, lambda, trunc, flags & ~BPS_FLAG_GRAPH, init, (cudaStream_t)stream);
+    const int f = flags & ~BPS_FLAG_GRAPH;
+    if (!(flags & BPS_FLAG_GRAPH) || (flags & BPS_FLAG_PROFILE))
+        return enqueue_bp(c, levels, iters, lambda, trunc, f, init, (cudaStream_t)stream);
+    // the solve recorded once as a graph, replayed while its arguments and the kernel choices hold
+    const std::vector<intptr_t> key = {levels, iters, lambda, trunc, f, (intptr_t)init, (intptr_t)c->config_version};
+    const int e = replay_or_record(c->solve_graph, key, c->cap, (cudaStream_t)stream, [&](cudaStream_t s) {
+        return enqueue_bp(c, levels, iters, lambda, trunc, f, init, s);
+    });
+    if (e == BPS_OK) {  // what recording set on the host, a replay sets again
+        c->last_levels = levels;
+        c->last_iters = iters;
+        c->last_sparse_k = (f & BPS_FLAG_PERSISTENT) ? 0 : c->sv.K;
+    }
+    return e;
 }
 
 extern "C" int bps_wta_disparity(bps_ctx *c, int32_t *disp, void *stream) {
@@ -721,6 +762,9 @@ extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
         c->gkey = key;
     }
     CK(cudaGraphLaunch(c->gexec, st));
+    c->last_levels = c->levels;  // what recording set on the host, a replay sets again
+    c->last_iters = iters;
+    c->last_sparse_k = (flags & BPS_FLAG_PERSISTENT) ? 0 : c->sv.K;
     return BPS_OK;
 }
 
@@ -939,7 +983,7 @@ extern "C" int bps_batch_create(bps_batch **out, bps_ctx *const *ctxs, int n) {
     ok = ok && cudaMalloc(&b->d_barrier, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && persistent_grid(b->msg_kind, &b->grid) == cudaSuccess;
+    for (int T = 1; ok && T <= 3; ++T) ok = persistent_grid(b->msg_kind, T, &b->grid) == cudaSuccess;
     if (!ok) {
         batch_free(b);
         return BPS_ERR_CUDA;
@@ -998,14 +1042,17 @@ static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *c
             if (rc == BPS_OK) rc = enqueue_cost(c, L[i], R[i], pitches[i], windows[i], trunc_data, nullptr, b->streams[i]);
             if (rc == BPS_OK) rc = enqueue_start(c, b->levels - 1, 0, nullptr, b->streams[i]);
             if (rc != BPS_OK) return rc;
-            if (iters) CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * b->levels * iters * 2, b->streams[i]));
+            if (iters) {
+                CK(cudaMemsetAsync(c->trace, 0, sizeof(unsigned long long) * b->levels * iters * 2, b->streams[i]));
+                CK(cudaMemsetAsync(c->list_counts, 0, sizeof(unsigned) * b->levels * iters * 2, b->streams[i]));
+            }
             CK(cudaEventRecord(b->events[i + 1], b->streams[i]));
             CK(cudaStreamWaitEvent(st, b->events[i + 1], 0));
         }
         CK(cudaMemsetAsync(b->d_barrier, 0, 2 * sizeof(unsigned), st));
         PersistParams P = persist_params(n, b->d_desc, b->d_prefix, b->d_prefix + (size_t)b->levels * (n + 1),
                                          b->d_barrier, b->levels, iters, lambda, trunc, flags);
-        CK(launch_persistent(b->msg_kind, P, b->grid, st));
+        CK(launch_persistent(b->msg_kind, P, st));
         for (int i = 0; i < n; ++i) {
             bps_ctx *c = b->ctxs[i];
             c->last_levels = b->levels;

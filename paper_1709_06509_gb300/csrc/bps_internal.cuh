@@ -40,6 +40,9 @@ struct LevelView {
     int start;
     int pWh;
     const void *pmsg[2];
+    // Read-out during the finest scale's half-sweeps (u8 form, exact skip rule): each recomputed
+    // pixel writes the argmin of the belief it forms to disp[y * W + x] (nullable: no read-out).
+    int32_t *disp;
 };
 
 // Programmatic dependent launch: every kernel of the stereo chain is launched so that it may

@@ -101,19 +101,25 @@ struct PairDesc {
     int D, Dp, Gp;
     unsigned long long *trace;  // per half-sweep counters of this pair (nullable)
     int32_t *disp;              // winner-take-all output (nullable: no read-out)
+    unsigned *lists[2];         // active lists of the even / odd pixels (sized for the finest scale)
+    unsigned *list_counts;      // entries appended during each half-sweep (zeroed before the launch)
 };
 struct PersistParams {
     const PairDesc *pairs;        // [npairs]
     const int *sweep_prefix;      // [levels][npairs + 1]: first work block of each pair in a half-sweep
     const int *wta_prefix;        // [npairs + 1]: first work block of each pair in the read-out
     int npairs, levels, iters, lam, lam_u8, trunc, skip;
+    int lists;                    // after a scale's first iteration, sweep only the listed dirty pixels
     unsigned *barrier;            // {arrival count, error word}, zeroed before the launch
     unsigned extra_arrivals;      // test hook: > 0 makes every barrier wait for blocks that never come
     unsigned long long timeout_ns;
     int32_t *disp_override;       // single-pair launches: read-out target of pair 0 (nullable)
 };
-cudaError_t persistent_grid(int form, int *grid);
-cudaError_t launch_persistent(int form, const PersistParams &P, int grid, cudaStream_t st);
+// Co-resident CTAs of the persistent kernel of this form and truncation (looked up once each).
+cudaError_t persistent_grid(int form, int trunc, int *grid);
+// Whether the persistent kernel of this form and truncation sweeps over active lists.
+bool persistent_takes_lists(int form, int trunc);
+cudaError_t launch_persistent(int form, const PersistParams &P, cudaStream_t st);
 
 // Load every kernel a launch sequence may use (CUDA loads modules lazily on first use,
 // which must not happen inside a stream capture).
@@ -123,6 +129,11 @@ cudaError_t preload_readout_kernels(int msg_kind);
 
 // Winner-take-all disparity at the finest scale.
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);
+// The rest of a read-out the finest scale's u8 half-sweeps started (LevelView::disp): the even
+// pixels dirtied by the last half-sweep, from the list of them (non-null `list`, device count
+// n_list) or from the skip flags (every even pixel with the skip off).
+cudaError_t launch_wta_rest(const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
+                            const unsigned *n_list, int32_t *disp, cudaStream_t st);
 
 // Sparse candidates of the finest scale (sparse.cu): per colour, Kp uint16 labels a slot, then
 // Kp int16 costs a slot (K candidates, Kp = K rounded up to a power of two).

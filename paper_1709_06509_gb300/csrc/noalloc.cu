@@ -1,18 +1,21 @@
 // noalloc.cu -- an energy entry point that allocates no memory at all.
 //
 // Some callers cannot allocate device memory when they need the energy of a labelling:
-// code that runs while a CUDA graph is being captured (allocation calls are not allowed
-// there), real-time loops whose budget forbids the latency of an allocator, or programs
-// that embed this library behind an allocator the library cannot reach.  For them
-// bps_energy_noalloc computes E(d) = E_D(d) + E_S(d) from a cost volume and a labelling the
-// caller already holds, with its scratch (one partial sum per block) in a fixed array
-// compiled into this library instead of a workspace or a cudaMalloc.
+// real-time loops whose latency budget forbids an allocator (cudaMalloc and cudaFree may
+// synchronise the whole device), programs that run this library inside a framework owning
+// all device memory through an allocator the library cannot reach, and code running under a
+// fixed memory budget where any new allocation may fail.  For them bps_energy_noalloc
+// computes E(d) = E_D(d) + E_S(d) from a cost volume and a labelling the caller already
+// holds, with its scratch (one partial sum per block) in a fixed array compiled into this
+// library instead of a workspace or a cudaMalloc.
 //
 // The scratch array lives in device memory of every GPU that loads the library and stays
 // there until the process exits.  Every call shares it, so two calls whose kernels overlap
 // on the GPU (different streams, or different host threads) race on it; calls that follow
 // each other on one stream are safe.  Each call writes all the partial sums it reads, so
-// nothing needs clearing between calls.
+// nothing needs clearing between calls.  The array's device address is looked up once per
+// device and cached; cudaDeviceReset invalidates it, and a failed launch drops the cached
+// address so that the next call looks it up again.
 #include <mutex>
 
 #include "../../include/bpstereo.h"
@@ -85,6 +88,14 @@ int scratch_for_current_device(long long **out) {
     return BPS_OK;
 }
 
+// After a failed launch (e.g. following a cudaDeviceReset) the cached address is looked up again.
+void forget_scratch_for_current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    g_scratch_addr[dev] = nullptr;
+}
+
 }  // namespace
 
 extern "C" int bps_energy_noalloc(const int32_t *d_cost, const int32_t *d_disp, int W, int H, int D, int lambda,
@@ -98,8 +109,14 @@ extern "C" int bps_energy_noalloc(const int32_t *d_cost, const int32_t *d_disp, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     energy_volume_partial_kernel<<<(unsigned)blocks, NA_THREADS, 0, st>>>(d_cost, d_disp, W, H, D, lambda, trunc,
                                                                           scratch);
-    if (cudaGetLastError() != cudaSuccess) return BPS_ERR_CUDA;
-    energy_volume_final_kernel<<<1, NA_THREADS, 0, st>>>(scratch, (int)blocks, d_energy);
-    if (cudaGetLastError() != cudaSuccess) return BPS_ERR_CUDA;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        energy_volume_final_kernel<<<1, NA_THREADS, 0, st>>>(scratch, (int)blocks, d_energy);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        forget_scratch_for_current_device();
+        return BPS_ERR_CUDA;
+    }
     return BPS_OK;
 }

@@ -13,7 +13,11 @@
 // Inside a half-sweep the work of all pairs is one list of 256-thread blocks (a prefix
 // sum per scale maps a block index to its pair); each CTA takes blocks grid-stride.  One
 // launch replaces the 2 * iters * levels dependent launches of the per-sweep path, and a
-// batch shares each barrier.
+// batch shares each barrier.  With the fast-converging skip, the u8 form and the fp16 form's
+// packed body keep the active lists of the chained path: a scale's first iteration sweeps
+// every pixel and starts the lists, and each later half-sweep takes only the pixels its
+// predecessor listed (the per-pair block counts come from the list lengths, summed over the
+// pairs after each barrier).  The minimisation is the stencil where T <= 2.
 //
 // Grid barrier: a monotonically increasing arrival counter (barrier k completes when it
 // reaches (k + 1) * gridDim.x), so it never needs a reset.  The wait is bounded by a
@@ -22,10 +26,14 @@
 // cooperative launch.
 #include <algorithm>
 
+#include "../../include/bpstereo.h"
 #include "bps_launch.h"
 #include "sweep_body.cuh"
+#include "sweep_f16_body.cuh"
 
 namespace bps {
+
+constexpr int BPS_MAX_BATCH_PAIRS = BPS_MAX_BATCH;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -73,8 +81,89 @@ __device__ __forceinline__ int find_pair(const int *prefix, int npairs, int v) {
     return lo;
 }
 
-template <int FORM>
-__global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_kernel(PersistParams P) {
+// Per-pair work blocks of a list half-sweep, exclusive prefix in shared memory: pair p's list
+// (count[t - 1] entries, 256 / Gp pixels a block) covers blocks [pre[p], pre[p + 1]).  Every thread
+// of the block takes part; npairs <= blockDim.x.
+__device__ __forceinline__ int list_prefix(const PersistParams &P, int t, int *pre) {
+    __shared__ int warp_sums[8];
+    const int p = threadIdx.x;
+    int blocks = 0;
+    if (p < P.npairs) {
+        const PairDesc &pd = P.pairs[p];
+        const unsigned n = *(volatile const unsigned *)(pd.list_counts + t - 1);
+        const int groups = (int)blockDim.x / pd.Gp;
+        blocks = (int)((n + groups - 1) / groups);
+    }
+    // inclusive scan over the block: within each warp, then over the warp totals
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v = blocks;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_sums[w] = v;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < w; ++k) before += warp_sums[k];
+    if (p < P.npairs) pre[p + 1] = before + v;
+    if (p == 0) pre[0] = 0;
+    __syncthreads();
+    const int total = pre[P.npairs];
+    __syncthreads();  // warp_sums is reused by the next call
+    return total;
+}
+
+// One pair's share of a half-sweep: work block b (of the dense sweep, or of the list when
+// `listed`), the u8 form's stencil or distance transform (TS), the fp16 form's packed body (TS >
+// 0) or the generic one.  APPEND: newly dirty pixels of the other colour go to its list.
+template <int FORM, int TS>
+__device__ __forceinline__ void persistent_group(const PersistParams &P, const PairDesc &pd, int l, int colour,
+                                                 int t, int64_t b, bool listed, bool append) {
+    const LevelView &lv = pd.lv[l];
+    unsigned long long *trace = pd.trace ? pd.trace + t : nullptr;
+    const ActiveList al{listed ? pd.lists[colour] : nullptr, listed ? pd.list_counts + t - 1 : nullptr,
+                        append ? pd.lists[colour ^ 1] : nullptr, append ? pd.list_counts + t : nullptr};
+    int64_t s_listed = 0;
+    if (listed) {
+        const int groups = (int)blockDim.x / pd.Gp;
+        const unsigned n = *(volatile const unsigned *)al.n_in;
+        const int64_t idx = b * groups + threadIdx.x / pd.Gp;
+        s_listed = idx < (int64_t)n ? (int64_t)al.in[idx] : (int64_t)lv.H * lv.Wh;
+    }
+    if constexpr (FORM == MSG_U8) {
+        const int lam = P.lam_u8, lamT = P.lam_u8 * P.trunc;
+        if (pd.D & 15) {
+            if (listed) sweep_group_u8<true, true, TS, true, 0, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, 1, trace, b, al, 0, s_listed);
+            else if (append) sweep_group_u8<true, true, TS, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b, al);
+            else sweep_group_u8<true, false, TS, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b);
+        } else {
+            if (listed) sweep_group_u8<false, true, TS, true, 0, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, 1, trace, b, al, 0, s_listed);
+            else if (append) sweep_group_u8<false, true, TS, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b, al);
+            else sweep_group_u8<false, false, TS, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b);
+        }
+    } else if constexpr (FORM == MSG_I32) {
+        sweep_group<int32_t, int32_t, true>(lv, colour, pd.D, pd.Dp, pd.Gp, P.lam, P.lam * P.trunc, P.skip, trace, b);
+    } else if constexpr (TS == 0) {
+        sweep_group<float, __half, true>(lv, colour, pd.D, pd.Dp, pd.Gp, (float)P.lam, (float)P.lam * (float)P.trunc,
+                                         P.skip, trace, b);
+    } else {
+        const float lam = P.trunc == 0 ? 0.f : (float)P.lam, lamT = lam * (float)P.trunc;
+        if (pd.D & 15) {
+            if (listed) sweep_group_f16<true, TS, false, true, true, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, 1, trace, b, al, s_listed);
+            else if (append) sweep_group_f16<true, TS, false, true, false, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b, al);
+            else sweep_group_f16<true, TS, false, false, false, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b);
+        } else {
+            if (listed) sweep_group_f16<false, TS, false, true, true, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, 1, trace, b, al, s_listed);
+            else if (append) sweep_group_f16<false, TS, false, true, false, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b, al);
+            else sweep_group_f16<false, TS, false, false, false, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b);
+        }
+    }
+}
+
+template <int FORM, int TS>
+__global__ void __launch_bounds__(256, FORM == MSG_I32 || (FORM == MSG_F16 && TS == 0) ? 1 : 2)
+bp_persistent_kernel(PersistParams P) {
+    __shared__ int list_pre[BPS_MAX_BATCH_PAIRS + 1];
     const int top = P.levels - 1;
     unsigned target = 0;
     auto sync = [&]() {
@@ -102,29 +191,22 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
         }
         if (!sync()) return;
         const int *prefix = P.sweep_prefix + l * (P.npairs + 1);
-        const int nblocks = prefix[P.npairs];
         for (int it = 0; it < P.iters; ++it)
             for (int colour = 0; colour < 2; ++colour) {
                 const int t = (top - l) * P.iters * 2 + it * 2 + colour;
+                // with lists, the scale's first iteration sweeps densely (every pixel is dirty) and
+                // its second half-sweep starts the lists; later half-sweeps take the listed pixels
+                const bool listed = P.lists && P.skip && it > 0;
+                const bool append = P.lists && P.skip && (it > 0 || colour == 1);
+                const int *pre = prefix;
+                int nblocks = prefix[P.npairs];
+                if (listed) {
+                    nblocks = list_prefix(P, t, list_pre);
+                    pre = list_pre;
+                }
                 for (int vb = blockIdx.x; vb < nblocks; vb += gridDim.x) {
-                    const int p = find_pair(prefix, P.npairs, vb);
-                    const PairDesc &pd = P.pairs[p];
-                    const int64_t b = vb - prefix[p];
-                    unsigned long long *trace = pd.trace ? pd.trace + t : nullptr;
-                    if constexpr (FORM == MSG_U8) {
-                        if (pd.D & 15)
-                            sweep_group_u8<true, false, 0, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
-                                                 P.skip, trace, b);
-                        else
-                            sweep_group_u8<false, false, 0, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam_u8, P.lam_u8 * P.trunc,
-                                                  P.skip, trace, b);
-                    } else if constexpr (FORM == MSG_I32) {
-                        sweep_group<int32_t, int32_t, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, P.lam, P.lam * P.trunc,
-                                                      P.skip, trace, b);
-                    } else {
-                        sweep_group<float, __half, true>(pd.lv[l], colour, pd.D, pd.Dp, pd.Gp, (float)P.lam,
-                                                   (float)P.lam * (float)P.trunc, P.skip, trace, b);
-                    }
+                    const int p = find_pair(pre, P.npairs, vb);
+                    persistent_group<FORM, TS>(P, P.pairs[p], l, colour, t, vb - pre[p], listed, append);
                 }
                 if (!sync()) return;
             }
@@ -141,28 +223,56 @@ __global__ void __launch_bounds__(256, FORM == MSG_U8 ? 3 : 1) bp_persistent_ker
     }
 }
 
-static const void *persistent_fn(int form) {
+// The minimisation form of a truncation: the stencils for T <= 2, the distance transform above
+// (the int32 form has the generic kernel only).
+static int persistent_ts(int form, int trunc) {
+    if (form == MSG_I32) return 0;
+    if (form == MSG_F16 && !sweep_f16_applies(trunc)) return 0;
+    return trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0);
+}
+
+// The u8 bodies (stencil or distance transform) and the fp16 form's packed body keep active lists;
+// the generic int32 and float bodies sweep densely.
+bool persistent_takes_lists(int form, int trunc) {
+    return form == MSG_U8 || (form == MSG_F16 && persistent_ts(form, trunc) != 0);
+}
+
+static const void *persistent_fn(int form, int ts) {
     switch (form) {
-    case MSG_I32: return (const void *)bp_persistent_kernel<MSG_I32>;
-    case MSG_U8: return (const void *)bp_persistent_kernel<MSG_U8>;
-    default: return (const void *)bp_persistent_kernel<MSG_F16>;
+    case MSG_I32: return (const void *)bp_persistent_kernel<MSG_I32, 0>;
+    case MSG_U8:
+        return ts == 1 ? (const void *)bp_persistent_kernel<MSG_U8, 1>
+                       : ts == 2 ? (const void *)bp_persistent_kernel<MSG_U8, 2> : (const void *)bp_persistent_kernel<MSG_U8, 0>;
+    default:
+        return ts == 1 ? (const void *)bp_persistent_kernel<MSG_F16, 1>
+                       : ts == 2 ? (const void *)bp_persistent_kernel<MSG_F16, 2> : (const void *)bp_persistent_kernel<MSG_F16, 0>;
     }
 }
 
-cudaError_t persistent_grid(int form, int *grid) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(form), 256, 0);
-    if (e != cudaSuccess) return e;
-    *grid = std::max(1, sms * per_sm);
+cudaError_t persistent_grid(int form, int trunc, int *grid) {
+    static int cached[3][3] = {};
+    const int ts = persistent_ts(form, trunc);
+    if (!cached[form][ts]) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(form, ts), 256, 0);
+        if (e != cudaSuccess) return e;
+        cached[form][ts] = std::max(1, sms * per_sm);
+    }
+    *grid = cached[form][ts];
     return cudaSuccess;
 }
 
-cudaError_t launch_persistent(int form, const PersistParams &P, int grid, cudaStream_t st) {
+cudaError_t launch_persistent(int form, const PersistParams &P, cudaStream_t st) {
+    int grid = 0;
+    const cudaError_t e = persistent_grid(form, P.trunc, &grid);
+    if (e != cudaSuccess) return e;
     PersistParams copy = P;
+    copy.lists = P.skip && persistent_takes_lists(form, P.trunc) ? 1 : 0;
     void *args[] = {&copy};
-    return cudaLaunchCooperativeKernel(persistent_fn(form), dim3(grid), dim3(256), args, 0, st);
+    return cudaLaunchCooperativeKernel(persistent_fn(form, persistent_ts(form, P.trunc)), dim3(grid), dim3(256), args,
+                                       0, st);
 }
 
 }  // namespace bps

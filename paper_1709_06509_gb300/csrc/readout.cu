@@ -24,13 +24,57 @@ __global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, i
     wta_group<CostT, MsgT>(lv, D, Dp, Gp, disp, blockIdx.x);
 }
 
+// The rest of a read-out that the finest scale's half-sweeps started (u8 form, exact skip rule):
+// every recomputed pixel already wrote the label of the belief it formed, and a pixel's belief
+// changes only when an incoming message does.  After the last half-sweep (the odd pixels) the
+// odd pixels' labels are final, and so are the even pixels' whose incoming messages did not
+// change since their own last update; the even pixels that the last half-sweep marked dirty
+// (with the skip off: every even pixel) are read out here, from the listed entries (`list`
+// non-null, `n_list` entries) or by their skip flags.  Grid-stride over the even pixels.
+template <typename CostT, typename MsgT>
+__global__ void __launch_bounds__(256)
+wta_rest_kernel(LevelView lv, int D, int Dp, int Gp, int skip, const unsigned *list, const unsigned *n_list,
+                int32_t *disp) {
+    pdl_enter();
+    const int groups = blockDim.x / Gp;
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t n = list ? (int64_t)*n_list : nslot;
+    for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x) {
+        const int64_t i = b * groups + threadIdx.x / Gp;
+        int64_t s = i < n ? (list ? (int64_t)list[i] : i) : nslot;
+        int x = 0, y = 0;
+        bool need = false;
+        if (s < nslot) {
+            y = (int)(s / lv.Wh);
+            x = 2 * (int)(s - (int64_t)y * lv.Wh) + (y & 1);  // even pixels: (x + y) & 1 == 0
+            need = x < lv.W && (list || !skip || lv.dirty[0][s] == 1u);
+        }
+        if (__ballot_sync(FULL, need) == 0u) continue;
+        wta_pixel<CostT, MsgT>(lv, D, Dp, Gp, disp, need ? x : 0, need ? y : 0, need);
+    }
+}
+
 cudaError_t preload_readout_kernels(int msg_kind) {
     cudaFuncAttributes a;
     switch (msg_kind) {
     case MSG_I32: return cudaFuncGetAttributes(&a, wta_kernel<int32_t, int32_t>);
-    case MSG_U8: return cudaFuncGetAttributes(&a, wta_kernel<int16_t, uint8_t>);
+    case MSG_U8: {
+        const cudaError_t e = cudaFuncGetAttributes(&a, wta_kernel<int16_t, uint8_t>);
+        return e == cudaSuccess ? cudaFuncGetAttributes(&a, wta_rest_kernel<int16_t, uint8_t>) : e;
+    }
     default: return cudaFuncGetAttributes(&a, wta_kernel<float, __half>);
     }
+}
+
+cudaError_t launch_wta_rest(const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
+                            const unsigned *n_list, int32_t *disp, cudaStream_t st) {
+    const int groups = 256 / Gp;
+    const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+    return launch_k(wta_rest_kernel<int16_t, uint8_t>, dim3(grid), dim3(256), 0, st, lv, D, Dp, Gp, skip, list, n_list,
+                    disp);
 }
 
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st) {

@@ -275,6 +275,20 @@ __device__ __forceinline__ void u8_message(const uint32_t (&h)[8], int lam, int 
     }
 }
 
+// The label of least belief of one pixel from its packed u8-form belief b (register j: labels
+// dbase + j and dbase + 8 + j as 16-bit halves; padding labels hold BIG16, above every real belief),
+// the lowest label on ties: the minimum over the group of (belief << 10 | label).  Every lane of
+// the warp takes part (the butterfly spans the Gp lanes of each pixel).
+__device__ __forceinline__ int u8_argmin(const uint32_t (&b)[8], int dbase, int Gp) {
+    unsigned key = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) key = min(key, ((b[j] & 0xffffu) << 10) | (unsigned)(dbase + j));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) key = min(key, ((b[j] >> 16) << 10) | (unsigned)(dbase + 8 + j));
+    for (int o = 1; o < Gp; o <<= 1) key = min(key, __shfl_xor_sync(FULL, key, o, Gp));
+    return (int)(key & 1023u);
+}
+
 // Stores under a predicate, without a branch around them.
 __device__ __forceinline__ void st_v4_if(uint4 *p, const uint4 &v, bool pred) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t@p st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
@@ -323,6 +337,17 @@ template <int n> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
 }
 
+// The start message of receiver (x, y) from direction `dir` in a scale's first iteration: its
+// parent's incoming message from that direction (the fused coarse-to-fine start).  `use`
+// false gives an in-bounds address that is not read.
+__device__ __forceinline__ const uint8_t *start_slot_u8(const LevelView &lv, int x, int y, int dir, int Dp, int dbase,
+                                                        bool use) {
+    if (!use) return reinterpret_cast<const uint8_t *>(lv.pmsg[0]);
+    const int px = x >> 1, py = y >> 1;
+    return reinterpret_cast<const uint8_t *>(colour_of(px, py) ? lv.pmsg[1] : lv.pmsg[0]) +
+           (slot_of(px, py, lv.pWh) * 4 + dir) * Dp + dbase;
+}
+
 // Issue the copies of block `block`'s inputs (eager: old messages of every valid pixel) into
 // `stage` (this thread's chunks).  LISTED: the slot is the caller's list entry s_listed (nslot
 // for none), and no flag is copied (a listed pixel is dirty by construction).
@@ -365,9 +390,12 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
     for (int q = 0; q < 4; ++q) {
         const bool hq = lane_data && has[q];
         cp_async16(stage + (2 + q) * T + t, mp + (hq ? q * Dp : 0), hq);
-        const bool oq = skip && hq;
-        const int64_t qs = oq ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
-        cp_async16(stage + (6 + q) * T + t, msg_out + (oq ? (qs * 4 + opp[q]) * Dp + dbase : 0), oq);
+        // the change test's old message: none in a scale's first half-sweep (start 1), the
+        // receiver's start message in its parent's record in the second (start 2)
+        const bool oq = skip && hq && lv.start != 1;
+        const uint8_t *op = lv.start == 2 ? start_slot_u8(lv, nbx[q], nby[q], opp[q], Dp, dbase, oq)
+                                          : msg_out + (oq ? (slot_of(nbx[q], nby[q], lv.Wh) * 4 + opp[q]) * Dp + dbase : 0);
+        cp_async16(stage + (6 + q) * T + t, op, oq);
     }
     if constexpr (!LISTED) cp_async4(stage + 10 * T + t, dirty_in + sc, valid);
 }
@@ -460,7 +488,13 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         for (int q = 0; q < 4; ++q) {
             const int64_t qs = (send && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
             qsv[q] = (unsigned)qs;
-            old[q] = (skip && send && has[q] && lane_data) ? *dst(q) : make_uint4(0u, 0u, 0u, 0u);
+            // the change test's old message: none in a scale's first half-sweep (start 1), the
+            // receiver's start message in its parent's record in the second (start 2)
+            const bool oq = skip && send && has[q] && lane_data && lv.start != 1;
+            old[q] = !oq ? make_uint4(0u, 0u, 0u, 0u)
+                         : lv.start == 2 ? load_u4<RW>(reinterpret_cast<const uint4 *>(
+                                               start_slot_u8(lv, nbx[q], nby[q], opp[q], Dp, dbase, true)))
+                                         : *dst(q);
         }
     };
     unsigned flag_staged = 0u;
@@ -506,14 +540,6 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) b[j] += t[j];
     }
-    if (lv.start == 1) {
-        // the start messages read from the parent become this pixel's records: the second
-        // half-sweep's change test compares the new messages with them
-        uint4 *own = reinterpret_cast<uint4 *>(const_cast<uint8_t *>(msg_in) + sc * 4 * Dp + dbase);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) st_v4_if(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(own) + q * Dp), in[q],
-                                             active && lane_data && has[q]);
-    }
     if constexpr (PADDED) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -522,6 +548,10 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         }
     }
 
+    if (lv.disp) {  // the read-out of a recomputed pixel of the finest scale, from the belief just formed
+        const int d = u8_argmin(b, dbase, Gp);
+        if (active && g == 0) lv.disp[(int64_t)y * lv.W + x] = d;
+    }
     const int gshift = lane & ~(Gp - 1);
     unsigned marks = 0u;  // bit q: this group marks neighbour q dirty (APPEND)
     const uint32_t EPS4 = (uint32_t)lv.eps * 0x01010101u;
@@ -537,7 +567,11 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 
         const bool send = active && has[q];
         const bool mine = send && lane_data;
-        if (skip) {
+        if (skip && lv.start == 1) {
+            // a scale's first half-sweep: every receiver is recomputed next, so nothing is compared
+            // or marked; the receivers' slots are written whole
+            st_v4_if(dst(q), out, mine);
+        } else if (skip) {
             const bool diff =
                 mine && ((old[q].x ^ out.x) | (old[q].y ^ out.y) | (old[q].z ^ out.z) | (old[q].w ^ out.w)) != 0u;
             bool big = false;
@@ -550,7 +584,9 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             const unsigned bm = lv.eps ? __ballot_sync(FULL, big) : dm;
             const bool changed = ((dm >> gshift) & group_bits(Gp)) != 0u;
             const bool significant = ((bm >> gshift) & group_bits(Gp)) != 0u;  // = changed when eps = 0
-            st_v4_if(dst(q), out, mine && changed);
+            // the second half-sweep of a scale writes every slot: the receivers' own records do
+            // not hold their start messages (those stay in the parent's records)
+            st_v4_if(dst(q), out, mine && (changed || lv.start == 2));
             const bool mk = send && significant;
             marked = marked || mk;
             const bool lead = mk && g == 0;  // one mark per pixel group
@@ -665,7 +701,12 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         const int64_t qs = (send && has_o) ? slot_of(nbx, nby, lv.Wh) : 0;
         qs_o = (unsigned)qs;
         dst = reinterpret_cast<uint4 *>(msg_out + (qs * 4 + (qo ^ 1)) * Dp + dbase);
-        old = (skip && send && has_o && lane_data) ? *dst : make_uint4(0u, 0u, 0u, 0u);
+        // the change test's old message: none at start 1, the receiver's parent record at start 2
+        const bool oq = skip && send && has_o && lane_data && lv.start != 1;
+        old = !oq ? make_uint4(0u, 0u, 0u, 0u)
+                  : lv.start == 2 ? __ldg(reinterpret_cast<const uint4 *>(
+                                        start_slot_u8(lv, nbx, nby, qo ^ 1, Dp, dbase, true)))
+                                  : *dst;
     };
     if constexpr (EAGER != 0) {
         load_cost();
@@ -697,10 +738,11 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
             b[j] = __vimax3_u16x2(b[j], pk(plo ? BIG16 : 0u, phi ? BIG16 : 0u), 0u);
         }
     }
+    if (lv.disp) {  // the read-out of a recomputed pixel of the finest scale (the up-direction group writes)
+        const int d = u8_argmin(b, dbase, Gp);
+        if (active && g == 0 && qo == 0) lv.disp[(int64_t)y * lv.W + x] = d;
+    }
     const uint4 in_o = qo == 0 ? in[0] : (qo == 1 ? in[1] : (qo == 2 ? in[2] : in[3]));
-    if (lv.start == 1)  // the start message read from the parent becomes this pixel's record
-        st_v4_if(reinterpret_cast<uint4 *>(const_cast<uint8_t *>(msg_in) + sc * 4 * Dp + qo * Dp + dbase), in_o,
-                 active && lane_data && has_o);
     uint32_t t[8], h[8], m[8];
     unpack_msg(in_o, t);
 #pragma unroll
@@ -712,7 +754,9 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     unsigned mark = 0u;  // slot + 1 of the neighbour to mark dirty (APPEND)
     bool marked = false;  // this group marked its receiver (skip rule freeze)
     const bool mine = send && lane_data;
-    if (skip) {
+    if (skip && lv.start == 1) {  // a scale's first half-sweep: nothing compared or marked
+        st_v4_if(dst, out, mine);
+    } else if (skip) {
         const bool diff = mine && ((old.x ^ out.x) | (old.y ^ out.y) | (old.z ^ out.z) | (old.w ^ out.w)) != 0u;
         bool big = false;
         if (lv.eps) {
@@ -724,7 +768,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         const unsigned bm = lv.eps ? __ballot_sync(FULL, big) : dm;
         const bool changed = ((dm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
         const bool significant = ((bm >> (lane & ~(Gp - 1))) & group_bits(Gp)) != 0u;
-        st_v4_if(dst, out, mine && changed);
+        st_v4_if(dst, out, mine && (changed || lv.start == 2));  // start 2: every slot written
         marked = send && significant;
         const bool lead = marked && g == 0;
         if constexpr (APPEND) {
@@ -773,14 +817,15 @@ __device__ __forceinline__ void upsample_chunk(const LevelView &coarse, const Le
 // ------------------------------------------------------------------ winner-take-all
 // Pixels of block `block` in raster order, Gp lanes each: argmin of the belief, the lowest
 // label on ties (labels are compared through the storage order of the form).
+// The read-out of pixel (x, y) by its group of Gp lanes (when `valid`); every lane of the warp
+// takes part in the butterfly.
 template <typename CostT, typename MsgT, bool RW = false>
-__device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, int64_t block) {
+__device__ __forceinline__ void wta_pixel(const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, int x, int y,
+                                          bool valid) {
     using Acc = typename AccOf<MsgT>::type;
     using A = Arith<Acc>;
     const int g = threadIdx.x & (Gp - 1);
-    const int64_t p = block * (blockDim.x / Gp) + threadIdx.x / Gp;
-    const bool valid = p < (int64_t)lv.W * lv.H;
-    const int x = valid ? (int)(p % lv.W) : 0, y = valid ? (int)(p / lv.W) : 0;
+    const int64_t p = (int64_t)y * lv.W + x;
     const int c = colour_of(x, y);
     const int64_t s = slot_of(x, y, lv.Wh);
     const int dbase = g * VEC;
@@ -816,6 +861,13 @@ __device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, in
         }
     }
     if (valid && g == 0) disp[p] = arg;
+}
+
+template <typename CostT, typename MsgT, bool RW = false>
+__device__ __forceinline__ void wta_group(const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, int64_t block) {
+    const int64_t p = block * (blockDim.x / Gp) + threadIdx.x / Gp;
+    const bool valid = p < (int64_t)lv.W * lv.H;
+    wta_pixel<CostT, MsgT, RW>(lv, D, Dp, Gp, disp, valid ? (int)(p % lv.W) : 0, valid ? (int)(p / lv.W) : 0, valid);
 }
 
 }  // namespace bps

@@ -151,7 +151,7 @@ def make_pair(seed: int, W: int, H: int, D: int, planes: int = 3, sigma: float =
     return StereoPair(L, R, disp, occluded, D, seed)
 
 
-# Workloads with the shapes of the paper's test pairs (P:57 [§Experimental Results]):
+# Workloads with the shapes of the paper's test pairs (section "Experimental Results"):
 # name -> (W, H, D, window, planes, sigma, seed)
 WORKLOADS = {
     "tiny_96x72_d16": (96, 72, 16, 5, 3, 2.0, 1),

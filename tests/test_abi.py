@@ -113,3 +113,16 @@ def test_autotuner_candidate_sets():
     assert wide and all(not (v & dp) for v in wide)
     assert all(v & bps.BPS_VARIANT_LISTS for v in at.LARGE_CANDIDATES if v & bps.BPS_VARIANT_STAGED_LISTS)
     assert set(at.CANDIDATES) == set(at.SMALL_CANDIDATES) | set(at.LARGE_CANDIDATES)
+
+
+def test_every_autotuner_candidate_has_an_exact_gpu_test():
+    # no sweep variant the autotuner can pick lacks an oracle-exact GPU test
+    import importlib.util
+
+    from paper_1709_06509_gb300 import autotune
+
+    spec = importlib.util.spec_from_file_location("gpu_parity", os.path.join(os.path.dirname(__file__),
+                                                                             "test_gpu_parity.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert set(autotune.CANDIDATES) <= set(mod.SWEEP_VARIANTS_TESTED)

@@ -321,8 +321,12 @@ def set_all_variants(st, variant):
     assert st.variants() == [variant] * st.levels
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 6, 8, 9, 10, 12, 13, 16, 17, 18, 24, 26, 27, 34, 43, 64, 65, 66, 67,
-                                     130, 131, 138, 194, 195, 162])
+# every variant the autotuner can pick, and more (tests/test_abi.py checks the tuner's candidates are here)
+SWEEP_VARIANTS_TESTED = [0, 1, 2, 3, 4, 6, 8, 9, 10, 11, 12, 13, 16, 17, 18, 24, 25, 26, 27, 34, 35, 42, 43, 64, 65, 66,
+                         67, 98, 99, 130, 131, 138, 139, 194, 195, 162]
+
+
+@pytest.mark.parametrize("variant", SWEEP_VARIANTS_TESTED)
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (45, 19, 33, 7, 3, 4, 7, 3), (40, 30, 64, 5, 3, 5, 5, 1),
                                   (24, 6, 256, 3, 2, 3, 10, 2), (150, 110, 48, 5, 3, 5, 10, 2)],
                          ids=lambda c: "x".join(map(str, c)))
@@ -509,6 +513,78 @@ def test_full_size_bit_exact(name):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("variant", [42, 34, 35, 98])
+def test_full_size_direction_parallel_lists_switch_lane_mapping(teddy, variant):
+    # the direction-parallel list launches pick their lane mapping from the list length: one
+    # group per (pixel, direction) on short lists, one group per pixel on long ones.  The long
+    # lists occur only at full size: 450x375 D64, the variant forced on every scale
+    pair, window = teddy
+    H, W = pair.left.shape
+    ref = oracle.stereo_int(pair.left, pair.right, pair.D, window, 20, 4, 10, 10, 2)
+    with bps.Stereo(W, H, pair.D, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        set_all_variants(st, variant)
+        disp = st.stereo(to_dev(pair.left), to_dev(pair.right), window, 20, 10, 10, 2, graph=True)
+        msg = st.export_messages(0)
+        torch.cuda.synchronize()
+        assert np.array_equal(msg.cpu().numpy(), ref["msg"])
+        assert np.array_equal(disp.cpu().numpy(), ref["disp"])
+        assert np.array_equal(st.get_trace(), ref["trace"])
+
+
+@pytest.mark.slow
+def test_full_size_pairs_bit_exact_under_the_joint_tuner(tmp_path):
+    """The two 384x288 D16 / 450x375 D64 pairs as the benchmark runs them: per-pair tuning, then
+    the joint batch tuner, one batch graph; bit-exact against the oracle."""
+    from paper_1709_06509_gb300 import autotune
+
+    pairs = [synth.workload_pair(n) for n in ("tsukuba_384x288_d16", "teddy_450x375_d64")]
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 4, bps.BPS_MSG_U8, device=DEV) for p, _ in pairs]
+    try:
+        Ls = [to_dev(p.left) for p, _ in pairs]
+        Rs = [to_dev(p.right) for p, _ in pairs]
+        ws = [w for _, w in pairs]
+        for st, L, R, w in zip(sts, Ls, Rs, ws):
+            autotune.tune_ncc(st, L, R, w, 20, reps=1)
+            autotune.tune(st, L, R, w, 20, 10, 10, 2, reps=1)
+        with bps.Batch(sts) as batch:
+            autotune.tune_batch(batch, sts, Ls, Rs, ws, 20, 10, 10, 2, reps=1)
+            outs = [torch.empty(p.left.shape, dtype=torch.int32, device=DEV) for p, _ in pairs]
+            batch.stereo(Ls, Rs, ws, 20, 10, 10, 2, graph=True, outs=outs)
+            batch.stereo(Ls, Rs, ws, 20, 10, 10, 2, graph=True, outs=outs)
+            torch.cuda.synchronize()
+            for (pair, window), st, o in zip(pairs, sts, outs):
+                ref = oracle.stereo_int(pair.left, pair.right, pair.D, window, 20, 4, 10, 10, 2)
+                assert np.array_equal(o.cpu().numpy(), ref["disp"]), st.variants()
+                assert np.array_equal(st.get_trace(), ref["trace"])
+                assert np.array_equal(st.export_messages(0).cpu().numpy(), ref["msg"])
+    finally:
+        for st in sts:
+            st.close()
+
+
+@pytest.mark.gpu
+def test_bp_solve_graph_replays_match_eager_solves():
+    # bps_bp_solve recorded as a graph and replayed: same messages, trace and labels as the eager
+    # solve; an eager solve with other arguments in between, then a replay, restores the trace length
+    pair = synth.make_pair(77, 96, 72, 16, 3, 2.0)
+    with bps.Stereo(96, 72, 16, 4, bps.BPS_MSG_U8, device=DEV) as st:
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 5, 20)
+        st.bp_solve(6, 10, 2, skip=True)
+        m0, t0, d0 = st.export_messages(0).clone(), st.get_trace(), st.wta_disparity().clone()
+        for _ in range(3):
+            st.bp_solve(6, 10, 2, skip=True, graph=True)
+            assert torch.equal(st.export_messages(0), m0) and np.array_equal(st.get_trace(), t0)
+            assert torch.equal(st.wta_disparity(), d0)
+        st.bp_solve(2, 10, 2, skip=True)
+        assert len(st.get_trace()) == 4 * 2 * 2
+        st.bp_solve(6, 10, 2, skip=True, graph=True)
+        assert np.array_equal(st.get_trace(), t0) and torch.equal(st.wta_disparity(), d0)
+        st.set_variant(0, 2)  # a kernel choice changes: the graph is recorded again
+        st.bp_solve(6, 10, 2, skip=True, graph=True)
+        assert torch.equal(st.export_messages(0), m0) and np.array_equal(st.get_trace(), t0)
+
+
+@pytest.mark.slow
 def test_hd_256_properties():
     """1920x1080, D=256, 9x9 window: too large for the oracle, so sampled NCC entries are
     checked one by one and the BP result through properties that hold at any size."""
@@ -573,6 +649,80 @@ def test_fp16_energy_gap(name):
     assert gap <= 0.005, gap
     assert abs(float(ef.item()) - e_gpu) / e_gpu < 1e-5  # the GPU's own FP64 energy reduction
     assert (d != ref["disp"]).mean() < 0.02
+
+
+@pytest.mark.parametrize("persistent", [False, True], ids=["chains", "persistent"])
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("trunc", [1, 2])
+def test_fp16_batch_matches_single_pairs_and_the_fp64_oracle(persistent, graph, trunc):
+    """fp16 messages in a batch of mixed pairs, as concurrent chains or one persistent launch (packed
+    half2 body, active lists after each scale's first iteration), plain or recorded as a graph:
+    every pair's messages, trace and labels equal its own chained solve's bit for bit, and its
+    energy is within 0.5% of the FP64 oracle's, under 2% of labels different."""
+    shapes = [(70, 40, 16, 5), (45, 33, 64, 7), (96, 20, 33, 3), (130, 60, 32, 5)]
+    pairs = [synth.make_pair(610 + k, W, H, D, 3, 2.0) for k, (W, H, D, _) in enumerate(shapes)]
+    windows = [w for *_, w in shapes]
+    singles = []
+    for p, w in zip(pairs, windows):
+        with bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 3, bps.BPS_MSG_FP16, device=DEV) as st:
+            st.build_cost_volume(to_dev(p.left), to_dev(p.right), w, 20)
+            st.bp_solve(5, 10, trunc, skip=True)
+            d = st.wta_disparity().cpu().numpy()
+            m = st.export_messages(0).cpu().numpy()
+            tr = st.get_trace()
+            if persistent:  # a single pair's persistent solve gives the same
+                st.bp_solve(5, 10, trunc, skip=True, persistent=True)
+                assert st.get_error() == bps.BPS_OK
+                assert np.array_equal(st.wta_disparity().cpu().numpy(), d)
+                assert np.array_equal(st.export_messages(0).cpu().numpy(), m)
+                assert np.array_equal(st.get_trace(), tr)
+        singles.append((d, m, tr))
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 3, bps.BPS_MSG_FP16, device=DEV) for p in pairs]
+    try:
+        with bps.Batch(sts) as batch:
+            Ls = [to_dev(p.left) for p in pairs]
+            Rs = [to_dev(p.right) for p in pairs]
+            for rep in range(2):
+                outs = batch.stereo(Ls, Rs, windows, 20, 5, 10, trunc, graph=graph, persistent=persistent)
+                torch.cuda.synchronize()
+                if persistent:
+                    assert batch.get_error() == bps.BPS_OK
+                for out, st, (d, m, tr) in zip(outs, sts, singles):
+                    assert np.array_equal(out.cpu().numpy(), d)
+                    assert np.array_equal(st.get_trace(), tr)
+                    assert np.array_equal(st.export_messages(0).cpu().numpy(), m)
+    finally:
+        for st in sts:
+            st.close()
+    for p, w, (d, _, _) in zip(pairs, windows, singles):
+        ref = oracle.stereo_f64(p.left, p.right, p.D, w, 20, 3, 5, 10.0, trunc)
+        e = oracle.energy(ref["cost"], d, 10.0, trunc)
+        assert abs(e - ref["energy"]) <= 0.005 * ref["energy"], (e, ref["energy"])
+        assert (d != ref["disp"]).mean() < 0.02
+
+
+@pytest.mark.slow
+def test_fp16_c3_style_batch_persistent_equals_chains():
+    # mixed sizes and label counts of the 64-pair configuration (a few of its pairs): the single
+    # persistent launch reproduces the concurrent chains' labels and traces bit for bit
+    specs = synth.batch_specs(6)
+    pairs = [synth.make_pair(seed, W, H, D, 8, 3.0) for seed, W, H, D in specs]
+    sts = [bps.Stereo(p.left.shape[1], p.left.shape[0], p.D, 4, bps.BPS_MSG_FP16, device=DEV) for p in pairs]
+    try:
+        with bps.Batch(sts) as batch:
+            Ls = [to_dev(p.left) for p in pairs]
+            Rs = [to_dev(p.right) for p in pairs]
+            ws = [7] * len(pairs)
+            chains = [o.clone() for o in batch.stereo(Ls, Rs, ws, 20, 10, 10, 2, graph=True)]
+            tr_chains = [st.get_trace() for st in sts]
+            outs = batch.stereo(Ls, Rs, ws, 20, 10, 10, 2, graph=True, persistent=True)
+            torch.cuda.synchronize()
+            assert batch.get_error() == bps.BPS_OK
+            for a, b, st, tr in zip(chains, outs, sts, tr_chains):
+                assert torch.equal(a, b) and np.array_equal(st.get_trace(), tr)
+    finally:
+        for st in sts:
+            st.close()
 
 
 @pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66, 130, 194])

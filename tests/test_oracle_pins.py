@@ -277,9 +277,9 @@ def test_message_equals_distance_transform_and_invariants():
 
 # ---------------------------------------------------------------- whole solver
 
-def read_chain_golden():
+def read_chain_golden(name="chain_3x1_hand.txt"):
     vals = {}
-    with open(os.path.join(GOLDEN, "chain_3x1_hand.txt")) as fh:
+    with open(os.path.join(GOLDEN, name)) as fh:
         for line in fh:
             line = line.strip()
             if line and not line.startswith("#"):
@@ -298,6 +298,24 @@ def test_chain_hand_worked():
     d = oracle.wta(cost, msg)
     assert d.ravel().tolist() == g["disp"]
     assert oracle.energy(cost, d, 1, 1) == g["energy"][0]
+
+
+def test_freeze_rule_hand_worked():
+    # eps = 1 with the permanent freeze (tests/golden/chain_4x1_freeze_hand.txt, derived by hand):
+    # a pixel whose messages moved by no more than eps marks nobody and is frozen, and stays
+    # frozen when a neighbour marks it later
+    g = read_chain_golden("chain_4x1_freeze_hand.txt")
+    cost = np.array(g["cost"], dtype=np.int32).reshape(1, 4, 2)
+    msg, trace = oracle.bp(cost, 1, 2, 2, 1, skip=True, eps=1, freeze=True)
+    for q, k in enumerate(("msg_up", "msg_down", "msg_left", "msg_right")):
+        assert msg[q].ravel().tolist() == g[k], k
+    assert trace.tolist() == g["trace"]
+    d = oracle.wta(cost, msg)
+    assert d.ravel().tolist() == g["disp"]
+    assert oracle.energy(cost, d, 2, 1) == g["energy"][0]
+    # the float form follows the same rule
+    msg_f, trace_f = oracle.bp(cost.astype(np.float64), 1, 2, 2.0, 1, skip=True, eps=1.0, freeze=True)
+    assert np.array_equal(msg_f, msg.astype(np.float64)) and trace_f.tolist() == g["trace"]
 
 
 @pytest.mark.parametrize("levels", [1, 3])
