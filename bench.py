@@ -82,6 +82,14 @@ def parse():
     ap.add_argument("--launch-report", action="store_true",
                     help="instead of the benchmark line: per-launch times (profile mode) and recomputed pixels of "
                          "every sweep launch of the headline pair, one JSON line")
+    ap.add_argument("--trace-jsonl", default=None, metavar="PATH",
+                    help="also write, after the timed region, one JSON line per iteration count k = 1..10 of "
+                         "the headline pair: the energy after k iterations per scale and, per half-sweep of the "
+                         "finest scale, the pixels recomputed and the converged fraction")
+    ap.add_argument("--sync-report", action="store_true",
+                    help="instead of the benchmark line: the cost of a grid barrier inside one cooperative launch "
+                         "against a programmatically chained kernel boundary in a graph, for grids of 1 to 3 CTAs "
+                         "a SM, one JSON line")
     ap.add_argument("--batch-form", choices=["u8", "fp16"], default="u8",
                     help="message form of --batch-report")
     ap.add_argument("--ncu-case", action="store_true",
@@ -786,6 +794,39 @@ def c2_key(bps, autotune, dev, args, flush, stream, rank) -> dict:
     return res
 
 
+def write_trace_jsonl(path, st, L, R, window, pair):
+    """Per iteration count k (every scale runs k iterations): the read-out's energy and, per
+    half-sweep of the finest scale, the pixels recomputed and the fraction of that colour's pixels
+    left alone (converged, in the fast-converging sense of the skip)."""
+    H, W = pair.left.shape
+    even = (W * H + 1) // 2
+    with open(path, "w") as fh:
+        for k in range(1, ITERS + 1):
+            disp = st.stereo(L, R, window, TRUNC_DATA, k, LAM, TRUNC, graph=False)
+            e = int(st.energy(disp, LAM, TRUNC)[0].item())
+            tr = [int(v) for v in st.get_trace()]
+            finest = tr[-2 * k:]
+            conv = [1.0 - n / (even if t % 2 == 0 else W * H - even) for t, n in enumerate(finest)]
+            fh.write(json.dumps({"workload": HEADLINE, "iters": k, "energy": e, "finest_recomputed": finest,
+                                 "finest_converged_frac": conv, "trace": tr}) + "\n")
+
+
+def sync_report(args):
+    """bps_measure_sync_costs for grids of 1, 2 and 3 CTAs a SM: the phase separation the persistent
+    form pays (a grid barrier) against the chained form's (a PDL kernel boundary in a graph)."""
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    rows = {}
+    for per_sm in (1, 2, 3):
+        barrier_us, boundary_us = bps.bps_measure_sync_costs(sms * per_sm, 2000)
+        rows[f"{per_sm * sms}_ctas"] = {"grid_barrier_us": barrier_us, "pdl_kernel_boundary_us": boundary_us}
+    print(json.dumps({"report": "phase separation costs", "phases": 2000, "sms": sms, "costs": rows}))
+
+
 def launch_report(args):
     """Per-launch CUDA-event times (profile mode) of every sweep launch of the headline pair, with
     the pixels each recomputed."""
@@ -828,6 +869,8 @@ def main():
         return warmstart_report(args)
     if args.launch_report:
         return launch_report(args)
+    if args.sync_report:
+        return sync_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     rank, world, local = dist_env()
     import torch
@@ -930,6 +973,8 @@ def main():
     h2d = 2 * pair.left.size
     d2h = 4 * pair.left.size + 8
     launches_per_step = pair_launches(bps, st)
+    if args.trace_jsonl and rank == 0:
+        write_trace_jsonl(args.trace_jsonl, st, L, R, window, pair)
     extras = {}
     if not args.no_extras:
         extras["fp16"] = fp16_key(bps, autotune, pair, window, dev, args, flush, stream, gold)

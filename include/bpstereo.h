@@ -49,6 +49,7 @@ typedef struct bps_ctx bps_ctx;
 #define BPS_ERR_WORKSPACE (-4)   /* workspace missing, too small or misaligned */
 #define BPS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
 #define BPS_ERR_STATE (-6)       /* call order violated (e.g. bp_solve before a cost volume) */
+#define BPS_ERR_INTERNAL (-7)    /* a device-side consistency check of the debug build failed */
 
 /* numerical forms */
 #define BPS_MSG_INT32 0
@@ -110,6 +111,14 @@ size_t bps_workspace_bytes(int W, int H, int D, int levels, int msg_type);
  */
 int bps_create(bps_ctx **out, int W, int H, int D, int levels, int msg_type, void *d_workspace,
                size_t workspace_bytes);
+
+/*
+ * Test hook, failure injection on the host: the next n resource acquisitions of bps_create and
+ * bps_batch_create (device allocations, streams, events) succeed and the one after that fails as
+ * if the CUDA runtime had refused it (the call then returns BPS_ERR_CUDA, having released
+ * everything it had acquired); n < 0 cancels a planned failure.  Process-wide.  Returns BPS_OK.
+ */
+int bps_test_fail_resources(int n);
 
 /* Destroy a context: synchronises its internal stream and frees what it allocated (cudaFree of
  * a context-owned workspace waits for the work in flight on the device; a caller-owned
@@ -197,9 +206,11 @@ int bps_stereo_host(bps_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                     int32_t *h_disp, int64_t *h_energy_i64, double *h_energy_f64, void *stream);
 
 /*
- * Status of the last persistent solve on this context: BPS_OK, or BPS_ERR_TIMEOUT when a
- * grid barrier of the persistent kernel gave up waiting (its results are then incomplete).
- * Synchronous (reads one device word).
+ * Status of this context's device-side checks: BPS_OK, BPS_ERR_TIMEOUT when a bounded wait gave
+ * up (a grid barrier of the last persistent solve, or a stage wait of a bulk-copy sweep since the
+ * last call; the results are then incomplete), or BPS_ERR_INTERNAL when a bounds check of the
+ * debug build (libbpstereo_debug.so, compiled with -DBPS_DEBUG_BOUNDS) failed since the last call.
+ * Reading reports the sweep and bounds errors once (they are cleared).  Synchronous.
  */
 int bps_get_error(bps_ctx *ctx);
 
@@ -291,6 +302,15 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  *                           for HBM-bound scales (not combined with BPS_VARIANT_DPAR);
  *   BPS_VARIANT_STAGED_LISTS the same on the list launches (with BPS_VARIANT_LISTS; not
  *                           combined with BPS_VARIANT_DPAR_LISTS).
+ *   BPS_VARIANT_BULK        dense launches: one warp of each CTA copies the whole records of
+ *                           the pixels that need computing (cost, incoming messages, the
+ *                           receivers' slots for the skip's change test) into a two-stage
+ *                           shared-memory ring with 1-D bulk copies (cp.async.bulk, mbarrier
+ *                           completion) while eight warps compute from the other stage; takes
+ *                           precedence over BPS_VARIANT_STAGED (not combined with BPS_VARIANT_DPAR).
+ *                           Its waits are bounded: one that gives up makes bps_get_error report
+ *                           BPS_ERR_TIMEOUT for the solve;
+ *   BPS_VARIANT_BULK_LISTS  the same on the list launches (with BPS_VARIANT_LISTS).
  * With BPS_FLAG_PROFILE a cluster launch's time is shared out evenly over its half-sweeps.
  * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
@@ -312,6 +332,8 @@ int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
 #define BPS_VARIANT_DPAR_LISTS 32
 #define BPS_VARIANT_STAGED 64
 #define BPS_VARIANT_STAGED_LISTS 128
+#define BPS_VARIANT_BULK 256
+#define BPS_VARIANT_BULK_LISTS 512
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 
@@ -379,6 +401,19 @@ int bps_warmnet_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64
                      float beta2, float eps, int step, void *d_w_bf16, void *stream);
 int bps_warmnet_features(const int32_t *d_cost, int H, int W, int D, float scale, void *d_feat, void *stream);
 int bps_warmnet_messages(const float *d_pred, int H, int W, int D, int cap, int32_t *d_init, void *stream);
+
+/*
+ * Diagnostic: what separating two phases of the solve costs on this GPU, as the chained and the
+ * persistent launch forms pay it.  h_barrier_us receives the time per grid barrier of `phases`
+ * barriers inside one cooperative launch of `ctas` 256-thread CTAs (the persistent kernel's
+ * barrier, bounded wait included); h_boundary_us the time per kernel of `phases` empty kernels of
+ * the same grid chained by programmatic dependent launch and replayed from a CUDA graph (the
+ * boundary between two half-sweeps of the chained form).  Best of three after a warm-up each.
+ * Synchronous; allocates and frees its own stream, events, graph and 16 bytes of device memory.
+ * Errors: BPS_ERR_ARG (ctas < 1, phases outside [1, 100000], NULL outputs), BPS_ERR_UNSUPPORTED
+ * (more CTAs than fit on the GPU at once), BPS_ERR_TIMEOUT (a barrier gave up), BPS_ERR_CUDA.
+ */
+int bps_measure_sync_costs(int ctas, int phases, double *h_barrier_us, double *h_boundary_us);
 
 /*
  * Energy of a labelling without allocating any memory.  The paper has no counterpart:

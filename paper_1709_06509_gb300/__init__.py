@@ -20,6 +20,7 @@ import os
 from . import _build
 
 LIB_PATH = _build.LIB
+LIB_DEBUG_PATH = _build.LIB_DEBUG
 
 BPS_OK = 0
 BPS_ERR_ARG = -1
@@ -28,6 +29,7 @@ BPS_ERR_CUDA = -3
 BPS_ERR_WORKSPACE = -4
 BPS_ERR_TIMEOUT = -5
 BPS_ERR_STATE = -6
+BPS_ERR_INTERNAL = -7
 
 BPS_MSG_INT32 = 0
 BPS_MSG_U8 = 1
@@ -55,6 +57,8 @@ BPS_VARIANT_DPAR = 16
 BPS_VARIANT_DPAR_LISTS = 32
 BPS_VARIANT_STAGED = 64
 BPS_VARIANT_STAGED_LISTS = 128
+BPS_VARIANT_BULK = 256
+BPS_VARIANT_BULK_LISTS = 512
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
@@ -92,6 +96,8 @@ _SIGS = {
     "bps_last_cuda_error": (_I, []),
     "bps_cuda_error_string": (ctypes.c_char_p, [_I]),
     "bps_energy_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "bps_test_fail_resources": (_I, [_I]),
+    "bps_measure_sync_costs": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "bps_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),
     "bps_batch_destroy": (_I, [_P]),
     "bps_batch_stereo": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
@@ -125,6 +131,26 @@ def lib() -> ctypes.CDLL:
             f.restype = res
             f.argtypes = args
     return _lib
+
+
+_lib_debug = None
+
+
+def lib_debug() -> ctypes.CDLL:
+    """Load libbpstereo_debug.so, the same library built with -DBPS_DEBUG_BOUNDS: its kernels check
+    list entries, list appends, cost stores and read-out pixels against their buffers and report a
+    failed check through bps_get_error (BPS_ERR_INTERNAL) instead of accessing out of bounds.  For
+    tests; raises if it has not been built (_build.build(debug=True))."""
+    global _lib_debug
+    if _lib_debug is None:
+        if not os.path.exists(LIB_DEBUG_PATH):
+            raise RuntimeError(f"{LIB_DEBUG_PATH} is missing: build it with paper_1709_06509_gb300._build.build(debug=True)")
+        _lib_debug = ctypes.CDLL(LIB_DEBUG_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(_lib_debug, name)
+            f.restype = res
+            f.argtypes = args
+    return _lib_debug
 
 
 def status_string(status: int) -> str:
@@ -226,6 +252,18 @@ def bps_energy_noalloc(cost, disp, W, H, D, lam, trunc, energy, stream=None):
     device tensor `energy`, with no memory allocated (scratch is a fixed device array)."""
     _check(lib().bps_energy_noalloc(_ptr(cost), _ptr(disp), W, H, D, lam, trunc, _ptr(energy), _stream(stream)),
            "bps_energy_noalloc")
+
+
+def bps_test_fail_resources(n: int) -> None:
+    """Plan a failure of the (n+1)-th resource acquisition of bps_create / bps_batch_create (n < 0: none)."""
+    _check(lib().bps_test_fail_resources(n), "bps_test_fail_resources")
+
+
+def bps_measure_sync_costs(ctas: int, phases: int = 2000) -> tuple[float, float]:
+    """(us per grid barrier in one cooperative launch, us per PDL-chained kernel boundary in a graph)."""
+    b, k = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bps_measure_sync_costs(ctas, phases, ctypes.byref(b), ctypes.byref(k)), "bps_measure_sync_costs")
+    return b.value, k.value
 
 
 def bps_batch_create(ctxs) -> int:
@@ -332,9 +370,10 @@ def bps_cuda_error_string(code: int) -> str:
 
 
 def bps_get_error(ctx) -> int:
-    """BPS_OK or BPS_ERR_TIMEOUT for the last persistent solve (returned, not raised)."""
+    """BPS_OK, BPS_ERR_TIMEOUT or BPS_ERR_INTERNAL from the context's device-side checks (returned, not
+    raised; see include/bpstereo.h)."""
     rc = lib().bps_get_error(ctx)
-    if rc not in (BPS_OK, BPS_ERR_TIMEOUT):
+    if rc not in (BPS_OK, BPS_ERR_TIMEOUT, BPS_ERR_INTERNAL):
         raise BPSError(rc, "bps_get_error")
     return rc
 

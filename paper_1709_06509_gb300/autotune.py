@@ -13,6 +13,8 @@ given scale size and label count (see bps_set_sweep_variant in include/bpstereo.
   DPAR_LISTS         ... on the list launches only
   STAGED             dense launches prefetch the next block's inputs into shared memory (large scales)
   STAGED_LISTS       ... list launches
+  BULK               dense launches fed by a copy warp's bulk copies of whole records (large scales)
+  BULK_LISTS         ... list launches
 and their combinations.  For one context and one representative input, tune() replays the
 whole pipeline from its CUDA graph (the way the variants run in production: consecutive
 launches overlap, which per-launch events would hide) and descends one scale at a time,
@@ -25,20 +27,22 @@ from __future__ import annotations
 import json
 import os
 
-from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS,
-               BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_STAGED,
-               BPS_VARIANT_STAGED_LISTS, BPSError, level_dims)
+from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_BULK, BPS_VARIANT_BULK_LISTS, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR,
+               BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS,
+               BPS_VARIANT_STAGED, BPS_VARIANT_STAGED_LISTS, BPSError, level_dims)
 
 _G, _L, _E, _C, _P, _PL, _S, _SL = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_CLUSTER,
                                     BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_STAGED,
                                     BPS_VARIANT_STAGED_LISTS)
+_B, _BL = BPS_VARIANT_BULK, BPS_VARIANT_BULK_LISTS
 # a cluster launch is only a candidate for scales of at most this many lanes (pixels x lanes per pixel)
 CLUSTER_MAX_LANES = 16 * 16 * 512
 SMALL_CANDIDATES = (0, _G, _E, _E | _G, _C, _C | _E, _C | _E | _G, _P, _P | _G, _P | _E, _P | _E | _G)
 LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, _P | _E, _P | _L, _P | _E | _L,
                     _L | _PL, _E | _L | _PL, _G | _L | _PL, _E | _G | _L | _PL, _S, _S | _G, _S | _L, _S | _G | _L,
                     _S | _L | _PL, _S | _G | _L | _PL, _L | _SL, _G | _L | _SL, _E | _L | _SL, _E | _G | _L | _SL,
-                    _S | _L | _SL, _S | _G | _L | _SL)
+                    _S | _L | _SL, _S | _G | _L | _SL, _B, _B | _L, _L | _BL, _B | _L | _BL, _B | _G | _L | _BL,
+                    _B | _L | _SL, _S | _L | _BL, _E | _L | _BL)
 CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
 DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
 # the list and staged candidates are tried on every scale of at least this many lanes (a scale
@@ -57,7 +61,7 @@ def _candidates(lanes: int, Gp: int) -> list[int]:
 def _key(gpu: str, w: int, h: int, D: int, msg_type: int, trunc: int, skip: bool) -> str:
     tclass = trunc if trunc <= 2 else 3  # the stencil forms exist for trunc 0, 1, 2 only
     Dp = (D + 15) // 16 * 16
-    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v5"
+    return f"{gpu}|{w}x{h}|Dp{Dp}|form{msg_type}|T{tclass}|skip{int(skip)}|v6"
 
 
 def _load(path: str | None) -> dict:
@@ -147,12 +151,12 @@ def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache
         return (0, 0)
     gpu = torch.cuda.get_device_name(st.device)
     Dp = (st.D + 15) // 16 * 16
-    key = f"{gpu}|ncc|{st.W}x{st.H}|Dp{Dp}|w{window}|form{st.msg_type}"
+    key = f"{gpu}|ncc|{st.W}x{st.H}|Dp{Dp}|w{window}|form{st.msg_type}|v2"
     table = _load(cache)
     if key in table:
         best = tuple(table[key])
     else:
-        xs_max = 1 if Dp >= 256 else 256 // Dp
+        xs_max = max(1, 512 // Dp)  # CTAs of up to 512 threads
         cands = [(0, 0)]
         xs = xs_max
         while xs >= 1:

@@ -1,7 +1,10 @@
 // api.cu -- the C ABI (include/bpstereo.h): context, workspace plan, argument checks and
 // the launch sequence of the hot path.  No exception crosses the boundary; every CUDA
 // error becomes BPS_ERR_CUDA.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -12,6 +15,33 @@
 using namespace bps;
 
 namespace {
+
+// Failure injection on the host (bps_test_fail_resources): the number of resource acquisitions
+// of bps_create / bps_batch_create still allowed to succeed, -1 when no failure is planned.
+std::atomic<int> g_fail_after{-1};
+
+// Whether this acquisition is the one planned to fail (the plan is used up by it).
+bool injected_failure() {
+    int v = g_fail_after.load();
+    while (v >= 0)
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+cudaError_t acquire_memory(void **p, size_t bytes) {
+    return injected_failure() ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes);
+}
+cudaError_t acquire_stream(cudaStream_t *s) {
+    return injected_failure() ? cudaErrorMemoryAllocation : cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+cudaError_t acquire_event(cudaEvent_t *e) {
+    return injected_failure() ? cudaErrorMemoryAllocation : cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+
+// Host-side ranges (NVTX) around the enqueued stages: visible in a timeline profiler, free otherwise.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 constexpr size_t ALIGN = 256;
 inline size_t up(size_t v, size_t a = ALIGN) { return (v + a - 1) / a * a; }
@@ -264,6 +294,7 @@ extern "C" const char *bps_status_string(int s) {
     case BPS_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
     case BPS_ERR_TIMEOUT: return "bounded device wait gave up";
     case BPS_ERR_STATE: return "call order violated";
+    case BPS_ERR_INTERNAL: return "a device-side consistency check failed";
     default: return "unknown status";
     }
 }
@@ -297,7 +328,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     if (d_workspace) {
         c->ws = static_cast<char *>(d_workspace);
     } else {
-        if (cudaMalloc(&c->ws, p.total) != cudaSuccess) {
+        if (acquire_memory(reinterpret_cast<void **>(&c->ws), p.total) != cudaSuccess) {
             delete c;
             return BPS_ERR_CUDA;
         }
@@ -314,6 +345,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.pWh = 0;
         v.pmsg[0] = v.pmsg[1] = nullptr;
         v.disp = nullptr;
+        v.err = nullptr;  // set below, once the workspace is laid out
         for (int k = 0; k < 2; ++k) {
             v.cost[k] = c->ws + p.cost[l][k];
             v.msg[k] = c->ws + p.msg[l][k];
@@ -330,6 +362,9 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->d_desc = reinterpret_cast<PairDesc *>(c->ws + p.desc);
     c->d_prefix = reinterpret_cast<int *>(c->ws + p.prefix);
     c->d_barrier = reinterpret_cast<unsigned *>(c->ws + p.barrier);
+    // words of the barrier area: arrivals and error of the persistent kernel, then the error word
+    // of the bounded waits of the chained sweeps
+    for (int l = 0; l < levels; ++l) c->lv[l].err = c->d_barrier + 2;
     c->lists[0] = reinterpret_cast<unsigned *>(c->ws + p.lists[0]);
     c->lists[1] = reinterpret_cast<unsigned *>(c->ws + p.lists[1]);
     c->list_counts = reinterpret_cast<unsigned *>(c->ws + p.list_counts);
@@ -345,7 +380,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     }
     prefix[2 * levels] = 0;
     prefix[2 * levels + 1] = wta_blocks(c);
-    bool ok = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = acquire_stream(&c->cap) == cudaSuccess;
     // every persistent kernel (one per minimisation form) is loaded and sized now, outside any capture
     for (int T = 1; ok && T <= 3; ++T) ok = persistent_grid(c->msg_kind, T, &c->grid) == cudaSuccess;
     // the NCC kernel's shared memory depends on D and the window; allow the largest window now so
@@ -404,6 +439,7 @@ static int check_cost_args(bps_ctx *c, const uint8_t *L, const uint8_t *R, int p
 
 static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitch, int window, int trunc_data,
                         float *ncc_out, cudaStream_t st) {
+    Range range("bps cost volume");
     const LevelView &v0 = c->lv[0];
     int first_pyramid = 1;
     if (window <= NCC_ROWS_MAX_WINDOW) {
@@ -577,7 +613,10 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
     // keep the dense launch, whose clean warps exit after one flag load.
     int t = 0;
     c->last_sparse_k = c->sv.K;
+    static const char *scale_names[BPS_MAX_LEVELS] = {"bps scale 0", "bps scale 1", "bps scale 2", "bps scale 3",
+                                                      "bps scale 4", "bps scale 5", "bps scale 6", "bps scale 7"};
     for (int l = top; l >= 0; --l) {
+        Range range(scale_names[l]);
         LevelView v = c->lv[l];
         if (l == 0) v.disp = readout;  // the finest scale's half-sweeps read out what they recompute
         if (l == 0 && c->sv.K > 0) {
@@ -828,11 +867,18 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
     return (flags & BPS_FLAG_PERSISTENT) ? bps_get_error(c) : BPS_OK;
 }
 
+extern "C" int bps_test_fail_resources(int n) {
+    g_fail_after.store(n < 0 ? -1 : n);
+    return BPS_OK;
+}
+
 extern "C" int bps_get_error(bps_ctx *c) {
     if (!c) return BPS_ERR_ARG;
-    unsigned w[2] = {0u, 0u};
+    unsigned w[3] = {0u, 0u, 0u};
     CK(cudaMemcpy(w, c->d_barrier, sizeof(w), cudaMemcpyDeviceToHost));
-    return w[1] ? BPS_ERR_TIMEOUT : BPS_OK;
+    if (w[2]) CK(cudaMemset(c->d_barrier + 2, 0, sizeof(unsigned)));  // reported once
+    if (w[2] >= 2u) return BPS_ERR_INTERNAL;
+    return (w[1] || w[2]) ? BPS_ERR_TIMEOUT : BPS_OK;
 }
 
 extern "C" int bps_get_trace(bps_ctx *c, int64_t *h_counts, int cap) {
@@ -960,15 +1006,15 @@ extern "C" int bps_batch_create(bps_batch **out, bps_ctx *const *ctxs, int n) {
     b->levels = ctxs[0]->levels;
     b->msg_type = ctxs[0]->msg_type;
     b->msg_kind = ctxs[0]->msg_kind;
-    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = acquire_stream(&b->cap) == cudaSuccess;
     for (int i = 0; ok && i < n; ++i) {
         cudaStream_t s;
-        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+        ok = acquire_stream(&s) == cudaSuccess;
         if (ok) b->streams.push_back(s);
     }
     for (int i = 0; ok && i <= n; ++i) {
         cudaEvent_t e;
-        ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        ok = acquire_event(&e) == cudaSuccess;
         if (ok) b->events.push_back(e);
     }
     // descriptors of the lockstep persistent launch
@@ -978,9 +1024,9 @@ extern "C" int bps_batch_create(bps_batch **out, bps_ctx *const *ctxs, int n) {
         for (int i = 0; i < n; ++i) prefix[(size_t)l * (n + 1) + i + 1] = prefix[(size_t)l * (n + 1) + i] + sweep_blocks(ctxs[i], l);
     for (int i = 0; i < n; ++i) prefix[(size_t)L * (n + 1) + i + 1] = prefix[(size_t)L * (n + 1) + i] + wta_blocks(ctxs[i]);
     for (int i = 0; i < n; ++i) b->h_desc.push_back(make_desc(ctxs[i]));
-    ok = ok && cudaMalloc(&b->d_desc, sizeof(PairDesc) * n) == cudaSuccess;
-    ok = ok && cudaMalloc(&b->d_prefix, sizeof(int) * prefix.size()) == cudaSuccess;
-    ok = ok && cudaMalloc(&b->d_barrier, 2 * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && acquire_memory(reinterpret_cast<void **>(&b->d_desc), sizeof(PairDesc) * n) == cudaSuccess;
+    ok = ok && acquire_memory(reinterpret_cast<void **>(&b->d_prefix), sizeof(int) * prefix.size()) == cudaSuccess;
+    ok = ok && acquire_memory(reinterpret_cast<void **>(&b->d_barrier), 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemcpy(b->d_desc, b->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     for (int T = 1; ok && T <= 3; ++T) ok = persistent_grid(b->msg_kind, T, &b->grid) == cudaSuccess;
@@ -1232,8 +1278,8 @@ extern "C" int bps_batch_stereo_host(bps_batch *b, const uint8_t *const *h_lefts
 extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     if (!c || level < 0 || level >= c->levels || variant < -1 ||
         variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER |
-                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED |
-                    BPS_VARIANT_STAGED_LISTS))
+                   BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED | BPS_VARIANT_STAGED_LISTS |
+                   BPS_VARIANT_BULK | BPS_VARIANT_BULK_LISTS))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp, c->msg_kind)

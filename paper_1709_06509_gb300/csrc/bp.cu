@@ -125,6 +125,213 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
 
 static size_t staged_smem_bytes() { return (size_t)2 * STAGE_CHUNKS * 256 * sizeof(uint4); }
 
+// ------------------------------------------------------------------ bulk-copy pipeline
+// sweep_u8_bulk_kernel: one warp of the CTA copies, eight compute.  The copy warp walks the CTA's
+// pixel blocks (grid-stride; consecutive slots, or the entries of an active list) and, for every
+// pixel that needs it, issues 1-D bulk copies (cp.async.bulk, completion counted in bytes on an
+// mbarrier) of its whole records into a stage of shared memory: the cost record (2 Dp bytes), the
+// incoming record (4 Dp; the parent's record in a scale's first half-sweep) and, for the skip's
+// change test, the receivers' four slots (Dp each; the parents' slots in a scale's second
+// half-sweep).  The compute warps wait for a stage, run the u8 body on it and release it.  Memory
+// parallelism then costs shared memory only, and the copies of the next block are in flight while
+// the current one computes, stores its messages and flips the skip flags.  Every wait is bounded:
+// a wait that gives up sets lv.err and the CTA returns (the copy warp first waits, again bounded,
+// for the stages it filled).
+constexpr int BULK_THREADS = BULK_CONSUMERS + 32, BULK_STAGES = 2;
+constexpr unsigned BULK_WAIT_LIMIT = 1u << 22;  // try_wait attempts before a wait gives up (seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of `bar` to complete, at most BULK_WAIT_LIMIT attempts; false (and the
+// error word set) when it gives up or another warp already has.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned *err) {
+    for (unsigned it = 0; it < BULK_WAIT_LIMIT; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && err && *reinterpret_cast<volatile unsigned *>(err)) return false;
+    }
+    if (err) atomicExch(err, 1u);
+    return false;
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__host__ __device__ inline size_t bulk_stage_bytes(int Dp, int Gp) {
+    return ((size_t)(BULK_CONSUMERS / Gp) * 10 * Dp + 127) / 128 * 128;
+}
+static size_t bulk_smem_bytes(int Dp, int Gp) {
+    return BULK_STAGES * bulk_stage_bytes(Dp, Gp) + 2 * BULK_STAGES * sizeof(uint64_t) +
+           (size_t)BULK_STAGES * (BULK_CONSUMERS / Gp) * sizeof(unsigned);
+}
+constexpr size_t BULK_SMEM_MAX = BULK_STAGES * (size_t)BULK_CONSUMERS * 10 * VEC + 2 * BULK_STAGES * 8 +
+                                 BULK_STAGES * BULK_CONSUMERS * 4;
+
+// LISTED: the pixels are the entries of al.in (count *al.n_in); otherwise consecutive slots, and a
+// pixel is copied and computed only when it needs it (scale start, skip off, or its flag set).
+template <bool PADDED, int TS, bool LISTED, bool APPEND>
+__global__ void __launch_bounds__(BULK_THREADS, 2)
+sweep_u8_bulk_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                     unsigned long long *trace, int nblocks, ActiveList al) {
+    extern __shared__ __align__(128) unsigned char bulk_mem[];
+    const int P = BULK_CONSUMERS / Gp;  // pixels a block
+    const size_t stage_bytes = bulk_stage_bytes(Dp, Gp);
+    uint64_t *full = reinterpret_cast<uint64_t *>(bulk_mem + BULK_STAGES * stage_bytes);
+    uint64_t *empty = full + BULK_STAGES;
+    unsigned *slots = reinterpret_cast<unsigned *>(empty + BULK_STAGES);  // [BULK_STAGES][P]
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < BULK_STAGES; ++k) {
+            mbar_init(&full[k], 1);                      // the copy warp's arrival (and the bytes)
+            mbar_init(&empty[k], BULK_CONSUMERS / 32);  // one arrival per compute warp
+        }
+    }
+    __syncthreads();
+    pdl_enter();
+    const int64_t nslot = (int64_t)lv.H * lv.Wh;
+    const int64_t n = LISTED ? (int64_t)*al.n_in : nslot;
+    const int64_t nb = LISTED ? (n + P - 1) / P : nblocks;
+    const int16_t *cost = reinterpret_cast<const int16_t *>(colour ? lv.cost[1] : lv.cost[0]);
+    const uint8_t *msg_in = reinterpret_cast<const uint8_t *>(colour ? lv.msg[1] : lv.msg[0]);
+    const uint8_t *msg_out = reinterpret_cast<const uint8_t *>(colour ? lv.msg[0] : lv.msg[1]);
+    const unsigned *dirty_in = colour ? lv.dirty[1] : lv.dirty[0];
+    const bool old_copies = skip && lv.start != 1;  // a scale's first half-sweep compares nothing
+
+    if (threadIdx.x >= BULK_CONSUMERS) {  // the copy warp
+        const int lane = threadIdx.x & 31;
+        int64_t k = 0;
+        bool ok = true;
+        for (int64_t b = blockIdx.x; b < nb; b += gridDim.x, ++k) {
+            const int st = (int)(k % BULK_STAGES);
+            if (k >= BULK_STAGES && !mbar_wait(&empty[st], (unsigned)((k / BULK_STAGES - 1) & 1), lv.err)) {
+                ok = false;
+                break;
+            }
+            unsigned char *base = bulk_mem + st * stage_bytes;
+            unsigned *sl = slots + st * P;
+            unsigned bytes = 0;
+            for (int i = lane; i < P; i += 32) {  // which pixels, and how many bytes they bring
+                int64_t s = b * P + i;
+                if (LISTED) s = s < n ? (int64_t)al.in[s] : nslot;
+                bool act = false;
+                if (s < nslot) {
+                    const int y = (int)(s / lv.Wh);
+                    const int x = 2 * (int)(s - (int64_t)y * lv.Wh) + ((y + colour) & 1);
+                    act = x < lv.W && (LISTED || !skip || lv.start != 0 || dirty_in[s] == 1u);
+                    if (act && old_copies) {
+                        const int nq = (y > 0) + (y < lv.H - 1) + (x > 0) + (x < lv.W - 1);
+                        bytes += (unsigned)(nq * Dp);
+                    }
+                }
+                sl[i] = act ? (unsigned)s : 0xffffffffu;
+                if (act) bytes += (unsigned)(6 * Dp);
+            }
+            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(FULL, bytes, o);
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes);
+            __syncwarp();
+            for (int i = lane; i < P; i += 32) {
+                const unsigned s = sl[i];
+                if (s == 0xffffffffu) continue;
+                const int y = (int)(s / (unsigned)lv.Wh);
+                const int x = 2 * (int)(s - (unsigned)y * (unsigned)lv.Wh) + ((y + colour) & 1);
+                bulk_copy(base + (size_t)i * 2 * Dp, cost + (int64_t)s * Dp, 2 * Dp, &full[st]);
+                const uint8_t *src = msg_in + (int64_t)s * 4 * Dp;
+                if (lv.start == 1) {  // a scale's first half-sweep: the parent's record
+                    const int px = x >> 1, py = y >> 1;
+                    src = reinterpret_cast<const uint8_t *>(colour_of(px, py) ? lv.pmsg[1] : lv.pmsg[0]) +
+                          slot_of(px, py, lv.pWh) * 4 * Dp;
+                }
+                bulk_copy(base + (size_t)P * 2 * Dp + (size_t)i * 4 * Dp, src, 4 * Dp, &full[st]);
+                if (old_copies) {
+                    const bool has[4] = {y > 0, y < lv.H - 1, x > 0, x < lv.W - 1};
+                    const int nbx[4] = {x, x, x - 1, x + 1};
+                    const int nby[4] = {y - 1, y + 1, y, y};
+                    const int opp[4] = {DIR_DOWN, DIR_UP, DIR_RIGHT, DIR_LEFT};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (!has[q]) continue;
+                        const uint8_t *o = lv.start == 2 ? start_slot_u8(lv, nbx[q], nby[q], opp[q], Dp, 0, true)
+                                                         : msg_out + (slot_of(nbx[q], nby[q], lv.Wh) * 4 + opp[q]) * Dp;
+                        bulk_copy(base + (size_t)P * 6 * Dp + (size_t)i * 4 * Dp + q * Dp, o, Dp, &full[st]);
+                    }
+                }
+            }
+        }
+        if (!ok) {
+            // a wait gave up: let the stages this warp filled land before the CTA returns
+            for (int64_t j = (k > BULK_STAGES ? k - BULK_STAGES : 0); j < k; ++j)
+                mbar_wait(&full[j % BULK_STAGES], (unsigned)((j / BULK_STAGES) & 1), nullptr);
+        }
+        return;
+    }
+    // the compute warps
+    int64_t k = 0;
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x, ++k) {
+        const int st = (int)(k % BULK_STAGES);
+        if (!mbar_wait(&full[st], (unsigned)((k / BULK_STAGES) & 1), lv.err)) break;
+        const unsigned s = slots[st * P + threadIdx.x / Gp];
+        sweep_group_u8<PADDED, APPEND, TS, false, 4, true>(
+            lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al, n, s == 0xffffffffu ? nslot : (int64_t)s,
+            reinterpret_cast<const uint4 *>(bulk_mem + st * stage_bytes));
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
+    }
+}
+
+// CTAs of the bulk-copy sweep resident at once for this shared-memory size.
+static int resident_bulk_blocks(size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_bulk_kernel<false, 2, true, true>, BULK_THREADS,
+                                                  smem);
+    return std::max(1, sms * std::max(1, per_sm));
+}
+
+template <bool PADDED, int TS>
+static cudaError_t launch_u8_bulk(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
+                                  unsigned long long *trace, const ActiveList &al, cudaStream_t st) {
+    static int cached_smem = -1, cached_grid = 0;  // the resident CTAs depend on the stage size only
+    const size_t smem = bulk_smem_bytes(Dp, Gp);
+    if ((int)smem != cached_smem) {
+        cached_grid = resident_bulk_blocks(smem);
+        cached_smem = (int)smem;
+    }
+    const int P = BULK_CONSUMERS / Gp;
+    const int64_t blocks = ((int64_t)lv.H * lv.Wh + P - 1) / P;
+    if (blocks == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, cached_grid);
+    if (skip && al.in)
+        return launch_k(sweep_u8_bulk_kernel<PADDED, TS, true, true>, dim3(grid), dim3(BULK_THREADS), smem, st, lv,
+                        colour, D, Dp, Gp, lam, lamT, skip, trace, (int)blocks, al);
+    const ActiveList dense{nullptr, nullptr, al.out, al.n_out};
+    if (al.out)
+        return launch_k(sweep_u8_bulk_kernel<PADDED, TS, false, true>, dim3(grid), dim3(BULK_THREADS), smem, st, lv,
+                        colour, D, Dp, Gp, lam, lamT, skip, trace, (int)blocks, dense);
+    return launch_k(sweep_u8_bulk_kernel<PADDED, TS, false, false>, dim3(grid), dim3(BULK_THREADS), smem, st, lv,
+                    colour, D, Dp, Gp, lam, lamT, skip, trace, (int)blocks, dense);
+}
+
 // A list launch's loop over the entries with one group of Gp lanes a pixel, or with 4 Gp lanes
 // a pixel (DP: one group per direction); `e` is this thread's first entry, read by the caller
 // together with the list length n.  Indexes are 32-bit: a colour has at most 2^30 pixels
@@ -296,8 +503,9 @@ static int resident_staged_blocks() {
 template <bool PADDED, int TS, bool DP>
 static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                                bool eager, cudaStream_t st, bool staged = false) {
+                                bool eager, cudaStream_t st, bool staged = false, bool bulk = false) {
     if constexpr (!DP) {
+        if (bulk) return launch_u8_bulk<PADDED, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, al, st);
         if (staged && skip && al.in)
             return launch_k(sweep_u8_staged_list_kernel<PADDED, TS>,
                             dim3((unsigned)std::min<int64_t>(blocks, resident_staged_blocks())), dim3(256),
@@ -332,26 +540,26 @@ static cudaError_t launch_u8_dp(const LevelView &lv, int colour, int D, int Dp, 
 template <bool PADDED, int TS>
 static cudaError_t launch_u8_ts(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                                 unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                                bool eager, bool dp, bool staged, cudaStream_t st) {
+                                bool eager, bool dp, bool staged, bool bulk, cudaStream_t st) {
     if (dp) return launch_u8_dp<PADDED, TS, true>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st);
     return launch_u8_dp<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, st,
-                                           staged);
+                                           staged, bulk);
 }
 
 template <bool PADDED>
 static cudaError_t launch_u8(int ts, const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                              unsigned long long *trace, int64_t blocks, unsigned grid, const ActiveList &al,
-                             bool eager, bool dp, bool staged, cudaStream_t st) {
+                             bool eager, bool dp, bool staged, bool bulk, cudaStream_t st) {
     switch (ts) {
     case 1:
         return launch_u8_ts<PADDED, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
-                                       staged, st);
+                                       staged, bulk, st);
     case 2:
         return launch_u8_ts<PADDED, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
-                                       staged, st);
+                                       staged, bulk, st);
     default:
         return launch_u8_ts<PADDED, 0>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blocks, grid, al, eager, dp,
-                                       staged, st);
+                                       staged, bulk, st);
     }
 }
 
@@ -407,11 +615,12 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
         const bool eager = (variant & VARIANT_EAGER) != 0;
         const bool staged = (variant & (list_launch ? VARIANT_STAGED_LISTS : VARIANT_STAGED)) != 0 && !dp;
+        const bool bulk = (variant & (list_launch ? VARIANT_BULK_LISTS : VARIANT_BULK)) != 0 && !dp;
         if (D & 15)
             return launch_u8<true>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
-                                   staged, st);
+                                   staged, bulk, st);
         return launch_u8<false>(ts, lv, colour, D, Dp, Gp, lam, lam * trunc, skip, trace, blocks, grid, al, eager, dp,
-                                staged, st);
+                                staged, bulk, st);
     }
     default:
         // packed half2 arithmetic where the stencil forms apply (the GENERAL_DT variant keeps the
@@ -567,6 +776,15 @@ template <bool PADDED, int TS> static cudaError_t preload_u8() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep_u8_staged_list_kernel<PADDED, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)staged_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_bulk_kernel<PADDED, TS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BULK_SMEM_MAX);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_bulk_kernel<PADDED, TS, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BULK_SMEM_MAX);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_u8_bulk_kernel<PADDED, TS, false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BULK_SMEM_MAX);
     return e;
 }
 

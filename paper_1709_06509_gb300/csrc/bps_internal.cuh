@@ -43,7 +43,25 @@ struct LevelView {
     // Read-out during the finest scale's half-sweeps (u8 form, exact skip rule): each recomputed
     // pixel writes the argmin of the belief it forms to disp[y * W + x] (nullable: no read-out).
     int32_t *disp;
+    // Error word of the context's device-side checks: 1 when a bounded wait of a bulk-copy sweep gave
+    // up, 2 and above from the debug build's bounds checks; read and cleared by bps_get_error.
+    unsigned *err;
 };
+
+// Device-side consistency checks of the debug build (compiled with -DBPS_DEBUG_BOUNDS): a failed
+// check records its code in the context's error word (the largest code wins) and the caller skips
+// the access it guards; bps_get_error then reports BPS_ERR_INTERNAL.  In the normal build a check
+// is the constant true and costs nothing.  Codes: 2 a list entry past the scale, 3 a list append
+// past its capacity, 4 a data-cost store outside its scale, 5 a read-out pixel outside the image.
+#ifdef BPS_DEBUG_BOUNDS
+__device__ __forceinline__ bool bps_check(bool ok, unsigned *err, unsigned code) {
+    if (!ok && err) atomicMax(err, code);
+    return ok;
+}
+#define BPS_CHECK(cond, err, code) ::bps::bps_check((cond), (err), (code))
+#else
+#define BPS_CHECK(cond, err, code) true
+#endif
 
 // Programmatic dependent launch: every kernel of the stereo chain is launched so that it may
 // start while its predecessor is still running; it waits here until the predecessor's grid

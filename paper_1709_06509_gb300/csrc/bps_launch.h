@@ -60,6 +60,8 @@ constexpr int VARIANT_DPAR = 16;       // one lane group per (pixel, direction),
 constexpr int VARIANT_DPAR_LISTS = 32; // ... on the list launches only
 constexpr int VARIANT_STAGED = 64;     // dense launches stage the next block's inputs in shared memory
 constexpr int VARIANT_STAGED_LISTS = 128; // ... list launches
+constexpr int VARIANT_BULK = 256;      // dense launches fed by a copy warp's cp.async.bulk pipeline
+constexpr int VARIANT_BULK_LISTS = 512; // ... list launches
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {

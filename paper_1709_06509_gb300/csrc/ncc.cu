@@ -194,7 +194,7 @@ static int smem_optin() {
 // of its exact value (see quantise_fp32); the FP64 sequence decides only where v lies within
 // (T + 1) 2^-17 of an integer, after the row, for the few outputs that need it.
 constexpr int NR_TX = 16;
-constexpr int NR_ITEMS = 4;  // staged columns per thread at most (checked by the launcher)
+constexpr int NR_ITEMS_MAX = 4;  // staged columns per thread at most (checked by the launcher)
 #ifndef NCC_ROWS_MAXNREG
 #define NCC_ROWS_MAXNREG 80  // registers a thread: 24 warps on an SM, CTAs of up to 512 threads
 #endif
@@ -248,13 +248,15 @@ __device__ __forceinline__ int quantise_fp32(float numf, float tra, float rb, fl
     return min((int)fl, T);
 }
 
-template <typename CostT, int R, bool NCC_OUT>
+template <typename CostT, int R, bool NCC_OUT, int NR_ITEMS>
 __global__ void __maxnreg__(NCC_ROWS_MAXNREG)
 ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Rimg, int pitch, int W, int H, int D,
                 int Dp, int T, int TYS, LevelView l0, LevelView l1, int write_l1, float *ncc_out) {
-    // blockDim.x = XS * Dp: XS column groups of 16, all labels
+    // blockDim.x = XS * Dp: XS column groups of 16, all labels.  Rows are processed in pairs
+    // (y, y + 1), y even: one shift-and-publish phase and one record phase per pair, each followed
+    // by a CTA barrier, then the outputs of both rows, whose 2x2 sums complete scale 1 at once.
     using Num = typename NccInt<R>::type;
-    constexpr int WIN = 2 * R + 1, VN = NR_TX + 2 * R;
+    constexpr int WIN = 2 * R + 1;
     constexpr int NW = WinWords<R>::NW, NWP = WinWords<R>::NWP;
     constexpr bool FLOAT_COST = CostOut<CostT>::is_float;
     using WinT = Win<NWP>;
@@ -267,16 +269,19 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
     const int x0 = blockIdx.x * CW, y0 = blockIdx.y * TYS, y1 = min(H, y0 + TYS);
     const int N = WIN * WIN;
 
-    // per-pixel and per-right-position records {S, N S_xx - S_x^2, its rsqrt, 0}: one 16-byte
-    // shared load each per output
-    int4 *PA = reinterpret_cast<int4 *>(smem);       // [CW]  left window at pixel x0 + i
-    int4 *PB = PA + CW;                              // [UW]  right window at u = x0 - (D-1) + i
-    WinT *LWn = reinterpret_cast<WinT *>(PB + UW);   // [2][LW] packed left column windows (by row parity)
-    WinT *RWn = LWn + 2 * LW;                        // [2][RW] ... right
-    int *colA = reinterpret_cast<int *>(RWn + 2 * RW);  // [LW]  column sums of L over the window rows
-    int *colAA = colA + LW;                          // [LW]
-    int *colB = colAA + LW;                          // [RW]
-    int *colBB = colB + RW;                          // [RW]
+    // per row h of the pair: the records the outputs read, {S, T / sqrt(N S_xx - S_x^2)} per left
+    // pixel and {S, 1 / sqrt(...)} per right position (8 bytes: one shared load each per output),
+    // and the ones only the FP64 decision and the correlation output read, {N S_xx - S_x^2, 1 / sqrt}
+    int2 *PA = reinterpret_cast<int2 *>(smem);       // [2][CW]  left window at pixel x0 + i
+    int2 *PB = PA + 2 * CW;                          // [2][UW]  right window at u = x0 - (D-1) + i
+    int2 *QA = PB + 2 * UW;                          // [2][CW]
+    int2 *QB = QA + 2 * CW;                          // [2][UW]
+    WinT *LWn = reinterpret_cast<WinT *>(QB + 2 * UW);  // [4][LW] packed left column windows (by row & 3)
+    WinT *RWn = LWn + 4 * LW;                        // [4][RW] ... right
+    int *colA = reinterpret_cast<int *>(RWn + 4 * RW);  // [2][LW]  column sums of L over the window rows
+    int *colAA = colA + 2 * LW;                      // [2][LW]
+    int *colB = colAA + 2 * LW;                      // [2][RW]
+    int *colBB = colB + 2 * RW;                      // [2][RW]
 
     // the staged columns this thread owns: item k is column tid + k * blockDim of the left
     // (index < LW) or the right (index - LW) image
@@ -307,19 +312,45 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
             win[k][(WIN - 1) / 4] |= bytes[k] << (8 * ((WIN - 1) % 4));
         }
     };
+    // publish the owned windows (row buffer wb) and their column sums (column buffer h)
+    auto publish = [&](int wb, int h) {
+#pragma unroll
+        for (int k = 0; k < NR_ITEMS; ++k) {
+            if (k >= nk) break;
+            const int it = threadIdx.x + k * blockDim.x;
+            unsigned s = 0u, ss = 0u;
+            WinT wv;
+#pragma unroll
+            for (int w = 0; w < NWP; ++w) {
+                wv.w[w] = win[k][w];
+                if (w < NW) {
+                    s = __dp4a(win[k][w], 0x01010101u, s);
+                    ss = __dp4a(win[k][w], win[k][w], ss);
+                }
+            }
+            if (it < LW) {
+                LWn[wb * LW + it] = wv;
+                colA[h * LW + it] = (int)s;
+                colAA[h * LW + it] = (int)ss;
+            } else {
+                RWn[wb * RW + it - LW] = wv;
+                colB[h * RW + it - LW] = (int)s;
+                colBB[h * RW + it - LW] = (int)ss;
+            }
+        }
+    };
 
     pdl_enter();
     // the 2R rows above the strip enter the owners' windows first
-    uint32_t next[NR_ITEMS];
+    uint32_t next0[NR_ITEMS], next1[NR_ITEMS];
     for (int e = y0 - R; e < y0 + R; ++e) {
-        load_row(e, next);
-        shift_in(next);
+        load_row(e, next0);
+        shift_in(next0);
     }
-    load_row(y0 + R, next);
+    load_row(y0 + R, next0);
+    load_row(y0 + 1 + R, next1);
 
     int acc[NR_TX / 2];
-#pragma unroll
-    for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
     const int lbase = xs * NR_TX;               // this thread's first staged left column
     const int rbase = xs * NR_TX + D - 1 - d;   // ... and the right column matching it at label d
     const int xb = x0 + lbase;
@@ -327,149 +358,155 @@ ncc_rows_kernel(const uint8_t *__restrict__ Limg, const uint8_t *__restrict__ Ri
     const bool lab = dl < D;
     const float T_half = (float)T + 0.5f, half_m = 0.5f - (float)(T + 1) * (1.f / 131072.f);
 
-    for (int y = y0; y < y1; ++y) {
-        const int par = y & 1;
-        // phase 1: the owners shift row y + R in, publish the words and the column sums
+    for (int y = y0; y < y1; y += 2) {
+        const int nrows = min(2, y1 - y);  // 1 only for the last row of an odd image height
+        // phase 1: the owners shift rows y + R and y + 1 + R in, publish the words and the column sums
         {
-            uint32_t cur[NR_ITEMS];
-#pragma unroll
-            for (int k = 0; k < NR_ITEMS; ++k) cur[k] = next[k];
-            if (y + 1 < y1) load_row(y + 1 + R, next);  // in flight during this row
-            shift_in(cur);
+            uint32_t cur0[NR_ITEMS], cur1[NR_ITEMS];
 #pragma unroll
             for (int k = 0; k < NR_ITEMS; ++k) {
-                if (k >= nk) break;
-                const int it = threadIdx.x + k * blockDim.x;
-                unsigned s = 0u, ss = 0u;
-                WinT wv;
+                cur0[k] = next0[k];
+                cur1[k] = next1[k];
+            }
+            if (y + 2 < y1) {  // the next pair's rows are in flight during this pair
+                load_row(y + 2 + R, next0);
+                load_row(y + 3 + R, next1);
+            }
+            shift_in(cur0);
+            publish(y & 3, 0);
+            if (nrows == 2) {
+                shift_in(cur1);
+                publish((y + 1) & 3, 1);
+            }
+        }
+        __syncthreads();
+        // phase 2: window records of every left pixel and every right position, both rows
+        for (int i = threadIdx.x; i < nrows * (CW + UW); i += blockDim.x) {
+            const int h = i >= CW + UW ? 1 : 0;
+            const int k = i - h * (CW + UW);
+            const bool left = k < CW;
+            const int c = left ? k : k - CW;
+            const int *cs = left ? colA + h * LW + c : colB + h * RW + c;
+            const int *css = left ? colAA + h * LW + c : colBB + h * RW + c;
+            int s = 0, ss = 0;
 #pragma unroll
-                for (int w = 0; w < NWP; ++w) {
-                    wv.w[w] = win[k][w];
-                    if (w < NW) {
-                        s = __dp4a(win[k][w], 0x01010101u, s);
-                        ss = __dp4a(win[k][w], win[k][w], ss);
+            for (int q = 0; q < WIN; ++q) {
+                s += cs[q];
+                ss += css[q];
+            }
+            const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
+            const float r = v ? rsqrtf((float)v) : 0.f;
+            if (left) {
+                PA[h * CW + c] = make_int2(s, __float_as_int(__fmul_rn((float)T, r)));
+                QA[h * CW + c] = make_int2((int)v, __float_as_int(r));
+            } else {
+                PB[h * UW + c] = make_int2(s, __float_as_int(r));
+                QB[h * UW + c] = make_int2((int)v, 0);
+            }
+        }
+        __syncthreads();
+        // phase 3: this thread's 16 outputs at label dl, in each row of the pair
+        if constexpr (!FLOAT_COST) {
+#pragma unroll
+            for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
+        }
+        for (int h = 0; h < nrows; ++h) {
+            const int yy = y + h;
+            const WinT *Lrow = LWn + (yy & 3) * LW + lbase;
+            const WinT *Rrow = RWn + (yy & 3) * RW + rbase;
+            const int2 *pa_row = PA + h * CW + lbase;
+            const int2 *pb_row = PB + h * UW + lbase + D - 1 - d;
+            // the window's column dot products (L x R over the 2R + 1 rows): a ring of the last
+            // 2R + 1, each formed when it enters the horizontal window (fewer live registers)
+            auto dot = [&](int i) {
+                const WinT a = Lrow[i], b = Rrow[i];
+                unsigned v = 0u;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
+                return (int)v;
+            };
+            int V[WIN];
+#pragma unroll
+            for (int i = 0; i < WIN; ++i) V[i] = dot(i);
+            // destinations: x0 + lbase is even, so column j has colour (j + yy) & 1 and slot
+            // row_slot + j / 2 in that colour's array
+            const int64_t row_slot = (int64_t)yy * l0.Wh + (xb >> 1);
+            CostT *const base_even = reinterpret_cast<CostT *>((yy & 1) ? l0.cost[1] : l0.cost[0]) + row_slot * Dp +
+                                     label_pos<CostT>(dl);
+            CostT *const base_odd = reinterpret_cast<CostT *>((yy & 1) ? l0.cost[0] : l0.cost[1]) + row_slot * Dp +
+                                    label_pos<CostT>(dl);
+            unsigned near_mask = 0u;  // outputs whose level the FP64 sequence must decide
+            int S = 0;
+#pragma unroll
+            for (int i = 0; i < WIN; ++i) S += V[i];
+#pragma unroll
+            for (int j = 0; j < NR_TX; ++j) {
+                if (j) {  // column j + 2R enters, column j - 1 leaves (its slot in the ring)
+                    const int vn = dot(j + 2 * R);
+                    S += vn - V[(j - 1) % WIN];
+                    V[(j - 1) % WIN] = vn;
+                }
+                const int2 pa = pa_row[j];
+                const int2 pb = pb_row[j];
+                const Num num = (Num)N * (Num)S - (Num)pa.x * (Num)pb.x;
+                bool near;
+                const int c = quantise_fp32((float)num, __int_as_float(pa.y), __int_as_float(pb.y), T_half, half_m, T,
+                                            &near);
+                float nccf = 0.f;
+                if constexpr (NCC_OUT || FLOAT_COST)
+                    nccf = __fmul_rn(__fmul_rn((float)num, __int_as_float(QA[h * CW + lbase + j].y)),
+                                     __int_as_float(pb.y));
+                const bool inside = j < nvalid;
+                CostT *dst = ((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp;
+                if constexpr (FLOAT_COST) {
+                    const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
+                    if (inside) *dst = lab ? cf : 0.f;
+                } else {
+                    const int cs = lab ? c : 0;
+                    store_if(dst, (CostT)cs,
+                             inside && BPS_CHECK(row_slot + (j >> 1) < (int64_t)l0.H * l0.Wh, l0.err, 4u));
+                    acc[j >> 1] += inside ? cs : 0;
+                    near_mask |= (near ? 1u : 0u) << j;
+                }
+                if constexpr (NCC_OUT) {
+                    if (inside && lab) ncc_out[((size_t)yy * W + xb + j) * D + dl] = nccf;
+                }
+            }
+            if constexpr (!FLOAT_COST) {
+                // rare: outputs whose fp32 value lies too near a level boundary are decided again
+                // in FP64, and their stores and scale-1 sums corrected
+                while (near_mask) {
+                    const int j = __ffs(near_mask) - 1;
+                    near_mask &= near_mask - 1;
+                    int Sj = 0;
+                    for (int i = j; i < j + WIN; ++i) {
+                        const WinT a = Lrow[i], b = Rrow[i];
+                        unsigned v = 0u;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
+                        Sj += (int)v;
+                    }
+                    const int2 pa = pa_row[j];
+                    const int2 pb = pb_row[j];
+                    const Num num = (Num)N * (Num)Sj - (Num)pa.x * (Num)pb.x;
+                    bool near;
+                    const int c32 = quantise_fp32((float)num, __int_as_float(pa.y), __int_as_float(pb.y), T_half,
+                                                  half_m, T, &near);
+                    const unsigned va = (unsigned)QA[h * CW + lbase + j].x;
+                    const unsigned vb = (unsigned)QB[h * UW + lbase + j + D - 1 - d].x;
+                    int c = quantise_fp64<Num>(num, va, vb, T);
+                    c = c < 0 ? 0 : (c > T ? T : c);
+                    if (j < nvalid && lab && c != c32) {
+                        (((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp)[0] = (CostT)c;
+#pragma unroll
+                        for (int i = 0; i < NR_TX / 2; ++i)
+                            if (i == (j >> 1)) acc[i] += c - c32;
                     }
                 }
-                if (it < LW) {
-                    LWn[par * LW + it] = wv;
-                    colA[it] = (int)s;
-                    colAA[it] = (int)ss;
-                } else {
-                    RWn[par * RW + it - LW] = wv;
-                    colB[it - LW] = (int)s;
-                    colBB[it - LW] = (int)ss;
-                }
-            }
-        }
-        __syncthreads();
-        // phase 2: window records of every left pixel and every right position
-        for (int i = threadIdx.x; i < CW; i += blockDim.x) {
-            int s = 0, ss = 0;
-#pragma unroll
-            for (int k = 0; k < WIN; ++k) {
-                s += colA[i + k];
-                ss += colAA[i + k];
-            }
-            const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            const float ra = v ? rsqrtf((float)v) : 0.f;
-            PA[i] = make_int4(s, (int)v, __float_as_int(ra), __float_as_int(__fmul_rn((float)T, ra)));
-        }
-        for (int i = threadIdx.x; i < UW; i += blockDim.x) {
-            int s = 0, ss = 0;
-#pragma unroll
-            for (int k = 0; k < WIN; ++k) {
-                s += colB[i + k];
-                ss += colBB[i + k];
-            }
-            const unsigned v = (unsigned)N * (unsigned)ss - (unsigned)s * (unsigned)s;
-            PB[i] = make_int4(s, (int)v, __float_as_int(v ? rsqrtf((float)v) : 0.f), 0);
-        }
-        __syncthreads();
-        // phase 3: this thread's 16 outputs at label dl
-        const WinT *Lrow = LWn + par * LW + lbase;
-        const WinT *Rrow = RWn + par * RW + rbase;
-        int V[VN];
-#pragma unroll
-        for (int i = 0; i < VN; ++i) {
-            const WinT a = Lrow[i], b = Rrow[i];
-            unsigned v = 0u;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
-            V[i] = (int)v;
-        }
-        // destinations: x0 + lbase is even, so column j has colour (j + y) & 1 and slot
-        // row_slot + j / 2 in that colour's array
-        const int64_t row_slot = (int64_t)y * l0.Wh + (xb >> 1);
-        CostT *const base_even = reinterpret_cast<CostT *>((y & 1) ? l0.cost[1] : l0.cost[0]) + row_slot * Dp +
-                                 label_pos<CostT>(dl);
-        CostT *const base_odd = reinterpret_cast<CostT *>((y & 1) ? l0.cost[0] : l0.cost[1]) + row_slot * Dp +
-                                label_pos<CostT>(dl);
-        if constexpr (!FLOAT_COST) {
-            if ((y & 1) == 0) {
-#pragma unroll
-                for (int i = 0; i < NR_TX / 2; ++i) acc[i] = 0;
-            }
-        }
-        unsigned near_mask = 0u;  // outputs whose level the FP64 sequence must decide
-        int S = 0;
-#pragma unroll
-        for (int i = 0; i < WIN; ++i) S += V[i];
-#pragma unroll
-        for (int j = 0; j < NR_TX; ++j) {
-            if (j) S += V[j + 2 * R] - V[j - 1];
-            const int4 pa = PA[lbase + j];
-            const int4 pb = PB[lbase + j + D - 1 - d];
-            const Num num = (Num)N * (Num)S - (Num)pa.x * (Num)pb.x;
-            bool near;
-            const int c = quantise_fp32((float)num, __int_as_float(pa.w), __int_as_float(pb.z), T_half, half_m, T, &near);
-            float nccf = 0.f;
-            if constexpr (NCC_OUT || FLOAT_COST)
-                nccf = __fmul_rn(__fmul_rn((float)num, __int_as_float(pa.z)), __int_as_float(pb.z));
-            const bool inside = j < nvalid;
-            CostT *dst = ((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp;
-            if constexpr (FLOAT_COST) {
-                const float cf = fminf(fmaxf((float)T * (1.f - nccf), 0.f), (float)T);
-                if (inside) *dst = lab ? cf : 0.f;
-            } else {
-                const int cs = lab ? c : 0;
-                store_if(dst, (CostT)cs, inside);
-                acc[j >> 1] += inside ? cs : 0;
-                near_mask |= (near ? 1u : 0u) << j;
-            }
-            if constexpr (NCC_OUT) {
-                if (inside && lab) ncc_out[((size_t)y * W + xb + j) * D + dl] = nccf;
             }
         }
         if constexpr (!FLOAT_COST) {
-            // rare: outputs whose fp32 value lies too near a level boundary are decided again
-            // in FP64, and their stores and scale-1 sums corrected
-            while (near_mask) {
-                const int j = __ffs(near_mask) - 1;
-                near_mask &= near_mask - 1;
-                int Sj = 0;
-                for (int i = j; i < j + WIN; ++i) {
-                    const WinT a = Lrow[i], b = Rrow[i];
-                    unsigned v = 0u;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) v = __dp4a(a.w[w], b.w[w], v);
-                    Sj += (int)v;
-                }
-                const int4 pa = PA[lbase + j];
-                const int4 pb = PB[lbase + j + D - 1 - d];
-                const Num num = (Num)N * (Num)Sj - (Num)pa.x * (Num)pb.x;
-                bool near;
-                const int c32 = quantise_fp32((float)num, __int_as_float(pa.w), __int_as_float(pb.z), T_half, half_m, T,
-                                              &near);
-                int c = quantise_fp64<Num>(num, (unsigned)pa.y, (unsigned)pb.y, T);
-                c = c < 0 ? 0 : (c > T ? T : c);
-                if (j < nvalid && lab && c != c32) {
-                    (((j & 1) ? base_odd : base_even) + (int64_t)(j >> 1) * Dp)[0] = (CostT)c;
-#pragma unroll
-                    for (int i = 0; i < NR_TX / 2; ++i)
-                        if (i == (j >> 1)) acc[i] += c - c32;
-                }
-            }
-            if (write_l1 && ((y & 1) || y == H - 1)) {  // the coarse pixels of this row pair are complete
+            if (write_l1) {  // the coarse pixels of this row pair are complete
                 const int cy = y >> 1;
 #pragma unroll
                 for (int jj = 0; jj < NR_TX / 2; ++jj) {
@@ -493,13 +530,16 @@ static int win_bytes(int window) {
 size_t ncc_rows_smem_bytes(int D, int XS, int window) {
     const int R = window / 2;
     const int CW = XS * NR_TX, LW = CW + 2 * R, RW = CW + 2 * R + D - 1, UW = CW + D - 1;
-    return (size_t)16 * (CW + UW) + (size_t)2 * win_bytes(window) * (LW + RW) + (size_t)4 * (2 * LW + 2 * RW);
+    // records [2 rows][hot, cold] 8 bytes each, windows [4 row buffers], column sums [2 rows][2]
+    return (size_t)32 * (CW + UW) + (size_t)4 * win_bytes(window) * (LW + RW) + (size_t)16 * (LW + RW);
 }
 
-// Whether every staged column has an owner: at most NR_ITEMS per thread.
-static bool ncc_rows_shape_ok(int D, int Dp, int XS, int window) {
+// Staged columns a thread owns at most for this shape (2 or 4: the kernel keeps that many
+// windows in registers), or 0 when the shape needs more.
+static int ncc_rows_items(int D, int Dp, int XS, int window) {
     const int R = window / 2, CW = XS * NR_TX;
-    return (CW + 2 * R) + (CW + 2 * R + D - 1) <= NR_ITEMS * XS * Dp;
+    const int items = (CW + 2 * R) + (CW + 2 * R + D - 1);
+    return items <= 2 * XS * Dp ? 2 : (items <= NR_ITEMS_MAX * XS * Dp ? NR_ITEMS_MAX : 0);
 }
 
 // Default CTA shape: every label of 256 / Dp column groups (256 threads), strips short
@@ -520,30 +560,48 @@ static cudaError_t launch_rows_t(const uint8_t *L, const uint8_t *Rim, int pitch
                                  const LevelView &l0, const LevelView *l1, float *ncc_out, cudaStream_t st, bool prep,
                                  int xs_req = 0, int tys_req = 0) {
     if (prep) {
-        const int XSmax = Dp >= 256 ? 1 : 256 / Dp;
+        const int XSmax = std::max(1, 512 / Dp);
         if ((int)ncc_rows_smem_bytes(D, XSmax, 2 * R + 1) > smem_optin()) return cudaErrorInvalidValue;
-        const cudaError_t e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, false>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem_optin());
+        cudaError_t e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, false, 2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_optin());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, false, NR_ITEMS_MAX>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ncc_rows_kernel<CostT, R, true, NR_ITEMS_MAX>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        return e;
     }
     int XS = 1, tys = 16;
     ncc_rows_default_shape(W, H, Dp, &XS, &tys);
     if (xs_req > 0) XS = xs_req;
     if (tys_req > 0) tys = tys_req;
-    if (!ncc_rows_shape_ok(D, Dp, XS, 2 * R + 1)) return cudaErrorInvalidConfiguration;
+    const int items = ncc_rows_items(D, Dp, XS, 2 * R + 1);
+    if (!items) return cudaErrorInvalidConfiguration;
     const size_t smem = ncc_rows_smem_bytes(D, XS, 2 * R + 1);
     const int threads = XS * Dp;
     const int CW = XS * NR_TX;
     const int nx = (W + CW - 1) / CW;
     const int ny = (H + tys - 1) / tys;
     LevelView none = l0;
+    const dim3 grid(nx, ny);
+    const LevelView l1v = l1 ? *l1 : none;
+    const int w1 = l1 ? 1 : 0;
+    if (items == 2) {
+        if (ncc_out)
+            return launch_k(ncc_rows_kernel<CostT, R, true, 2>, grid, dim3(threads), smem, st, L, Rim, pitch, W, H, D,
+                            Dp, T, tys, l0, l1v, w1, ncc_out);
+        return launch_k(ncc_rows_kernel<CostT, R, false, 2>, grid, dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp,
+                        T, tys, l0, l1v, w1, ncc_out);
+    }
     if (ncc_out)
-        return launch_k(ncc_rows_kernel<CostT, R, true>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D,
-                        Dp, T, tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
-    return launch_k(ncc_rows_kernel<CostT, R, false>, dim3(nx, ny), dim3(threads), smem, st, L, Rim, pitch, W, H, D, Dp,
-                    T, tys, l0, l1 ? *l1 : none, l1 ? 1 : 0, ncc_out);
+        return launch_k(ncc_rows_kernel<CostT, R, true, NR_ITEMS_MAX>, grid, dim3(threads), smem, st, L, Rim, pitch, W,
+                        H, D, Dp, T, tys, l0, l1v, w1, ncc_out);
+    return launch_k(ncc_rows_kernel<CostT, R, false, NR_ITEMS_MAX>, grid, dim3(threads), smem, st, L, Rim, pitch, W, H,
+                    D, Dp, T, tys, l0, l1v, w1, ncc_out);
 }
 
 template <typename CostT>

@@ -275,4 +275,86 @@ cudaError_t launch_persistent(int form, const PersistParams &P, cudaStream_t st)
                                        0, st);
 }
 
+// ------------------------------------------------------------------ synchronisation costs
+// What separating two phases costs: `phases` grid barriers inside one cooperative launch (the
+// barrier of the persistent kernel, with its bounded wait), against `phases` empty kernels chained
+// by programmatic dependent launch and replayed from a CUDA graph (the boundary between two
+// half-sweeps of the chained path).  Same grid in both.
+__global__ void __launch_bounds__(256) barrier_probe_kernel(unsigned *state, int phases, unsigned long long timeout_ns) {
+    unsigned target = 0;
+    for (int k = 0; k < phases; ++k) {
+        target += gridDim.x;
+        if (!grid_barrier(state, target, timeout_ns)) return;
+    }
+}
+
+__global__ void __launch_bounds__(256) boundary_probe_kernel() { pdl_enter(); }
+
 }  // namespace bps
+
+extern "C" int bps_measure_sync_costs(int ctas, int phases, double *h_barrier_us, double *h_boundary_us) {
+    using namespace bps;
+    if (ctas < 1 || phases < 1 || phases > 100000 || !h_barrier_us || !h_boundary_us) return BPS_ERR_ARG;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_probe_kernel, 256, 0) != cudaSuccess)
+        return BPS_ERR_CUDA;
+    if (ctas > sms * per_sm) return BPS_ERR_UNSUPPORTED;  // a cooperative launch needs every CTA resident
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    unsigned *state = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = BPS_ERR_CUDA;
+    do {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        if (cudaMalloc(&state, 4 * sizeof(unsigned)) != cudaSuccess) break;
+        // grid barriers: best of three launches
+        float best = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+            unsigned long long timeout = 4000000000ull;
+            int ph = phases;
+            void *args[] = {&state, &ph, &timeout};
+            ok = cudaMemsetAsync(state, 0, 4 * sizeof(unsigned), st) == cudaSuccess &&
+                 cudaEventRecord(e0, st) == cudaSuccess &&
+                 cudaLaunchCooperativeKernel((const void *)barrier_probe_kernel, dim3(ctas), dim3(256), args, 0, st) ==
+                     cudaSuccess &&
+                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.f;
+            if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
+        }
+        unsigned w[2] = {0u, 0u};
+        if (!ok || cudaMemcpy(w, state, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) break;
+        if (w[1]) {
+            rc = BPS_ERR_TIMEOUT;
+            break;
+        }
+        *h_barrier_us = 1e3 * best / phases;
+        // kernel boundaries: a graph of `phases` chained empty kernels, best of three replays
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+        for (int k = 0; k < phases && ok; ++k)
+            ok = launch_k(boundary_probe_kernel, dim3(ctas), dim3(256), 0, st) == cudaSuccess;
+        if (cudaStreamEndCapture(st, &graph) != cudaSuccess || !ok) break;
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+        best = 1e30f;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+            float ms = 0.f;
+            ok = cudaEventRecord(e0, st) == cudaSuccess && cudaGraphLaunch(exec, st) == cudaSuccess &&
+                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (ok && rep > 0) best = std::min(best, ms);
+        }
+        if (!ok) break;
+        *h_boundary_us = 1e3 * best / phases;
+        rc = BPS_OK;
+    } while (false);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (state) cudaFree(state);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}

@@ -320,6 +320,7 @@ struct ActiveList {
 // of thread t is stage[k * blockDim.x + t]: 0-1 cost, 2-5 incoming, 6-9 old outgoing, 10 flag.
 // Chunks of absent inputs are zero-filled by the copy (source size 0, an in-bounds address).
 constexpr int STAGE_CHUNKS = 11;
+constexpr int BULK_CONSUMERS = 256;  // computing threads of a bulk-copy sweep CTA (one more warp copies)
 
 __device__ __forceinline__ void cp_async16(uint4 *smem, const void *gmem, bool pred) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -415,7 +416,8 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
 //           for nothing: for small, latency-bound scales);
 //        2, as 1, and the cost loads also precede the wait on the predecessor kernel (no BP
 //           kernel writes the cost volume); the caller then must not have called pdl_enter().
-//        3, the inputs were staged by the caller (stage_u8, waited for): read from `stage`.
+//        3, the inputs were staged by the caller (stage_u8, waited for): read from `stage`;
+//        4, the inputs landed in a bulk-copy stage of the caller (sweep_u8_bulk_kernel; with LISTED).
 // LISTED: the caller gives the slot (s_listed; nslot for none), an entry of the active list:
 //         a listed pixel is dirty by construction (it was appended when its flag flipped from
 //         0 to 1, and only its own update clears the flag), so its flag is not read.
@@ -432,7 +434,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     else if (al.in) s = s < n_in ? (int64_t)al.in[s] : nslot;
     int x = 0, y = 0;
     bool valid = false;
-    if (s < nslot) {
+    if (BPS_CHECK(s <= nslot, lv.err, 2u) && s < nslot) {  // nslot: no pixel
         const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
         y = (int)(su / wh);
         x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);
@@ -515,6 +517,32 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             qsv[q] = (unsigned)qs;
         }
         flag_staged = stage[10 * T + t].x;
+    } else if constexpr (EAGER == 4) {
+        // inputs landed in a bulk-copy stage (see sweep_u8_bulk_kernel): per pixel of the block its
+        // cost record [P][2 Dp], its incoming record [P][4 Dp] and the four old outgoing slots
+        // [P][4][Dp] (absent neighbours' chunks are not copied and are not read)
+        const int pix = threadIdx.x / Gp, P = BULK_CONSUMERS / Gp;
+        const uint8_t *base = reinterpret_cast<const uint8_t *>(stage);
+        if (lane_data) {
+            const uint4 *cp = reinterpret_cast<const uint4 *>(base + (size_t)pix * 2 * Dp + 2 * dbase);
+            const uint4 c0 = cp[0], c1 = cp[1];
+            b[0] = c0.x; b[1] = c0.y; b[2] = c0.z; b[3] = c0.w;
+            b[4] = c1.x; b[5] = c1.y; b[6] = c1.z; b[7] = c1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = pk(BIG16, BIG16);
+        }
+        const uint8_t *ip = base + (size_t)P * 2 * Dp + (size_t)pix * 4 * Dp + dbase;
+        const uint8_t *op = base + (size_t)P * 6 * Dp + (size_t)pix * 4 * Dp + dbase;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool hq = lane_data && has[q];
+            in[q] = hq ? *reinterpret_cast<const uint4 *>(ip + q * Dp) : make_uint4(0u, 0u, 0u, 0u);
+            old[q] = (hq && skip && lv.start != 1) ? *reinterpret_cast<const uint4 *>(op + q * Dp)
+                                                   : make_uint4(0u, 0u, 0u, 0u);
+            const int64_t qs = (valid && has[q]) ? slot_of(nbx[q], nby[q], lv.Wh) : 0;
+            qsv[q] = (unsigned)qs;
+        }
     } else if constexpr (EAGER != 0) {
         load_cost();
         if constexpr (EAGER == 2) pdl_enter();
@@ -621,7 +649,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             const unsigned below = (1u << lane) - 1u;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = qsv[q];
+                const unsigned at = base + __popc(am[q] & below);
+                if (was[q] == 0u && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = qsv[q];
                 base += __popc(am[q]);
             }
         }
@@ -788,7 +817,8 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
             unsigned base = 0u;
             if (lane == 0) base = atomicAdd(al.n_out, (unsigned)__popc(am));
             base = __shfl_sync(FULL, base, 0);
-            if (app) al.out[base + __popc(am & ((1u << lane) - 1u))] = mark - 1u;
+            const unsigned at = base + __popc(am & ((1u << lane) - 1u));
+            if (app && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = mark - 1u;
         }
     }
     // the pixel's four direction groups: did any mark its receiver?
@@ -860,7 +890,7 @@ __device__ __forceinline__ void wta_pixel(const LevelView &lv, int D, int Dp, in
             arg = oa;
         }
     }
-    if (valid && g == 0) disp[p] = arg;
+    if (valid && g == 0 && BPS_CHECK(p < (int64_t)lv.W * lv.H, lv.err, 5u)) disp[p] = arg;
 }
 
 template <typename CostT, typename MsgT, bool RW = false>

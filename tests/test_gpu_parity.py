@@ -323,7 +323,7 @@ def set_all_variants(st, variant):
 
 # every variant the autotuner can pick, and more (tests/test_abi.py checks the tuner's candidates are here)
 SWEEP_VARIANTS_TESTED = [0, 1, 2, 3, 4, 6, 8, 9, 10, 11, 12, 13, 16, 17, 18, 24, 25, 26, 27, 34, 35, 42, 43, 64, 65, 66,
-                         67, 98, 99, 130, 131, 138, 139, 194, 195, 162]
+                         67, 98, 99, 130, 131, 138, 139, 194, 195, 162, 256, 257, 258, 386, 514, 522, 578, 770, 771]
 
 
 @pytest.mark.parametrize("variant", SWEEP_VARIANTS_TESTED)
@@ -352,7 +352,7 @@ def test_every_sweep_variant_is_exact(case, variant):
 _STAGED_REF = {}
 
 
-@pytest.mark.parametrize("variant", [64, 66, 130, 194])
+@pytest.mark.parametrize("variant", [64, 66, 130, 194, 256, 258, 514, 770])
 @pytest.mark.parametrize("case", [(160, 72, 256, 5, 1, 4, 10, 2), (520, 330, 16, 5, 3, 5, 10, 2), (400, 64, 100, 5, 2, 4, 7, 3)],
                          ids=lambda c: "x".join(map(str, c)))
 def test_staged_variants_exact_where_every_cta_loops(case, variant):
@@ -368,6 +368,7 @@ def test_staged_variants_exact_where_every_cta_loops(case, variant):
         msg = st.export_messages(0).cpu().numpy()
         trace = st.get_trace()
         disp = st.wta_disparity().cpu().numpy()
+        assert st.get_error() == bps.BPS_OK  # no bounded wait gave up
     if case not in _STAGED_REF:
         c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
         ref_msg, ref_trace = oracle.bp(c0, levels, iters, lam, trunc, skip=True)
@@ -377,7 +378,7 @@ def test_staged_variants_exact_where_every_cta_loops(case, variant):
     assert np.array_equal(disp, ref_disp)
 
 
-@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25, 64, 65])
+@pytest.mark.parametrize("variant", [4, 6, 8, 9, 12, 16, 24, 25, 64, 65, 256, 770])
 def test_cluster_and_eager_variants_without_skip_and_in_a_graph(variant):
     # the cluster launch and the eager loads with every pixel recomputed (no skip), then
     # captured in the cached graph of the whole pipeline; the profile shares a cluster
@@ -409,6 +410,26 @@ def test_ncc_shapes_are_exact(shape):
         costs = [st.export_cost(l).cpu().numpy() for l in range(2)]
     want = oracle.pyramid(oracle.quantise(oracle.ncc(pair.left, pair.right, 16, 7), 20), 2)
     assert np.array_equal(costs[0], want[0]) and np.array_equal(costs[1], want[1])
+
+
+@pytest.mark.parametrize("case", [(70, 37, 256, 9, (1, 2)), (70, 37, 256, 9, (2, 4)), (70, 37, 256, 9, (1, 16)),
+                                  (70, 37, 256, 9, (2, 64)), (53, 29, 100, 15, (4, 6)), (53, 29, 100, 15, (1, 2)),
+                                  (40, 33, 48, 11, (8, 10)), (31, 9, 16, 3, (32, 2))],
+                         ids=lambda c: "x".join(map(str, c[:4])) + f"-shape{c[4][0]}x{c[4][1]}")
+def test_ncc_row_pairs_exact_for_every_shape(case):
+    # rows are processed in pairs (odd heights end with a single row), one or two column groups
+    # of 16 a thread's label; costs of scale 0 and the fused scale 1 must be the oracle's
+    W, H, D, window, shape = case
+    pair = synth.make_pair(45 + D, W, H, D, 3, 2.0)
+    with bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        st.set_ncc_shape(*shape)
+        ncc = st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20, want_ncc=True)
+        costs = [st.export_cost(l).cpu().numpy() for l in range(3)]
+    ref = oracle.ncc(pair.left, pair.right, D, window)
+    assert np.abs(ncc.cpu().numpy() - ref).max() < 1e-5
+    want = oracle.pyramid(oracle.quantise(ref, 20), 3)
+    for lvl in range(3):
+        assert np.array_equal(costs[lvl], want[lvl]), lvl
 
 
 def test_autotuner_picks_exact_variants(tmp_path):
@@ -725,7 +746,7 @@ def test_fp16_c3_style_batch_persistent_equals_chains():
             st.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66, 130, 194])
+@pytest.mark.parametrize("variant", [0, 2, 8, 16, 18, 24, 64, 66, 130, 194, 258, 770])
 @pytest.mark.parametrize("eps,freeze", [(1, False), (3, False), (0, True), (2, True)])
 @pytest.mark.parametrize("case", [(96, 72, 16, 5, 4, 6, 10, 2), (60, 44, 40, 5, 3, 5, 8, 3)],
                          ids=lambda c: "x".join(map(str, c)))
