@@ -62,8 +62,10 @@ def parse():
     ap.add_argument("--warmstart-report", action="store_true",
                     help="instead of the benchmark line: train the learned warm start on seeded 450x375 D64 "
                          "pairs and report energy and throughput against the plain solve, one JSON line")
-    ap.add_argument("--train-pairs", type=int, default=2000)
-    ap.add_argument("--eval-pairs", type=int, default=200)
+    ap.add_argument("--train-pairs", type=int, default=None, help="default 2000 (450x375) or 48 (1920x1080)")
+    ap.add_argument("--eval-pairs", type=int, default=None, help="default 200 (450x375) or 8 (1920x1080)")
+    ap.add_argument("--warmstart-workload", choices=["teddy", "hd"], default="teddy",
+                    help="with --warmstart-report: 450x375 D64 pairs (7x7) or 1920x1080 D256 pairs (9x9)")
     ap.add_argument("--batch-report", type=int, default=0, metavar="N",
                     help="instead of the benchmark line: throughput of a batch of N mixed pairs (320-1280 x "
                          "240-720, D in {32,64,96,128}) in every batch mode, one JSON line")
@@ -98,6 +100,8 @@ def parse():
     ap.add_argument("--workload", default=None,
                     help="with --ncu-case: one named pair of paper_1709_06509_gb300.synth.WORKLOADS instead of "
                          "the full-HD pair")
+    ap.add_argument("--variants", default=None, metavar="V0,V1,V2,V3",
+                    help="with --ncu-case: the sweep variant of each scale (finest first) instead of the tuned ones")
     return ap.parse_args()
 
 
@@ -406,22 +410,43 @@ def warmstart_report(args):
     import paper_1709_06509_gb300 as bps
     from paper_1709_06509_gb300 import warmstart
 
-    W, H, D, window = 450, 375, 64, 7
+    hd = args.warmstart_workload == "hd"
+    W, H, D, window = (1920, 1080, 256, 9) if hd else (450, 375, 64, 7)
+    n_train = args.train_pairs or (48 if hd else 2000)
+    n_eval = args.eval_pairs or (8 if hd else 200)
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
-    train_imgs = warmstart.generate_pairs(range(10000, 10000 + args.train_pairs), W, H, D)
-    eval_imgs = warmstart.generate_pairs(range(20000, 20000 + args.eval_pairs), W, H, D)
+    train_imgs = warmstart.generate_pairs(range(10000, 10000 + n_train), W, H, D)
+    eval_imgs = warmstart.generate_pairs(range(20000, 20000 + n_eval), W, H, D)
     t_gen = time.perf_counter() - t0
     feats, targets = warmstart.make_dataset(None, W, H, D, window, TRUNC_DATA, LAM, TRUNC, label_iters=40,
                                             device=dev, images=train_imgs)
     net = warmstart.WarmNet(D, seed=0, device=dev)
     t1 = time.perf_counter()
-    losses = warmstart.train(net, feats, targets, epochs=15, batch=32, lr=2e-3)
+    losses = warmstart.train(net, feats, targets, epochs=15, batch=8 if hd else 32, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
+    del feats, targets
     res = warmstart.evaluate(net, None, W, H, D, window, TRUNC_DATA, LAM, TRUNC, iters_list=(1, 2, 3, 4, 5, 6, 8, 10),
                              device=dev, images=eval_imgs)
     eq = warmstart.iterations_at_equal_energy(res, ITERS)
+    # the warm start acts on the coarse scales: fewer iterations there, the finest scale's fixed
+    sched = warmstart.evaluate_schedules(net, eval_imgs, W, H, D, window, TRUNC_DATA, LAM, TRUNC,
+                                         finest_iters=ITERS, device=dev)
+    # the network's own cost at this size (tensor-core forward convolutions)
+    with bps.Stereo(W, H, D, LEVELS, bps.BPS_MSG_U8, device=dev) as st:
+        st.build_cost_volume(torch.from_numpy(eval_imgs[0][0]).to(dev), torch.from_numpy(eval_imgs[0][1]).to(dev),
+                             window, TRUNC_DATA)
+        for _ in range(3):
+            net.predict_messages(st, LAM, TRUNC)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            net.predict_messages(st, LAM, TRUNC)
+        b.record()
+        torch.cuda.synchronize()
+        net_ms = a.elapsed_time(b) / 10
     # throughput at equal energy: plain solve with ITERS iterations against the warm-started
     # solve (network included) with the fewest iterations reaching the same total energy
     units = W * H * D
@@ -448,9 +473,11 @@ def warmstart_report(args):
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / len(Ls)
             timing[form] = {"iters": k, "ms_per_pair": ms, "value": units / ms / 1e3}
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "learned warm start, 450x375 D64 pairs",
-                      "train_pairs": args.train_pairs, "eval_pairs": args.eval_pairs, "label_iters": 40,
+    print(json.dumps({"metric": METRIC, "unit": UNIT,
+                      "workload": f"learned warm start, {W}x{H} D{D} pairs ({window}x{window} window)",
+                      "train_pairs": n_train, "eval_pairs": n_eval, "label_iters": 40,
                       "loss_per_epoch": losses, "energy_sum_by_iters": res, "iters_at_equal_energy": eq,
+                      "coarse_schedules": sched, "network_ms_per_pair": net_ms,
                       "timing_at_equal_energy": timing, "seconds": {"generate": t_gen, "train": t_train}}))
 
 
@@ -894,6 +921,9 @@ def main():
     pair, window = synth.workload_pair(name, shard.seed_offset(rank))
     form = bps.BPS_MSG_FP16 if (args.ncu_case and args.form == "fp16") else bps.BPS_MSG_U8
     st, L, R, tuned = setup_ctx(bps, autotune, pair, window, form, dev, args.tune_cache)
+    if args.ncu_case and args.variants:
+        for lvl, v in enumerate(int(x) for x in args.variants.split(",")):
+            st.set_variant(lvl, v)
     disp = torch.empty(pair.left.shape, dtype=torch.int32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()

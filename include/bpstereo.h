@@ -166,6 +166,16 @@ int bps_bp_solve(bps_ctx *ctx, int levels, int iters, int lambda, int trunc, int
                  const void *d_init_msgs, void *stream);
 
 /*
+ * bps_bp_solve with its own iteration count at every scale: h_iters[l] iterations at scale l
+ * (0 = the finest, levels - 1 = the coarsest; host array of `levels` entries, read during the
+ * call).  A scale with no iterations passes its start messages down unchanged.  The trace holds
+ * 2 h_iters[l] entries per scale, coarsest first.  Flags and errors as bps_bp_solve (each count
+ * within [0, BPS_MAX_ITERS]); BPS_FLAG_PERSISTENT needs equal counts (BPS_ERR_UNSUPPORTED).
+ */
+int bps_bp_solve_schedule(bps_ctx *ctx, int levels, const int *h_iters, int lambda, int trunc, int flags,
+                          const void *d_init_msgs, void *stream);
+
+/*
  * Winner-take-all read-out at the finest scale: d(p) = argmin_d [c(p, d) + sum of the
  * messages into p], the lowest d on ties.  d_disp: device int32 [H][W].
  * Errors: BPS_ERR_STATE (no cost volume), BPS_ERR_ARG (NULL).
@@ -375,7 +385,12 @@ int bps_export_sparse(bps_ctx *ctx, int32_t *d_cand, int32_t *d_msgs, void *stre
  * accumulated in FP32.  3x3 convolutions with zero padding keep H x W.  All asynchronous on
  * `stream`; the caller owns every buffer.  Errors: BPS_ERR_ARG (NULL, sizes < 1), BPS_ERR_CUDA.
  *
- * bps_warmnet_conv3x3          out = conv(in, w) + bias, then max(., 0) when relu
+ * bps_warmnet_conv3x3          out = conv(in, w) + bias, then max(., 0) when relu; with BF16 input
+ *                              an implicit GEMM on the tensor cores (tcgen05, FP32 accumulator in
+ *                              tensor memory); Cin * 9 <= 2^20, B * H * W <= 2^31 (BPS_ERR_ARG)
+ * bps_warmnet_get_error        BPS_ERR_TIMEOUT when a bounded wait of a tensor-core convolution
+ *                              gave up since the last call (its output is then unwritten), else
+ *                              BPS_OK; synchronous
  * bps_warmnet_conv3x3_backward gradients of one such layer from d_gout (the gradient of its
  *                              output; masked by d_relu_out > 0 when the layer had a ReLU):
  *                              d_gw (and d_gb when not NULL) always, d_gin when not NULL
@@ -392,6 +407,7 @@ int bps_export_sparse(bps_ctx *ctx, int32_t *d_cand, int32_t *d_msgs, void *stre
  */
 int bps_warmnet_conv3x3(const void *d_in, int in_bf16, int B, int Cin, int H, int W, const void *d_w,
                         const float *d_bias, int Cout, int relu, void *d_out, int out_bf16, void *stream);
+int bps_warmnet_get_error(void);
 int bps_warmnet_conv3x3_backward(const float *d_gout, const void *d_relu_out, const void *d_in, int in_bf16, int B,
                                  int Cin, int H, int W, const void *d_w, int Cout, float *d_gin, float *d_gw,
                                  float *d_gb, void *stream);

@@ -86,6 +86,7 @@ def _load(openmp_build: bool) -> ctypes.CDLL:
             "oracle_bp_rule_i32": (i, [P, i, i, i, i, i, i, i, i, i, i, P, u64, P, P]),
             "oracle_bp_rule_f64": (i, [P, i, i, i, i, i, d, i, i, d, i, P, u64, P, P]),
             "oracle_bp_wta_i32": (i, [P, i, i, i, i, i, i, i, i, P, P]),
+            "oracle_bp_schedule_i32": (i, [P, i, i, i, i, P, i, i, i, P, P, P]),
             "oracle_bp_wta_f64": (i, [P, i, i, i, i, i, d, i, i, P, P]),
             "oracle_candidates": (i, [P, i, i, i, i, P]),
             "oracle_bp_sparse_i32": (i, [P, i, i, i, i, i, i, i, i, i, P, P, P]),
@@ -195,6 +196,22 @@ def bp(cost0: np.ndarray, levels: int, iters: int, lam, trunc: int, skip: bool =
         rc = lib().oracle_bp_rule_f64(_p(a), W, H, D, levels, iters, float(lam), trunc, int(skip), float(eps),
                                       int(freeze), _p(init), order_seed, _p(out), _p(trace))
     _check(rc, "oracle_bp")
+    return out, trace[:ntrace]
+
+
+def bp_schedule(cost0: np.ndarray, iters, lam: int, trunc: int, skip: bool = True,
+                init_coarsest: np.ndarray | None = None):
+    """Hierarchical BP (integer costs) with iters[l] iterations at scale l (0 = the finest); the
+    number of scales is len(iters).  Returns (finest messages [4][H][W][D], trace per half-sweep)."""
+    H, W, D = cost0.shape
+    its = np.ascontiguousarray(iters, dtype=np.int32)
+    levels = len(its)
+    ntrace = int(2 * its.sum())
+    trace = np.zeros(max(ntrace, 1), dtype=np.int64)
+    out = np.empty((4, H, W, D), dtype=np.int32)
+    init = None if init_coarsest is None else np.ascontiguousarray(init_coarsest, dtype=np.int32)
+    _check(lib().oracle_bp_schedule_i32(_p(np.ascontiguousarray(cost0, dtype=np.int32)), W, H, D, levels, _p(its),
+                                        int(lam), trunc, int(skip), _p(init), _p(out), _p(trace)), "oracle_bp_schedule")
     return out, trace[:ntrace]
 
 

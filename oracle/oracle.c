@@ -319,13 +319,16 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
  * coarsest first, each starting from its parent's messages.  Returns the finest scale's
  * messages [4][H][W][D] in a buffer the caller frees, or NULL on bad arguments or allocation
  * failure. */
-static double *bp_hierarchy(const double *cost0, int W, int H, int D, int levels, int iters, double lambda,
+static double *bp_hierarchy(const double *cost0, int W, int H, int D, int levels, const int *iters, double lambda,
                             int trunc, int skip, double eps, int freeze, const double *init_coarsest,
                             uint64_t order_seed, int64_t *trace)
 {
     int Ws[32], Hs[32];
-    if (!cost0 || D < 1 || levels > 32 || iters < 0 || trunc < 0 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+    if (!cost0 || !iters || D < 1 || levels > 32 || trunc < 0 || oracle_level_dims(W, H, levels, Ws, Hs) < 0)
         return NULL;
+    for (int l = 0; l < levels; ++l)
+        if (iters[l] < 0)
+            return NULL;
     size_t off[33];
     off[0] = 0;
     for (int l = 0; l < levels; ++l)
@@ -360,7 +363,7 @@ static double *bp_hierarchy(const double *cost0, int W, int H, int D, int levels
                                sizeof(double) * D);
         }
         free(parent);
-        tr = bp_level(pyr + off[l], M, w, h, D, iters, lambda, trunc, skip, eps, freeze, order_seed, tr);
+        tr = bp_level(pyr + off[l], M, w, h, D, iters[l], lambda, trunc, skip, eps, freeze, order_seed, tr);
         parent = M;
     }
     free(pyr);
@@ -371,9 +374,12 @@ int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int
                        int trunc, int skip, double eps, int freeze, const double *init_coarsest,
                        uint64_t order_seed, double *msg0_out, int64_t *trace)
 {
-    if (!msg0_out)
+    if (!msg0_out || iters < 0 || levels < 1 || levels > 32)
         return -1;
-    double *M = bp_hierarchy(cost0, W, H, D, levels, iters, lambda, trunc, skip, eps, freeze, init_coarsest,
+    int it[32];
+    for (int l = 0; l < levels; ++l)
+        it[l] = iters;
+    double *M = bp_hierarchy(cost0, W, H, D, levels, it, lambda, trunc, skip, eps, freeze, init_coarsest,
                              order_seed, trace);
     if (!M)
         return -1;
@@ -385,14 +391,49 @@ int oracle_bp_rule_f64(const double *cost0, int W, int H, int D, int levels, int
 int oracle_bp_wta_f64(const double *cost0, int W, int H, int D, int levels, int iters, double lambda, int trunc,
                       int skip, int32_t *disp, int64_t *trace)
 {
-    if (!disp)
+    if (!disp || iters < 0 || levels < 1 || levels > 32)
         return -1;
-    double *M = bp_hierarchy(cost0, W, H, D, levels, iters, lambda, trunc, skip, 0.0, 0, NULL, 0, trace);
+    int it[32];
+    for (int l = 0; l < levels; ++l)
+        it[l] = iters;
+    double *M = bp_hierarchy(cost0, W, H, D, levels, it, lambda, trunc, skip, 0.0, 0, NULL, 0, trace);
     if (!M)
         return -1;
     const int rc = oracle_wta_f64(cost0, M, W, H, D, disp);
     free(M);
     return rc;
+}
+
+int oracle_bp_schedule_i32(const int32_t *cost0, int W, int H, int D, int levels, const int *iters, int lambda,
+                           int trunc, int skip, const int32_t *init_coarsest, int32_t *msg0_out, int64_t *trace)
+{
+    int Ws[32], Hs[32];
+    if (!cost0 || !msg0_out || !iters || W < 1 || H < 1 || D < 1 || levels < 1 || levels > 32 ||
+        oracle_level_dims(W, H, levels, Ws, Hs) < 0)
+        return -1;
+    const size_t n0 = (size_t)W * H * D;
+    const size_t nc = (size_t)Ws[levels - 1] * Hs[levels - 1] * D;
+    double *c = malloc(sizeof(double) * n0);
+    double *init = init_coarsest ? malloc(sizeof(double) * 4 * nc) : NULL;
+    if (!c || (init_coarsest && !init)) {
+        free(c);
+        free(init);
+        return -1;
+    }
+    for (size_t k = 0; k < n0; ++k)
+        c[k] = cost0[k];
+    if (init)
+        for (size_t k = 0; k < 4 * nc; ++k)
+            init[k] = init_coarsest[k];
+    double *M = bp_hierarchy(c, W, H, D, levels, iters, (double)lambda, trunc, skip, 0.0, 0, init, 0, trace);
+    free(c);
+    free(init);
+    if (!M)
+        return -1;
+    for (size_t k = 0; k < 4 * n0; ++k)
+        msg0_out[k] = (int32_t)M[k];
+    free(M);
+    return 0;
 }
 
 int oracle_bp_wta_i32(const int32_t *cost0, int W, int H, int D, int levels, int iters, int lambda, int trunc,

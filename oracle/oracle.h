@@ -77,6 +77,12 @@ int oracle_bp_f64(const double *cost0, int W, int H, int D, int levels, int iter
                   int trunc, int skip, const double *init_coarsest, uint64_t order_seed,
                   double *msg0_out, int64_t *trace);
 
+/* Hierarchical BP with an iteration count per scale: iters[l] iterations at scale l (0 = the
+ * finest, levels - 1 = the coarsest), the exact skip rule, raster order; otherwise as
+ * oracle_bp_i32.  trace: nullable, sum over the scales of 2 iters[l] entries, coarsest first. */
+int oracle_bp_schedule_i32(const int32_t *cost0, int W, int H, int D, int levels, const int *iters, int lambda,
+                           int trunc, int skip, const int32_t *init_coarsest, int32_t *msg0_out, int64_t *trace);
+
 /* Hierarchical BP (exact skip rule, zero start messages, raster order) followed by the
  * winner-take-all read-out, without handing the messages back: disp [H][W]; trace as above.
  * Same results as oracle_bp_* then oracle_wta_*, in half the host memory (for full-HD pairs

@@ -97,6 +97,8 @@ _SIGS = {
     "bps_cuda_error_string": (ctypes.c_char_p, [_I]),
     "bps_energy_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P]),
     "bps_test_fail_resources": (_I, [_I]),
+    "bps_bp_solve_schedule": (_I, [_P, _I, _P, _I, _I, _I, _P, _P]),
+    "bps_warmnet_get_error": (_I, []),
     "bps_measure_sync_costs": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "bps_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),
     "bps_batch_destroy": (_I, [_P]),
@@ -206,6 +208,14 @@ def bps_build_cost_volume(ctx, left, right, pitch, window, trunc_data, ncc_out=N
 def bps_bp_solve(ctx, levels, iters, lam, trunc, flags, init_msgs=None, stream=None):
     _check(lib().bps_bp_solve(ctx, levels, iters, lam, trunc, flags, _ptr(init_msgs), _stream(stream)),
            "bps_bp_solve")
+
+
+def bps_bp_solve_schedule(ctx, iters_per_scale, lam, trunc, flags, init_msgs=None, stream=None):
+    """iters_per_scale[l] iterations at scale l (0 = the finest); len() scales."""
+    n = len(iters_per_scale)
+    arr = (_I * n)(*[int(v) for v in iters_per_scale])
+    _check(lib().bps_bp_solve_schedule(ctx, n, arr, lam, trunc, flags, _ptr(init_msgs), _stream(stream)),
+           "bps_bp_solve_schedule")
 
 
 def bps_wta_disparity(ctx, disp, stream=None):
@@ -337,6 +347,14 @@ def bps_warmnet_conv3x3(x, x_bf16, B, Cin, H, W, w, bias, Cout, relu, out, out_b
                                      int(out_bf16), _stream(stream)), "bps_warmnet_conv3x3")
 
 
+def bps_warmnet_get_error() -> int:
+    """BPS_OK, or BPS_ERR_TIMEOUT when a tensor-core convolution's bounded wait gave up (cleared)."""
+    rc = lib().bps_warmnet_get_error()
+    if rc not in (BPS_OK, BPS_ERR_TIMEOUT):
+        raise BPSError(rc, "bps_warmnet_get_error")
+    return rc
+
+
 def bps_warmnet_conv3x3_backward(gout, relu_out, x, x_bf16, B, Cin, H, W, w, Cout, gin, gw, gb, stream=None):
     _check(lib().bps_warmnet_conv3x3_backward(_ptr(gout), _ptr(relu_out), _ptr(x), int(x_bf16), B, Cin, H, W, _ptr(w),
                                               Cout, _ptr(gin), _ptr(gw), _ptr(gb), _stream(stream)),
@@ -444,6 +462,13 @@ class Stereo:
         flags |= (BPS_FLAG_PROFILE if profile else 0) | (BPS_FLAG_PERSISTENT if persistent else 0)
         flags |= (BPS_FLAG_TEST_TIMEOUT if test_timeout else 0) | (BPS_FLAG_GRAPH if graph else 0)
         bps_bp_solve(self.ctx, levels or self.levels, iters, lam, trunc, flags, init_msgs, stream)
+
+    def bp_solve_schedule(self, iters_per_scale, lam: int, trunc: int, skip: bool = True, init_msgs=None,
+                          graph: bool = False, stream=None):
+        """The solve with iters_per_scale[l] iterations at scale l (0 = the finest)."""
+        flags = (BPS_FLAG_FAST_SKIP if skip else 0) | (BPS_FLAG_WARM_START if init_msgs is not None else 0)
+        flags |= BPS_FLAG_GRAPH if graph else 0
+        bps_bp_solve_schedule(self.ctx, iters_per_scale, lam, trunc, flags, init_msgs, stream)
 
     def wta_disparity(self, out=None, stream=None):
         import torch

@@ -119,6 +119,26 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
     return true;
 }
 
+// Iterations per scale of a solve (0 = the finest scale).
+struct Iters {
+    int n[BPS_MAX_LEVELS] = {};
+    static Iters uniform(int levels, int iters) {
+        Iters it;
+        for (int l = 0; l < levels; ++l) it.n[l] = iters;
+        return it;
+    }
+    int trace_len(int levels) const {  // half-sweeps of the solve
+        int t = 0;
+        for (int l = 0; l < levels; ++l) t += 2 * n[l];
+        return t;
+    }
+    bool uniform_over(int levels) const {
+        for (int l = 1; l < levels; ++l)
+            if (n[l] != n[0]) return false;
+        return true;
+    }
+};
+
 struct GraphKey {
     const void *L, *R;
     int32_t *disp;
@@ -189,7 +209,7 @@ struct bps_ctx {
     int64_t *e_i64 = nullptr;
     double *e_f64 = nullptr;
     bool has_cost = false;
-    int last_levels = 0, last_iters = 0;
+    int last_levels = 0, last_trace_n = 0;  // scales and half-sweeps of the last solve
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
@@ -485,8 +505,8 @@ static int check_bp_args(bps_ctx *c, int levels, int iters, int lambda, int trun
     return BPS_OK;
 }
 
-static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
-                             cudaStream_t st, int32_t *readout = nullptr);
+static int enqueue_bp_sweeps(bps_ctx *c, int levels, const Iters &its, int lambda, int trunc, int flags,
+                             const void *init, cudaStream_t st, int32_t *readout = nullptr);
 
 // The start messages of the coarsest scale: zero, or imported from the caller.
 static int enqueue_start(bps_ctx *c, int top, int flags, const void *init, cudaStream_t st) {
@@ -521,23 +541,28 @@ static PersistParams persist_params(int npairs, const PairDesc *pairs, const int
 }
 
 // The whole solve (and the read-out into disp when it is not NULL) as one persistent launch.
-static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
+static int enqueue_bp(bps_ctx *c, int levels, const Iters &its, int lambda, int trunc, int flags, const void *init,
                       cudaStream_t st, int32_t *disp = nullptr) {
     if (!(flags & BPS_FLAG_PERSISTENT)) {
         // u8 form, exact skip rule: the finest scale's half-sweeps read out every pixel they
         // recompute, and only the even pixels the last half-sweep dirtied are read out after it
         const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
-        const bool fused = disp && c->msg_kind == MSG_U8 && c->sv.K == 0 && c->lv[0].eps == 0 && !c->lv[0].freeze &&
-                           iters > 0;
-        const int rc = enqueue_bp_sweeps(c, levels, iters, lambda, trunc, flags, init, st, fused ? disp : nullptr);
+        // (the fp16 form where its packed sweep runs the finest scale, which forms the same belief)
+        const bool packed_f16 = c->msg_kind == MSG_F16 && sweep_f16_applies(trunc) &&
+                                !(c->variant[0] & VARIANT_GENERAL_DT);
+        const bool fused = disp && (c->msg_kind == MSG_U8 || packed_f16) && c->sv.K == 0 && c->lv[0].eps == 0 &&
+                           !c->lv[0].freeze && its.n[0] > 0;
+        const int rc = enqueue_bp_sweeps(c, levels, its, lambda, trunc, flags, init, st, fused ? disp : nullptr);
         if (rc == BPS_OK && disp) {
             if (c->last_sparse_k) {
                 CK(launch_sparse_wta(c->lv[0], c->sv, disp, st));
             } else if (fused) {
                 // the last half-sweep's list of newly dirty even pixels, where the scale keeps lists
-                const bool listed = skip && (c->variant[0] & VARIANT_LISTS) && !(c->variant[0] & VARIANT_CLUSTER);
-                const int t_last = levels * iters * 2 - 1;
-                CK(launch_wta_rest(c->lv[0], c->D, c->Dp, c->Gp, skip ? 1 : 0, listed ? c->lists[0] : nullptr,
+                const bool listed = skip && (c->variant[0] & VARIANT_LISTS) &&
+                                    !(c->msg_kind == MSG_U8 && (c->variant[0] & VARIANT_CLUSTER));
+                const int t_last = its.trace_len(levels) - 1;
+                CK(launch_wta_rest(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, skip ? 1 : 0,
+                                   listed ? c->lists[0] : nullptr,
                                    listed ? c->list_counts + t_last : nullptr, disp, st));
             } else {
                 CK(launch_wta(c->msg_kind, c->lv[0], c->D, c->Dp, c->Gp, disp, st));
@@ -546,6 +571,8 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
         return rc;
     }
     const int top = levels - 1;
+    const int iters = its.n[0];  // the persistent kernel runs the same count at every scale
+    if (!its.uniform_over(levels)) return BPS_ERR_UNSUPPORTED;
     const int ntrace = levels * iters * 2;
     c->last_sparse_k = 0;
     if (ntrace) {
@@ -579,19 +606,19 @@ static int enqueue_bp(bps_ctx *c, int levels, int iters, int lambda, int trunc, 
         c->prof_trace_n = ntrace;
     }
     c->last_levels = levels;
-    c->last_iters = iters;
+    c->last_trace_n = ntrace;
     return BPS_OK;
 }
 
-static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
-                             cudaStream_t st, int32_t *readout) {
+static int enqueue_bp_sweeps(bps_ctx *c, int levels, const Iters &its, int lambda, int trunc, int flags,
+                             const void *init, cudaStream_t st, int32_t *readout) {
     const bool skip = (flags & BPS_FLAG_FAST_SKIP) != 0;
     const bool prof = (flags & BPS_FLAG_PROFILE) != 0;
     const int top = levels - 1;
-    const int ntrace = levels * iters * 2;
+    const int ntrace = its.trace_len(levels);
     if (prof) {
-        const size_t need = 2 * (size_t)levels * iters * 2;
-        c->prof_span.assign((size_t)levels * iters * 2 + 1, 1);
+        const size_t need = 2 * (size_t)ntrace;
+        c->prof_span.assign((size_t)ntrace + 1, 1);
         while (c->ev.size() < need) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
@@ -599,8 +626,8 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
         }
         c->prof_launches = 0;
         c->prof_all = 0;
-        c->prof_first_trace = top * iters * 2;
-        c->prof_trace_n = iters * 2;
+        c->prof_first_trace = ntrace - 2 * its.n[0];
+        c->prof_trace_n = 2 * its.n[0];
     }
     // a chain of kernels only (no memset nodes), so that every launch overlaps its predecessor
     const bool warm = (flags & BPS_FLAG_WARM_START) != 0;
@@ -617,6 +644,7 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
                                                       "bps scale 4", "bps scale 5", "bps scale 6", "bps scale 7"};
     for (int l = top; l >= 0; --l) {
         Range range(scale_names[l]);
+        const int iters = its.n[l];
         LevelView v = c->lv[l];
         if (l == 0) v.disp = readout;  // the finest scale's half-sweeps read out what they recompute
         if (l == 0 && c->sv.K > 0) {
@@ -702,28 +730,47 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, int iters, int lambda, int 
             }
     }
     c->last_levels = levels;
-    c->last_iters = iters;
+    c->last_trace_n = ntrace;
     return BPS_OK;
+}
+
+// A solve with `its` iterations per scale: enqueued, or recorded once as a graph and replayed.
+static int solve_iters(bps_ctx *c, int levels, const Iters &its, int lambda, int trunc, int flags, const void *init,
+                       cudaStream_t st) {
+    const int f = flags & ~BPS_FLAG_GRAPH;
+    if (!(flags & BPS_FLAG_GRAPH) || (flags & BPS_FLAG_PROFILE)) return enqueue_bp(c, levels, its, lambda, trunc, f, init, st);
+    // the solve recorded once as a graph, replayed while its arguments and the kernel choices hold
+    std::vector<intptr_t> key = {levels, lambda, trunc, f, (intptr_t)init, (intptr_t)c->config_version};
+    for (int l = 0; l < levels; ++l) key.push_back(its.n[l]);
+    const int e = replay_or_record(c->solve_graph, key, c->cap, st, [&](cudaStream_t s) {
+        return enqueue_bp(c, levels, its, lambda, trunc, f, init, s);
+    });
+    if (e == BPS_OK) {  // what recording set on the host, a replay sets again
+        c->last_levels = levels;
+        c->last_trace_n = its.trace_len(levels);
+        c->last_sparse_k = (f & BPS_FLAG_PERSISTENT) ? 0 : c->sv.K;
+    }
+    return e;
 }
 
 extern "C" int bps_bp_solve(bps_ctx *c, int levels, int iters, int lambda, int trunc, int flags, const void *init,
                             void *stream) {
     const int rc = check_bp_args(c, levels, iters, lambda, trunc, flags & ~BPS_FLAG_GRAPH, init);
     if (rc != BPS_OK) return rc;
-    const int f = flags & ~BPS_FLAG_GRAPH;
-    if (!(flags & BPS_FLAG_GRAPH) || (flags & BPS_FLAG_PROFILE))
-        return enqueue_bp(c, levels, iters, lambda, trunc, f, init, (cudaStream_t)stream);
-    // the solve recorded once as a graph, replayed while its arguments and the kernel choices hold
-    const std::vector<intptr_t> key = {levels, iters, lambda, trunc, f, (intptr_t)init, (intptr_t)c->config_version};
-    const int e = replay_or_record(c->solve_graph, key, c->cap, (cudaStream_t)stream, [&](cudaStream_t s) {
-        return enqueue_bp(c, levels, iters, lambda, trunc, f, init, s);
-    });
-    if (e == BPS_OK) {  // what recording set on the host, a replay sets again
-        c->last_levels = levels;
-        c->last_iters = iters;
-        c->last_sparse_k = (f & BPS_FLAG_PERSISTENT) ? 0 : c->sv.K;
+    return solve_iters(c, levels, Iters::uniform(levels, iters), lambda, trunc, flags, init, (cudaStream_t)stream);
+}
+
+extern "C" int bps_bp_solve_schedule(bps_ctx *c, int levels, const int *h_iters, int lambda, int trunc, int flags,
+                                     const void *init, void *stream) {
+    if (!c || !h_iters || levels < 1 || levels > c->levels) return BPS_ERR_ARG;
+    Iters its;
+    for (int l = 0; l < levels; ++l) {
+        const int rc = check_bp_args(c, levels, h_iters[l], lambda, trunc, flags & ~BPS_FLAG_GRAPH, init);
+        if (rc != BPS_OK) return rc;
+        its.n[l] = h_iters[l];
     }
-    return e;
+    if ((flags & BPS_FLAG_PERSISTENT) && !its.uniform_over(levels)) return BPS_ERR_UNSUPPORTED;
+    return solve_iters(c, levels, its, lambda, trunc, flags, init, (cudaStream_t)stream);
 }
 
 extern "C" int bps_wta_disparity(bps_ctx *c, int32_t *disp, void *stream) {
@@ -747,7 +794,8 @@ static int enqueue_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
                           int iters, int lambda, int trunc, int flags, int32_t *disp, cudaStream_t st) {
     int rc = enqueue_cost(c, L, R, pitch, window, trunc_data, nullptr, st);
     if (rc != BPS_OK) return rc;
-    return enqueue_bp(c, c->levels, iters, lambda, trunc, flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PERSISTENT), nullptr,
+    return enqueue_bp(c, c->levels, Iters::uniform(c->levels, iters), lambda, trunc,
+                      flags & (BPS_FLAG_FAST_SKIP | BPS_FLAG_PERSISTENT), nullptr,
                       st, disp);
 }
 
@@ -802,7 +850,7 @@ extern "C" int bps_stereo(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pi
     }
     CK(cudaGraphLaunch(c->gexec, st));
     c->last_levels = c->levels;  // what recording set on the host, a replay sets again
-    c->last_iters = iters;
+    c->last_trace_n = c->levels * iters * 2;
     c->last_sparse_k = (flags & BPS_FLAG_PERSISTENT) ? 0 : c->sv.K;
     return BPS_OK;
 }
@@ -883,7 +931,7 @@ extern "C" int bps_get_error(bps_ctx *c) {
 
 extern "C" int bps_get_trace(bps_ctx *c, int64_t *h_counts, int cap) {
     if (!c || (!h_counts && cap > 0) || cap < 0) return BPS_ERR_ARG;
-    const int n = std::min(cap, c->last_levels * c->last_iters * 2);
+    const int n = std::min(cap, c->last_trace_n);
     if (n <= 0) return 0;
     std::vector<unsigned long long> tmp(n);
     CK(cudaMemcpy(tmp.data(), c->trace, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
@@ -1102,7 +1150,7 @@ static int enqueue_batch(bps_batch *b, const uint8_t *const *L, const uint8_t *c
         for (int i = 0; i < n; ++i) {
             bps_ctx *c = b->ctxs[i];
             c->last_levels = b->levels;
-            c->last_iters = iters;
+            c->last_trace_n = b->levels * iters * 2;
             const int rc = enqueue_pair_output(c, io, i, lambda, trunc, st);
             if (rc != BPS_OK) return rc;
         }

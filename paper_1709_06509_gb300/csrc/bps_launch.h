@@ -131,10 +131,10 @@ cudaError_t preload_readout_kernels(int msg_kind);
 
 // Winner-take-all disparity at the finest scale.
 cudaError_t launch_wta(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int32_t *disp, cudaStream_t st);
-// The rest of a read-out the finest scale's u8 half-sweeps started (LevelView::disp): the even
+// The rest of a read-out the finest scale's half-sweeps started (LevelView::disp): the even
 // pixels dirtied by the last half-sweep, from the list of them (non-null `list`, device count
 // n_list) or from the skip flags (every even pixel with the skip off).
-cudaError_t launch_wta_rest(const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
+cudaError_t launch_wta_rest(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
                             const unsigned *n_list, int32_t *disp, cudaStream_t st);
 
 // Sparse candidates of the finest scale (sparse.cu): per colour, Kp uint16 labels a slot, then

@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(256) wta_kernel(LevelView lv, int D, int Dp, i
     wta_group<CostT, MsgT>(lv, D, Dp, Gp, disp, blockIdx.x);
 }
 
-// The rest of a read-out that the finest scale's half-sweeps started (u8 form, exact skip rule):
+// The rest of a read-out that the finest scale's half-sweeps started (u8 form, or the fp16 form's
+// packed sweep; exact skip rule):
 // every recomputed pixel already wrote the label of the belief it formed, and a pixel's belief
 // changes only when an incoming message does.  After the last half-sweep (the odd pixels) the
 // odd pixels' labels are final, and so are the even pixels' whose incoming messages did not
@@ -62,17 +63,23 @@ cudaError_t preload_readout_kernels(int msg_kind) {
         const cudaError_t e = cudaFuncGetAttributes(&a, wta_kernel<int16_t, uint8_t>);
         return e == cudaSuccess ? cudaFuncGetAttributes(&a, wta_rest_kernel<int16_t, uint8_t>) : e;
     }
-    default: return cudaFuncGetAttributes(&a, wta_kernel<float, __half>);
+    default: {
+        const cudaError_t e = cudaFuncGetAttributes(&a, wta_kernel<float, __half>);
+        return e == cudaSuccess ? cudaFuncGetAttributes(&a, wta_rest_kernel<float, __half>) : e;
+    }
     }
 }
 
-cudaError_t launch_wta_rest(const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
+cudaError_t launch_wta_rest(int msg_kind, const LevelView &lv, int D, int Dp, int Gp, int skip, const unsigned *list,
                             const unsigned *n_list, int32_t *disp, cudaStream_t st) {
     const int groups = 256 / Gp;
     const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+    if (msg_kind == MSG_F16)
+        return launch_k(wta_rest_kernel<float, __half>, dim3(grid), dim3(256), 0, st, lv, D, Dp, Gp, skip, list, n_list,
+                        disp);
     return launch_k(wta_rest_kernel<int16_t, uint8_t>, dim3(grid), dim3(256), 0, st, lv, D, Dp, Gp, skip, list, n_list,
                     disp);
 }

@@ -434,7 +434,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
     else if (al.in) s = s < n_in ? (int64_t)al.in[s] : nslot;
     int x = 0, y = 0;
     bool valid = false;
-    if (BPS_CHECK(s <= nslot, lv.err, 2u) && s < nslot) {  // nslot: no pixel
+    // a list entry (or the caller's) names a slot of the scale, or nslot for none
+    if (BPS_CHECK(!(LISTED || al.in) || s <= nslot, lv.err, 2u) && s < nslot) {
         const unsigned su = (unsigned)s, wh = (unsigned)lv.Wh;  // slots stay below 2^31: 32-bit division
         y = (int)(su / wh);
         x = 2 * (int)(su - (unsigned)y * wh) + ((y + colour) & 1);

@@ -118,6 +118,37 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
 #pragma unroll
         for (int q = 0; q < 4; ++q) b[j] = __hadd2(b[j], u2h(word(in[q], j)));
     }
+    if (lv.disp) {
+        // the read-out of a recomputed pixel of the finest scale: the belief in FP32 from the cost
+        // and the existing incoming messages in the order the standalone read-out adds them (the
+        // same label, the lowest on ties)
+        float best = __int_as_float(0x7f800000);
+        int arg = 0x7fffffff;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            float f = c[k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!has[q]) continue;
+                const __half2 hv = u2h(word(in[q], k >> 1));
+                f += (k & 1) ? __high2float(hv) : __low2float(hv);
+            }
+            const int lab = dbase + k;
+            if (lane_data && lab < D && f < best) {
+                best = f;
+                arg = lab;
+            }
+        }
+        for (int o = Gp >> 1; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, best, o, Gp);
+            const int oa = __shfl_xor_sync(FULL, arg, o, Gp);
+            if (ob < best || (ob == best && oa < arg)) {
+                best = ob;
+                arg = oa;
+            }
+        }
+        if (active && g == 0) lv.disp[(int64_t)y * lv.W + x] = arg;
+    }
     const __half2 L2 = __float2half2_rn(lam), LT2 = __float2half2_rn(lamT);
     const int gshift = lane & ~(Gp - 1);
     unsigned mark[4] = {0u, 0u, 0u, 0u};  // slot + 1 of each neighbour to mark (APPEND)

@@ -5,9 +5,10 @@
 //
 // Layout: activations [B][C][H][W] in BF16, weights [Cout][Cin][3][3] in BF16 (training keeps
 // FP32 master copies), biases, gradients and optimiser state in FP32; every product is
-// accumulated in FP32.  3x3 convolutions with zero padding ("same" size).  The network is
-// 0.5 GFLOP per 57x47 map, microseconds next to a solve, so the kernels are direct
-// convolutions on the CUDA cores: one thread per output element.
+// accumulated in FP32.  3x3 convolutions with zero padding ("same" size).  The forward
+// convolution of BF16 activations (every layer of the network) runs on the tensor cores
+// (conv_tc.cu); the FP32-input forward and the backward kernels below are direct convolutions
+// on the CUDA cores, one thread per output element (training only).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -231,14 +232,33 @@ __global__ void messages_kernel(const float *__restrict__ pred, int H, int W, in
         if ((x) != cudaSuccess) return BPS_ERR_CUDA;             \
     } while (0)
 
+namespace bps {
+cudaError_t launch_conv3x3_tc(const void *in, int B, int Cin, int H, int W, const void *w, const float *bias, int Cout,
+                              int relu, void *out, int out_bf16, cudaStream_t st);
+int conv3x3_tc_error(int *flag);
+}  // namespace bps
+
 extern "C" int bps_warmnet_conv3x3(const void *d_in, int in_bf16, int B, int Cin, int H, int W, const void *d_w,
                                    const float *d_bias, int Cout, int relu, void *d_out, int out_bf16, void *stream) {
     if (!d_in || !d_w || !d_out || B < 1 || Cin < 1 || Cout < 1 || H < 1 || W < 1) return BPS_ERR_ARG;
+    if ((int64_t)Cin * 9 > (1 << 20) || (int64_t)B * H * W > ((int64_t)1 << 31)) return BPS_ERR_ARG;
+    if (in_bf16) {  // BF16 activations: an implicit GEMM on the tensor cores (conv_tc.cu)
+        WN_CK(bps::launch_conv3x3_tc(d_in, B, Cin, H, W, d_w, d_bias, Cout, relu, d_out, out_bf16,
+                                     (cudaStream_t)stream));
+        return BPS_OK;
+    }
     const int64_t n = (int64_t)B * Cout * H * W;
     conv3x3_fwd_kernel<<<std::min<unsigned>(blocks_for(n), 152 * 64), WN_THREADS, 0, (cudaStream_t)stream>>>(
         d_in, in_bf16, B, Cin, H, W, (const __nv_bfloat16 *)d_w, d_bias, Cout, relu, d_out, out_bf16);
     WN_CK(cudaGetLastError());
     return BPS_OK;
+}
+
+extern "C" int bps_warmnet_get_error(void) {
+    int flag = 0;
+    const int rc = bps::conv3x3_tc_error(&flag);
+    if (rc != BPS_OK) return rc;
+    return flag ? BPS_ERR_TIMEOUT : BPS_OK;
 }
 
 extern "C" int bps_warmnet_conv3x3_backward(const float *d_gout, const void *d_relu_out, const void *d_in, int in_bf16,

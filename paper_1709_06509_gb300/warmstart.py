@@ -234,6 +234,41 @@ def evaluate(net: WarmNet, seeds, W: int, H: int, D: int, window: int, trunc_dat
     return {"plain": plain, "warm": warm, "warm_not_worse_pairs": better, "pairs": len(images)}
 
 
+def evaluate_schedules(net: WarmNet, images, W: int, H: int, D: int, window: int, trunc_data: int, lam: int,
+                       trunc: int, coarse_iters=(0, 1, 2, 3, 4, 6, 10), finest_iters: int = 10, levels: int = 4,
+                       device="cuda"):
+    """Iterations the warm start saves at the coarse scales, the finest scale's count fixed: for
+    each scale l >= 1 alone (the others at finest_iters) and for all coarse scales together, the
+    final energy (int64, summed over the pairs) of the plain and the warm-started solve per coarse
+    iteration count (bps_bp_solve_schedule)."""
+    import torch
+
+    groups = {f"scale_{l}": [l] for l in range(1, levels)}
+    groups["all_coarse"] = list(range(1, levels))
+    out = {g: {"plain": {k: 0 for k in coarse_iters}, "warm": {k: 0 for k in coarse_iters}} for g in groups}
+    with Stereo(W, H, D, levels, BPS_MSG_U8, device=device) as st:
+        for left, right in images:
+            st.build_cost_volume(torch.from_numpy(left).to(device), torch.from_numpy(right).to(device), window,
+                                 trunc_data)
+            init = net.predict_messages(st, lam, trunc)
+            for g, scales in groups.items():
+                for k in coarse_iters:
+                    sched = [finest_iters] * levels
+                    for l in scales:
+                        sched[l] = k
+                    for form, start in (("plain", None), ("warm", init)):
+                        st.bp_solve_schedule(sched, lam, trunc, init_msgs=start)
+                        out[g][form][k] += int(st.energy(st.wta_disparity(), lam, trunc)[0].item())
+    for g in groups:
+        ref = out[g]["plain"][max(coarse_iters)]
+        for form in ("plain", "warm"):
+            ks = [k for k in sorted(coarse_iters) if out[g][form][k] <= ref]
+            out[g][f"{form}_iters_at_equal_energy"] = ks[0] if ks else None
+        p, w = out[g]["plain_iters_at_equal_energy"], out[g]["warm_iters_at_equal_energy"]
+        out[g]["iterations_saved"] = (p - w) if (p is not None and w is not None) else None
+    return out
+
+
 def iterations_at_equal_energy(result, reference_iters: int = 10):
     """Smallest iteration count whose total energy is at most the plain solve's at
     reference_iters, for the plain and the warm-started solve (None if never)."""

@@ -583,6 +583,33 @@ def test_full_size_pairs_bit_exact_under_the_joint_tuner(tmp_path):
             st.close()
 
 
+@pytest.mark.parametrize("variant", [0, 2, 194, 770])
+@pytest.mark.parametrize("schedule", [[5, 5, 5], [3, 0, 4], [0, 2, 6], [6, 1, 0], [2, 3, 1]],
+                         ids=lambda s: "-".join(map(str, s)))
+def test_iteration_schedule_matches_the_oracle(schedule, variant):
+    # bps_bp_solve_schedule: its own iteration count at every scale (0 = the finest), zero counts
+    # included, plain and recorded as a graph, cold and warm-started
+    W, H, D, window, lam, trunc = 150, 110, 48, 5, 10, 2
+    pair = synth.make_pair(990 + sum(schedule), W, H, D, 4, 2.0)
+    c0 = oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), 20)
+    rng = np.random.default_rng(3)
+    wc, hc = oracle.level_dims(W, H, 3)[-1]
+    init = rng.integers(0, lam * trunc + 1, (4, hc, wc, D)).astype(np.int32)
+    # slots of neighbours outside the image hold 0 (no sender ever writes them)
+    init[0, 0], init[1, -1], init[2, :, 0], init[3, :, -1] = 0, 0, 0, 0
+    with bps.Stereo(W, H, D, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        set_all_variants(st, variant)
+        st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), window, 20)
+        for start in (None, init):
+            ref_msg, ref_trace = oracle.bp_schedule(c0, schedule, lam, trunc, init_coarsest=start)
+            for graph in (False, True, True):
+                st.bp_solve_schedule(schedule, lam, trunc, init_msgs=None if start is None else to_dev(start),
+                                     graph=graph)
+                assert np.array_equal(st.export_messages(0).cpu().numpy(), ref_msg)
+                assert np.array_equal(st.get_trace(), ref_trace)
+                assert np.array_equal(st.wta_disparity().cpu().numpy(), oracle.wta(c0, ref_msg))
+
+
 @pytest.mark.gpu
 def test_bp_solve_graph_replays_match_eager_solves():
     # bps_bp_solve recorded as a graph and replayed: same messages, trace and labels as the eager

@@ -318,6 +318,39 @@ def test_freeze_rule_hand_worked():
     assert np.array_equal(msg_f, msg.astype(np.float64)) and trace_f.tolist() == g["trace"]
 
 
+@pytest.mark.parametrize("dtype", [np.int32, np.float64])
+def test_solve_then_read_out_without_messages_equals_the_two_steps(dtype):
+    # oracle_bp_wta_*: the solve and the read-out in one call (no messages handed back) is the
+    # solve followed by the read-out
+    rng = np.random.default_rng(23)
+    cost = rng.integers(0, 21, (19, 23, 9)).astype(dtype)
+    m, t = oracle.bp(cost, 3, 4, 10, 2)
+    d, t2 = oracle.bp_wta(cost, 3, 4, 10, 2)
+    assert np.array_equal(d, oracle.wta(cost, m)) and np.array_equal(t, t2)
+
+
+def test_iteration_schedule_reduces_to_the_uniform_and_the_flat_solve():
+    # a per-scale schedule with equal counts is the uniform solve; scales with no iterations pass
+    # their (zero or given) start messages down unchanged, so [k, 0, 0, 0] is the flat solve of the
+    # finest scale and [k, 0] from coarse messages M is the flat solve from M copied down
+    rng = np.random.default_rng(17)
+    cost = rng.integers(0, 21, (13, 17, 6)).astype(np.int32)
+    m, t = oracle.bp(cost, 4, 3, 10, 2)
+    ms, ts = oracle.bp_schedule(cost, [3, 3, 3, 3], 10, 2)
+    assert np.array_equal(m, ms) and np.array_equal(t, ts)
+    m, t = oracle.bp(cost, 1, 4, 10, 2)
+    ms, ts = oracle.bp_schedule(cost, [4, 0, 0, 0], 10, 2)
+    assert np.array_equal(m, ms) and np.array_equal(t, ts)
+    coarse = rng.integers(0, 21, (4, 7, 9, 6)).astype(np.int32)
+    up = np.repeat(np.repeat(coarse, 2, axis=1), 2, axis=2)[:, :13, :17]
+    m, t = oracle.bp(cost, 1, 4, 10, 2, init_coarsest=up)
+    ms, ts = oracle.bp_schedule(cost, [4, 0], 10, 2, init_coarsest=coarse)
+    assert np.array_equal(m, ms) and np.array_equal(t, ts)
+    # and the trace has one entry per half-sweep of each scale, coarsest first
+    _, ts = oracle.bp_schedule(cost, [2, 0, 1], 10, 2)
+    assert len(ts) == 6 and ts[0] + ts[1] == 4 * 5 and ts[2] + ts[3] == 13 * 17
+
+
 @pytest.mark.parametrize("levels", [1, 3])
 @pytest.mark.parametrize("vertical", [False, True])
 def test_chain_equals_viterbi(levels, vertical):

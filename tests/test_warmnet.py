@@ -43,6 +43,31 @@ def test_conv_forward(relu, in_bf16):
     assert torch.allclose(out.cpu(), ref, rtol=1e-4, atol=1e-4)
 
 
+@pytest.mark.parametrize("shape", [(2, 32, 32, 47, 57), (1, 8, 256, 47, 57), (1, 32, 1024, 20, 30), (3, 5, 7, 9, 11),
+                                   (1, 1, 17, 130, 3), (2, 3, 300, 7, 5)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("out_bf16", [0, 1])
+def test_tensor_core_conv_matches_fp32_conv2d(shape, out_bf16):
+    # BF16 activations take the tensor-core implicit GEMM: against an FP32 convolution of the same
+    # BF16 values on the CPU (every product exact in FP32, only the summation order differs)
+    B, Cin, Cout, H, W = shape
+    g = torch.Generator().manual_seed(B * 1000 + Cin * 10 + Cout)
+    x = bf16_round(torch.randn(B, Cin, H, W, generator=g))
+    w = bf16_round(torch.randn(Cout, Cin, 3, 3, generator=g) * 0.2)
+    b = torch.randn(Cout, generator=g)
+    ref = F.conv2d(x, w, b, padding=1).clamp(min=0)
+    out = torch.empty(B, Cout, H, W, dtype=torch.bfloat16 if out_bf16 else torch.float32, device=DEV)
+    bps.bps_warmnet_conv3x3(x.to(torch.bfloat16).to(DEV), 1, B, Cin, H, W, w.to(torch.bfloat16).to(DEV), b.to(DEV),
+                            Cout, 1, out, out_bf16)
+    torch.cuda.synchronize()
+    assert bps.bps_warmnet_get_error() == bps.BPS_OK
+    got = out.to(torch.float32).cpu()
+    if out_bf16:  # one BF16 rounding of nearly equal FP32 sums: at most one unit apart
+        assert torch.allclose(got, bf16_round(ref), rtol=2 ** -7, atol=1e-3)
+    else:
+        assert torch.allclose(got, ref, rtol=1e-4, atol=1e-4)
+
+
 @pytest.mark.parametrize("relu", [0, 1])
 def test_conv_backward(relu):
     g = torch.Generator().manual_seed(2)
