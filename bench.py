@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--workload", default=None,
                     help="with --ncu-case: one named pair of paper_1709_06509_gb300.synth.WORKLOADS instead of "
                          "the full-HD pair")
+    ap.add_argument("--ncc-kernel", choices=["tensor", "rows"], default=None,
+                    help="with --ncu-case: the NCC kernel instead of the tuned one")
     ap.add_argument("--variants", default=None, metavar="V0,V1,V2,V3",
                     help="with --ncu-case: the sweep variant of each scale (finest first) instead of the tuned ones")
     return ap.parse_args()
@@ -679,7 +681,9 @@ def setup_ctx(bps, autotune, pair, window, form, dev, tune_cache):
     L, R = torch_from(pair.left, dev), torch_from(pair.right, dev)
     tuned = {}
     if form == bps.BPS_MSG_U8:  # the NCC shapes are tuned on the u8 form's int16 costs
-        tuned["ncc_shape"] = list(autotune.tune_ncc(st, L, R, window, TRUNC_DATA, cache=tune_cache))
+        shape = list(autotune.tune_ncc(st, L, R, window, TRUNC_DATA, cache=tune_cache))
+        tuned["ncc_kernel"] = "tensor-core" if shape[0] < 0 else "rows"
+        tuned["ncc_shape"] = shape
     tuned["sweep_variants"] = autotune.tune(st, L, R, window, TRUNC_DATA, ITERS, LAM, TRUNC, reps=3, cache=tune_cache)
     return st, L, R, tuned
 
@@ -921,6 +925,8 @@ def main():
     pair, window = synth.workload_pair(name, shard.seed_offset(rank))
     form = bps.BPS_MSG_FP16 if (args.ncu_case and args.form == "fp16") else bps.BPS_MSG_U8
     st, L, R, tuned = setup_ctx(bps, autotune, pair, window, form, dev, args.tune_cache)
+    if args.ncu_case and args.ncc_kernel:
+        st.set_ncc_kernel(bps.BPS_NCC_TENSOR if args.ncc_kernel == "tensor" else bps.BPS_NCC_ROWS)
     if args.ncu_case and args.variants:
         for lvl, v in enumerate(int(x) for x in args.variants.split(",")):
             st.set_variant(lvl, v)

@@ -223,6 +223,13 @@ int bps_stereo_host(bps_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
  * Reading reports the sweep and bounds errors once (they are cleared).  Synchronous.
  */
 int bps_get_error(bps_ctx *ctx);
+/*
+ * The raw error word of the context's device-side checks, left as it is (bps_get_error clears it):
+ * 0 none, 1 a bounded wait gave up, 2 and above the code of the largest failed check of the debug
+ * build (2 list entry, 3 list append, 4 and 6 data-cost store, 5 read-out pixel, 7 scale-1 store,
+ * 8 FP64 list entry, 9 accumulator column, 10 window record, 11 slab row, 12 FP64 pass store).
+ */
+int bps_peek_error_code(bps_ctx *ctx);
 
 /*
  * Per half-sweep count of recomputed pixels of the last bps_bp_solve (coarsest scale
@@ -333,6 +340,27 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  * picks it by measurement.  Drops a graph recorded by bps_stereo.
  */
 int bps_set_ncc_shape(bps_ctx *ctx, int column_groups, int rows);
+
+/*
+ * Which kernel forms the NCC cost volume (section "Correlation volume computation"):
+ *   BPS_NCC_DEFAULT  the tensor-core kernel where it applies, else a CUDA-core kernel;
+ *   BPS_NCC_ROWS     a CUDA-core kernel (the row-streaming one for windows up to 15);
+ *   BPS_NCC_TENSOR   the tensor-core kernel where it applies (as the default).
+ * The tensor-core kernel forms every window sum of products S_ab of a 128-pixel tile and a block
+ * of up to 128 labels as one banded matrix product on tcgen05 (BF16 image bytes, FP32
+ * accumulation: exact, since every S_ab is an integer below 2^24), then quantises like the
+ * row kernel: the costs are the same bits.  It applies to the integer cost forms (BPS_MSG_INT32,
+ * BPS_MSG_U8), odd windows up to 9, trunc_data up to 127, and calls without ncc_out.
+ * rows: image rows per strip of the tensor-core kernel (even; 0: strips that cover the SMs about
+ * once).  Results do not depend on either choice.  Drops a graph recorded by bps_stereo.
+ * bps_get_ncc_kernel returns the kernel (BPS_NCC_TENSOR or BPS_NCC_ROWS) that
+ * bps_build_cost_volume would use for this window and trunc_data without ncc_out.
+ */
+#define BPS_NCC_DEFAULT 0
+#define BPS_NCC_ROWS 1
+#define BPS_NCC_TENSOR 2
+int bps_set_ncc_kernel(bps_ctx *ctx, int kernel, int rows);
+int bps_get_ncc_kernel(bps_ctx *ctx, int window, int trunc_data);
 
 #define BPS_VARIANT_GENERAL_DT 1
 #define BPS_VARIANT_LISTS 2

@@ -59,6 +59,9 @@ BPS_VARIANT_STAGED = 64
 BPS_VARIANT_STAGED_LISTS = 128
 BPS_VARIANT_BULK = 256
 BPS_VARIANT_BULK_LISTS = 512
+BPS_NCC_DEFAULT = 0
+BPS_NCC_ROWS = 1
+BPS_NCC_TENSOR = 2
 BPS_NOALLOC_MAX_BLOCKS = 16384
 BPS_NOALLOC_MAX_PIXELS = BPS_NOALLOC_MAX_BLOCKS * 1024
 
@@ -111,6 +114,9 @@ _SIGS = {
     "bps_set_candidates": (_I, [_P, _I]),
     "bps_export_sparse": (_I, [_P, _P, _P, _P]),
     "bps_set_ncc_shape": (_I, [_P, _I, _I]),
+    "bps_set_ncc_kernel": (_I, [_P, _I, _I]),
+    "bps_peek_error_code": (_I, [_P]),
+    "bps_get_ncc_kernel": (_I, [_P, _I, _I]),
     "bps_warmnet_conv3x3": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P]),
     "bps_warmnet_conv3x3_backward": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
     "bps_warmnet_mse": (_I, [_P, _P, _P, _I64, _P, _P, _I, _P]),
@@ -324,6 +330,19 @@ def bps_set_sweep_variant(ctx, level: int, variant: int) -> None:
 
 def bps_set_ncc_shape(ctx, column_groups: int, rows: int) -> None:
     _check(lib().bps_set_ncc_shape(ctx, column_groups, rows), "bps_set_ncc_shape")
+
+
+def bps_peek_error_code(ctx) -> int:
+    """The raw error word of the device-side checks, not cleared (see include/bpstereo.h)."""
+    return _check(lib().bps_peek_error_code(ctx), "bps_peek_error_code")
+
+
+def bps_set_ncc_kernel(ctx, kernel: int, rows: int = 0) -> None:
+    _check(lib().bps_set_ncc_kernel(ctx, kernel, rows), "bps_set_ncc_kernel")
+
+
+def bps_get_ncc_kernel(ctx, window: int, trunc_data: int) -> int:
+    return _check(lib().bps_get_ncc_kernel(ctx, window, trunc_data), "bps_get_ncc_kernel")
 
 
 def bps_get_sweep_variant(ctx, level: int) -> int:
@@ -574,6 +593,12 @@ class Stereo:
 
     def set_ncc_shape(self, column_groups: int, rows: int) -> None:
         bps_set_ncc_shape(self.ctx, column_groups, rows)
+
+    def set_ncc_kernel(self, kernel: int, rows: int = 0) -> None:
+        bps_set_ncc_kernel(self.ctx, kernel, rows)
+
+    def ncc_kernel(self, window: int, trunc_data: int) -> int:
+        return bps_get_ncc_kernel(self.ctx, window, trunc_data)
 
     def variants(self) -> list[int]:
         return [bps_get_sweep_variant(self.ctx, l) for l in range(self.levels)]

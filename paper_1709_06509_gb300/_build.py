@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbpstereo.so")
 LIB_DEBUG = os.path.join(HERE, "libbpstereo_debug.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["api.cu", "ncc.cu", "bp.cu", "readout.cu", "persist.cu", "noalloc.cu", "warmnet.cu", "sparse.cu", "sweep_f16.cu", "conv_tc.cu"]
+SOURCES = ["api.cu", "ncc.cu", "bp.cu", "readout.cu", "persist.cu", "noalloc.cu", "warmnet.cu", "sparse.cu", "sweep_f16.cu", "conv_tc.cu", "ncc_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

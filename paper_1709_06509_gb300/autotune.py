@@ -142,16 +142,32 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
     return chosen
 
 
+def _set_ncc(st, choice) -> None:
+    """Apply an NCC choice: (-1, rows) is the tensor-core kernel with `rows` rows per strip,
+    (column_groups, rows) the row kernel's CTA shape."""
+    import paper_1709_06509_gb300 as bps
+
+    xs, rows = choice
+    if xs < 0:
+        st.set_ncc_kernel(bps.BPS_NCC_TENSOR, rows)
+    else:
+        st.set_ncc_kernel(bps.BPS_NCC_ROWS)
+        st.set_ncc_shape(xs, rows)
+
+
 def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache: str | None = None):
-    """Pick and set the NCC CTA shape (column groups per CTA, rows per strip) of `st` for
-    windows up to 15; returns it.  Every shape computes the same costs."""
+    """Pick and set the NCC kernel of `st` for windows up to 15 and return the choice: the
+    tensor-core kernel as (-1, rows per strip) where it applies, or the row kernel's CTA shape
+    (column groups per CTA, rows per strip).  Every choice computes the same costs."""
     import torch
+
+    import paper_1709_06509_gb300 as bps
 
     if window > 15:
         return (0, 0)
     gpu = torch.cuda.get_device_name(st.device)
     Dp = (st.D + 15) // 16 * 16
-    key = f"{gpu}|ncc|{st.W}x{st.H}|Dp{Dp}|w{window}|form{st.msg_type}|v2"
+    key = f"{gpu}|ncc|{st.W}x{st.H}|Dp{Dp}|w{window}|t{trunc_data}|form{st.msg_type}|v3"
     table = _load(cache)
     if key in table:
         best = tuple(table[key])
@@ -163,10 +179,13 @@ def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache
             if 32 <= xs * Dp <= 512:
                 cands += [(xs, r) for r in (2, 4, 8, 16, 32, 64) if r <= max(2, st.H)]
             xs //= 2
+        st.set_ncc_kernel(bps.BPS_NCC_DEFAULT)
+        if st.ncc_kernel(window, trunc_data) == bps.BPS_NCC_TENSOR:
+            cands += [(-1, 0)] + [(-1, r) for r in (8, 16, 32, 64, 128, 256) if r < st.H]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         timed = {}
         for c in cands:
-            st.set_ncc_shape(*c)
+            _set_ncc(st, c)
             st.build_cost_volume(left, right, window, trunc_data)
             e0.record()
             for _ in range(reps):
@@ -180,7 +199,7 @@ def tune_ncc(st, left, right, window: int, trunc_data: int, reps: int = 5, cache
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
             with open(cache, "w") as fh:
                 json.dump(table, fh, indent=1, sort_keys=True)
-    st.set_ncc_shape(*best)
+    _set_ncc(st, best)
     return best
 
 

@@ -50,7 +50,8 @@ struct Plan {
     int levels = 0;
     int Ws[BPS_MAX_LEVELS], Hs[BPS_MAX_LEVELS], Whs[BPS_MAX_LEVELS];
     size_t cost[BPS_MAX_LEVELS][2], msg[BPS_MAX_LEVELS][2], dirty[BPS_MAX_LEVELS][2];
-    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, lists[2], list_counts, sparse[2], total;
+    size_t trace, partials, img[2], disp, energy, desc, prefix, barrier, lists[2], list_counts, sparse[2], ncc_fix,
+        ncc_fix_bytes, total;
 };
 
 int cost_kind_of(int msg_type) { return msg_type == BPS_MSG_INT32 ? COST_I32 : msg_type == BPS_MSG_U8 ? COST_I16 : COST_F32; }
@@ -115,6 +116,10 @@ bool make_plan(int W, int H, int D, int levels, int msg_type, Plan &p) {
         p.sparse[c] = off;
         if (msg_type == BPS_MSG_U8) off += up((size_t)p.Hs[0] * p.Whs[0] * BPS_MAX_CANDIDATES * 4);
     }
+    // values the tensor-core NCC leaves to its FP64 pass (integer forms)
+    p.ncc_fix = off;
+    p.ncc_fix_bytes = msg_type == BPS_MSG_FP16 ? 0 : ncc_tc_fix_bytes(W, H, (int)Dp);
+    off += up(p.ncc_fix_bytes);
     p.total = off;
     return true;
 }
@@ -222,6 +227,9 @@ struct bps_ctx {
     unsigned *list_counts = nullptr;          // entries appended during each half-sweep
     int variant[BPS_MAX_LEVELS] = {};         // u8 sweep kernel variant per scale
     int ncc_xs = 0, ncc_rows = 0;             // NCC CTA shape (0: default)
+    int ncc_kernel = BPS_NCC_DEFAULT, ncc_tc_rows = 0;  // NCC kernel choice, tensor-core rows per strip
+    void *ncc_fix = nullptr;                  // the tensor-core NCC's list for its FP64 pass
+    size_t ncc_fix_bytes = 0;
     int prof_launches = 0;  // finest-scale sweep launches of the last profiled solve
     int prof_all = 0;       // all sweep launches of the last profiled solve
     int prof_first_trace = 0;
@@ -388,6 +396,8 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     c->lists[0] = reinterpret_cast<unsigned *>(c->ws + p.lists[0]);
     c->lists[1] = reinterpret_cast<unsigned *>(c->ws + p.lists[1]);
     c->list_counts = reinterpret_cast<unsigned *>(c->ws + p.list_counts);
+    c->ncc_fix = p.ncc_fix_bytes ? c->ws + p.ncc_fix : nullptr;
+    c->ncc_fix_bytes = p.ncc_fix_bytes;
     c->sv.cand[0] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[0]);
     c->sv.cand[1] = reinterpret_cast<uint16_t *>(c->ws + p.sparse[1]);
     c->sv.K = c->sv.Kp = 0;
@@ -407,6 +417,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
     // that no attribute call happens while a launch sequence is being captured
     ok = ok && ncc_prepare(c->cost_kind, D, BPS_MAX_WINDOW) == cudaSuccess;
     ok = ok && ncc_rows_prepare(c->cost_kind, D, c->Dp) == cudaSuccess;
+    ok = ok && ncc_tc_prepare(c->cost_kind, c->Dp) == cudaSuccess;
     ok = ok && preload_cost_kernels(c->cost_kind) == cudaSuccess;
     ok = ok && preload_bp_kernels(c->msg_kind) == cudaSuccess;
     ok = ok && (c->msg_kind != MSG_U8 || preload_sparse_kernels() == cudaSuccess);
@@ -462,7 +473,15 @@ static int enqueue_cost(bps_ctx *c, const uint8_t *L, const uint8_t *R, int pitc
     Range range("bps cost volume");
     const LevelView &v0 = c->lv[0];
     int first_pyramid = 1;
-    if (window <= NCC_ROWS_MAX_WINDOW) {
+    const bool tc = c->ncc_kernel != BPS_NCC_ROWS && !ncc_out &&
+                    ncc_tc_supported(c->cost_kind, c->Dp, window, trunc_data);
+    if (tc) {
+        // the tensor-core kernel (integer forms) writes scale 1 as well
+        const bool fuse = c->levels > 1;
+        CK(launch_ncc_tc(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0,
+                         fuse ? &c->lv[1] : nullptr, st, c->ncc_tc_rows, c->ncc_fix, c->ncc_fix_bytes));
+        if (fuse) first_pyramid = 2;
+    } else if (window <= NCC_ROWS_MAX_WINDOW) {
         // the row-streaming kernel also writes scale 1 in the integer forms
         const bool fuse = c->levels > 1 && c->cost_kind != COST_F32;
         CK(launch_ncc_rows(c->cost_kind, L, R, pitch, c->W, c->H, c->D, c->Dp, window, trunc_data, v0,
@@ -913,6 +932,13 @@ extern "C" int bps_stereo_host(bps_ctx *c, const uint8_t *hL, const uint8_t *hR,
     CK(cudaStreamSynchronize(st));
     // only the persistent kernel's barrier can time out
     return (flags & BPS_FLAG_PERSISTENT) ? bps_get_error(c) : BPS_OK;
+}
+
+extern "C" int bps_peek_error_code(bps_ctx *c) {
+    if (!c) return BPS_ERR_ARG;
+    unsigned w = 0u;
+    CK(cudaMemcpy(&w, c->d_barrier + 2, sizeof(w), cudaMemcpyDeviceToHost));
+    return (int)w;
 }
 
 extern "C" int bps_test_fail_resources(int n) {
@@ -1384,6 +1410,24 @@ extern "C" int bps_set_skip_rule(bps_ctx *c, int eps, int freeze) {
 extern "C" int bps_get_sweep_variant(bps_ctx *c, int level) {
     if (!c || level < 0 || level >= c->levels) return BPS_ERR_ARG;
     return c->variant[level];
+}
+
+extern "C" int bps_set_ncc_kernel(bps_ctx *c, int kernel, int rows) {
+    if (!c || kernel < BPS_NCC_DEFAULT || kernel > BPS_NCC_TENSOR || rows < 0 || (rows & 1)) return BPS_ERR_ARG;
+    c->ncc_kernel = kernel;
+    c->ncc_tc_rows = rows;
+    ++c->config_version;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BPS_OK;
+}
+
+extern "C" int bps_get_ncc_kernel(bps_ctx *c, int window, int trunc_data) {
+    if (!c) return BPS_ERR_ARG;
+    const bool tc = c->ncc_kernel != BPS_NCC_ROWS && ncc_tc_supported(c->cost_kind, c->Dp, window, trunc_data);
+    return tc ? BPS_NCC_TENSOR : BPS_NCC_ROWS;
 }
 
 extern "C" int bps_set_ncc_shape(bps_ctx *c, int column_groups, int rows) {

@@ -52,7 +52,9 @@ struct LevelView {
 // check records its code in the context's error word (the largest code wins) and the caller skips
 // the access it guards; bps_get_error then reports BPS_ERR_INTERNAL.  In the normal build a check
 // is the constant true and costs nothing.  Codes: 2 a list entry past the scale, 3 a list append
-// past its capacity, 4 a data-cost store outside its scale, 5 a read-out pixel outside the image.
+// past its capacity, 4 a data-cost store outside its scale, 5 a read-out pixel outside the image;
+// the tensor-core NCC: 6 a data-cost store, 7 a scale-1 store, 8 an FP64 list entry, 9 an
+// accumulator column or stage label, 10 a window record, 11 a slab row, 12 an FP64 pass store.
 #ifdef BPS_DEBUG_BOUNDS
 __device__ __forceinline__ bool bps_check(bool ok, unsigned *err, unsigned code) {
     if (!ok && err) atomicMax(err, code);

@@ -51,6 +51,20 @@ cudaError_t launch_ncc_rows(int cost_kind, const uint8_t *L, const uint8_t *R, i
                             cudaStream_t st, int xs = 0, int tys = 0);
 cudaError_t ncc_rows_prepare(int cost_kind, int D, int Dp);
 
+// Tensor-core NCC (integer forms, odd windows up to NCC_TC_MAX_WINDOW, trunc_data up to 8191):
+// the same costs as the row kernel, and scale 1 with l1 != NULL.  rows: image rows per strip
+// (0: the default, strips that cover the SMs about once).
+constexpr int NCC_TC_MAX_WINDOW = 9;
+bool ncc_tc_supported(int cost_kind, int Dp, int window, int T);
+size_t ncc_tc_smem_bytes(int Dp, int window);
+cudaError_t ncc_tc_prepare(int cost_kind, int Dp);
+// fix: a workspace buffer of ncc_tc_fix_bytes (zeroed once) for the values the kernel leaves to a
+// second, FP64 pass (null: every row decides them itself, slower).
+size_t ncc_tc_fix_bytes(int W, int H, int Dp);
+cudaError_t launch_ncc_tc(int cost_kind, const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int D, int Dp,
+                          int window, int T, const LevelView &l0, const LevelView *l1, cudaStream_t st, int rows,
+                          void *fix, size_t fix_bytes);
+
 // Kernel variant of the u8 half-sweep at one scale (bit set; see bps_set_sweep_variant).
 constexpr int VARIANT_GENERAL_DT = 1;  // the distance transform even where a stencil form exists
 constexpr int VARIANT_LISTS = 2;       // active lists after the scale's first iteration (skip on)

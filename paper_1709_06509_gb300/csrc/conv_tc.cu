@@ -181,12 +181,13 @@ conv3x3_tc_kernel(const __nv_bfloat16 *__restrict__ in, int B, int Cin, int H, i
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
         for (int nc = 0; nc < NT; nc += 8) {
             uint32_t r[8];
+            // the load and its wait in one statement: the load writes its registers asynchronously
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+                "tcgen05.wait::ld.sync.aligned;"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                 : "r"(lane_base + (uint32_t)nc)
                 : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int64_t q = p0 + 32 * warp + lane;
             if (q < npix) {
                 const int qb = (int)(q / HW), qp = (int)(q % HW);

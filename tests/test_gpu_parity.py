@@ -127,17 +127,22 @@ def test_pitched_images_and_random_texture():
     assert np.array_equal(got, oracle.quantise(oracle.ncc(L, R, D, 5), 20))
 
 
-def test_quantiser_rounding_boundaries():
-    # windows whose NCC sits on a rounding boundary of the quantiser exercise the FP64 fallback
+@pytest.mark.parametrize("msg_type", INT_FORMS)
+@pytest.mark.parametrize("kernel", ["tensor", "rows"])
+def test_quantiser_rounding_boundaries(kernel, msg_type):
+    # windows whose NCC sits on a rounding boundary of the quantiser exercise the FP64 decision
+    # (the tensor-core kernel's second pass, which also corrects the scale-1 sums)
     H, W, D = 16, 40, 8
     base = synth.texture(21, 1, W, H)
     L = base
     R = np.clip(base.astype(int) * 3 // 4 + (np.arange(W) % 3)[None, :] * 9, 0, 255).astype(np.uint8)
-    for T in (1, 7, 20, 64, 255):
-        with bps.Stereo(W, H, D, 1, bps.BPS_MSG_INT32, device=DEV) as st:
+    for T in (1, 7, 20, 64, 127, 255):
+        with bps.Stereo(W, H, D, 2, msg_type, device=DEV) as st:
+            st.set_ncc_kernel(bps.BPS_NCC_TENSOR if kernel == "tensor" else bps.BPS_NCC_ROWS)
             st.build_cost_volume(to_dev(L), to_dev(R), 3, T)
-            got = st.export_cost(0).cpu().numpy()
-        assert np.array_equal(got, oracle.quantise(oracle.ncc(L, R, D, 3), T)), T
+            got = [st.export_cost(l).cpu().numpy() for l in range(2)]
+        want = oracle.pyramid(oracle.quantise(oracle.ncc(L, R, D, 3), T), 2)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), T
 
 
 def test_u8_form_equals_int32_form():
@@ -405,7 +410,9 @@ def test_cluster_and_eager_variants_without_skip_and_in_a_graph(variant):
 def test_ncc_shapes_are_exact(shape):
     pair = synth.make_pair(44, 75, 41, 16, 3, 2.0)
     with bps.Stereo(75, 41, 16, 3, bps.BPS_MSG_U8, device=DEV) as st:
+        st.set_ncc_kernel(bps.BPS_NCC_ROWS)  # the CTA shapes of the row kernel
         st.set_ncc_shape(*shape)
+        assert st.ncc_kernel(7, 20) == bps.BPS_NCC_ROWS
         st.build_cost_volume(to_dev(pair.left), to_dev(pair.right), 7, 20)
         costs = [st.export_cost(l).cpu().numpy() for l in range(2)]
     want = oracle.pyramid(oracle.quantise(oracle.ncc(pair.left, pair.right, 16, 7), 20), 2)
@@ -430,6 +437,55 @@ def test_ncc_row_pairs_exact_for_every_shape(case):
     want = oracle.pyramid(oracle.quantise(ref, 20), 3)
     for lvl in range(3):
         assert np.array_equal(costs[lvl], want[lvl]), lvl
+
+
+# (W, H, D, window, trunc_data, levels, rows per strip, form): tiles of 128 pixels with ragged
+# tails and images narrower than a tile; label blocks of 128 with a partial last one; odd heights
+# (a last row without a partner); strips of 2 rows up to the whole image; every window radius
+TC_NCC_CASES = [
+    (300, 37, 256, 9, 20, 3, 0, "u8"), (300, 37, 256, 9, 20, 3, 4, "u8"), (300, 38, 256, 9, 20, 3, 2, "u8"),
+    (129, 21, 200, 9, 20, 3, 6, "u8"), (97, 31, 48, 7, 20, 3, 0, "u8"), (64, 17, 16, 5, 20, 2, 0, "u8"),
+    (257, 19, 100, 3, 20, 3, 8, "u8"), (130, 9, 304, 1, 20, 2, 0, "u8"), (45, 33, 64, 9, 127, 1, 0, "u8"),
+    (200, 25, 144, 9, 20, 3, 0, "int32"), (131, 23, 32, 9, 100, 2, 2, "int32"), (17, 5, 16, 3, 20, 3, 0, "int32"),
+]
+
+
+@pytest.mark.parametrize("case", TC_NCC_CASES, ids=lambda c: "x".join(map(str, c[:5])) + f"-L{c[5]}-r{c[6]}-{c[7]}")
+def test_tensor_core_ncc_exact(case):
+    # the tensor-core kernel: costs of scale 0 and its fused scale 1 (and the pyramid after it)
+    # bit-identical to the oracle's quantised NCC and to the row kernel's
+    W, H, D, window, td, levels, rows, form = case
+    msg = bps.BPS_MSG_U8 if form == "u8" else bps.BPS_MSG_INT32
+    pair = synth.make_pair(300 + W + D, W, H, D, 3, 2.0)
+    L, R = to_dev(pair.left), to_dev(pair.right)
+    with bps.Stereo(W, H, D, levels, msg, device=DEV) as st:
+        st.set_ncc_kernel(bps.BPS_NCC_TENSOR, rows)
+        assert st.ncc_kernel(window, td) == bps.BPS_NCC_TENSOR
+        st.build_cost_volume(L, R, window, td)
+        got = [st.export_cost(l).cpu().numpy() for l in range(levels)]
+        assert st.get_error() == bps.BPS_OK
+        st.set_ncc_kernel(bps.BPS_NCC_ROWS)
+        st.build_cost_volume(L, R, window, td)
+        rows_k = [st.export_cost(l).cpu().numpy() for l in range(levels)]
+    want = oracle.pyramid(oracle.quantise(oracle.ncc(pair.left, pair.right, D, window), td), levels)
+    for lvl in range(levels):
+        assert np.array_equal(got[lvl], want[lvl]), lvl
+        assert np.array_equal(rows_k[lvl], want[lvl]), lvl
+
+
+def test_tensor_core_ncc_applies_where_documented():
+    with bps.Stereo(64, 16, 64, 2, bps.BPS_MSG_U8, device=DEV) as st:
+        assert st.ncc_kernel(9, 20) == bps.BPS_NCC_TENSOR  # the default
+        assert st.ncc_kernel(11, 20) == bps.BPS_NCC_ROWS   # windows up to 9
+        assert st.ncc_kernel(9, 128) == bps.BPS_NCC_ROWS   # trunc_data up to 127
+        st.set_ncc_kernel(bps.BPS_NCC_ROWS)
+        assert st.ncc_kernel(9, 20) == bps.BPS_NCC_ROWS
+        with pytest.raises(bps.BPSError):
+            st.set_ncc_kernel(3)
+        with pytest.raises(bps.BPSError):
+            st.set_ncc_kernel(bps.BPS_NCC_TENSOR, 3)  # odd rows per strip
+    with bps.Stereo(64, 16, 64, 2, bps.BPS_MSG_FP16, device=DEV) as st:
+        assert st.ncc_kernel(9, 20) == bps.BPS_NCC_ROWS   # the float form keeps the row kernel
 
 
 def test_autotuner_picks_exact_variants(tmp_path):

@@ -87,10 +87,15 @@ def test_hd_u8_cost_volume_and_graph_solve_match_the_oracle(built, gold, pair):
     H, W = pair.left.shape
     with bps.Stereo(W, H, pair.D, LEVELS, bps.BPS_MSG_U8, device=dev) as st:
         L, R = torch.from_numpy(pair.left).to(dev), torch.from_numpy(pair.right).to(dev)
-        st.build_cost_volume(L, R, WINDOW, TRUNC_DATA)
-        cost = st.export_cost(0)
-        assert sha(cost.cpu().numpy().astype("<i4")) == gold["int"]["cost_sha256"]
-        del cost
+        # both NCC kernels: the tensor-core one (the default here) and the row kernel
+        for kernel in (bps.BPS_NCC_TENSOR, bps.BPS_NCC_ROWS):
+            st.set_ncc_kernel(kernel)
+            assert st.ncc_kernel(WINDOW, TRUNC_DATA) == kernel
+            st.build_cost_volume(L, R, WINDOW, TRUNC_DATA)
+            cost = st.export_cost(0)
+            assert sha(cost.cpu().numpy().astype("<i4")) == gold["int"]["cost_sha256"], kernel
+            del cost
+        st.set_ncc_kernel(bps.BPS_NCC_DEFAULT)
         disp = st.stereo(L, R, WINDOW, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True)
         disp = st.stereo(L, R, WINDOW, TRUNC_DATA, ITERS, LAM, TRUNC, graph=True)  # a replay
         ei, _ = st.energy(disp, LAM, TRUNC)
