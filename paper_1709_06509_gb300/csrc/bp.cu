@@ -20,8 +20,10 @@ __global__ void __launch_bounds__(256)
 sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<MsgT>::type lam,
              typename AccOf<MsgT>::type lamT, int skip, unsigned long long *trace, int nblocks) {
     pdl_enter();
+    Tally tally(trace);
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+        sweep_group<CostT, MsgT>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b);
+    tally.flush();
 }
 
 // Grid-stride over the colour's pixel blocks: the grid is capped at what is resident at
@@ -35,10 +37,12 @@ __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                 unsigned long long *trace, int nblocks, ActiveList al) {
     pdl_enter();
+    Tally tally(trace);
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        if constexpr (DP) sweep_group_u8_dp<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
-        else sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+        if constexpr (DP) sweep_group_u8_dp<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
+        else sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
     }
+    tally.flush();
 }
 
 // The same half-sweep with every load issued at once (see EAGER in sweep_group_u8): the first
@@ -47,15 +51,17 @@ template <bool PADDED, int TS, bool DP>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_eager_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                       unsigned long long *trace, int nblocks) {
+    Tally tally(trace);
     if constexpr (DP) {
-        sweep_group_u8_dp<PADDED, false, TS, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+        sweep_group_u8_dp<PADDED, false, TS, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, blockIdx.x);
         for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
-            sweep_group_u8_dp<PADDED, false, TS, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+            sweep_group_u8_dp<PADDED, false, TS, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b);
     } else {
-        sweep_group_u8<PADDED, false, TS, false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, blockIdx.x);
+        sweep_group_u8<PADDED, false, TS, false, 2>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, blockIdx.x);
         for (int b = blockIdx.x + gridDim.x; b < nblocks; b += gridDim.x)
-            sweep_group_u8<PADDED, false, TS, false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b);
+            sweep_group_u8<PADDED, false, TS, false, 1>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b);
     }
+    tally.flush();
 }
 
 // The same half-sweep with staged inputs (see stage_u8): each thread copies the next block's
@@ -72,6 +78,7 @@ sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam,
     pdl_enter();
     const int stage_len = STAGE_CHUNKS * blockDim.x;
     int buf = 0;
+    Tally tally(trace);
     if (blockIdx.x < (unsigned)nblocks) stage_u8(lv, colour, Dp, Gp, skip, blockIdx.x, stage_mem);
     cp_async_commit();
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x, buf ^= 1) {
@@ -79,9 +86,10 @@ sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam,
             stage_u8(lv, colour, Dp, Gp, skip, b + gridDim.x, stage_mem + (buf ^ 1) * stage_len);
         cp_async_commit();
         cp_async_wait<1>();  // block b's copies have landed; the next block's may be in flight
-        sweep_group_u8<PADDED, APPEND, TS, false, 3>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al, 0, 0,
+        sweep_group_u8<PADDED, APPEND, TS, false, 3>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al, 0, 0,
                                                      stage_mem + buf * stage_len);
     }
+    tally.flush();
     cp_async_wait<0>();
 }
 
@@ -107,6 +115,7 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
     int64_t cur = idx < n ? (int64_t)e0 : nslot;
     int64_t nxt = idx + stride < n ? (int64_t)e1 : nslot;
     int buf = 0;
+    Tally tally(trace);
     if ((int64_t)blockIdx.x * groups < n) stage_u8<true>(lv, colour, Dp, Gp, 1, blockIdx.x, stage_mem, cur);
     cp_async_commit();
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride, buf ^= 1) {
@@ -115,11 +124,12 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
         cp_async_commit();
         const int64_t after = idx + 2 * stride < n ? (int64_t)al.in[idx + 2 * stride] : nslot;
         cp_async_wait<1>();  // block b's copies have landed; the next block's may be in flight
-        sweep_group_u8<PADDED, true, TS, false, 3, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, n, cur,
+        sweep_group_u8<PADDED, true, TS, false, 3, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, tally, b, al, n, cur,
                                                          stage_mem + buf * stage_len);
         cur = nxt;
         nxt = after;
     }
+    tally.flush();
     cp_async_wait<0>();
 }
 
@@ -285,17 +295,19 @@ sweep_u8_bulk_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
         return;
     }
     // the compute warps
+    Tally tally(trace);
     int64_t k = 0;
     for (int64_t b = blockIdx.x; b < nb; b += gridDim.x, ++k) {
         const int st = (int)(k % BULK_STAGES);
         if (!mbar_wait(&full[st], (unsigned)((k / BULK_STAGES) & 1), lv.err)) break;
         const unsigned s = slots[st * P + threadIdx.x / Gp];
         sweep_group_u8<PADDED, APPEND, TS, false, 4, true>(
-            lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al, n, s == 0xffffffffu ? nslot : (int64_t)s,
+            lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al, n, s == 0xffffffffu ? nslot : (int64_t)s,
             reinterpret_cast<const uint4 *>(bulk_mem + st * stage_bytes));
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
     }
+    tally.flush();
 }
 
 // CTAs of the bulk-copy sweep resident at once for this shared-memory size.
@@ -338,7 +350,7 @@ static cudaError_t launch_u8_bulk(const LevelView &lv, int colour, int D, int Dp
 // (bps_create admits at most 2^31 pixels), so n, idx + stride and b * groups stay below 2^31.
 template <bool PADDED, int TS, bool DP>
 __device__ __forceinline__ void list_loop(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
-                                          unsigned long long *trace, const ActiveList &al, unsigned n, unsigned e) {
+                                          Tally &trace, const ActiveList &al, unsigned n, unsigned e) {
     const unsigned lpp = DP ? 4 * Gp : Gp;  // lanes a pixel
     const unsigned groups = blockDim.x / lpp;
     const unsigned nslot = (unsigned)lv.H * (unsigned)lv.Wh;
@@ -373,8 +385,10 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
         e_dp = i_dp < nslot ? al.in[i_dp] : 0u;
     }
     const unsigned n = *al.n_in;
-    if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_dp);
-    else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, trace, al, n, e_pix);
+    Tally tally(trace);
+    if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_dp);
+    else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_pix);
+    tally.flush();
 }
 
 // Every iteration of one small scale in ONE launch of ONE thread-block cluster.  The CTAs of
@@ -393,9 +407,10 @@ sweep_u8_cluster_kernel(LevelView lv, int D, int Dp, int Gp, int lam, int lamT, 
     const int ncta = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     for (int it = 0; it < iters; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            unsigned long long *tr = trace ? trace + 2 * it + colour : nullptr;
+            Tally tr(trace ? trace + 2 * it + colour : nullptr);
             for (int b = rank; b < nblocks; b += ncta)
                 sweep_group_u8<PADDED, false, TS, true, EAGER>(lv, colour, D, Dp, Gp, lam, lamT, skip, tr, b);
+            tr.flush();
             cl.sync();
         }
 }

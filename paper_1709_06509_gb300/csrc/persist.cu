@@ -120,7 +120,7 @@ template <int FORM, int TS>
 __device__ __forceinline__ void persistent_group(const PersistParams &P, const PairDesc &pd, int l, int colour,
                                                  int t, int64_t b, bool listed, bool append) {
     const LevelView &lv = pd.lv[l];
-    unsigned long long *trace = pd.trace ? pd.trace + t : nullptr;
+    Tally trace(pd.trace ? pd.trace + t : nullptr);  // one block of the launch-free schedule: flushed below
     const ActiveList al{listed ? pd.lists[colour] : nullptr, listed ? pd.list_counts + t - 1 : nullptr,
                         append ? pd.lists[colour ^ 1] : nullptr, append ? pd.list_counts + t : nullptr};
     int64_t s_listed = 0;
@@ -158,6 +158,7 @@ __device__ __forceinline__ void persistent_group(const PersistParams &P, const P
             else sweep_group_f16<false, TS, false, false, false, true>(lv, colour, pd.D, pd.Dp, pd.Gp, lam, lamT, P.skip, trace, b);
         }
     }
+    trace.flush();
 }
 
 template <int FORM, int TS>

@@ -108,14 +108,13 @@ __global__ void sparse_start_kernel(LevelView fine, LevelView coarse, SparseView
 }
 
 // ------------------------------------------------------------------ the sweep
-__global__ void __launch_bounds__(256)
-sparse_sweep_kernel(LevelView lv, SparseView sv, int colour, int lam, int lamT, int trunc, int skip,
-                    unsigned long long *trace) {
-    pdl_enter();
+// One block of blockDim / Kp pixels of the half-sweep.
+__device__ __forceinline__ void sparse_group(const LevelView &lv, const SparseView &sv, int colour, int lam, int trunc,
+                                             int skip, Tally &trace, int64_t block) {
     const int Kp = sv.Kp, K = sv.K;
     const int lane = threadIdx.x & 31;
     const int j = threadIdx.x & (Kp - 1);
-    const int64_t s = (int64_t)blockIdx.x * (blockDim.x / Kp) + threadIdx.x / Kp;
+    const int64_t s = block * (blockDim.x / Kp) + threadIdx.x / Kp;
     const int64_t nslot = (int64_t)lv.H * lv.Wh;
     int x = 0, y = 0;
     bool valid = false;
@@ -152,10 +151,7 @@ sparse_sweep_kernel(LevelView lv, SparseView sv, int colour, int lam, int lamT, 
     const bool active = valid && (!skip || flag == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(Kp));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
+    trace.add(act, Kp);
 #pragma unroll
     for (int q = 0; q < 4; ++q) b += in[q];
     const int BIG = 1 << 28;
@@ -184,7 +180,17 @@ sparse_sweep_kernel(LevelView lv, SparseView sv, int colour, int lam, int lamT, 
         }
     }
     if (skip && active && j == 0) dirty_in[s] = 0u;
-    (void)lamT;
+}
+
+// Grid-stride over the pixel blocks with the CTAs resident at once (the trace count of a warp is
+// added once, at the end).
+__global__ void __launch_bounds__(256)
+sparse_sweep_kernel(LevelView lv, SparseView sv, int colour, int lam, int trunc, int skip, unsigned long long *trace,
+                    int64_t nblocks) {
+    pdl_enter();
+    Tally tally(trace);
+    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) sparse_group(lv, sv, colour, lam, trunc, skip, tally, b);
+    tally.flush();
 }
 
 // ------------------------------------------------------------------ read-out
@@ -252,9 +258,18 @@ cudaError_t launch_sparse_sweep(const LevelView &lv, const SparseView &sv, int c
                                 unsigned long long *trace, cudaStream_t st) {
     const int groups = 256 / sv.Kp;
     const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
+    if (blocks == 0) return cudaSuccess;
+    static int resident = 0;  // CTAs resident at once (looked up once per process)
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_sweep_kernel, 256, 0);
+        resident = std::max(1, sms * std::max(1, per_sm));
+    }
     const int lam = trunc == 0 ? 0 : lambda;
-    return launch_k(sparse_sweep_kernel, dim3((unsigned)blocks), dim3(256), 0, st, lv, sv, colour, lam, lam * trunc,
-                    trunc, skip, trace);
+    return launch_k(sparse_sweep_kernel, dim3((unsigned)std::min<int64_t>(blocks, resident)), dim3(256), 0, st, lv, sv,
+                    colour, lam, trunc, skip, trace, blocks);
 }
 
 cudaError_t launch_sparse_wta(const LevelView &lv, const SparseView &sv, int32_t *disp, cudaStream_t st) {

@@ -33,6 +33,21 @@ __device__ inline unsigned leader_bits(int Gp) {
     return m;
 }
 
+// The recomputed-pixel count of a launch (the skip trace): a warp counts its pixels in a register
+// over all the blocks it computes and adds them to the counter once, when the launch ends (flush).
+// The counter is one address for the whole grid, and atomics on one address serialise in L2: one
+// a warp and block cost as much time as a dense half-sweep of the finest scale itself.
+struct Tally {
+    unsigned long long *ptr;  // the launch's counter (nullable: no trace)
+    unsigned n;               // this warp's pixels so far (the same in every lane)
+    __device__ explicit Tally(unsigned long long *p) : ptr(p), n(0u) {}
+    __device__ __forceinline__ void add(unsigned act, int lanes_a_pixel) { n += __popc(act & leader_bits(lanes_a_pixel)); }
+    __device__ __forceinline__ void flush() {
+        if (ptr && n && (threadIdx.x & 31) == 0) atomicAdd(ptr, (unsigned long long)n);
+        n = 0u;
+    }
+};
+
 template <typename Acc>
 __device__ inline void min_convolve(const Acc (&h)[VEC], Acc lam, Acc lamT, int g, int Gp, Acc (&m)[VEC]) {
     using A = Arith<Acc>;
@@ -75,7 +90,7 @@ __device__ inline void min_convolve(const Acc (&h)[VEC], Acc lam, Acc lamT, int 
 template <typename CostT, typename MsgT, bool RW = false>
 __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int D, int Dp, int Gp,
                                             typename AccOf<MsgT>::type lam, typename AccOf<MsgT>::type lamT,
-                                            int skip, unsigned long long *trace, int64_t block) {
+                                            int skip, Tally &trace, int64_t block) {
     using Acc = typename AccOf<MsgT>::type;
     using A = Arith<Acc>;
     const int lane = threadIdx.x & 31;
@@ -93,10 +108,7 @@ __device__ __forceinline__ void sweep_group(const LevelView &lv, int colour, int
     const bool active = valid && (!skip || (colour ? lv.dirty[1] : lv.dirty[0])[s] != 0u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(Gp));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
+    trace.add(act, Gp);
     const int64_t sc = valid ? s : 0;
     const int dbase = g * VEC;
     const bool lane_data = dbase < Dp;
@@ -423,7 +435,7 @@ __device__ __forceinline__ void stage_u8(const LevelView &lv, int colour, int Dp
 //         0 to 1, and only its own update clears the flag), so its flag is not read.
 template <bool PADDED, bool APPEND = false, int TS = 0, bool RW = false, int EAGER = 0, bool LISTED = false>
 __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
-                                               int lamT, int skip, unsigned long long *trace, int64_t block,
+                                               int lamT, int skip, Tally &trace, int64_t block,
                                                const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
                                                int64_t n_in = 0, int64_t s_listed = 0, const uint4 *stage = nullptr) {
     const int lane = threadIdx.x & 31;
@@ -554,10 +566,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         valid && (LISTED || !skip || lv.start != 0 || (EAGER == 3 ? flag_staged : dirty_in[s]) == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(Gp));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
+    trace.add(act, Gp);
     if constexpr (EAGER == 0) {
         load_cost();
         load_messages(active);
@@ -670,7 +679,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
 // parameters as for sweep_group_u8; `block` counts blockDim / (4 Gp) pixels.
 template <bool PADDED, bool APPEND = false, int TS = 0, int EAGER = 0, bool LISTED = false>
 __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colour, int D, int Dp, int Gp, int lam,
-                                                  int lamT, int skip, unsigned long long *trace, int64_t block,
+                                                  int lamT, int skip, Tally &trace, int64_t block,
                                                   const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
                                                   int64_t s_listed = 0) {
     const int lane = threadIdx.x & 31;
@@ -746,10 +755,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     const bool active = valid && (LISTED || !skip || lv.start != 0 || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(LP));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
+    trace.add(act, LP);
     if constexpr (EAGER == 0) {
         load_cost();
         load_messages(active);

@@ -17,8 +17,10 @@ __global__ void __launch_bounds__(256, 2)
 sweep_f16_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam, float lamT, int skip,
                  unsigned long long *trace, int nblocks, ActiveList al) {
     pdl_enter();
+    Tally tally(trace);
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
-        sweep_group_f16<PADDED, TS, EAGER, APPEND>(lv, colour, D, Dp, Gp, lam, lamT, skip, trace, b, al);
+        sweep_group_f16<PADDED, TS, EAGER, APPEND>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
+    tally.flush();
 }
 
 // Over the pixels of an active list (its length read on the device), like the u8 list sweep.
@@ -33,11 +35,13 @@ sweep_f16_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam
     int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
     unsigned e = idx < nslot ? al.in[idx] : 0u;
     const int64_t n = *al.n_in;
+    Tally tally(trace);
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
         const int64_t s = idx < n ? (int64_t)e : nslot;
         if (idx + stride < n) e = al.in[idx + stride];
-        sweep_group_f16<PADDED, TS, false, true, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, trace, b, al, s);
+        sweep_group_f16<PADDED, TS, false, true, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, tally, b, al, s);
     }
+    tally.flush();
 }
 
 static int resident_f16() {  // CTAs of the fp16 sweep resident at once (looked up once per process)

@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t word(const uint4 (&v)[2], int j) {
 // loads (a kernel that wrote them earlier in the same launch, across a grid barrier).
 template <bool PADDED, int TS, bool EAGER, bool APPEND = false, bool LISTED = false, bool RW = false>
 __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour, int D, int Dp, int Gp, float lam,
-                                                float lamT, int skip, unsigned long long *trace, int64_t block,
+                                                float lamT, int skip, Tally &trace, int64_t block,
                                                 const ActiveList &al = ActiveList{nullptr, nullptr, nullptr, nullptr},
                                                 int64_t s_listed = 0) {
     const int lane = threadIdx.x & 31;
@@ -95,10 +95,7 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
     const bool active = valid && (LISTED || !skip || dirty_in[s] == 1u);
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) return;
-    if (trace && lane == 0) {
-        const int n = __popc(act & leader_bits(Gp));
-        if (n) atomicAdd(trace, (unsigned long long)n);
-    }
+    trace.add(act, Gp);
     if constexpr (!EAGER) {
         load_cost();
         load_messages(active);
