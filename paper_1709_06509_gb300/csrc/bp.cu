@@ -36,12 +36,18 @@ template <bool PADDED, bool APPEND, int TS, bool DP>
 __global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                 unsigned long long *trace, int nblocks, ActiveList al) {
+    unsigned *abuf = nullptr;
+    if constexpr (APPEND) {
+        BPS_LIST_BUFFER(list_buf);
+        abuf = list_buf[threadIdx.x >> 5];
+    }
     pdl_enter();
-    Tally tally(trace);
+    Tally tally(trace, abuf);
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
         if constexpr (DP) sweep_group_u8_dp<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
         else sweep_group_u8<PADDED, APPEND, TS>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
     }
+    if constexpr (APPEND) tally.flush_appends(al.out, al.n_out, (unsigned)lv.H * (unsigned)lv.Wh, lv.err);
     tally.flush();
 }
 
@@ -78,7 +84,12 @@ sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam,
     pdl_enter();
     const int stage_len = STAGE_CHUNKS * blockDim.x;
     int buf = 0;
-    Tally tally(trace);
+    unsigned *abuf = nullptr;
+    if constexpr (APPEND) {
+        BPS_LIST_BUFFER(list_buf);
+        abuf = list_buf[threadIdx.x >> 5];
+    }
+    Tally tally(trace, abuf);
     if (blockIdx.x < (unsigned)nblocks) stage_u8(lv, colour, Dp, Gp, skip, blockIdx.x, stage_mem);
     cp_async_commit();
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x, buf ^= 1) {
@@ -89,6 +100,7 @@ sweep_u8_staged_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam,
         sweep_group_u8<PADDED, APPEND, TS, false, 3>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al, 0, 0,
                                                      stage_mem + buf * stage_len);
     }
+    if constexpr (APPEND) tally.flush_appends(al.out, al.n_out, (unsigned)lv.H * (unsigned)lv.Wh, lv.err);
     tally.flush();
     cp_async_wait<0>();
 }
@@ -115,7 +127,8 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
     int64_t cur = idx < n ? (int64_t)e0 : nslot;
     int64_t nxt = idx + stride < n ? (int64_t)e1 : nslot;
     int buf = 0;
-    Tally tally(trace);
+    BPS_LIST_BUFFER(list_buf);
+    Tally tally(trace, list_buf[threadIdx.x >> 5]);
     if ((int64_t)blockIdx.x * groups < n) stage_u8<true>(lv, colour, Dp, Gp, 1, blockIdx.x, stage_mem, cur);
     cp_async_commit();
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride, buf ^= 1) {
@@ -129,6 +142,7 @@ sweep_u8_staged_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int
         cur = nxt;
         nxt = after;
     }
+    tally.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
     tally.flush();
     cp_async_wait<0>();
 }
@@ -385,9 +399,11 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
         e_dp = i_dp < nslot ? al.in[i_dp] : 0u;
     }
     const unsigned n = *al.n_in;
-    Tally tally(trace);
+    BPS_LIST_BUFFER(list_buf);
+    Tally tally(trace, list_buf[threadIdx.x >> 5]);
     if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_dp);
     else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_pix);
+    tally.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
     tally.flush();
 }
 

@@ -37,14 +37,63 @@ __device__ inline unsigned leader_bits(int Gp) {
 // over all the blocks it computes and adds them to the counter once, when the launch ends (flush).
 // The counter is one address for the whole grid, and atomics on one address serialise in L2: one
 // a warp and block cost as much time as a dense half-sweep of the finest scale itself.
+//
+// The same holds for the active lists' length counter: a warp that appends newly dirty pixels
+// can gather them in a buffer of its own in shared memory (abuf, LIST_BUF_CAP entries) and
+// reserve room in the list once per LIST_BUF_CAP entries instead of once per pixel block
+// (flush_appends; the launch's kernel calls it before it ends).  Without a buffer (abuf null:
+// kernels that read a list they append to in the same launch) the warp reserves at once.  The
+// order of the entries in a list is free: it only decides which pixel a later launch takes
+// first, never a message.
+constexpr unsigned LIST_BUF_CAP = 256;  // >= 4 appends a pixel x 32 pixels of a warp (Gp = 1)
+// The append buffers of a 256-thread CTA's eight warps (a static shared array of the kernel).
+#define BPS_LIST_BUFFER(name) __shared__ unsigned name[256 / 32][::bps::LIST_BUF_CAP]
 struct Tally {
     unsigned long long *ptr;  // the launch's counter (nullable: no trace)
     unsigned n;               // this warp's pixels so far (the same in every lane)
-    __device__ explicit Tally(unsigned long long *p) : ptr(p), n(0u) {}
+    unsigned *abuf;           // this warp's append buffer in shared memory (nullable: none)
+    unsigned an;              // entries in it (the same in every lane)
+    __device__ explicit Tally(unsigned long long *p, unsigned *append_buf = nullptr)
+        : ptr(p), n(0u), abuf(append_buf), an(0u) {}
     __device__ __forceinline__ void add(unsigned act, int lanes_a_pixel) { n += __popc(act & leader_bits(lanes_a_pixel)); }
     __device__ __forceinline__ void flush() {
         if (ptr && n && (threadIdx.x & 31) == 0) atomicAdd(ptr, (unsigned long long)n);
         n = 0u;
+    }
+    // Move the buffered entries into the list `out` (length counter n_out, capacity cap): one
+    // reservation, then coalesced stores.  Called by every lane of the warp together.
+    __device__ __forceinline__ void flush_appends(unsigned *out, unsigned *n_out, unsigned cap, unsigned *err) {
+        if (!abuf || an == 0u) return;
+        __syncwarp();
+        const unsigned lane = threadIdx.x & 31u;
+        unsigned base = 0u;
+        if (lane == 0u) base = atomicAdd(n_out, an);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (unsigned i = lane; i < an; i += 32u)
+            if (BPS_CHECK(base + i < cap, err, 3u)) out[base + i] = abuf[i];
+        an = 0u;
+        __syncwarp();
+    }
+    // Append the entries that lanes with `pred` hold in `v` (the ballot of pred is `am`, taken by
+    // the caller), at positions `base` + (the rank of the lane among them).  Buffered when the warp
+    // has a buffer, else reserved at once.
+    __device__ __forceinline__ void append(unsigned am, bool pred, unsigned v, unsigned *out, unsigned *n_out,
+                                           unsigned cap, unsigned *err) {
+        if (am == 0u) return;
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned cnt = (unsigned)__popc(am);
+        const unsigned rank = (unsigned)__popc(am & ((1u << lane) - 1u));
+        if (abuf) {
+            if (an + cnt > LIST_BUF_CAP) flush_appends(out, n_out, cap, err);
+            if (pred) abuf[an + rank] = v;
+            an += cnt;
+            __syncwarp();
+        } else {
+            unsigned base = 0u;
+            if (lane == 0u) base = atomicAdd(n_out, cnt);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (pred && BPS_CHECK(base + rank < cap, err, 3u)) out[base + rank] = v;
+        }
     }
 };
 
@@ -653,15 +702,27 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             total += __popc(am[q]);
         }
         if (total) {
-            unsigned base = 0u;
-            if (lane == 0) base = atomicAdd(al.n_out, total);
-            base = __shfl_sync(FULL, base, 0);
             const unsigned below = (1u << lane) - 1u;
+            if (trace.abuf) {  // gathered in the warp's buffer (see Tally)
+                if (trace.an + total > LIST_BUF_CAP) trace.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
+                unsigned base = trace.an;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const unsigned at = base + __popc(am[q] & below);
-                if (was[q] == 0u && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = qsv[q];
-                base += __popc(am[q]);
+                for (int q = 0; q < 4; ++q) {
+                    if (was[q] == 0u) trace.abuf[base + __popc(am[q] & below)] = qsv[q];
+                    base += __popc(am[q]);
+                }
+                trace.an += total;
+                __syncwarp();
+            } else {
+                unsigned base = 0u;
+                if (lane == 0) base = atomicAdd(al.n_out, total);
+                base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned at = base + __popc(am[q] & below);
+                    if (was[q] == 0u && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = qsv[q];
+                    base += __popc(am[q]);
+                }
             }
         }
     }
@@ -820,13 +881,7 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
     if constexpr (APPEND) {
         const bool app = mark != 0u && atomicOr(dirty_out + (mark - 1u), 1u) == 0u;
         const unsigned am = __ballot_sync(FULL, app);
-        if (am) {
-            unsigned base = 0u;
-            if (lane == 0) base = atomicAdd(al.n_out, (unsigned)__popc(am));
-            base = __shfl_sync(FULL, base, 0);
-            const unsigned at = base + __popc(am & ((1u << lane) - 1u));
-            if (app && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = mark - 1u;
-        }
+        trace.append(am, app, mark - 1u, al.out, al.n_out, (unsigned)nslot, lv.err);
     }
     // the pixel's four direction groups: did any mark its receiver?
     const unsigned mk = __ballot_sync(FULL, marked && g == 0);

@@ -16,10 +16,16 @@ template <bool PADDED, int TS, bool EAGER, bool APPEND>
 __global__ void __launch_bounds__(256, 2)
 sweep_f16_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam, float lamT, int skip,
                  unsigned long long *trace, int nblocks, ActiveList al) {
+    unsigned *abuf = nullptr;
+    if constexpr (APPEND) {
+        BPS_LIST_BUFFER(list_buf);
+        abuf = list_buf[threadIdx.x >> 5];
+    }
     pdl_enter();
-    Tally tally(trace);
+    Tally tally(trace, abuf);
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x)
         sweep_group_f16<PADDED, TS, EAGER, APPEND>(lv, colour, D, Dp, Gp, lam, lamT, skip, tally, b, al);
+    if constexpr (APPEND) tally.flush_appends(al.out, al.n_out, (unsigned)lv.H * (unsigned)lv.Wh, lv.err);
     tally.flush();
 }
 
@@ -35,12 +41,14 @@ sweep_f16_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, float lam
     int64_t idx = (int64_t)blockIdx.x * groups + threadIdx.x / Gp;
     unsigned e = idx < nslot ? al.in[idx] : 0u;
     const int64_t n = *al.n_in;
-    Tally tally(trace);
+    BPS_LIST_BUFFER(list_buf);
+    Tally tally(trace, list_buf[threadIdx.x >> 5]);
     for (int64_t b = blockIdx.x; b * groups < n; b += gridDim.x, idx += stride) {
         const int64_t s = idx < n ? (int64_t)e : nslot;
         if (idx + stride < n) e = al.in[idx + stride];
         sweep_group_f16<PADDED, TS, false, true, true>(lv, colour, D, Dp, Gp, lam, lamT, 1, tally, b, al, s);
     }
+    tally.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
     tally.flush();
 }
 

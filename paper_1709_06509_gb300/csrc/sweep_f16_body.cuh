@@ -221,14 +221,26 @@ __device__ __forceinline__ void sweep_group_f16(const LevelView &lv, int colour,
             total += __popc(am[q]);
         }
         if (total) {
-            unsigned base = 0u;
-            if (lane == 0) base = atomicAdd(al.n_out, total);
-            base = __shfl_sync(FULL, base, 0);
             const unsigned below = (1u << lane) - 1u;
+            if (trace.abuf) {  // gathered in the warp's buffer (see Tally)
+                if (trace.an + total > LIST_BUF_CAP) trace.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
+                unsigned base = trace.an;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = mark[q] - 1u;
-                base += __popc(am[q]);
+                for (int q = 0; q < 4; ++q) {
+                    if (was[q] == 0u) trace.abuf[base + __popc(am[q] & below)] = mark[q] - 1u;
+                    base += __popc(am[q]);
+                }
+                trace.an += total;
+                __syncwarp();
+            } else {
+                unsigned base = 0u;
+                if (lane == 0) base = atomicAdd(al.n_out, total);
+                base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (was[q] == 0u) al.out[base + __popc(am[q] & below)] = mark[q] - 1u;
+                    base += __popc(am[q]);
+                }
             }
         }
     }
