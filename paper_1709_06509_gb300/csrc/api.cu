@@ -369,6 +369,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.Wh = p.Whs[l];
         v.eps = 0;  // the exact skip rule
         v.freeze = 0;
+        v.bsum8 = 0;
         v.start = 0;
         v.pWh = 0;
         v.pmsg[0] = v.pmsg[1] = nullptr;
@@ -666,6 +667,9 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, const Iters &its, int lambd
         const int iters = its.n[l];
         LevelView v = c->lv[l];
         if (l == 0) v.disp = readout;  // the finest scale's half-sweeps read out what they recompute
+        // every message the sweeps read is one they wrote, normalised to [0, lambda * trunc], or a
+        // zero start message, unless the caller gave the start messages
+        v.bsum8 = (!warm && (int64_t)lambda * trunc <= 63) ? 1 : 0;
         if (l == 0 && c->sv.K > 0) {
             // the finest scale over sparse candidates: selection, start from the parent's messages
             // at each candidate's label, then the half-sweeps

@@ -33,6 +33,9 @@ struct LevelView {
     unsigned *dirty[2];  // 32-bit words so a sender can flip them atomically: bit 0 dirty, bit 1 frozen
     int eps;             // skip rule: a receiver is marked when its message moves by more than eps
     int freeze;          // skip rule: a recomputed pixel that marked no receiver is frozen
+    // u8 form: 1 when every message a half-sweep reads is at most 63 (lambda * trunc <= 63 and no
+    // caller-given start messages), so four of them add up bytewise without a carry
+    int bsum8;
     // A scale's first iteration without a separate coarse-to-fine copy (u8 sweeps): start = 1, the
     // first half-sweep reads each even pixel's start messages straight from its parent's record
     // (pmsg, pWh: the parent scale's message arrays and slots per row) and recomputes every

@@ -280,8 +280,8 @@ __device__ __forceinline__ void u8_message(const uint32_t (&h)[8], int lam, int 
                 // except across the lane edge and across the middle (labels 7 | 8)
                 const uint32_t lft = j > 0 ? h[j - 1] : pk((uint32_t)left, h[7] & 0xffffu);
                 const uint32_t rgt = j < 7 ? h[j + 1] : pk(h[0] >> 16, (uint32_t)right);
-                m[j] = __vimin3_u16x2(__viaddmin_u16x2(lft, LAM2, h[j]), __viaddmin_u16x2(rgt, LAM2, CAP2), CAP2) -
-                       HM2;
+                // rgt + LAM2 cannot carry between the halves (both stay below 2^15 + 255)
+                m[j] = __vimin3_u16x2(__viaddmin_u16x2(lft, LAM2, h[j]), rgt + LAM2, CAP2) - HM2;
             }
         }
     } else {
@@ -620,12 +620,23 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         load_cost();
         load_messages(active);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    if (lv.bsum8) {
+        // every incoming message is at most 63: the four add up bytewise without a carry, and the
+        // sum is unpacked once
+        const uint4 sum = make_uint4(in[0].x + in[1].x + in[2].x + in[3].x, in[0].y + in[1].y + in[2].y + in[3].y,
+                                     in[0].z + in[1].z + in[2].z + in[3].z, in[0].w + in[1].w + in[2].w + in[3].w);
         uint32_t t[8];
-        unpack_msg(in[q], t);
+        unpack_msg(sum, t);
 #pragma unroll
         for (int j = 0; j < 8; ++j) b[j] += t[j];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t t[8];
+            unpack_msg(in[q], t);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] += t[j];
+        }
     }
     if constexpr (PADDED) {
 #pragma unroll
@@ -821,12 +832,23 @@ __device__ __forceinline__ void sweep_group_u8_dp(const LevelView &lv, int colou
         load_cost();
         load_messages(active);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    if (lv.bsum8) {
+        // every incoming message is at most 63: the four add up bytewise without a carry, and the
+        // sum is unpacked once
+        const uint4 sum = make_uint4(in[0].x + in[1].x + in[2].x + in[3].x, in[0].y + in[1].y + in[2].y + in[3].y,
+                                     in[0].z + in[1].z + in[2].z + in[3].z, in[0].w + in[1].w + in[2].w + in[3].w);
         uint32_t t[8];
-        unpack_msg(in[q], t);
+        unpack_msg(sum, t);
 #pragma unroll
         for (int j = 0; j < 8; ++j) b[j] += t[j];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t t[8];
+            unpack_msg(in[q], t);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] += t[j];
+        }
     }
     if constexpr (PADDED) {
 #pragma unroll

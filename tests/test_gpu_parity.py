@@ -81,6 +81,9 @@ CASES = [
     (40, 30, 12, 5, 3, 3, 10, 0),     # trunc = 0
     (24, 6, 256, 3, 2, 2, 10, 2),     # D = 256: 16 lanes per pixel
     (12, 5, 512, 3, 1, 1, 3, 7),      # D = 512: a full warp per pixel
+    (37, 21, 20, 5, 3, 4, 21, 3),     # lambda * trunc = 63: four messages still add up bytewise
+    (37, 21, 20, 5, 3, 4, 16, 4),     # lambda * trunc = 64: they do not
+    (50, 23, 24, 5, 3, 4, 30, 3),     # lambda * trunc = 90
 ]
 
 
@@ -154,11 +157,14 @@ def test_u8_form_equals_int32_form():
 
 
 @pytest.mark.parametrize("msg_type", INT_FORMS)
-def test_warm_start_matches_oracle(msg_type):
+@pytest.mark.parametrize("init_hi", [21, 256], ids=["normalised", "up_to_255"])
+def test_warm_start_matches_oracle(msg_type, init_hi):
+    # start messages need not be normalised: up to 255 they still fit the u8 form's bytes, but four
+    # of them no longer add up bytewise
     pair = synth.make_pair(9, 50, 40, 10, 3, 2.0)
     dims = oracle.level_dims(50, 40, 3)
     wc, hc = dims[-1]
-    init = np.random.default_rng(1).integers(0, 21, (4, hc, wc, 10)).astype(np.int32)
+    init = np.random.default_rng(1).integers(0, init_hi, (4, hc, wc, 10)).astype(np.int32)
     # slots of neighbours outside the image hold 0 (the layout both sides document)
     init[0, 0] = init[1, -1] = 0
     init[2, :, 0] = init[3, :, -1] = 0
