@@ -29,11 +29,18 @@ sweep_kernel(LevelView lv, int colour, int D, int Dp, int Gp, typename AccOf<Msg
 // Grid-stride over the colour's pixel blocks: the grid is capped at what is resident at
 // once, so a launch pays for block scheduling once, not once per wave.
 #ifndef BPS_SWEEP_MIN_BLOCKS
-#define BPS_SWEEP_MIN_BLOCKS 3  // resident CTAs per SM the u8 sweep is compiled for
+#define BPS_SWEEP_MIN_BLOCKS 3  // resident CTAs per SM the u8 sweep is compiled for (distance transform)
 #endif
+#ifndef BPS_SWEEP_STENCIL_MIN_BLOCKS
+// ... and with the stencil minimisation (T <= 2) and D a multiple of 16: 64 registers a thread,
+// 32 warps an SM, which hides more of the dependent round trips to memory than 24 (spills of at
+// most 8 bytes a thread)
+#define BPS_SWEEP_STENCIL_MIN_BLOCKS 4
+#endif
+#define BPS_SWEEP_BLOCKS(PADDED, TS) (((TS) == 0 || (PADDED)) ? BPS_SWEEP_MIN_BLOCKS : BPS_SWEEP_STENCIL_MIN_BLOCKS)
 
 template <bool PADDED, bool APPEND, int TS, bool DP>
-__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, BPS_SWEEP_BLOCKS(PADDED, TS))
 sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                 unsigned long long *trace, int nblocks, ActiveList al) {
     unsigned *abuf = nullptr;
@@ -54,7 +61,7 @@ sweep_u8_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int la
 // The same half-sweep with every load issued at once (see EAGER in sweep_group_u8): the first
 // block of each CTA loads its costs before waiting for the predecessor kernel.
 template <bool PADDED, int TS, bool DP>
-__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, BPS_SWEEP_BLOCKS(PADDED, TS))
 sweep_u8_eager_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT, int skip,
                       unsigned long long *trace, int nblocks) {
     Tally tally(trace);
@@ -383,7 +390,7 @@ __device__ __forceinline__ void list_loop(const LevelView &lv, int colour, int D
 // lanes while the list has at most dp_max entries (short lists: a quarter of the dependent work
 // per lane), one group a pixel on longer ones (fewer passes of the resident CTAs).
 template <bool PADDED, int TS, bool DP>
-__global__ void __launch_bounds__(256, BPS_SWEEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, BPS_SWEEP_BLOCKS(PADDED, TS))
 sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, int lamT,
                      unsigned long long *trace, ActiveList al, int64_t dp_max) {
     pdl_enter();
@@ -615,17 +622,20 @@ static cudaError_t sweep_t(const LevelView &lv, int colour, int D, int Dp, int G
                     (Acc)lambda * (Acc)trunc, skip, trace, (int)blocks);
 }
 
-// CTAs of the u8 sweep that fit on the GPU at once (looked up once per process).
-static int resident_blocks(int msg_kind) {
-    static int cached[3] = {0, 0, 0};
-    if (!cached[msg_kind]) {
+// CTAs of the u8 sweep that fit on the GPU at once: the distance-transform or padded kernels, or
+// the stencil kernels of D a multiple of 16 (looked up once per process).
+static int resident_blocks(int ts, bool padded) {
+    static int cached[2] = {0, 0};
+    const int k = (ts == 0 || padded) ? 0 : 1;
+    if (!cached[k]) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 0, false>, 256, 0);
-        cached[msg_kind] = std::max(1, sms * std::max(1, per_sm));
+        if (k == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 0, false>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_u8_kernel<false, false, 2, false>, 256, 0);
+        cached[k] = std::max(1, sms * std::max(1, per_sm));
     }
-    return cached[msg_kind];
+    return cached[k];
 }
 
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda, int trunc,
@@ -641,9 +651,9 @@ cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, i
         const int64_t blocks = ((int64_t)lv.H * lv.Wh + groups - 1) / groups;
         if (blocks == 0) return cudaSuccess;
         const int lam = trunc == 0 ? 0 : lambda;  // with trunc 0 every message is 0 whatever lambda is
-        const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_blocks(MSG_U8));
-        const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
         const int ts = (variant & VARIANT_GENERAL_DT) ? 0 : (trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0));
+        const unsigned grid = (unsigned)std::min<int64_t>(blocks, resident_blocks(ts, (D & 15) != 0));
+        const ActiveList al{lists.in, lists.n_in, skip ? lists.out : nullptr, lists.n_out};
         const bool eager = (variant & VARIANT_EAGER) != 0;
         const bool staged = (variant & (list_launch ? VARIANT_STAGED_LISTS : VARIANT_STAGED)) != 0 && !dp;
         const bool bulk = (variant & (list_launch ? VARIANT_BULK_LISTS : VARIANT_BULK)) != 0 && !dp;
@@ -836,7 +846,8 @@ cudaError_t preload_bp_kernels(int msg_kind) {
         if (e == cudaSuccess) e = preload_u8<true, 0>();
         if (e == cudaSuccess) e = preload_u8<true, 1>();
         if (e == cudaSuccess) e = preload_u8<true, 2>();
-        if (e == cudaSuccess) resident_blocks(MSG_U8);
+        if (e == cudaSuccess) resident_blocks(0, false);
+        if (e == cudaSuccess) resident_blocks(2, false);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, import_kernel<uint8_t, int32_t>);
         break;
     default:
