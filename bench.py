@@ -334,19 +334,21 @@ def time_region(fn, steps, flush, stream, flush_value=1) -> list[float]:
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def pair_launches(bps, st) -> int:
-    """Kernels one bps_stereo call of a context launches: the NCC kernel (scale 1 fused), the
-    pyramid kernels of scales 2.. (two scales a launch), the solve-start kernel, one copy kernel
-    per scale that does not start from its parent's records itself, 2 * ITERS half-sweeps per
-    scale (one launch for a cluster scale), and the read-out."""
+def pair_launches(bps, st, window: int) -> int:
+    """Kernels one bps_stereo call of a context launches: the NCC kernel (scale 1 fused; the
+    tensor-core kernel adds its FP64 follow-up), the pyramid kernels of scales 2.. (two scales a
+    launch), the solve-start kernel, one copy kernel per scale that does not start from its parent's
+    records itself, 2 * ITERS half-sweeps per scale (one launch for a cluster scale), and the
+    read-out."""
     if st.msg_type == bps.BPS_MSG_FP16:
         # float costs: scale 1 is not fused into the NCC kernel; every finer scale's start is copied
         return 1 + LEVELS // 2 + 1 + (LEVELS - 1) + 2 * ITERS * LEVELS + 1
+    ncc = 2 if st.ncc_kernel(window, TRUNC_DATA) == bps.BPS_NCC_TENSOR else 1
     vs = st.variants()
     cluster_scales = [lvl for lvl in range(LEVELS) if vs[lvl] & bps.BPS_VARIANT_CLUSTER]
     sweeps = sum(1 if lvl in cluster_scales else 2 * ITERS for lvl in range(LEVELS))
     copies = sum(1 for lvl in cluster_scales if lvl < LEVELS - 1)
-    return 1 + (max(0, LEVELS - 2) + 1) // 2 + 1 + copies + sweeps + 1
+    return ncc + (max(0, LEVELS - 2) + 1) // 2 + 1 + copies + sweeps + 1
 
 
 def batch_report(args):
@@ -766,7 +768,7 @@ def fp16_key(bps, autotune, pair, window, dev, args, flush, stream, gold) -> dic
     out["roofline"] = {"bound": "hbm", "achieved": roof["achieved"], "peak": roof["peak"], "unit": "GB/s",
                        "frac": roof["frac"], "bytes_model": "(8s + c) = 20 B per recomputed pixel-label "
                        "(s = 2 B fp16 message, c = 4 B fp32 cost)", "solve_ms": roof["solve_ms"]}
-    out["gpu_launches_per_step"] = pair_launches(bps, st)
+    out["gpu_launches_per_step"] = pair_launches(bps, st, window)
     st.close()
     return out
 
@@ -1008,7 +1010,7 @@ def main():
         e2e_s, e2e_sync_s = (float(v) for v in t.tolist())
     h2d = 2 * pair.left.size
     d2h = 4 * pair.left.size + 8
-    launches_per_step = pair_launches(bps, st)
+    launches_per_step = pair_launches(bps, st, window)
     if args.trace_jsonl and rank == 0:
         write_trace_jsonl(args.trace_jsonl, st, L, R, window, pair)
     extras = {}
