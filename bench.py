@@ -88,6 +88,9 @@ def parse():
                     help="also write, after the timed region, one JSON line per iteration count k = 1..10 of "
                          "the headline pair: the energy after k iterations per scale and, per half-sweep of the "
                          "finest scale, the pixels recomputed and the converged fraction")
+    ap.add_argument("--blocking-report", action="store_true",
+                    help="temporal blocking of a scale's first iteration: depth 1 (two launches) against depth 2 "
+                         "(BPS_VARIANT_BLOCK2) on the 1280x720 D64 pair and the full-HD pair")
     ap.add_argument("--sync-report", action="store_true",
                     help="instead of the benchmark line: the cost of a grid barrier inside one cooperative launch "
                          "against a programmatically chained kernel boundary in a graph, for grids of 1 to 3 CTAs "
@@ -844,6 +847,58 @@ def write_trace_jsonl(path, st, L, R, window, pair):
                                  "finest_converged_frac": conv, "trace": tr}) + "\n")
 
 
+def blocking_report(args):
+    """Blocking depth 1 against 2 for a scale's first iteration (BPS_VARIANT_BLOCK2 cleared or set
+    on every scale below the coarsest, the other variant bits as tuned): the graph-replayed solve
+    time (median, L2 flushed) and the first iteration's profile-mode launch time per scale; both
+    depths must give the same disparities, energy and trace."""
+    import numpy as np
+    import torch
+
+    import paper_1709_06509_gb300 as bps
+    from paper_1709_06509_gb300 import autotune, synth
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    K = bps.BPS_VARIANT_BLOCK2
+    out = {"report": "temporal blocking of a scale's first iteration", "pairs": {}}
+    for name in ("c3_1280x720_d64", HEADLINE):
+        pair, window = synth.workload_pair(name)
+        st, L, R, tuned = setup_ctx(bps, autotune, pair, window, bps.BPS_MSG_U8, dev, args.tune_cache)
+        base = st.variants()
+        rows, ref = {}, None
+        for depth in (1, 2):
+            vs = [(v | K) if depth == 2 and lvl < LEVELS - 1 else (v & ~K) for lvl, v in enumerate(base)]
+            for lvl, v in enumerate(vs):
+                st.set_variant(lvl, v)
+            st.build_cost_volume(L, R, window, TRUNC_DATA)
+            solve = lambda: st.bp_solve(ITERS, LAM, TRUNC, skip=True, graph=True)
+            for _ in range(3):
+                solve()
+            ms = statistics.median(time_region(solve, max(5, args.steps), flush, stream, flush_value=13))
+            firsts = []
+            for _ in range(3):
+                flush.fill_(5)
+                st.build_cost_volume(L, R, window, TRUNC_DATA)
+                st.bp_solve(ITERS, LAM, TRUNC, skip=True, profile=True)
+                t = st.read_launch_times()
+                firsts.append([t[2 * ITERS * (LEVELS - 1 - lvl)] + t[2 * ITERS * (LEVELS - 1 - lvl) + 1]
+                               for lvl in range(LEVELS)])
+            disp = st.wta_disparity()
+            res = (np.asarray(disp.cpu()).tobytes(), int(st.energy(disp, LAM, TRUNC)[0].item()),
+                   [int(v) for v in st.get_trace()])
+            if ref is None:
+                ref = res
+            elif res != ref:
+                raise RuntimeError(f"{name}: blocking depth 2 changed the result")
+            rows[f"depth{depth}"] = {"sweep_variants": vs, "solve_ms": ms,
+                                     "first_iteration_ms_per_scale": [min(f[l] for f in firsts) for l in range(LEVELS)]}
+        out["pairs"][name] = {"tuned": tuned, **rows, "same_result": True}
+        st.close()
+    print(json.dumps(out))
+
+
 def sync_report(args):
     """bps_measure_sync_costs for grids of 1, 2 and 3 CTAs a SM: the phase separation the persistent
     form pays (a grid barrier) against the chained form's (a PDL kernel boundary in a graph)."""
@@ -904,6 +959,8 @@ def main():
         return launch_report(args)
     if args.sync_report:
         return sync_report(args)
+    if args.blocking_report:
+        return blocking_report(args)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     rank, world, local = dist_env()
     import torch

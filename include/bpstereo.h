@@ -328,6 +328,12 @@ int bps_batch_stereo_host(bps_batch *batch, const uint8_t *const *h_lefts, const
  *                           Its waits are bounded: one that gives up makes bps_get_error report
  *                           BPS_ERR_TIMEOUT for the solve;
  *   BPS_VARIANT_BULK_LISTS  the same on the list launches (with BPS_VARIANT_LISTS).
+ *   BPS_VARIANT_BLOCK2      temporal blocking to depth 2 of the scale's first iteration (with
+ *                           the fast-converging skip, on scales below the coarsest, without the
+ *                           freeze rule): one launch runs both half-sweeps tile by tile (32 x 16
+ *                           pixels), each tile's odd pixels reading back from L2 the messages
+ *                           its even pixels (and the even pixels bordering it, computed again)
+ *                           have just written; ignored elsewhere.
  * With BPS_FLAG_PROFILE a cluster launch's time is shared out evenly over its half-sweeps.
  * variant = -1 restores the default (chosen from the scale's size).  Setting a variant
  * drops a graph recorded by bps_stereo.  bps_get_sweep_variant returns the current one.
@@ -372,6 +378,7 @@ int bps_get_ncc_kernel(bps_ctx *ctx, int window, int trunc_data);
 #define BPS_VARIANT_STAGED_LISTS 128
 #define BPS_VARIANT_BULK 256
 #define BPS_VARIANT_BULK_LISTS 512
+#define BPS_VARIANT_BLOCK2 1024
 int bps_set_sweep_variant(bps_ctx *ctx, int level, int variant);
 int bps_get_sweep_variant(bps_ctx *ctx, int level);
 

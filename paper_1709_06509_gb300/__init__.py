@@ -59,6 +59,7 @@ BPS_VARIANT_STAGED = 64
 BPS_VARIANT_STAGED_LISTS = 128
 BPS_VARIANT_BULK = 256
 BPS_VARIANT_BULK_LISTS = 512
+BPS_VARIANT_BLOCK2 = 1024
 BPS_NCC_DEFAULT = 0
 BPS_NCC_ROWS = 1
 BPS_NCC_TENSOR = 2

@@ -27,7 +27,8 @@ from __future__ import annotations
 import json
 import os
 
-from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_BULK, BPS_VARIANT_BULK_LISTS, BPS_VARIANT_CLUSTER, BPS_VARIANT_DPAR,
+from . import (BPS_ERR_UNSUPPORTED, BPS_VARIANT_BLOCK2, BPS_VARIANT_BULK, BPS_VARIANT_BULK_LISTS, BPS_VARIANT_CLUSTER,
+               BPS_VARIANT_DPAR,
                BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_EAGER, BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS,
                BPS_VARIANT_STAGED, BPS_VARIANT_STAGED_LISTS, BPSError, level_dims)
 
@@ -35,6 +36,7 @@ _G, _L, _E, _C, _P, _PL, _S, _SL = (BPS_VARIANT_GENERAL_DT, BPS_VARIANT_LISTS, B
                                     BPS_VARIANT_DPAR, BPS_VARIANT_DPAR_LISTS, BPS_VARIANT_STAGED,
                                     BPS_VARIANT_STAGED_LISTS)
 _B, _BL = BPS_VARIANT_BULK, BPS_VARIANT_BULK_LISTS
+_K = BPS_VARIANT_BLOCK2  # blocking depth 2 for a scale's first iteration (depth 1 without it)
 # a cluster launch is only a candidate for scales of at most this many lanes (pixels x lanes per pixel)
 CLUSTER_MAX_LANES = 16 * 16 * 512
 SMALL_CANDIDATES = (0, _G, _E, _E | _G, _C, _C | _E, _C | _E | _G, _P, _P | _G, _P | _E, _P | _E | _G)
@@ -43,18 +45,26 @@ LARGE_CANDIDATES = (0, _G, _L, _G | _L, _E, _E | _G, _E | _L, _E | _G | _L, _P, 
                     _S | _L | _PL, _S | _G | _L | _PL, _L | _SL, _G | _L | _SL, _E | _L | _SL, _E | _G | _L | _SL,
                     _S | _L | _SL, _S | _G | _L | _SL, _B, _B | _L, _L | _BL, _B | _L | _BL, _B | _G | _L | _BL,
                     _B | _L | _SL, _S | _L | _BL, _E | _L | _BL)
-CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES)))
+# the blocking-depth axis: depth 2 (a scale's first iteration in one tiled launch) is offered only
+# when asked for (tune(depths=(1, 2))); it measured slower on every workload tried (the half-sweeps
+# are bound by instruction issue, and depth 2 recomputes the even pixels around each tile), so by
+# default the tuner does not spend its time on it nor risk picking it on noise
+BLOCKED_CANDIDATES = (_K, _K | _L, _K | _E | _L, _K | _L | _SL)
+CANDIDATES = tuple(sorted(set(SMALL_CANDIDATES) | set(LARGE_CANDIDATES) | set(BLOCKED_CANDIDATES)))
 DPAR_MAX_LANES_PER_PIXEL = 8  # direction-parallel lanes exist up to 128 labels
 # the list and staged candidates are tried on every scale of at least this many lanes (a scale
 # small enough for the cluster launch may still have enough pixels for active lists to pay)
 LIST_MIN_LANES = 8 * 1024
 
 
-def _candidates(lanes: int, Gp: int) -> list[int]:
-    """The variants tried on a scale of `lanes` lanes (pixels of a colour x lanes a pixel)."""
+def _candidates(lanes: int, Gp: int, depths: tuple = (1,)) -> list[int]:
+    """The variants tried on a scale of `lanes` lanes (pixels of a colour x lanes a pixel), at the
+    blocking depths `depths` of a scale's first iteration (1, or 1 and 2)."""
     cands = list(SMALL_CANDIDATES) if lanes <= CLUSTER_MAX_LANES else []
     if lanes > CLUSTER_MAX_LANES or lanes >= LIST_MIN_LANES:
         cands += [v for v in LARGE_CANDIDATES if v not in cands]
+        if 2 in depths:
+            cands += [v for v in BLOCKED_CANDIDATES if v not in cands]
     return [v for v in cands if not (v & (_P | _PL) and Gp > DPAR_MAX_LANES_PER_PIXEL)]
 
 
@@ -79,13 +89,14 @@ def _lanes_per_pixel(D: int) -> int:
 
 
 def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, trunc: int, skip: bool = True,
-         reps: int = 3, cache: str | None = None, target_ms: float = 10.0) -> list[int]:
-    """Pick and set the variant of every scale of `st` (a Stereo); returns them per scale."""
+         reps: int = 3, cache: str | None = None, target_ms: float = 10.0, depths: tuple = (1,)) -> list[int]:
+    """Pick and set the variant of every scale of `st` (a Stereo); returns them per scale.
+    depths: the blocking depths of a scale's first iteration to consider, (1,) or (1, 2)."""
     import torch
 
     gpu = torch.cuda.get_device_name(st.device)
     dims = level_dims(st.W, st.H, st.levels)
-    keys = [_key(gpu, w, h, st.D, st.msg_type, trunc, skip) for w, h in dims]
+    keys = [_key(gpu, w, h, st.D, st.msg_type, trunc, skip) + ("|depth2" if 2 in depths else "") for w, h in dims]
     table = _load(cache)
     if all(k in table for k in keys):
         chosen = [int(table[k]) for k in keys]
@@ -121,7 +132,7 @@ def tune(st, left, right, window: int, trunc_data: int, iters: int, lam: int, tr
         current = st.variants()
         for lvl in reversed(range(st.levels)):
             times = {}
-            for v in _candidates(lanes[lvl], Gp):
+            for v in _candidates(lanes[lvl], Gp, depths):
                 trial = list(current)
                 trial[lvl] = v
                 try:

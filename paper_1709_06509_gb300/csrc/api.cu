@@ -370,6 +370,7 @@ extern "C" int bps_create(bps_ctx **out, int W, int H, int D, int levels, int ms
         v.eps = 0;  // the exact skip rule
         v.freeze = 0;
         v.bsum8 = 0;
+        v.keep_flag = 0;
         v.start = 0;
         v.pWh = 0;
         v.pmsg[0] = v.pmsg[1] = nullptr;
@@ -726,7 +727,29 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, const Iters &its, int lambd
             t += 2 * iters;
             continue;
         }
-        for (int it = 0; it < iters; ++it)
+        // the first iteration temporally blocked: both half-sweeps in one launch (u8, fused start, skip)
+        const bool block2 = fused_start && skip && (c->variant[l] & VARIANT_BLOCK2);
+        for (int it = 0; it < iters; ++it) {
+            if (it == 0 && block2) {
+                if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
+                SweepLists sl{nullptr, nullptr, nullptr, nullptr};
+                if ((c->variant[l] & VARIANT_LISTS) && sweep_takes_lists(c->msg_kind, c->variant[l], trunc)) {
+                    sl.out = c->lists[0];  // the even pixels the second half marks, for the next iteration
+                    sl.n_out = c->list_counts + t + 1;
+                }
+                LevelView a = first;
+                a.keep_flag = 1;  // the even flags are cleared before the launch and only marked in it
+                CK(launch_sweep_block2(a, second, c->D, c->Dp, c->Gp, lambda, trunc, c->trace + t, c->trace + t + 1,
+                                       sl, st));
+                if (prof) {
+                    CK(cudaEventRecord(c->ev[2 * c->prof_all + 1], st));
+                    c->prof_span[c->prof_all] = 2;
+                    ++c->prof_all;
+                    if (l == 0) c->prof_launches += 2;
+                }
+                t += 2;
+                continue;
+            }
             for (int colour = 0; colour < 2; ++colour, ++t) {
                 if (prof) CK(cudaEventRecord(c->ev[2 * c->prof_all], st));
                 SweepLists sl{nullptr, nullptr, nullptr, nullptr};
@@ -751,6 +774,7 @@ static int enqueue_bp_sweeps(bps_ctx *c, int levels, const Iters &its, int lambd
                     if (l == 0) ++c->prof_launches;
                 }
             }
+        }
     }
     c->last_levels = levels;
     c->last_trace_n = ntrace;
@@ -1357,7 +1381,7 @@ extern "C" int bps_set_sweep_variant(bps_ctx *c, int level, int variant) {
     if (!c || level < 0 || level >= c->levels || variant < -1 ||
         variant > (BPS_VARIANT_GENERAL_DT | BPS_VARIANT_LISTS | BPS_VARIANT_CLUSTER | BPS_VARIANT_EAGER |
                    BPS_VARIANT_DPAR | BPS_VARIANT_DPAR_LISTS | BPS_VARIANT_STAGED | BPS_VARIANT_STAGED_LISTS |
-                   BPS_VARIANT_BULK | BPS_VARIANT_BULK_LISTS))
+                   BPS_VARIANT_BULK | BPS_VARIANT_BULK_LISTS | BPS_VARIANT_BLOCK2))
         return BPS_ERR_ARG;
     if (variant > 0 && (variant & VARIANT_CLUSTER) && !cluster_sweep_available()) return BPS_ERR_UNSUPPORTED;
     c->variant[level] = variant < 0 ? default_variant((int64_t)c->plan.Hs[level] * c->plan.Whs[level], c->Gp, c->msg_kind)

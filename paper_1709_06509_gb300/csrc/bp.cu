@@ -414,6 +414,122 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
     tally.flush();
 }
 
+// ------------------------------------------------------------------ temporal blocking, depth 2
+// A scale's first iteration with the fused coarse-to-fine start in ONE launch, tile by tile: a CTA
+// takes a tile of BLK_TW x BLK_TH pixels and computes first every even pixel of the tile, then the
+// even pixels just outside it that send to its odd pixels (the rows above and below, the columns
+// to the left and right), all from their parents' start messages (start 1), and, after a CTA
+// barrier, every odd pixel of the tile (start 2) from the messages just written, which it reads
+// back from L2 instead of HBM.  An even pixel is computed by its own tile and by every tile it
+// borders: each writes the same bytes (its inputs are its cost and its parent's record, which no
+// pixel of this launch writes), and only its own tile counts it in the trace.  The first half
+// changes no skip flag (the even flags are cleared before the launch), so the marks that a
+// neighbouring tile's second half sets are never lost; the second half marks and lists exactly as
+// the unblocked second half-sweep.  Results are those of the two separate half-sweeps.
+constexpr int BLK_TW = 32, BLK_TH = 16;  // tile width (even) and height (even)
+
+template <bool PADDED, bool APPEND, int TS>
+__global__ void __launch_bounds__(256, BPS_SWEEP_BLOCKS(PADDED, TS))
+sweep_u8_block2_kernel(LevelView first, LevelView second, int D, int Dp, int Gp, int lam, int lamT,
+                       unsigned long long *trace0, unsigned long long *trace1, ActiveList al, int tiles_x, int tiles) {
+    unsigned *abuf = nullptr;
+    if constexpr (APPEND) {
+        BPS_LIST_BUFFER(list_buf);
+        abuf = list_buf[threadIdx.x >> 5];
+    }
+    pdl_enter();
+    Tally t0(trace0), t1(trace1, abuf), ring(nullptr);
+    const int W = first.W, H = first.H, Wh = first.Wh;
+    const int64_t nslot = (int64_t)H * Wh;
+    const int groups = blockDim.x / Gp, gi = threadIdx.x / Gp;
+    constexpr int HALF = BLK_TW / 2;                  // pixels of one colour in a tile row
+    constexpr int OWN = BLK_TH * HALF;                // entries of one colour in a tile
+    constexpr int RING = 2 * HALF + BLK_TH;           // even pixels around it (rows, then columns)
+    const ActiveList none{nullptr, nullptr, nullptr, nullptr};
+    // the slot of the k-th pixel of colour c in the tile's rows y0 .. y0 + th - 1, columns x0 .. x0 + tw - 1
+    auto own_slot = [&](int c, int k, int x0, int y0, int tw, int th) -> int64_t {
+        const int row = k / HALF, i = k % HALF, y = y0 + row, x = x0 + ((c + y) & 1) + 2 * i;
+        return (row < th && x < x0 + tw) ? (int64_t)y * Wh + (x >> 1) : nslot;
+    };
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * BLK_TW, y0 = (tile / tiles_x) * BLK_TH;
+        const int tw = min(BLK_TW, W - x0), th = min(BLK_TH, H - y0);
+        for (int k0 = 0; k0 < OWN; k0 += groups)
+            sweep_group_u8<PADDED, false, TS, false, 0, true>(first, 0, D, Dp, Gp, lam, lamT, 1, t0, 0, none, 0,
+                                                              own_slot(0, k0 + gi, x0, y0, tw, th));
+        for (int r0 = 0; r0 < RING; r0 += groups) {
+            const int r = r0 + gi;
+            int x = -1, y = -1;
+            if (r < 2 * HALF) {  // the rows above and below: their even pixels over the tile's columns
+                y = r < HALF ? y0 - 1 : y0 + th;
+                x = x0 + (y & 1) + 2 * (r % HALF);
+                if (x >= x0 + tw) x = -1;
+            } else if (r < 2 * HALF + BLK_TH / 2) {  // the column to the left: even where y is odd
+                x = x0 - 1;
+                y = y0 + 1 + 2 * (r - 2 * HALF);
+            } else if (r < RING) {  // the column to the right
+                x = x0 + tw;
+                y = y0 + (x & 1) + 2 * (r - 2 * HALF - BLK_TH / 2);
+            }
+            // a column pixel must border a tile row; a row pixel is one row outside the tile
+            const bool in = x >= 0 && x < W && y >= 0 && y < H && (r < 2 * HALF || y < y0 + th);
+            sweep_group_u8<PADDED, false, TS, false, 0, true>(first, 0, D, Dp, Gp, lam, lamT, 1, ring, 0, none, 0,
+                                                              in ? (int64_t)y * Wh + (x >> 1) : nslot);
+        }
+        __syncthreads();  // the tile's odd pixels' incoming messages are written
+        for (int k0 = 0; k0 < OWN; k0 += groups)
+            sweep_group_u8<PADDED, APPEND, TS, true, 0, true>(second, 1, D, Dp, Gp, lam, lamT, 1, t1, 0, al, 0,
+                                                              own_slot(1, k0 + gi, x0, y0, tw, th));
+    }
+    if constexpr (APPEND) t1.flush_appends(al.out, al.n_out, (unsigned)nslot, second.err);
+    t0.flush();
+    t1.flush();
+}
+
+__global__ void clear_flags_kernel(unsigned *flags, int64_t n) {
+    pdl_enter();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        flags[k] = 0u;
+}
+
+template <bool PADDED, int TS>
+static cudaError_t launch_block2_t(const LevelView &first, const LevelView &second, int D, int Dp, int Gp, int lam,
+                                   int lamT, unsigned long long *trace0, unsigned long long *trace1,
+                                   const ActiveList &al, int grid, int tiles_x, int tiles, cudaStream_t st) {
+    if (al.out)
+        return launch_k(sweep_u8_block2_kernel<PADDED, true, TS>, dim3(grid), dim3(256), 0, st, first, second, D, Dp,
+                        Gp, lam, lamT, trace0, trace1, al, tiles_x, tiles);
+    return launch_k(sweep_u8_block2_kernel<PADDED, false, TS>, dim3(grid), dim3(256), 0, st, first, second, D, Dp, Gp,
+                    lam, lamT, trace0, trace1, al, tiles_x, tiles);
+}
+
+static int resident_blocks(int ts, bool padded);
+
+cudaError_t launch_sweep_block2(const LevelView &first, const LevelView &second, int D, int Dp, int Gp, int lambda,
+                                int trunc, unsigned long long *trace0, unsigned long long *trace1,
+                                const SweepLists &lists, cudaStream_t st) {
+    const int64_t nslot = (int64_t)first.H * first.Wh;
+    if (nslot == 0) return cudaSuccess;
+    cudaError_t e = launch_k(clear_flags_kernel, dim3((unsigned)std::min<int64_t>((nslot + 255) / 256, 4096)),
+                             dim3(256), 0, st, first.dirty[0], nslot);
+    if (e != cudaSuccess) return e;
+    const int tiles_x = (first.W + BLK_TW - 1) / BLK_TW, tiles_y = (first.H + BLK_TH - 1) / BLK_TH;
+    const int tiles = tiles_x * tiles_y;
+    const int lam = trunc == 0 ? 0 : lambda;
+    const int ts = trunc <= 1 ? 1 : (trunc == 2 ? 2 : 0);
+    const bool padded = (D & 15) != 0;
+    const int grid = (int)std::min<int64_t>(tiles, resident_blocks(ts, padded));
+    const ActiveList al{nullptr, nullptr, lists.out, lists.n_out};
+    switch (ts) {
+    case 1: return padded ? launch_block2_t<true, 1>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st)
+                          : launch_block2_t<false, 1>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st);
+    case 2: return padded ? launch_block2_t<true, 2>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st)
+                          : launch_block2_t<false, 2>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st);
+    default: return padded ? launch_block2_t<true, 0>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st)
+                           : launch_block2_t<false, 0>(first, second, D, Dp, Gp, lam, lam * trunc, trace0, trace1, al, grid, tiles_x, tiles, st);
+    }
+}
+
 // Every iteration of one small scale in ONE launch of ONE thread-block cluster.  The CTAs of
 // a cluster are co-scheduled, so the hardware cluster barrier (release / acquire at cluster
 // scope, covering global memory) separates the half-sweeps: no software spin, no launch per

@@ -36,6 +36,9 @@ struct LevelView {
     // u8 form: 1 when every message a half-sweep reads is at most 63 (lambda * trunc <= 63 and no
     // caller-given start messages), so four of them add up bytewise without a carry
     int bsum8;
+    // 1: a recomputed pixel leaves its own skip flag alone (the first half of a temporally blocked
+    // first iteration, whose flags are cleared before the launch)
+    int keep_flag;
     // A scale's first iteration without a separate coarse-to-fine copy (u8 sweeps): start = 1, the
     // first half-sweep reads each even pixel's start messages straight from its parent's record
     // (pmsg, pWh: the parent scale's message arrays and slots per row) and recomputes every

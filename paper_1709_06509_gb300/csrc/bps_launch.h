@@ -76,6 +76,7 @@ constexpr int VARIANT_STAGED = 64;     // dense launches stage the next block's 
 constexpr int VARIANT_STAGED_LISTS = 128; // ... list launches
 constexpr int VARIANT_BULK = 256;      // dense launches fed by a copy warp's cp.async.bulk pipeline
 constexpr int VARIANT_BULK_LISTS = 512; // ... list launches
+constexpr int VARIANT_BLOCK2 = 1024;   // the first iteration temporally blocked: both half-sweeps in one launch
 
 // Active lists of a half-sweep (u8 form with the skip on; all members nullable).
 struct SweepLists {
@@ -90,6 +91,13 @@ struct SweepLists {
 cudaError_t launch_sweep(int msg_kind, const LevelView &lv, int colour, int D, int Dp, int Gp, int lambda,
                          int trunc, int skip, unsigned long long *trace, cudaStream_t st,
                          const SweepLists &lists = SweepLists{nullptr, nullptr, nullptr, nullptr}, int variant = 0);
+// The first iteration of a scale with the fused coarse-to-fine start (u8 form, skip on) in one
+// launch, tile by tile (temporal blocking to depth 2): `first` / `second` are the views of its two
+// half-sweeps (start 1 and 2), trace0 / trace1 their trace counters, `lists` the list the second
+// appends to (members nullable).  The even pixels' flags are cleared first (a second launch).
+cudaError_t launch_sweep_block2(const LevelView &first, const LevelView &second, int D, int Dp, int Gp, int lambda,
+                                int trunc, unsigned long long *trace0, unsigned long long *trace1,
+                                const SweepLists &lists, cudaStream_t st);
 // All iterations of one scale (u8 form) in one launch of one 16-CTA cluster; available only
 // where such a cluster fits (cluster_sweep_available).
 bool cluster_sweep_available();

@@ -737,7 +737,7 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
             }
         }
     }
-    if (skip && active && g == 0)
+    if (skip && active && g == 0 && !lv.keep_flag)
         (colour ? lv.dirty[1] : lv.dirty[0])[s] = (lv.freeze && !marked) ? 2u : 0u;  // frozen: bit 1
 }
 

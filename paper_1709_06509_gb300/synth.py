@@ -159,6 +159,7 @@ WORKLOADS = {
     "teddy_450x375_d64": (450, 375, 64, 7, 8, 3.0, 3),
     "hd_1920x1080_d256": (1920, 1080, 256, 9, 8, 3.0, 5),
     "qhd_960x540_d256": (960, 540, 256, 9, 8, 3.0, 6),  # a quarter of the HD pair, for profiling
+    "c3_1280x720_d64": (1280, 720, 64, 7, 8, 3.0, 7),  # the largest pair size of the mixed batches
 }
 
 

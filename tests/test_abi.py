@@ -112,7 +112,13 @@ def test_autotuner_candidate_sets():
     dp = bps.BPS_VARIANT_DPAR | bps.BPS_VARIANT_DPAR_LISTS
     assert wide and all(not (v & dp) for v in wide)
     assert all(v & bps.BPS_VARIANT_LISTS for v in at.LARGE_CANDIDATES if v & bps.BPS_VARIANT_STAGED_LISTS)
-    assert set(at.CANDIDATES) == set(at.SMALL_CANDIDATES) | set(at.LARGE_CANDIDATES)
+    # the blocking-depth axis: depth 2 only when asked for, on the scales that get the large set
+    assert not any(v & bps.BPS_VARIANT_BLOCK2 for v in big + mid + tiny)
+    deep = at._candidates(at.CLUSTER_MAX_LANES + 1, 4, depths=(1, 2))
+    assert set(deep) == set(at.LARGE_CANDIDATES) | set(at.BLOCKED_CANDIDATES) and len(deep) == len(set(deep))
+    assert set(at._candidates(1000, 4, depths=(1, 2))) == set(at.SMALL_CANDIDATES)
+    assert all(v & bps.BPS_VARIANT_BLOCK2 for v in at.BLOCKED_CANDIDATES)
+    assert set(at.CANDIDATES) == set(at.SMALL_CANDIDATES) | set(at.LARGE_CANDIDATES) | set(at.BLOCKED_CANDIDATES)
 
 
 def test_every_autotuner_candidate_has_an_exact_gpu_test():

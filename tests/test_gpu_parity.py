@@ -334,7 +334,8 @@ def set_all_variants(st, variant):
 
 # every variant the autotuner can pick, and more (tests/test_abi.py checks the tuner's candidates are here)
 SWEEP_VARIANTS_TESTED = [0, 1, 2, 3, 4, 6, 8, 9, 10, 11, 12, 13, 16, 17, 18, 24, 25, 26, 27, 34, 35, 42, 43, 64, 65, 66,
-                         67, 98, 99, 130, 131, 138, 139, 194, 195, 162, 256, 257, 258, 386, 514, 522, 578, 770, 771]
+                         67, 98, 99, 130, 131, 138, 139, 194, 195, 162, 256, 257, 258, 386, 514, 522, 578, 770, 771,
+                         1024, 1026, 1027, 1034, 1154]
 
 
 @pytest.mark.parametrize("variant", SWEEP_VARIANTS_TESTED)

@@ -77,7 +77,7 @@ def built():
 # variants forced on every scale: the defaults, and every candidate the autotuner offers at these
 # sizes (lanes a pixel 16: no direction-parallel forms)
 HD_VARIANTS = [-1, 0, 1, 2, 3, 8, 9, 10, 11, 64, 65, 66, 67, 130, 131, 138, 139, 194, 195, 256, 258, 386, 514, 522,
-               578, 770, 771]
+               578, 770, 771, 1024, 1026, 1034, 1154]
 
 
 @pytest.mark.gpu
