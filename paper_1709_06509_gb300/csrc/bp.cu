@@ -407,9 +407,10 @@ sweep_u8_list_kernel(LevelView lv, int colour, int D, int Dp, int Gp, int lam, i
     }
     const unsigned n = *al.n_in;
     BPS_LIST_BUFFER(list_buf);
-    Tally tally(trace, list_buf[threadIdx.x >> 5]);
+    Tally tally(trace, list_buf[threadIdx.x >> 5], true);
     if (DP && n <= dp_max) list_loop<PADDED, TS, DP>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_dp);
     else list_loop<PADDED, TS, false>(lv, colour, D, Dp, Gp, lam, lamT, tally, al, n, e_pix);
+    tally.settle(al.out, al.n_out, (unsigned)nslot, lv.err);  // the last block's deferred appends
     tally.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
     tally.flush();
 }

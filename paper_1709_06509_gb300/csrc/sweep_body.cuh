@@ -48,13 +48,20 @@ __device__ inline unsigned leader_bits(int Gp) {
 constexpr unsigned LIST_BUF_CAP = 256;  // >= 4 appends a pixel x 32 pixels of a warp (Gp = 1)
 // The append buffers of a 256-thread CTA's eight warps (a static shared array of the kernel).
 #define BPS_LIST_BUFFER(name) __shared__ unsigned name[256 / 32][::bps::LIST_BUF_CAP]
+//
+// A list launch may also defer the append decision of a pixel block (`defer`): the flags of its
+// marked neighbours are flipped with atomics whose results are consumed only once the next block's
+// loads are in flight (settle), so the two round trips to memory overlap.
 struct Tally {
     unsigned long long *ptr;  // the launch's counter (nullable: no trace)
     unsigned n;               // this warp's pixels so far (the same in every lane)
     unsigned *abuf;           // this warp's append buffer in shared memory (nullable: none)
     unsigned an;              // entries in it (the same in every lane)
-    __device__ explicit Tally(unsigned long long *p, unsigned *append_buf = nullptr)
-        : ptr(p), n(0u), abuf(append_buf), an(0u) {}
+    bool defer;               // settle a block's appends during the next block (the same in every lane)
+    bool pend;                // appends of a block await settling (the same in every lane)
+    unsigned pwas[4], pqs[4]; // per neighbour: the flag before the atomic (1: not marked) and the slot
+    __device__ explicit Tally(unsigned long long *p, unsigned *append_buf = nullptr, bool defer_appends = false)
+        : ptr(p), n(0u), abuf(append_buf), an(0u), defer(defer_appends), pend(false) {}
     __device__ __forceinline__ void add(unsigned act, int lanes_a_pixel) { n += __popc(act & leader_bits(lanes_a_pixel)); }
     __device__ __forceinline__ void flush() {
         if (ptr && n && (threadIdx.x & 31) == 0) atomicAdd(ptr, (unsigned long long)n);
@@ -73,6 +80,43 @@ struct Tally {
             if (BPS_CHECK(base + i < cap, err, 3u)) out[base + i] = abuf[i];
         an = 0u;
         __syncwarp();
+    }
+    // Append the neighbours whose flag this lane's atomics flipped from 0 (pwas, pqs): the warp's
+    // ballots, then one reservation (or the warp's buffer).  Called by every lane of the warp together.
+    __device__ __forceinline__ void settle(unsigned *out, unsigned *n_out, unsigned cap, unsigned *err) {
+        if (!pend) return;
+        pend = false;
+        const unsigned lane = threadIdx.x & 31u;
+        unsigned am[4];
+        unsigned total = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            am[q] = __ballot_sync(0xffffffffu, pwas[q] == 0u);
+            total += (unsigned)__popc(am[q]);
+        }
+        if (!total) return;
+        const unsigned below = (1u << lane) - 1u;
+        if (abuf) {
+            if (an + total > LIST_BUF_CAP) flush_appends(out, n_out, cap, err);
+            unsigned base = an;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (pwas[q] == 0u) abuf[base + __popc(am[q] & below)] = pqs[q];
+                base += (unsigned)__popc(am[q]);
+            }
+            an += total;
+            __syncwarp();
+        } else {
+            unsigned base = 0u;
+            if (lane == 0u) base = atomicAdd(n_out, total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned at = base + (unsigned)__popc(am[q] & below);
+                if (pwas[q] == 0u && BPS_CHECK(at < cap, err, 3u)) out[at] = pqs[q];
+                base += (unsigned)__popc(am[q]);
+            }
+        }
     }
     // Append the entries that lanes with `pred` hold in `v` (the ballot of pred is `am`, taken by
     // the caller), at positions `base` + (the rank of the lane among them).  Buffered when the warp
@@ -620,6 +664,8 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         load_cost();
         load_messages(active);
     }
+    // the previous block's appends, now that this block's loads are in flight
+    if constexpr (APPEND) trace.settle(al.out, al.n_out, (unsigned)nslot, lv.err);
     if (lv.bsum8) {
         // every incoming message is at most 63: the four add up bytewise without a carry, and the
         // sum is unpacked once
@@ -700,42 +746,15 @@ __device__ __forceinline__ void sweep_group_u8(const LevelView &lv, int colour, 
         }
     }
     if constexpr (APPEND) {
-        // the flags of the marked neighbours flip together (one round trip), then the warp
-        // appends the ones that were clean with a single reservation
-        unsigned was[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) was[q] = ((marks >> q) & 1u) ? atomicOr(dirty_out + qsv[q], 1u) : 1u;
-        unsigned am[4];
-        unsigned total = 0u;
+        // the flags of the marked neighbours flip together (one round trip); the warp appends the
+        // ones that were clean with a single reservation, now or (deferred) during its next block
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            am[q] = __ballot_sync(FULL, was[q] == 0u);
-            total += __popc(am[q]);
+            trace.pwas[q] = ((marks >> q) & 1u) ? atomicOr(dirty_out + qsv[q], 1u) : 1u;
+            trace.pqs[q] = qsv[q];
         }
-        if (total) {
-            const unsigned below = (1u << lane) - 1u;
-            if (trace.abuf) {  // gathered in the warp's buffer (see Tally)
-                if (trace.an + total > LIST_BUF_CAP) trace.flush_appends(al.out, al.n_out, (unsigned)nslot, lv.err);
-                unsigned base = trace.an;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (was[q] == 0u) trace.abuf[base + __popc(am[q] & below)] = qsv[q];
-                    base += __popc(am[q]);
-                }
-                trace.an += total;
-                __syncwarp();
-            } else {
-                unsigned base = 0u;
-                if (lane == 0) base = atomicAdd(al.n_out, total);
-                base = __shfl_sync(FULL, base, 0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const unsigned at = base + __popc(am[q] & below);
-                    if (was[q] == 0u && BPS_CHECK(at < (unsigned)nslot, lv.err, 3u)) al.out[at] = qsv[q];
-                    base += __popc(am[q]);
-                }
-            }
-        }
+        trace.pend = true;
+        if (!trace.defer) trace.settle(al.out, al.n_out, (unsigned)nslot, lv.err);
     }
     if (skip && active && g == 0 && !lv.keep_flag)
         (colour ? lv.dirty[1] : lv.dirty[0])[s] = (lv.freeze && !marked) ? 2u : 0u;  // frozen: bit 1
