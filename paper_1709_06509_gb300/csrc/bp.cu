@@ -914,12 +914,19 @@ __global__ void export_cost_kernel(LevelView lv, int D, int Dp, DstT *out) {
     }
 }
 
+// The one-launch-per-half-sweep kernels need little shared memory (the list buffers, 8 KB a CTA):
+// they ask for a carveout that leaves most of the SM's 256 KB to the L1 cache (spilled words,
+// parent records read by two children), whatever the kernel before them needed (the tensor-core
+// NCC takes 224 KB).  29 % of the 228 KB maximum is 66 KB: room for four CTAs' list buffers.
+constexpr int SWEEP_CARVEOUT_PCT = 29;
+template <typename K> static cudaError_t prefer_l1(K kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, SWEEP_CARVEOUT_PCT);
+}
 template <bool PADDED, int TS, bool DP> static cudaError_t preload_u8_dp() {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, false, TS, DP>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_kernel<PADDED, true, TS, DP>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_list_kernel<PADDED, TS, DP>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sweep_u8_eager_kernel<PADDED, TS, DP>);
+    cudaError_t e = prefer_l1(sweep_u8_kernel<PADDED, false, TS, DP>);
+    if (e == cudaSuccess) e = prefer_l1(sweep_u8_kernel<PADDED, true, TS, DP>);
+    if (e == cudaSuccess) e = prefer_l1(sweep_u8_list_kernel<PADDED, TS, DP>);
+    if (e == cudaSuccess) e = prefer_l1(sweep_u8_eager_kernel<PADDED, TS, DP>);
     return e;
 }
 template <bool PADDED, int TS> static cudaError_t preload_u8() {
